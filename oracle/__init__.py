@@ -1,0 +1,23 @@
+"""FP64 CPU oracle for the compressible semi-Lagrangian lattice Boltzmann step.
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously-correct
+restatement of the method (Spelten et al., "Supersonic shear and wall-bounded
+flows with body-fitted meshes using the SLLBM", Sec. 3) written in numpy
+float64.  Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import it.  It shares no code with the CUDA library in
+``paper_2412_09051_gb300``; the only shared module is ``workloads`` (seeded
+input generators and plain configuration numbers, no method arithmetic).
+
+Modules and the passage each follows:
+  velocity_sets  Sec. 3.2 (cubature velocity sets, degree 9)
+  equilibrium    Sec. 3.1, equilibrium Hermite expansion (N = 4) and g-equilibrium
+  mesh           Sec. 3.1 Eq. (intf): cells with order-p Lagrange support points
+  departure      Sec. 3.1 (departure point) and Sec. 3.3 (boundary schemes)
+  step           Sec. 3.1 Eq. (1), moment definitions, Sec. 3.3 boundary schemes
+  mlp            learned collision correction (not in the paper)
+
+Parity status: every function is pinned by tests in tests/test_oracle_*.py
+except the quasi-equilibrium term for Pr != 1 (pinned only by its defining
+invariants) and the curved-wall / outlet boundary schemes (pinned by
+invariants and special cases, not by printed values): "parity partly unpinned".
+"""

@@ -1,0 +1,190 @@
+"""Pins of the oracle step (Sec. 3.1 Eq. 1, moments, Sec. 3.3 boundary schemes)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import step as st
+from oracle.departure import REC_BB, REC_BB_ISO, REC_EQ, REC_INTERIOR, REC_OUTLET
+from oracle.equilibrium import feq, geq
+from oracle.velocity_sets import velocity_set
+from tests.oracle_cases import box_cfg, oracle_case, random_neq_state
+from workloads import get_config
+
+
+def _conserved(f, g, xi):
+    return np.concatenate([[f.sum()], xi.T @ f.sum(1), [((xi ** 2).sum(1) @ f + g.sum(0)).sum()]])
+
+
+@pytest.mark.parametrize("name,Pr,mexp", [("D2Q19", 1.0, 0.0), ("D2Q19", 0.71, 0.7), ("D3Q45", 0.7, 0.7),
+                                          ("D2Q25", 0.5, 0.0)])
+def test_collision_conserves(name, Pr, mexp):
+    """Eq. 1 conserves mass, momentum and total energy exactly (to round-off)."""
+    xi, w, _ = velocity_set(name)
+    par = st.Params(dt=0.01, Pr=Pr, mu_ref=0.02, mu_exp=mexp)
+    f, g = random_neq_state(xi, w, par.cv, 64, seed=5)
+    f1, g1 = st.collide(f, g, xi, w, par)
+    for n in range(0, 64, 7):
+        a = _conserved(f[:, n:n + 1], g[:, n:n + 1], xi)
+        b = _conserved(f1[:, n:n + 1], g1[:, n:n + 1], xi)
+        assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+
+
+def test_collision_fixed_point():
+    xi, w, _ = velocity_set("D2Q19")
+    par = st.Params(dt=0.01, Pr=0.7, mu_ref=0.02)
+    rho, u, T = np.array([1.1]), np.array([[0.3, -0.2]]), np.array([0.9])
+    f, g = feq(rho, u, T, xi, w), geq(rho, u, T, xi, w, par.cv)
+    f1, g1 = st.collide(f, g, xi, w, par)
+    assert np.abs(f1 - f).max() < 1e-15 and np.abs(g1 - g).max() < 1e-15
+
+
+def test_relaxation_rates():
+    """Non-equilibrium stress relaxes with 1 - 1/tau; the central heat flux with
+    1 - 1/tau_Pr (the reading of the quasi-equilibrium term h*); tau = mu/(p dt) + 1/2."""
+    xi, w, _ = velocity_set("D2Q19")
+    par = st.Params(dt=0.01, Pr=0.6, mu_ref=0.03)
+    f, g = random_neq_state(xi, w, par.cv, 8, seed=9)
+    rho, u, T = st.moments(f, g, xi, par.cv)
+    fe, ge = feq(rho, u, T, xi, w), geq(rho, u, T, xi, w, par.cv)
+    f1, g1 = st.collide(f, g, xi, w, par)
+    tau = par.mu_ref / (rho * T * par.dt) + 0.5
+    tau_pr = (tau - 0.5) / par.Pr + 0.5
+    s0 = np.einsum("qa,qb,qn->nab", xi, xi, f - fe)
+    s1 = np.einsum("qa,qb,qn->nab", xi, xi, f1 - fe)
+    assert np.abs(s1 - (1 - 1 / tau)[:, None, None] * s0).max() < 1e-13
+    c = xi[:, None, :] - u[None]
+    c2 = (c ** 2).sum(2)
+    q0 = 0.5 * np.einsum("qnd,qn->nd", c, c2 * (f - fe) + (g - ge))
+    q1 = 0.5 * np.einsum("qnd,qn->nd", c, c2 * (f1 - fe) + (g1 - ge))
+    assert np.abs(q1 - (1 - 1 / tau_pr)[:, None] * q0).max() < 1e-13
+
+
+def test_uniform_flow_invariant_periodic():
+    cfg = box_cfg(cells=(4, 4), L=(1.0, 1.0), dt=0.02)
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    N = mesh.n_nodes
+    rho, u, T = np.full(N, 1.2), np.tile([0.9, -0.4], (N, 1)), np.full(N, 1.3)
+    f, g = st.init_equilibrium(rho, u, T, xi, w, par.cv)
+    f1, g1 = f, g
+    for _ in range(3):
+        f1, g1 = st.step(mesh, rec, f1, g1, xi, w, par)
+    assert np.abs(f1 - f).max() < 1e-13 and np.abs(g1 - g).max() < 1e-13
+
+
+def test_uniform_flow_invariant_equilibrium_bc():
+    """Equilibrium inflow at the state of the interior keeps a uniform flow (Sec. 3.3.1)."""
+    cfg = get_config("mixing", cells=(2, 4, 2))
+    cfg["bcs"] = [dict(kind=1, rho=1.1, u=(0.3, 0.2, -0.1), T=0.95)] * 2
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    assert (rec["kind"] == REC_EQ).any()
+    N = mesh.n_nodes
+    f, g = st.init_equilibrium(np.full(N, 1.1), np.tile([0.3, 0.2, -0.1], (N, 1)), np.full(N, 0.95), xi, w,
+                               par.cv)
+    f1, g1 = st.step(mesh, rec, f, g, xi, w, par)
+    assert np.abs(f1 - f).max() < 1e-13 and np.abs(g1 - g).max() < 1e-13
+
+
+def test_classic_lbm_special_case():
+    """Sec. 2: D2Q9, unit time step on a regular grid -> streaming is an index shift."""
+    p, C = 2, 6
+    h = 1.0 / (C * p)
+    dt = h / math.sqrt(3.0)
+    cfg = box_cfg(cells=(C, C), p=p, L=(1.0, 1.0), dt=dt, velset="D2Q9")
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    rng = np.random.default_rng(0)
+    f = rng.uniform(0.5, 1.5, (9, mesh.n_nodes))
+    g = rng.uniform(0.5, 1.5, (9, mesh.n_nodes))
+    fs, gs = st.stream(mesh, rec, f, g, xi, w, par)
+    Nx = mesh.N[0]
+    for i in range(9):
+        s = np.rint(xi[i] * dt / h).astype(int)
+        ref = np.roll(f[i].reshape(Nx, Nx), shift=(s[1], s[0]), axis=(0, 1)).ravel()
+        assert np.abs(fs[i] - ref).max() < 1e-12, i
+
+
+def test_thermal_correction_sets_wall_temperature():
+    """Eq. thermalBC: T(AP) becomes T_w; rho and rho u are unchanged (Sec. 3.3.2)."""
+    xi, w, _ = velocity_set("D3Q45")
+    par = st.Params(dt=0.01)
+    f, g = random_neq_state(xi, w, par.cv, 10, seed=2)
+    Tw = np.full(10, 0.75)
+    Tw[3] = np.nan
+    f1, g1 = st.thermal_correction(f, g, xi, w, par, Tw)
+    r0, u0, T0 = st.moments(f, g, xi, par.cv)
+    r1, u1, T1 = st.moments(f1, g1, xi, par.cv)
+    assert np.abs(r1 - r0).max() < 1e-14 and np.abs(u1 - u0).max() < 1e-14
+    m = ~np.isnan(Tw)
+    assert np.abs(T1[m] - 0.75).max() < 1e-13 and abs(T1[3] - T0[3]) < 1e-15
+
+
+def test_bounce_back_geometry():
+    """Sec. 3.3.2: x_DP = x_W + iota lies on the line through x_AP, the wall
+    point lies on the wall plane, and the population read is ibar."""
+    cfg = get_config("channel", cells=(2, 6, 2))
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    bb = np.argwhere(rec["kind"] == REC_BB_ISO)
+    assert len(bb) > 0
+    V = mesh.vertices[1]
+    for i, n in bb[:200]:
+        x = mesh.X[n]
+        tw = rec["tw"][i, n]
+        xw = x - tw * cfg["dt"] * xi[i]
+        assert min(abs(xw[1] - V[0]), abs(xw[1] - V[-1])) < 1e-13
+        xr = x + (1 - 2 * tw) * cfg["dt"] * xi[i]
+        d = rec["xsrc"][i, n] - mesh.wrap(xr[None])[0]
+        assert np.abs(d).max() < 1e-12
+        assert rec["src"][i, n] == opp[i]
+
+
+def test_outlet_mirror_point():
+    """Sec. 3.3.3: an outlet record reads population i at x_AP + zeta_i dt."""
+    cfg = get_config("naca", cells=(16, 4))
+    cfg["mesh"]["stretch"] = 1.6
+    cfg["dt"] = 0.05
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    out = np.argwhere(rec["kind"] == REC_OUTLET)
+    eq = np.argwhere(rec["kind"] == REC_EQ)
+    assert len(out) > 0 and len(eq) > 0
+    from oracle.departure import Locator
+    loc = Locator(mesh)
+    xm = np.array([mesh.X[n] + cfg["dt"] * xi[i] for i, n in out])
+    inside = loc.locate(xm)[0] >= 0
+    assert inside.sum() > 0
+    for (i, n), x, ins in zip(out, xm, inside):
+        if ins:    # mirrored point inside: read there; otherwise clamped back along the segment
+            assert np.abs(rec["xsrc"][i, n] - x).max() < 1e-12
+        else:
+            assert np.linalg.norm(rec["xsrc"][i, n] - mesh.X[n]) < np.linalg.norm(x - mesh.X[n])
+        assert rec["src"][i, n] == i
+
+
+def _shear_decay_rate(cells, dt, mu, steps):
+    cfg = box_cfg(cells=(cells, 1), p=2, L=(2 * math.pi, 2 * math.pi / cells), dt=dt, mu=mu)
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    X = mesh.X
+    N = mesh.n_nodes
+    A = 1e-3
+    u = np.zeros((N, 2))
+    u[:, 1] = A * np.sin(X[:, 0])
+    f, g = st.init_equilibrium(np.ones(N), u, np.ones(N), xi, w, par.cv)
+    amps = []
+    for k in range(steps + 1):
+        r, uu, T = st.moments(f, g, xi, par.cv)
+        amps.append(2 * (uu[:, 1] * np.sin(X[:, 0])).mean())
+        if k < steps:
+            f, g = st.step(mesh, rec, f, g, xi, w, par)
+    t = dt * np.arange(steps + 1)
+    return -np.polyfit(t[5:], np.log(amps[5:]), 1)[0]
+
+
+def test_shear_wave_viscosity():
+    """A shear wave decays at nu k^2 with nu = mu/rho (reading: tau = mu/(p dt) + 1/2);
+    the deviation from the continuum rate shrinks with refinement."""
+    mu, dt = 0.05, 0.02
+    errs = []
+    for cells in (6, 12):
+        rate = _shear_decay_rate(cells, dt, mu, 60)
+        errs.append(abs(rate - mu) / mu)
+    assert errs[1] < 0.03
+    assert errs[1] < errs[0]
