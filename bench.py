@@ -1,0 +1,299 @@
+"""Benchmark of the fused SLLBM step (MLUPS and HBM roofline fraction).
+
+Default workload: the 3D supersonic channel, 64 x 48 x 48 order-2 cells
+(128 x 97 x 96 = 1,191,936 nodes), D3Q45, FP32-offset storage, structured
+streaming; one step = one launch of the fused stream + collide kernel over
+all nodes.  The populations (2 x 45 x 4 B x N per buffer, 429 MB) exceed the
+129 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME] [--impl reference]
+Under torchrun each rank runs an independent replica on its own GPU (the
+method does not exchange data between replicas); value sums all ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+               "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 6:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[2 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def algorithmic_bytes_per_node(Q, real_bytes):
+    """Every population of f and g read once and written once."""
+    return 2 * 2 * Q * real_bytes
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_sample_rate(cfg_name, target_s=10.0, cores=1):
+    """Oracle (FP64 numpy) MLUPS on a bounded sample of arrival nodes of the
+    workload: one step (stream, thermal correction, collision) for M nodes,
+    departure tracing excluded (setup).  Runs in this process."""
+    import numpy as np
+    from oracle import step as ost
+    from oracle.departure import trace
+    from oracle.mesh import Mesh
+    from oracle.velocity_sets import velocity_set
+    from workloads import get_config, initial_fields
+    cfg = get_config(cfg_name)
+    m = cfg["mesh"]
+    mesh = Mesh(m["kind"], m["p"], m["cells"], m["length"], m.get("stretch", 1.0), m.get("central", 0),
+                m.get("thickness", 0.12))
+    xi, w, opp = velocity_set(cfg["velset"])
+    par = ost.Params(cfg["dt"], cfg["gamma"], cfg["Pr"], cfg["mu_ref"], cfg["T_ref"], cfg["mu_exp"], cfg["bcs"])
+    rho, u, T = initial_fields(cfg, mesh.X)
+    rng = np.random.default_rng(0)
+    M = 256
+    total_nodes, total_t = 0, 0.0
+    while total_t < target_s:
+        nodes = np.unique(rng.integers(0, mesh.n_nodes, M))
+        rec = trace(mesh, xi, opp, cfg["dt"], cfg["bcs"], nodes=nodes)
+        need = rec["kind"] != 0
+        cells = np.unique(rec["cell"][rec["cell"] >= 0])
+        sup = np.unique(mesh.cell_nodes(cells).ravel())
+        f = np.zeros((len(xi), mesh.n_nodes))
+        g = np.zeros((len(xi), mesh.n_nodes))
+        f[:, sup], g[:, sup] = ost.init_equilibrium(rho[sup], u[sup], T[sup], xi, w, par.cv)
+        Tw = ost.isothermal_nodes(rec, par)
+        t0 = time.perf_counter()
+        fs, gs = ost.stream(mesh, rec, f, g, xi, w, par)
+        fs, gs = ost.thermal_correction(fs, gs, xi, w, par, Tw)
+        ost.collide(fs, gs, xi, w, par)
+        dt = time.perf_counter() - t0
+        total_nodes += len(nodes)
+        total_t += dt
+        M = min(200000, M * 2)
+    return {"value": total_nodes / total_t / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{total_nodes} random arrival nodes of {cfg['name']}, one step each "
+                      f"(stream + thermal correction + collision, FP64 numpy), {total_t:.1f} s"}
+
+
+def run_oracle_subprocess(cfg_name, target_s):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample_rate(%r, %r, 1)))" % (ROOT, cfg_name, target_s))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        return {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_2412_09051_gb300.sim import Sim
+    from workloads import get_config, initial_fields
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = get_config(args.config)
+    stream = torch.cuda.Stream()
+    sim = Sim(cfg, device=local, stream=stream.cuda_stream)
+    N, Q = sim.N, sim.Q
+    X = sim.node_coords()
+    rho, u, T = initial_fields(cfg, X)
+    sim.init_state(rho, u, T)
+    real_bytes = 8 if sim.fp64 else 4
+    # warm-up
+    sim.step(args.warmup)
+    sim.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for k in range(args.steps):
+                sim.step(1)
+                ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms_total = ev[0].elapsed_time(ev[-1])
+    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    cons, rc = sim.conservation(check=False)
+
+    # end to end through the C ABI with host buffers: H2D of the step's input
+    # state from pinned memory, one step, D2H of the moments
+    raw_f = torch.empty((Q, N), dtype=torch.float32 if real_bytes == 4 else torch.float64).pin_memory()
+    raw_g = torch.empty_like(raw_f).pin_memory()
+    sim.get_state_raw(raw_f, raw_g)
+    sim.sync()
+    mr = torch.empty(N, dtype=torch.float64).pin_memory()
+    mu_ = torch.empty((N, sim.D), dtype=torch.float64).pin_memory()
+    mT = torch.empty(N, dtype=torch.float64).pin_memory()
+    ke = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        sim.set_state_raw(raw_f, raw_g)
+        sim.step(1)
+        sim.moments_into(mr, mu_, mT)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    h2d = 2 * Q * N * real_bytes
+    d2h = N * (sim.D + 2) * 8
+
+    mlups_rank = N * args.steps / (ms_max / 1e3) / 1e6
+    total_nodes = N * ws
+    value = total_nodes * args.steps / (ms_max / 1e3) / 1e6
+    avg_launch_ms = statistics.mean(per)
+    peaks, psrc = _peaks()
+    alg_bytes = algorithmic_bytes_per_node(Q, real_bytes) * N
+    achieved = alg_bytes / (avg_launch_ms / 1e3) / 1e9
+    line = None
+    if rank == 0:
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tf):
+            try:
+                traffic = json.load(open(tf)).get(cfg["name"])
+            except Exception:
+                traffic = None
+        line = {
+            "metric": "MLUPS (node updates/s, all Q of f and g)",
+            "value": round(value, 2),
+            "unit": "MLUPS",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_max / args.steps, 5),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32" if real_bytes == 4 else "f64",
+            "data": "synthetic (seeded laminar profile + 10% Philox perturbation)" if args.config == "channel"
+                    else "synthetic (seeded)",
+            "config": {"workload": f"{cfg['name']} ({cfg['velset']}, "
+                                   f"{'FP32-offset' if real_bytes == 4 else 'FP64'}, structured streaming)",
+                       "nodes": N, "Q": Q, "replicas": ws,
+                       "l2": f"inputs larger than L2: state {2 * Q * N * real_bytes / 1e6:.0f} MB per buffer pair"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                         "peak_source": f"{psrc} (copy bandwidth)",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel": "k_step_structured<D3Q45,P=2,float>" if args.config == "channel" else "k_step"},
+            "e2e": {"value": round(N / e2e_s / 1e6, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "conservation_rc": rc,
+            "per_rank_mlups": round(mlups_rank, 2),
+        }
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--config", default="channel")
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cb = run_oracle_subprocess(args.config, max(5.0, args.cpu_seconds * args.steps / max(args.steps, 1)))
+        line = {"impl": "reference", "metric": "MLUPS (node updates/s, all Q of f and g)", "value": cb["value"],
+                "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded)", "config": {"workload": args.config},
+                "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                                            "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+    from paper_2412_09051_gb300 import build as b
+    if rank == 0:
+        b.build()
+    line = run_gpu(args, ws, rank, local)
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = run_oracle_subprocess(args.config, args.cpu_seconds)
+        print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

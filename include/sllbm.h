@@ -1,0 +1,249 @@
+/*
+ * sllbm.h -- C ABI of the GB300 semi-Lagrangian lattice Boltzmann library.
+ *
+ * The library implements the fused per-node pull step of the compressible
+ * semi-Lagrangian lattice Boltzmann method (SLLBM) of Spelten, Wilde,
+ * Bedrunka, Reith and Foysi (arXiv 2412.09051):
+ *   - stream by interpolation at the departure point (Sec. 3.1, Eq. 1 and
+ *     Eq. intf: order-p Lagrange interpolation in the departure cell),
+ *   - density / momentum / energy moments (Sec. 3.1, moment equations),
+ *   - relaxation towards the order-4 Hermite equilibrium with the
+ *     quasi-equilibrium term for Pr != 1 (Sec. 3.1, Eq. 1),
+ *   - the boundary schemes of Sec. 3.3: equilibrium (3.3.1), bounce-back and
+ *     isothermal wall (3.3.2, Eq. thermalBC) and zero-gradient outlet (3.3.3),
+ * on one CUDA device (sm_103a).  A one-time FP64 setup pass traces every
+ * departure point, inverts curved cell maps by Newton iteration and stores
+ * departure records (Sec. 3.1: departure point x_AP - dt zeta_i).
+ *
+ * Conventions
+ *   - Every call returns an int status: SLLBM_OK (0) or a negative SLLBM_ERR_*.
+ *     No C++ exception crosses this boundary.  sllbm_last_error() returns a
+ *     human-readable message for the last failing call on a context.
+ *   - Units: gas constant R = 1, lattice reference state rho0 = T0 = 1,
+ *     c_v = 1/(gamma - 1); abscissae zeta_i = xi_i (sqrt(T0) = 1).
+ *   - Node numbering is structured: n = k0 + N0 (k1 + N1 k2), first dimension
+ *     fastest; periodic duplicates are removed.  Cell numbering likewise.
+ *   - Population arrays are [Q][N] (velocity-major, node fastest).
+ *   - Pointers flagged `on_device` are CUDA device pointers on the context's
+ *     device; otherwise host pointers (pageable or pinned).  The caller owns
+ *     every buffer it passes; the context owns only what it allocates itself
+ *     and frees it in sllbm_destroy().
+ *   - All work is enqueued on the context's stream.  Calls that return data
+ *     to host memory synchronise that stream before returning.
+ *   - There is no CPU fallback: a context can only be created on a device of
+ *     compute capability 10.3 (sm_103a); otherwise SLLBM_ERR_ARCH.
+ */
+#ifndef SLLBM_H
+#define SLLBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define SLLBM_OK                 0
+#define SLLBM_ERR_ARG           -1   /* invalid argument or descriptor          */
+#define SLLBM_ERR_CUDA          -2   /* a CUDA runtime call failed               */
+#define SLLBM_ERR_ARCH          -3   /* device is not sm_103 or not present      */
+#define SLLBM_ERR_NOMEM         -4   /* device allocation failed                 */
+#define SLLBM_ERR_DP_NOT_FOUND  -5   /* setup: a departure point was not located
+                                        within the Newton / cell-walk caps       */
+#define SLLBM_ERR_UNSTABLE      -6   /* non-positive density or temperature      */
+#define SLLBM_ERR_STATE         -7   /* call out of order (e.g. step before init) */
+#define SLLBM_ERR_UNSUPPORTED   -8   /* combination not built in this library    */
+
+/* ------------------------------------------------------------------ enums */
+/* Mesh kinds (Sec. 3.1: cells with order-p Lagrange support points at the
+ * Gauss-Lobatto-Chebyshev positions -cos(pi k / p), Tab. 2 caption). */
+#define SLLBM_MESH_BOX       0  /* periodic in every dimension, uniform cells on [0, L_d)    */
+#define SLLBM_MESH_CHANNEL   1  /* x,z periodic uniform; y in [0, L_y] with tanh clustering:
+                                   y_j = L_y/2 [1 - tanh(s (1 - 2 j / C_y)) / tanh(s)]        */
+#define SLLBM_MESH_MIXING    2  /* x,z periodic uniform; y in [-L_y/2, L_y/2]: `central`
+                                   uniform cells, neighbours grow by the factor s outwards   */
+#define SLLBM_MESH_NACA      3  /* 2D O-grid around a NACA-00tt profile (closed trailing edge
+                                   form of the thickness formula); surface point at angle
+                                   phi = 2 pi s / C_0: x = 1 - (1 - cos phi)/2
+                                   - 0.25 |sin phi| (1 + cos phi)/2, y = sign(sin phi) y_t(x);
+                                   radial line to the far-field point at the same angle;
+                                   dim 0 around (periodic),
+                                   dim 1 radial, growth factor s per cell up to a circle of
+                                   radius L_1 about mid-chord; isoparametric degree-p cells  */
+
+/* Velocity sets (Sec. 3.2).  Ordering: index 0 rest, then shells; inside a
+ * shell of n points the second half are the negatives of the first half.
+ *   D2Q9   classic lattice, xi in {0, +-sqrt3}^2 (classic-LBM special case, Sec. 2)
+ *   D2Q19  degree-9 cubature: rest, ring r^2 = (48 - 8 sqrt15)/7 at k 60 deg,
+ *          ring r = 2 sqrt2 at 30 + k 60 deg, ring r^2 = (48 + 8 sqrt15)/7 at k 60 deg
+ *   D2Q25  product 5-point Gauss-Hermite rule (degree 9), x fastest over
+ *          nodes {0, r1, r2, -r1, -r2}, r1,2 = sqrt(5 -+ sqrt10)
+ *   D3Q45  degree-9 cubature: rest, icosahedron (cyclic perms of (0,+-phi,+-1)) at
+ *          radius sqrt3, dodecahedron ((+-1)^3, cyclic perms of (0,+-1/phi,+-phi)) at
+ *          radius 3, icosahedron (same orientation) at radius sqrt15 */
+#define SLLBM_D2Q9    0
+#define SLLBM_D2Q19   1
+#define SLLBM_D2Q25   2
+#define SLLBM_D3Q45   3
+
+/* Boundary kinds (Sec. 3.3).  Boundary id 0 is the low-y side of channel /
+ * mixing meshes and the profile wall of the NACA O-grid; id 1 is the high-y
+ * side and the O-grid far field. */
+#define SLLBM_BC_PERIODIC     0
+#define SLLBM_BC_EQUILIBRIUM  1  /* f_i(AP) = f_i^eq(rho_w, u_w, T_w)                      (3.3.1) */
+#define SLLBM_BC_BOUNCEBACK   2  /* f_i(AP) = f_ibar(x_W + iota) [+ 2 w_i rho_w zeta_i.u_w] (3.3.2) */
+#define SLLBM_BC_ISOTHERMAL   3  /* bounce-back plus f += f^eq(T_w) - f^eq(T)    (Eq. thermalBC) */
+#define SLLBM_BC_OUTLET       4  /* f_i(AP) = f_i(x_AP + zeta_i dt)                        (3.3.3) */
+#define SLLBM_BC_FARFIELD     5  /* equilibrium where the wall point lies upstream of mid-chord,
+                                    outlet downstream (NACA far field)                           */
+
+#define SLLBM_FP64  0   /* populations and arithmetic in FP64                       */
+#define SLLBM_FP32  1   /* populations stored in FP32 as deviations from w_i rho0 (f)
+                           and w_i rho0 T0 (2 c_v - D) (g); compensated FP32 moments  */
+
+#define SLLBM_STREAM_AUTO        0  /* structured kernel where cells are axis-aligned, else gather */
+#define SLLBM_STREAM_GATHER      1  /* one departure record per (node, velocity)                  */
+#define SLLBM_STREAM_STRUCTURED  2  /* one record per (velocity, translation class of nodes)     */
+
+/* ------------------------------------------------------------------ descriptors */
+typedef struct {
+    int32_t kind;          /* SLLBM_BC_* */
+    double  rho;           /* wall / inflow density rho_w     */
+    double  u[3];          /* wall / inflow velocity u_w      */
+    double  T;             /* wall / inflow temperature T_w   */
+} sllbm_bc;
+
+typedef struct {
+    int32_t  kind;         /* SLLBM_MESH_*                                         */
+    int32_t  dim;          /* D = 2 or 3                                           */
+    int32_t  p;            /* Lagrange order, 1..4                                 */
+    int32_t  cells[3];     /* cells per dimension                                  */
+    double   length[3];    /* domain extent per dimension (NACA: [chord=1, R, -])  */
+    double   stretch;      /* tanh parameter (channel), growth factor (mixing, NACA) */
+    int32_t  central;      /* mixing: number of uniform central cells in y         */
+    double   thickness;    /* NACA relative thickness t (0.12 for NACA-0012)       */
+    sllbm_bc bc[2];        /* boundary ids 0 and 1                                 */
+} sllbm_mesh_desc;
+
+typedef struct {
+    double  dt;            /* time step                                             */
+    double  gamma;         /* ratio of specific heats                                */
+    double  Pr;            /* Prandtl number                                          */
+    double  mu_ref;        /* mu(T) = mu_ref (T / T_ref)^mu_exp  (Sec. 4.3 power law) */
+    double  T_ref;
+    double  mu_exp;
+    int32_t precision;     /* SLLBM_FP64 / SLLBM_FP32                                */
+    int32_t stream_mode;   /* SLLBM_STREAM_*                                          */
+    int32_t device;        /* CUDA device ordinal                                      */
+    int32_t max_newton;    /* setup Newton cap (0: default 40)                        */
+    int32_t max_walk;      /* setup cell-walk cap (0: default 64)                     */
+    void*   stream;        /* cudaStream_t to enqueue on (NULL: a stream owned by the ctx) */
+} sllbm_params;
+
+typedef struct {
+    int64_t n_nodes;       /* N                                                  */
+    int32_t Q, dim, p;
+    int32_t nodes[3];      /* nodes per dimension                                */
+    int32_t cells[3];
+    int32_t precision;
+    int32_t stream_mode;   /* resolved mode actually used                       */
+    int64_t state_bytes;   /* device bytes of one population buffer pair (f and g) */
+    int64_t table_bytes;   /* device bytes of the departure records used by step   */
+    int64_t n_records;     /* number of departure records                          */
+    int64_t n_boundary_records;  /* records whose trajectory left the domain       */
+    int64_t n_isothermal_nodes;  /* nodes with an isothermal-wall trajectory       */
+} sllbm_info_t;
+
+typedef struct sllbm_ctx sllbm_ctx;
+
+/* ------------------------------------------------------------------ lifecycle */
+
+/* Create a context: builds the mesh and the velocity set on the host (FP64),
+ * runs the FP64 departure-point setup kernels on the device (Sec. 3.1: DP =
+ * x_AP - dt zeta_i; curved cells inverted by Newton iteration; Sec. 3.3 for
+ * trajectories that leave the domain) and allocates two population buffers.
+ * Errors: SLLBM_ERR_ARG (bad descriptor), SLLBM_ERR_ARCH (not sm_103),
+ * SLLBM_ERR_NOMEM, SLLBM_ERR_DP_NOT_FOUND (setup caps exceeded), SLLBM_ERR_CUDA.
+ * On error *out is NULL and the message is available from sllbm_error_text(). */
+int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params* params,
+                 sllbm_ctx** out);
+
+/* Free everything the context owns.  NULL is accepted. */
+int sllbm_destroy(sllbm_ctx* ctx);
+
+/* Message of the last failing call on ctx (ctx may be NULL: last create error). */
+const char* sllbm_last_error(const sllbm_ctx* ctx);
+
+/* Sizes and resolved options of a context. */
+int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* out);
+
+/* Node coordinates, x[N][D] (row per node), FP64. */
+int sllbm_node_coords(sllbm_ctx* ctx, double* x, int32_t on_device);
+
+/* Velocity set: xi[Q][D], w[Q], opp[Q] (index of -xi_i).  Host pointers. */
+int sllbm_velocity_set(const sllbm_ctx* ctx, double* xi, double* w, int32_t* opp);
+
+/* ------------------------------------------------------------------ state */
+
+/* Initialise the populations to the equilibria f^eq, g^eq (Sec. 3.1) of the
+ * given macroscopic fields rho[N], u[N][D], T[N] (FP64). */
+int sllbm_init_state(sllbm_ctx* ctx, const double* rho, const double* u, const double* T,
+                     int32_t on_device);
+
+/* Full populations f[Q][N], g[Q][N] in FP64 (storage deviations plus their
+ * reference values). */
+int sllbm_get_state(sllbm_ctx* ctx, double* f, double* g, int32_t on_device);
+int sllbm_set_state(sllbm_ctx* ctx, const double* f, const double* g, int32_t on_device);
+
+/* Native storage (deviations, FP32 or FP64 per the context's precision),
+ * bitwise checkpoint / restore of the current step's populations. */
+int sllbm_get_state_raw(sllbm_ctx* ctx, void* f, void* g, int32_t on_device);
+int sllbm_set_state_raw(sllbm_ctx* ctx, const void* f, const void* g, int32_t on_device);
+
+/* ------------------------------------------------------------------ stepping */
+
+/* Advance n time steps (Eq. 1 with the boundary schemes of Sec. 3.3): one
+ * fused stream + moments + collision kernel launch per step, ping-ponging the
+ * two population buffers.  Asynchronous on the context stream. */
+int sllbm_step(sllbm_ctx* ctx, int64_t n);
+
+/* Number of steps taken since the last init / set_state. */
+int sllbm_step_count(const sllbm_ctx* ctx, int64_t* out);
+
+/* ------------------------------------------------------------------ readout */
+
+/* Per-node moments (Sec. 3.1): rho[N], u[N][D], T[N] in FP64. */
+int sllbm_read_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int32_t on_device);
+
+/* Conservation sums in FP64 over all nodes: out[0] = sum rho,
+ * out[1..D] = sum rho u, out[D+1] = sum (rho |u|^2 + 2 rho c_v T) (= 2 rho E).
+ * Also checks positivity: returns SLLBM_ERR_UNSTABLE if any node has
+ * rho <= 0 or T <= 0 or a non-finite value (out is still filled). */
+int sllbm_conservation(sllbm_ctx* ctx, double* out);
+
+/* ------------------------------------------------------------------ setup data */
+
+/* FP64 departure records as produced by the setup pass, one per
+ * (velocity i, node n), arrays [Q][N]:
+ *   kind  0 interior, 1 equilibrium, 2 bounce-back, 3 isothermal bounce-back, 4 outlet
+ *   src   population read (i, or opp[i] for bounce-back)
+ *   bid   boundary id crossed (-1 if none)
+ *   cell  departure cell (-1 for equilibrium records)
+ *   xi    reference coordinates [Q][N][D]
+ *   xsrc  physical source point [Q][N][D] (equals the cell map of (cell, xi))
+ * Host pointers; any of them may be NULL.  For the structured mode the
+ * records are expanded from the per-class records. */
+int sllbm_departure_records(sllbm_ctx* ctx, int32_t* kind, int32_t* src, int32_t* bid,
+                            int32_t* cell, double* xi, double* xsrc);
+
+/* Synchronise the context stream. */
+int sllbm_sync(sllbm_ctx* ctx);
+
+/* cudaStream_t the context enqueues on. */
+void* sllbm_stream(const sllbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLLBM_H */

@@ -101,16 +101,18 @@ def boundary_id(mesh, xw, x_dp):
     return (x_dp[:, 1] > V[-1]).astype(np.int64)
 
 
-def trace(mesh, xi_set, opp, dt, bcs):
+def trace(mesh, xi_set, opp, dt, bcs, nodes=None):
     """Departure records for every (velocity i, node n), all velocities at once.
 
     bcs: list of two dicts (bid 0, bid 1) with key 'kind' (BC_* constant).
+    nodes: optional subset of arrival nodes (default: all nodes).
     Returns dict of arrays [Q, N]: kind, src, bid, cell, tw, xi [Q, N, D], xsrc [Q, N, D].
     """
     loc = Locator(mesh)
     Q = len(xi_set)
-    N, D = mesh.n_nodes, mesh.D
-    X = np.broadcast_to(mesh.X[None], (Q, N, D)).reshape(-1, D)
+    Xa = mesh.X if nodes is None else mesh.X[np.asarray(nodes)]
+    N, D = len(Xa), mesh.D
+    X = np.broadcast_to(Xa[None], (Q, N, D)).reshape(-1, D)
     step = np.broadcast_to((dt * xi_set)[:, None, :], (Q, N, D)).reshape(-1, D)
     vel = np.repeat(np.arange(Q), N)
     M = Q * N

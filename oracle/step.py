@@ -52,10 +52,11 @@ def moments(f, g, xi, cv):
 
 
 def stream(mesh, rec, f, g, xi, w, par):
-    Q, N = f.shape
+    """Streamed values for the arrival nodes the records were traced for."""
+    Q, N = rec["kind"].shape
     D = mesh.D
-    fs = np.zeros_like(f)
-    gs = np.zeros_like(g)
+    fs = np.zeros((Q, N))
+    gs = np.zeros((Q, N))
     for i in range(Q):
         kind, src, cell = rec["kind"][i], rec["src"][i], rec["cell"][i]
         inter = kind != REC_EQ
@@ -143,3 +144,20 @@ def step(mesh, rec, f, g, xi, w, par, Tw=None, mlp=None):
     if mlp is not None:
         f1 = f1 + mlp(fs, gs, f1, g1)
     return f1, g1
+
+
+def step_sample_from_fields(mesh, rec, rho, u, T, xi, w, par):
+    """One step for a subset of arrival nodes (records traced with `nodes=`),
+    starting from the equilibrium of the full-mesh fields rho, u, T.  Only the
+    support points that the records read are initialised."""
+    Q = len(xi)
+    need = rec["kind"] != REC_EQ
+    cells = np.unique(rec["cell"][need])
+    nodes = np.unique(mesh.cell_nodes(cells).ravel())
+    f = np.zeros((Q, mesh.n_nodes))
+    g = np.zeros((Q, mesh.n_nodes))
+    f[:, nodes], g[:, nodes] = init_equilibrium(rho[nodes], u[nodes], T[nodes], xi, w, par.cv)
+    Tw = isothermal_nodes(rec, par)
+    fs, gs = stream(mesh, rec, f, g, xi, w, par)
+    fs, gs = thermal_correction(fs, gs, xi, w, par, Tw)
+    return collide(fs, gs, xi, w, par)

@@ -1,0 +1,101 @@
+"""ctypes binding of the C ABI declared in include/sllbm.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library libsllbm.so built in-tree by
+``paper_2412_09051_gb300.build``.  Importing this module does not load the
+library; ``lib()`` does, and raises if it is missing: there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsllbm.so")
+
+OK = 0
+ERRORS = {-1: "SLLBM_ERR_ARG", -2: "SLLBM_ERR_CUDA", -3: "SLLBM_ERR_ARCH", -4: "SLLBM_ERR_NOMEM",
+          -5: "SLLBM_ERR_DP_NOT_FOUND", -6: "SLLBM_ERR_UNSTABLE", -7: "SLLBM_ERR_STATE",
+          -8: "SLLBM_ERR_UNSUPPORTED"}
+MESH = dict(box=0, channel=1, mixing=2, naca=3)
+VELSET = dict(D2Q9=0, D2Q19=1, D2Q25=2, D3Q45=3)
+FP64, FP32 = 0, 1
+STREAM_AUTO, STREAM_GATHER, STREAM_STRUCTURED = 0, 1, 2
+
+
+class Bc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("rho", C.c_double), ("u", C.c_double * 3), ("T", C.c_double)]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dim", C.c_int32), ("p", C.c_int32), ("cells", C.c_int32 * 3),
+                ("length", C.c_double * 3), ("stretch", C.c_double), ("central", C.c_int32),
+                ("thickness", C.c_double), ("bc", Bc * 2)]
+
+
+class Params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("gamma", C.c_double), ("Pr", C.c_double), ("mu_ref", C.c_double),
+                ("T_ref", C.c_double), ("mu_exp", C.c_double), ("precision", C.c_int32),
+                ("stream_mode", C.c_int32), ("device", C.c_int32), ("max_newton", C.c_int32),
+                ("max_walk", C.c_int32), ("stream", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("Q", C.c_int32), ("dim", C.c_int32), ("p", C.c_int32),
+                ("nodes", C.c_int32 * 3), ("cells", C.c_int32 * 3), ("precision", C.c_int32),
+                ("stream_mode", C.c_int32), ("state_bytes", C.c_int64), ("table_bytes", C.c_int64),
+                ("n_records", C.c_int64), ("n_boundary_records", C.c_int64),
+                ("n_isothermal_nodes", C.c_int64)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "sllbm_create": (C.c_int, [C.POINTER(MeshDesc), C.c_int32, C.POINTER(Params), C.POINTER(_P)]),
+    "sllbm_destroy": (C.c_int, [_P]),
+    "sllbm_last_error": (C.c_char_p, [_P]),
+    "sllbm_info": (C.c_int, [_P, C.POINTER(Info)]),
+    "sllbm_node_coords": (C.c_int, [_P, _P, C.c_int32]),
+    "sllbm_velocity_set": (C.c_int, [_P, _P, _P, _P]),
+    "sllbm_init_state": (C.c_int, [_P, _P, _P, _P, C.c_int32]),
+    "sllbm_get_state": (C.c_int, [_P, _P, _P, C.c_int32]),
+    "sllbm_set_state": (C.c_int, [_P, _P, _P, C.c_int32]),
+    "sllbm_get_state_raw": (C.c_int, [_P, _P, _P, C.c_int32]),
+    "sllbm_set_state_raw": (C.c_int, [_P, _P, _P, C.c_int32]),
+    "sllbm_step": (C.c_int, [_P, C.c_int64]),
+    "sllbm_step_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "sllbm_read_moments": (C.c_int, [_P, _P, _P, _P, C.c_int32]),
+    "sllbm_conservation": (C.c_int, [_P, _P]),
+    "sllbm_departure_records": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "sllbm_sync": (C.c_int, [_P]),
+    "sllbm_stream": (C.c_void_p, [_P]),
+}
+EXPORTED = sorted(_SIGS)
+
+_lib = None
+
+
+def lib(path=None):
+    """Load libsllbm.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise OSError(f"{p} is missing: build it with `python -m paper_2412_09051_gb300.build` "
+                          "(there is no CPU fallback)")
+        L = C.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SllbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(rc, ctx=None):
+    if rc != OK:
+        msg = lib().sllbm_last_error(ctx)
+        raise SllbmError(rc, msg.decode() if msg else "")
+    return rc

@@ -1,0 +1,765 @@
+// C ABI of the SLLBM library: context lifecycle, setup orchestration, step
+// dispatch and readouts.  See include/sllbm.h for the contract of each call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sllbm_internal.h"
+#include "step_kernels.cuh"
+
+namespace sllbm {
+int launch_trace(const TraceArgs& A, const double* dX, int64_t n_units, int structured, int ncls0, int ncls1,
+                 Rec64* out, int* d_fail, cudaStream_t s);
+int launch_isothermal(const Rec64* rec, int64_t n_units, int Q, const double* bcT, double* Tw,
+                      unsigned long long* counts, cudaStream_t s);
+template <typename real>
+int launch_pack_gather(const Rec64* rec, int64_t N, int Q, int D, int32_t* code, real* xi, cudaStream_t s);
+template <typename real>
+int launch_init(int vs, const double* rho, const double* u, const double* T, int64_t N, const CollideConst<double>& C,
+                real* f, real* g, cudaStream_t s);
+template <typename real>
+int launch_convert(real* fd, real* gd, double* ff, double* gf, int64_t N, int Q, const double* w, const double* wg,
+                   int dir, cudaStream_t s);
+template <typename real>
+int launch_moments(int vs, const real* f, const real* g, int64_t N, const CollideConst<double>& C, double* rho,
+                   double* u, double* T, cudaStream_t s);
+template <typename real>
+int launch_conserve(int vs, int D, const real* f, const real* g, int64_t N, const CollideConst<double>& C,
+                    double* part, int* flag, double* out, cudaStream_t s);
+int conserve_blocks();
+SLLBM_EXTERN_STEP(0, 2, float)
+SLLBM_EXTERN_STEP(1, 2, float)
+SLLBM_EXTERN_STEP(1, 3, float)
+SLLBM_EXTERN_STEP(2, 2, float)
+SLLBM_EXTERN_STEP(3, 2, float)
+SLLBM_EXTERN_STEP(0, 2, double)
+SLLBM_EXTERN_STEP(1, 2, double)
+SLLBM_EXTERN_STEP(1, 3, double)
+SLLBM_EXTERN_STEP(2, 2, double)
+SLLBM_EXTERN_STEP(3, 2, double)
+}  // namespace sllbm
+
+using namespace sllbm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(sllbm_ctx* c, int code, const std::string& msg) {
+    if (c) c->last_error = msg; else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(sllbm_ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? SLLBM_ERR_NOMEM : SLLBM_ERR_CUDA, m);
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+size_t real_size(const sllbm_ctx* c) { return c->precision == SLLBM_FP64 ? 8 : 4; }
+
+// host evaluation of the equilibrium deviations (same scalar polynomial as the kernels)
+void host_eq_dev(const sllbm_ctx* c, double rho, const double* u, double T, double* fdev, double* gdev) {
+    const HostVelSet& vs = c->vs;
+    const int D = vs.D;
+    const double cv = 1.0 / (c->params.gamma - 1.0);
+    const double gf = 2.0 * cv - D;
+    double U = 0;
+    for (int d = 0; d < D; ++d) U += u[d] * u[d];
+    const double t = T - 1.0;
+    for (int i = 0; i < vs.Q; ++i) {
+        double s = 0, cd = 0;
+        for (int d = 0; d < D; ++d) {
+            s += vs.xi[i * D + d] * vs.xi[i * D + d];
+            cd += vs.xi[i * D + d] * u[d];
+        }
+        const double A = s - D, B = s - D - 2, Cc = s - D - 4, E = s * s - 2.0 * (D + 2) * s + D * (D + 2.0);
+        const double k2 = 0.5 - 0.25 * U + 0.25 * t * Cc;
+        const double k1 = 1.0 - 0.5 * U + 0.5 * t * B;
+        const double k0 = -0.5 * U + 0.125 * U * U + 0.5 * t * A - 0.25 * t * U * B + 0.125 * t * t * E;
+        const double P1 = (((cd / 24.0 + 1.0 / 6.0) * cd + k2) * cd + k1) * cd + k0;
+        fdev[i] = vs.w[i] * (rho * P1 + (rho - 1.0));
+        gdev[i] = vs.w[i] * gf * (rho * T * P1 + (rho * T - 1.0));
+    }
+}
+
+template <typename real>
+void fill_collide_const(sllbm_ctx* c, CollideConst<real>& C) {
+    std::memset(&C, 0, sizeof(C));
+    const HostVelSet& vs = c->vs;
+    const int D = vs.D;
+    const double cv = 1.0 / (c->params.gamma - 1.0);
+    const double gf = 2.0 * cv - D;
+    for (int i = 0; i < vs.Q; ++i) {
+        for (int d = 0; d < D; ++d) C.xi[i][d] = real(vs.xi[i * D + d]);
+        C.w[i] = real(vs.w[i]);
+        C.wg[i] = real(vs.w[i] * gf);
+        C.opp[i] = vs.opp[i];
+    }
+    for (size_t h = 0; h < vs.shell_s.size(); ++h) {
+        const double s = vs.shell_s[h];
+        C.sA[h] = real(s - D);
+        C.sB[h] = real(s - D - 2);
+        C.sC[h] = real(s - D - 4);
+        C.sE[h] = real(s * s - 2.0 * (D + 2) * s + D * (D + 2.0));
+        C.s2[h] = real(s);
+    }
+    C.cv = real(cv);
+    C.gfac = real(gf);
+    C.dt = real(c->params.dt);
+    C.inv_Pr = real(1.0 / c->params.Pr);
+    C.mu_ref = real(c->params.mu_ref);
+    C.inv_T_ref = real(1.0 / c->params.T_ref);
+    C.mu_exp = real(c->params.mu_exp);
+    C.var_mu = c->params.mu_exp != 0.0;
+    C.quasi = c->params.Pr != 1.0;
+    for (int b = 0; b < 2; ++b) {
+        const sllbm_bc& bc = c->desc.bc[b];
+        double fe[SLLBM_QMAX], ge[SLLBM_QMAX];
+        host_eq_dev(c, bc.rho, bc.u, bc.T, fe, ge);
+        for (int i = 0; i < vs.Q; ++i) {
+            C.eqf[b][i] = real(fe[i]);
+            C.eqg[b][i] = real(ge[i]);
+            double cu = 0;
+            for (int d = 0; d < D; ++d) cu += vs.xi[i * D + d] * bc.u[d];
+            C.mw[b][i] = real(2.0 * vs.w[i] * bc.rho * cu);
+        }
+    }
+}
+
+template <typename real>
+void build_class_table(const sllbm_ctx* c, const std::vector<Rec64>& rec, std::vector<ClassRec<real>>& out) {
+    const HostMesh& m = c->mesh;
+    const int Q = c->vs.Q, D = m.D, p = m.p;
+    const int64_t U = c->n_rec_units;
+    out.assign(size_t(Q * U), ClassRec<real>());
+    for (int i = 0; i < Q; ++i)
+        for (int64_t u = 0; u < U; ++u) {
+            const Rec64& r = rec[size_t(i * U + u)];
+            ClassRec<real>& o = out[size_t(i * U + u)];
+            std::memset(&o, 0, sizeof(o));
+            o.meta = r.meta;
+            if (r.cell < 0) continue;
+            int cc[3] = {0, 0, 0};
+            int64_t cl = r.cell;
+            for (int d = 0; d < D; ++d) {
+                cc[d] = int(cl % m.cells[d]);
+                cl /= m.cells[d];
+            }
+            for (int d = 0; d < D; ++d) {
+                o.cell[d] = cc[d];   // periodic dims: representative home cell is 0 -> offset
+                for (int a = 0; a <= p; ++a) {
+                    double v = 1.0;
+                    for (int q = 0; q <= p; ++q)
+                        if (q != a) v *= (r.xi[d] - m.glc[q]) / (m.glc[a] - m.glc[q]);
+                    o.wt[d][a] = real(v);
+                }
+            }
+        }
+}
+
+template <typename real>
+int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
+    const int vs = ctx->velset, p = ctx->mesh.p;
+    const bool st = ctx->mode == SLLBM_STREAM_STRUCTURED;
+#define CASE(VS, P)                                                                      \
+    if (vs == VS && p == P) return st ? launch_step_structured<VS, P, real>(L) : launch_step_gather<VS, P, real>(L);
+    CASE(0, 2)
+    CASE(1, 2)
+    CASE(1, 3)
+    CASE(2, 2)
+    CASE(3, 2)
+#undef CASE
+    return fail(ctx, SLLBM_ERR_UNSUPPORTED, "velocity set / order combination not built (p must be 2, or 3 for D2Q19)");
+}
+
+bool supported(int vs, int p) { return p == 2 || (vs == SLLBM_D2Q19 && p == 3); }
+
+}  // namespace
+
+// ====================================================================== API
+extern "C" {
+
+const char* sllbm_last_error(const sllbm_ctx* ctx) {
+    return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
+
+int sllbm_destroy(sllbm_ctx* ctx) {
+    if (!ctx) return SLLBM_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
+                    ctx->tw_tab, ctx->f[0], ctx->f[1], ctx->g[0], ctx->g[1], ctx->d_red, ctx->d_flag};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return SLLBM_OK;
+}
+
+int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params* params, sllbm_ctx** out) {
+    if (!out) return fail(nullptr, SLLBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!mesh || !params) return fail(nullptr, SLLBM_ERR_ARG, "NULL descriptor");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(nullptr, SLLBM_ERR_ARCH, "no CUDA device available");
+    if (params->device < 0 || params->device >= ndev) return fail(nullptr, SLLBM_ERR_ARG, "bad device ordinal");
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, params->device) != cudaSuccess)
+        return fail(nullptr, SLLBM_ERR_CUDA, "cudaGetDeviceProperties failed");
+    if (!(prop.major == 10 && prop.minor == 3))
+        return fail(nullptr, SLLBM_ERR_ARCH, "device is not compute capability 10.3 (sm_103)");
+    if (!(params->dt > 0) || !(params->gamma > 1.0) || !(params->Pr > 0) || !(params->mu_ref > 0) ||
+        !(params->T_ref > 0))
+        return fail(nullptr, SLLBM_ERR_ARG, "dt > 0, gamma > 1, Pr > 0, mu_ref > 0, T_ref > 0 required");
+    if (params->precision != SLLBM_FP32 && params->precision != SLLBM_FP64)
+        return fail(nullptr, SLLBM_ERR_ARG, "bad precision");
+
+    sllbm_ctx* ctx = new (std::nothrow) sllbm_ctx();
+    if (!ctx) return fail(nullptr, SLLBM_ERR_NOMEM, "host allocation failed");
+    ctx->desc = *mesh;
+    ctx->params = *params;
+    ctx->velset = velset;
+    ctx->device = params->device;
+    ctx->precision = params->precision;
+    auto bail = [&](int code) {
+        g_create_error = ctx->last_error;
+        sllbm_destroy(ctx);
+        return code;
+    };
+    int rc = build_velocity_set(velset, ctx->vs, ctx->last_error);
+    if (rc) return bail(rc);
+    rc = build_mesh(*mesh, ctx->mesh, ctx->last_error);
+    if (rc) return bail(rc);
+    if (ctx->vs.D != ctx->mesh.D) {
+        ctx->last_error = "velocity set dimension differs from mesh dimension";
+        return bail(SLLBM_ERR_ARG);
+    }
+    if (!supported(velset, ctx->mesh.p)) {
+        ctx->last_error = "velocity set / order combination not built (p must be 2, or 3 for D2Q19)";
+        return bail(SLLBM_ERR_UNSUPPORTED);
+    }
+    for (int b = 0; b < 2; ++b) {
+        const int k = mesh->bc[b].kind;
+        if (k < 0 || k > SLLBM_BC_FARFIELD || !(mesh->bc[b].rho > 0) || !(mesh->bc[b].T > 0)) {
+            ctx->last_error = "bad boundary descriptor";
+            return bail(SLLBM_ERR_ARG);
+        }
+        if (ctx->mesh.kind != SLLBM_MESH_BOX && k == SLLBM_BC_PERIODIC) {
+            ctx->last_error = "non-periodic boundary needs a boundary kind";
+            return bail(SLLBM_ERR_ARG);
+        }
+    }
+    const bool axis = ctx->mesh.kind != SLLBM_MESH_NACA;
+    int mode = params->stream_mode;
+    if (mode == SLLBM_STREAM_AUTO) mode = axis ? SLLBM_STREAM_STRUCTURED : SLLBM_STREAM_GATHER;
+    if (mode == SLLBM_STREAM_STRUCTURED && !axis) {
+        ctx->last_error = "structured streaming needs axis-aligned cells";
+        return bail(SLLBM_ERR_ARG);
+    }
+    if (mode != SLLBM_STREAM_STRUCTURED && mode != SLLBM_STREAM_GATHER) {
+        ctx->last_error = "bad stream mode";
+        return bail(SLLBM_ERR_ARG);
+    }
+    ctx->mode = mode;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        ctx->last_error = "cudaSetDevice failed";
+        return bail(SLLBM_ERR_CUDA);
+    }
+    if (params->stream) {
+        ctx->stream = static_cast<cudaStream_t>(params->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            ctx->last_error = "cudaStreamCreate failed";
+            return bail(SLLBM_ERR_CUDA);
+        }
+        ctx->own_stream = true;
+    }
+    fill_collide_const(ctx, ctx->cc32);
+    fill_collide_const(ctx, ctx->cc64);
+    rc = [&]() -> int {
+        const HostMesh& m = ctx->mesh;
+        const int Q = ctx->vs.Q, D = m.D;
+        const int64_t N = m.n_nodes;
+        cudaStream_t s = ctx->stream;
+        // ---- geometry upload
+        CK(cudaMalloc(&ctx->dX, sizeof(double) * N * D));
+        CK(cudaMemcpyAsync(ctx->dX, m.X.data(), sizeof(double) * N * D, cudaMemcpyHostToDevice, s));
+        MeshView MV;
+        std::memset(&MV, 0, sizeof(MV));
+        MV.kind = m.kind;
+        MV.D = D;
+        MV.p = m.p;
+        for (int d = 0; d < 3; ++d) {
+            MV.cells[d] = m.cells[d];
+            MV.N[d] = m.N[d];
+            MV.periodic[d] = m.periodic[d];
+            MV.length[d] = m.length[d];
+        }
+        if (axis)
+            for (int d = 0; d < D; ++d) {
+                CK(cudaMalloc(&ctx->dV[d], sizeof(double) * m.V[d].size()));
+                CK(cudaMemcpyAsync(ctx->dV[d], m.V[d].data(), sizeof(double) * m.V[d].size(),
+                                   cudaMemcpyHostToDevice, s));
+                MV.V[d] = ctx->dV[d];
+            }
+        MV.X = ctx->dX;
+        for (int a = 0; a <= m.p; ++a) {
+            MV.glc[a] = m.glc[a];
+            double den = 1.0;
+            for (int q = 0; q <= m.p; ++q)
+                if (q != a) den *= (m.glc[a] - m.glc[q]);
+            MV.glc_inv_den[a] = 1.0 / den;
+        }
+        MV.bc_kind[0] = ctx->desc.bc[0].kind;
+        MV.bc_kind[1] = ctx->desc.bc[1].kind;
+        MV.R = m.length[1];
+        TraceArgs A;
+        std::memset(&A, 0, sizeof(A));
+        A.M = MV;
+        A.Q = Q;
+        A.dt = params->dt;
+        A.max_newton = params->max_newton > 0 ? params->max_newton : 40;
+        A.max_walk = params->max_walk > 0 ? params->max_walk : 64;
+        for (int i = 0; i < Q; ++i) {
+            for (int d = 0; d < D; ++d) A.xi[i][d] = ctx->vs.xi[i * D + d];
+            A.opp[i] = ctx->vs.opp[i];
+        }
+        // ---- geometry of the step kernels
+        StepGeom& G = ctx->geom;
+        std::memset(&G, 0, sizeof(G));
+        G.n_nodes = N;
+        G.n_classes = 1;
+        for (int d = 0; d < 3; ++d) {
+            G.N[d] = m.N[d];
+            G.cells[d] = m.cells[d];
+            G.periodic[d] = d < D ? m.periodic[d] : 0;
+            G.ncls[d] = d < D ? (m.periodic[d] ? m.p : m.N[d]) : 1;
+            G.n_classes *= G.ncls[d];
+        }
+        const bool st = ctx->mode == SLLBM_STREAM_STRUCTURED;
+        ctx->n_rec_units = st ? G.n_classes : N;
+        const int64_t U = ctx->n_rec_units;
+        // ---- FP64 trace
+        CK(cudaMalloc(&ctx->rec64, sizeof(Rec64) * U * Q));
+        CK(cudaMalloc(&ctx->d_flag, sizeof(int) * 4));
+        CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int) * 4, s));
+        int r2 = launch_trace(A, ctx->dX, U, st ? 1 : 0, G.ncls[0], G.ncls[1], ctx->rec64, ctx->d_flag, s);
+        if (r2) return fail(ctx, r2, "trace launch failed");
+        int nfail = 0;
+        CK(cudaMemcpyAsync(&nfail, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (nfail)
+            return fail(ctx, SLLBM_ERR_DP_NOT_FOUND,
+                        std::to_string(nfail) + " departure records not resolved within the Newton / walk caps");
+        // ---- isothermal wall temperatures per unit
+        double bcT[16];
+        for (int k = 0; k < 16; ++k) bcT[k] = 1.0;
+        bcT[0] = ctx->desc.bc[0].T;
+        bcT[1] = ctx->desc.bc[1].T;
+        double* d_bcT = nullptr;
+        double* d_tw64 = nullptr;
+        unsigned long long* d_cnt = nullptr;
+        CK(cudaMalloc(&d_bcT, sizeof(bcT)));
+        CK(cudaMalloc(&d_tw64, sizeof(double) * U));
+        CK(cudaMalloc(&d_cnt, sizeof(unsigned long long) * 2));
+        CK(cudaMemcpyAsync(d_bcT, bcT, sizeof(bcT), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * 2, s));
+        r2 = launch_isothermal(ctx->rec64, U, Q, d_bcT, d_tw64, d_cnt, s);
+        if (r2) return fail(ctx, r2, "isothermal launch failed");
+        std::vector<double> tw(U);
+        unsigned long long cnt[2];
+        CK(cudaMemcpyAsync(tw.data(), d_tw64, sizeof(double) * U, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        cudaFree(d_bcT);
+        cudaFree(d_tw64);
+        cudaFree(d_cnt);
+        ctx->n_boundary_records = int64_t(cnt[0]);
+        ctx->n_isothermal_nodes = int64_t(cnt[1]);
+        if (st) {   // isothermal count per node = per class x class multiplicity
+            int64_t mult = 1;
+            for (int d = 0; d < D; ++d)
+                if (m.periodic[d]) mult *= m.N[d] / m.p;
+            ctx->n_boundary_records *= mult;
+            ctx->n_isothermal_nodes *= mult;
+        }
+        const size_t rs = real_size(ctx);
+        CK(cudaMalloc(&ctx->tw_tab, rs * U));
+        if (rs == 8) {
+            CK(cudaMemcpyAsync(ctx->tw_tab, tw.data(), 8 * U, cudaMemcpyHostToDevice, s));
+        } else {
+            std::vector<float> tw32(U);
+            for (int64_t u = 0; u < U; ++u) tw32[u] = float(tw[u]);
+            CK(cudaMemcpyAsync(ctx->tw_tab, tw32.data(), 4 * U, cudaMemcpyHostToDevice, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        // ---- step tables
+        if (st) {
+            std::vector<Rec64> rec(size_t(U * Q));
+            CK(cudaMemcpyAsync(rec.data(), ctx->rec64, sizeof(Rec64) * U * Q, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (rs == 8) {
+                std::vector<ClassRec<double>> t;
+                build_class_table(ctx, rec, t);
+                CK(cudaMalloc(&ctx->cls_tab, sizeof(ClassRec<double>) * t.size()));
+                CK(cudaMemcpyAsync(ctx->cls_tab, t.data(), sizeof(ClassRec<double>) * t.size(),
+                                   cudaMemcpyHostToDevice, s));
+                ctx->table_bytes = int64_t(sizeof(ClassRec<double>) * t.size());
+                CK(cudaStreamSynchronize(s));
+            } else {
+                std::vector<ClassRec<float>> t;
+                build_class_table(ctx, rec, t);
+                CK(cudaMalloc(&ctx->cls_tab, sizeof(ClassRec<float>) * t.size()));
+                CK(cudaMemcpyAsync(ctx->cls_tab, t.data(), sizeof(ClassRec<float>) * t.size(),
+                                   cudaMemcpyHostToDevice, s));
+                ctx->table_bytes = int64_t(sizeof(ClassRec<float>) * t.size());
+                CK(cudaStreamSynchronize(s));
+            }
+        } else {
+            CK(cudaMalloc(&ctx->g_code, sizeof(int32_t) * N * Q));
+            CK(cudaMalloc(&ctx->g_xi, rs * N * Q * D));
+            ctx->table_bytes = int64_t((4 + rs * D) * N * Q);
+            r2 = rs == 8 ? launch_pack_gather<double>(ctx->rec64, N, Q, D, ctx->g_code, (double*)ctx->g_xi, s)
+                         : launch_pack_gather<float>(ctx->rec64, N, Q, D, ctx->g_code, (float*)ctx->g_xi, s);
+            if (r2) return fail(ctx, r2, "pack launch failed");
+        }
+        // ---- state buffers
+        for (int b = 0; b < 2; ++b) {
+            CK(cudaMalloc(&ctx->f[b], rs * N * Q));
+            CK(cudaMalloc(&ctx->g[b], rs * N * Q));
+        }
+        CK(cudaMalloc(&ctx->d_red, sizeof(double) * (conserve_blocks() * 5 + 8)));
+        CK(cudaStreamSynchronize(s));
+        return SLLBM_OK;
+    }();
+    if (rc) return bail(rc);
+    *out = ctx;
+    return SLLBM_OK;
+}
+
+int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
+    if (!ctx || !o) return SLLBM_ERR_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->n_nodes = ctx->mesh.n_nodes;
+    o->Q = ctx->vs.Q;
+    o->dim = ctx->mesh.D;
+    o->p = ctx->mesh.p;
+    for (int d = 0; d < 3; ++d) {
+        o->nodes[d] = ctx->mesh.N[d];
+        o->cells[d] = ctx->mesh.cells[d];
+    }
+    o->precision = ctx->precision;
+    o->stream_mode = ctx->mode;
+    o->state_bytes = int64_t(2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q);
+    o->table_bytes = ctx->table_bytes;
+    o->n_records = int64_t(ctx->mesh.n_nodes) * ctx->vs.Q;
+    o->n_boundary_records = ctx->n_boundary_records;
+    o->n_isothermal_nodes = ctx->n_isothermal_nodes;
+    return SLLBM_OK;
+}
+
+int sllbm_node_coords(sllbm_ctx* ctx, double* x, int32_t on_device) {
+    if (!ctx || !x) return SLLBM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    const size_t bytes = sizeof(double) * ctx->mesh.n_nodes * ctx->mesh.D;
+    CK(cudaMemcpyAsync(x, ctx->dX, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SLLBM_OK;
+}
+
+int sllbm_velocity_set(const sllbm_ctx* ctx, double* xi, double* w, int32_t* opp) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    const int Q = ctx->vs.Q, D = ctx->vs.D;
+    if (xi) std::memcpy(xi, ctx->vs.xi.data(), sizeof(double) * Q * D);
+    if (w) std::memcpy(w, ctx->vs.w.data(), sizeof(double) * Q);
+    if (opp)
+        for (int i = 0; i < Q; ++i) opp[i] = ctx->vs.opp[i];
+    return SLLBM_OK;
+}
+
+int sllbm_init_state(sllbm_ctx* ctx, const double* rho, const double* u, const double* T, int32_t on_device) {
+    if (!ctx || !rho || !u || !T) return SLLBM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    const int64_t N = ctx->mesh.n_nodes;
+    const int D = ctx->mesh.D;
+    cudaStream_t s = ctx->stream;
+    const double *dr = rho, *du = u, *dT = T;
+    double* tmp = nullptr;
+    if (!on_device) {
+        CK(cudaMalloc(&tmp, sizeof(double) * N * (D + 2)));
+        CK(cudaMemcpyAsync(tmp, rho, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(tmp + N, u, sizeof(double) * N * D, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(tmp + N * (D + 1), T, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+        dr = tmp;
+        du = tmp + N;
+        dT = tmp + N * (D + 1);
+    }
+    int rc = ctx->precision == SLLBM_FP64
+                 ? launch_init<double>(ctx->velset, dr, du, dT, N, ctx->cc64, (double*)ctx->f[0], (double*)ctx->g[0], s)
+                 : launch_init<float>(ctx->velset, dr, du, dT, N, ctx->cc64, (float*)ctx->f[0], (float*)ctx->g[0], s);
+    if (tmp) {
+        CK(cudaStreamSynchronize(s));
+        cudaFree(tmp);
+    }
+    if (rc) return fail(ctx, rc, "init launch failed");
+    ctx->cur = 0;
+    ctx->steps = 0;
+    ctx->initialised = true;
+    return SLLBM_OK;
+}
+
+namespace {
+int state_io(sllbm_ctx* ctx, double* f, double* g, const double* cf, const double* cg, int32_t on_device, int dir) {
+    cudaSetDevice(ctx->device);
+    const int64_t N = ctx->mesh.n_nodes;
+    const int Q = ctx->vs.Q;
+    cudaStream_t s = ctx->stream;
+    const size_t bytes = sizeof(double) * N * Q;
+    double* buf = nullptr;
+    CK(cudaMalloc(&buf, 2 * bytes + sizeof(double) * 2 * Q));
+    double* dw = buf + 2 * N * Q;
+    std::vector<double> wv(2 * Q);
+    const double gf = 2.0 / (ctx->params.gamma - 1.0) - ctx->mesh.D;
+    for (int i = 0; i < Q; ++i) {
+        wv[i] = ctx->vs.w[i];
+        wv[Q + i] = ctx->vs.w[i] * gf;
+    }
+    CK(cudaMemcpyAsync(dw, wv.data(), sizeof(double) * 2 * Q, cudaMemcpyHostToDevice, s));
+    const cudaMemcpyKind k_in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind k_out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (dir == 1) {
+        CK(cudaMemcpyAsync(buf, cf, bytes, k_in, s));
+        CK(cudaMemcpyAsync(buf + N * Q, cg, bytes, k_in, s));
+    }
+    const int c = ctx->cur;
+    int rc = ctx->precision == SLLBM_FP64
+                 ? launch_convert<double>((double*)ctx->f[c], (double*)ctx->g[c], buf, buf + N * Q, N, Q, dw, dw + Q,
+                                          dir, s)
+                 : launch_convert<float>((float*)ctx->f[c], (float*)ctx->g[c], buf, buf + N * Q, N, Q, dw, dw + Q,
+                                         dir, s);
+    if (rc == SLLBM_OK && dir == 0) {
+        if (f) CK(cudaMemcpyAsync(f, buf, bytes, k_out, s));
+        if (g) CK(cudaMemcpyAsync(g, buf + N * Q, bytes, k_out, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    cudaFree(buf);
+    return rc ? fail(ctx, rc, "convert launch failed") : SLLBM_OK;
+}
+}  // namespace
+
+int sllbm_get_state(sllbm_ctx* ctx, double* f, double* g, int32_t on_device) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    return state_io(ctx, f, g, nullptr, nullptr, on_device, 0);
+}
+
+int sllbm_set_state(sllbm_ctx* ctx, const double* f, const double* g, int32_t on_device) {
+    if (!ctx || !f || !g) return SLLBM_ERR_ARG;
+    ctx->cur = 0;
+    int rc = state_io(ctx, nullptr, nullptr, f, g, on_device, 1);
+    if (rc) return rc;
+    ctx->steps = 0;
+    ctx->initialised = true;
+    return SLLBM_OK;
+}
+
+int sllbm_get_state_raw(sllbm_ctx* ctx, void* f, void* g, int32_t on_device) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    cudaSetDevice(ctx->device);
+    const size_t bytes = real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (f) CK(cudaMemcpyAsync(f, ctx->f[ctx->cur], bytes, k, ctx->stream));
+    if (g) CK(cudaMemcpyAsync(g, ctx->g[ctx->cur], bytes, k, ctx->stream));
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+    return SLLBM_OK;
+}
+
+int sllbm_set_state_raw(sllbm_ctx* ctx, const void* f, const void* g, int32_t on_device) {
+    if (!ctx || !f || !g) return SLLBM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    const size_t bytes = real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    ctx->cur = 0;
+    CK(cudaMemcpyAsync(ctx->f[0], f, bytes, k, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->g[0], g, bytes, k, ctx->stream));
+    ctx->steps = 0;
+    ctx->initialised = true;
+    return SLLBM_OK;
+}
+
+int sllbm_step(sllbm_ctx* ctx, int64_t n) {
+    if (!ctx || n < 0) return SLLBM_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    cudaSetDevice(ctx->device);
+    for (int64_t k = 0; k < n; ++k) {
+        const int a = ctx->cur, b = 1 - a;
+        int rc;
+        if (ctx->precision == SLLBM_FP64) {
+            StepLaunch<double> L{(const double*)ctx->f[a], (const double*)ctx->g[a], (double*)ctx->f[b],
+                                 (double*)ctx->g[b], (const ClassRec<double>*)ctx->cls_tab, ctx->g_code,
+                                 (const double*)ctx->g_xi, (const double*)ctx->tw_tab, ctx->geom, &ctx->cc64,
+                                 ctx->stream};
+            rc = dispatch_step<double>(ctx, L);
+        } else {
+            StepLaunch<float> L{(const float*)ctx->f[a], (const float*)ctx->g[a], (float*)ctx->f[b],
+                                (float*)ctx->g[b], (const ClassRec<float>*)ctx->cls_tab, ctx->g_code,
+                                (const float*)ctx->g_xi, (const float*)ctx->tw_tab, ctx->geom, &ctx->cc32,
+                                ctx->stream};
+            rc = dispatch_step<float>(ctx, L);
+        }
+        if (rc) return rc == SLLBM_ERR_CUDA ? fail(ctx, rc, "step launch failed") : rc;
+        ctx->cur = b;
+        ++ctx->steps;
+    }
+    return SLLBM_OK;
+}
+
+int sllbm_step_count(const sllbm_ctx* ctx, int64_t* out) {
+    if (!ctx || !out) return SLLBM_ERR_ARG;
+    *out = ctx->steps;
+    return SLLBM_OK;
+}
+
+int sllbm_read_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int32_t on_device) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    cudaSetDevice(ctx->device);
+    const int64_t N = ctx->mesh.n_nodes;
+    const int D = ctx->mesh.D;
+    cudaStream_t s = ctx->stream;
+    double *dr = rho, *du = u, *dT = T, *tmp = nullptr;
+    if (!on_device) {
+        CK(cudaMalloc(&tmp, sizeof(double) * N * (D + 2)));
+        dr = rho ? tmp : nullptr;
+        du = u ? tmp + N : nullptr;
+        dT = T ? tmp + N * (D + 1) : nullptr;
+    }
+    const int c = ctx->cur;
+    int rc = ctx->precision == SLLBM_FP64
+                 ? launch_moments<double>(ctx->velset, (double*)ctx->f[c], (double*)ctx->g[c], N, ctx->cc64, dr, du,
+                                          dT, s)
+                 : launch_moments<float>(ctx->velset, (float*)ctx->f[c], (float*)ctx->g[c], N, ctx->cc64, dr, du, dT,
+                                         s);
+    if (rc) return fail(ctx, rc, "moments launch failed");
+    if (!on_device) {
+        if (rho) CK(cudaMemcpyAsync(rho, dr, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+        if (u) CK(cudaMemcpyAsync(u, du, sizeof(double) * N * D, cudaMemcpyDeviceToHost, s));
+        if (T) CK(cudaMemcpyAsync(T, dT, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        cudaFree(tmp);
+    }
+    return SLLBM_OK;
+}
+
+int sllbm_conservation(sllbm_ctx* ctx, double* out) {
+    if (!ctx || !out) return SLLBM_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    cudaSetDevice(ctx->device);
+    const int64_t N = ctx->mesh.n_nodes;
+    const int D = ctx->mesh.D;
+    cudaStream_t s = ctx->stream;
+    double* part = ctx->d_red;
+    double* dout = ctx->d_red + conserve_blocks() * 5;
+    CK(cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s));
+    const int c = ctx->cur;
+    int rc = ctx->precision == SLLBM_FP64
+                 ? launch_conserve<double>(ctx->velset, D, (double*)ctx->f[c], (double*)ctx->g[c], N, ctx->cc64, part,
+                                           ctx->d_flag + 1, dout, s)
+                 : launch_conserve<float>(ctx->velset, D, (float*)ctx->f[c], (float*)ctx->g[c], N, ctx->cc64, part,
+                                          ctx->d_flag + 1, dout, s);
+    if (rc) return fail(ctx, rc, "conservation launch failed");
+    int flag = 0;
+    CK(cudaMemcpyAsync(out, dout, sizeof(double) * (D + 2), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&flag, ctx->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (flag) return fail(ctx, SLLBM_ERR_UNSTABLE, "non-positive density or temperature, or non-finite state");
+    return SLLBM_OK;
+}
+
+int sllbm_departure_records(sllbm_ctx* ctx, int32_t* kind, int32_t* src, int32_t* bid, int32_t* cell, double* xi,
+                            double* xsrc) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    const HostMesh& m = ctx->mesh;
+    const int Q = ctx->vs.Q, D = m.D;
+    const int64_t N = m.n_nodes, U = ctx->n_rec_units;
+    std::vector<Rec64> rec(size_t(U * Q));
+    CK(cudaMemcpyAsync(rec.data(), ctx->rec64, sizeof(Rec64) * U * Q, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const bool st = ctx->mode == SLLBM_STREAM_STRUCTURED;
+    for (int i = 0; i < Q; ++i)
+        for (int64_t n = 0; n < N; ++n) {
+            int k[3] = {0, 0, 0};
+            int64_t r = n;
+            for (int d = 0; d < D; ++d) {
+                k[d] = int(r % m.N[d]);
+                r /= m.N[d];
+            }
+            int64_t u = n;
+            if (st) {
+                const StepGeom& G = ctx->geom;
+                int cl[3] = {0, 0, 0};
+                for (int d = 0; d < D; ++d) cl[d] = m.periodic[d] ? k[d] % m.p : k[d];
+                u = cl[0] + int64_t(G.ncls[0]) * (cl[1] + int64_t(G.ncls[1]) * cl[2]);
+            }
+            const Rec64& R = rec[size_t(i * U + u)];
+            const int64_t o = i * N + n;
+            const int kd = R.meta & 15;
+            const int b = (R.meta >> 4) & 15;
+            if (kind) kind[o] = kd;
+            if (src) src[o] = (R.meta >> 8) & 255;
+            if (bid) bid[o] = b == 15 ? -1 : b;
+            int cc[3] = {0, 0, 0};
+            if (R.cell >= 0) {
+                int64_t cl = R.cell;
+                for (int d = 0; d < D; ++d) {
+                    cc[d] = int(cl % m.cells[d]);
+                    cl /= m.cells[d];
+                }
+                if (st)
+                    for (int d = 0; d < D; ++d)
+                        if (m.periodic[d]) {
+                            const int home = k[d] / m.p;
+                            cc[d] = ((cc[d] + home) % m.cells[d] + m.cells[d]) % m.cells[d];
+                        }
+            }
+            int64_t lin = -1;
+            if (R.cell >= 0) lin = cc[0] + int64_t(m.cells[0]) * (cc[1] + int64_t(m.cells[1]) * cc[2]);
+            if (cell) cell[o] = int32_t(lin);
+            for (int d = 0; d < D; ++d) {
+                if (xi) xi[o * D + d] = R.xi[d];
+                if (xsrc) {
+                    if (!st || R.cell < 0) {
+                        xsrc[o * D + d] = R.xsrc[d];
+                    } else {
+                        const auto& V = m.V[d];
+                        xsrc[o * D + d] = V[cc[d]] + 0.5 * (R.xi[d] + 1.0) * (V[cc[d] + 1] - V[cc[d]]);
+                    }
+                }
+            }
+        }
+    return SLLBM_OK;
+}
+
+int sllbm_sync(sllbm_ctx* ctx) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SLLBM_OK;
+}
+
+void* sllbm_stream(const sllbm_ctx* ctx) { return ctx ? static_cast<void*>(ctx->stream) : nullptr; }
+
+}  // extern "C"

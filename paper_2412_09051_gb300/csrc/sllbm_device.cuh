@@ -1,0 +1,251 @@
+// Device-side building blocks of the fused SLLBM step.
+//
+// Equilibrium (Sec. 3.1, order-4 Hermite expansion, Shan et al. 2006 form):
+// with c = xi_i . u, s = |xi_i|^2, U = |u|^2, t = T - 1 (T0 = 1) the
+// contraction sum_n a^(n) : H^(n)_i / n! collapses to the scalar polynomial
+//   P_i = 1 + c + c^2/2 + c^3/6 + c^4/24
+//           + c^2 (-U/4 + t C/4) + c (-U/2 + t B/2)
+//           + (-U/2 + U^2/8 + t A/2 - t U B/4 + t^2 E/8)
+// where A = s - D, B = s - D - 2, C = s - D - 4, E = s^2 - 2(D+2)s + D(D+2)
+// depend only on the velocity shell.  f_i^eq = w_i rho P_i and
+// g_i^eq = T (2 c_v - D) f_i^eq.  Populations are carried as deviations
+// from the reference values w_i (f) and w_i (2 c_v - D) (g).
+#pragma once
+#include <cmath>
+#include <cstdint>
+#include <type_traits>
+
+#define SLLBM_QMAX 45
+#define SLLBM_SMAX 6
+
+namespace sllbm {
+
+// ------------------------------------------------------------ velocity sets
+// Compile-time structure (Q, D, shell of each index); numeric values arrive
+// at run time in CollideConst.
+template <int VS> struct VelSet;
+
+template <> struct VelSet<0> {   // D2Q9
+    static constexpr int Q = 9, D = 2, NS = 3;
+    __host__ __device__ static constexpr int shell(int i) {
+        return i == 0 ? 0 : ((i == 1 || i == 2 || i == 5 || i == 6) ? 1 : 2);
+    }
+};
+template <> struct VelSet<1> {   // D2Q19
+    static constexpr int Q = 19, D = 2, NS = 4;
+    __host__ __device__ static constexpr int shell(int i) { return i == 0 ? 0 : 1 + (i - 1) / 6; }
+};
+template <> struct VelSet<2> {   // D2Q25
+    static constexpr int Q = 25, D = 2, NS = 6;
+    __host__ __device__ static constexpr int cls(int a) { return a == 0 ? 0 : ((a == 1 || a == 3) ? 1 : 2); }
+    __host__ __device__ static constexpr int shell(int i) {
+        // unordered pair of 1D node classes -> 0..5
+        return (cls(i % 5) <= cls(i / 5))
+                   ? (cls(i % 5) == 0 ? cls(i / 5) : (cls(i % 5) == 1 ? 2 + cls(i / 5) : 5))
+                   : (cls(i / 5) == 0 ? cls(i % 5) : (cls(i / 5) == 1 ? 2 + cls(i % 5) : 5));
+    }
+};
+template <> struct VelSet<3> {   // D3Q45
+    static constexpr int Q = 45, D = 3, NS = 4;
+    __host__ __device__ static constexpr int shell(int i) {
+        return i == 0 ? 0 : (i <= 12 ? 1 : (i <= 32 ? 2 : 3));
+    }
+};
+
+// ------------------------------------------------------------ constants
+template <typename real>
+struct CollideConst {
+    real xi[SLLBM_QMAX][3];
+    real w[SLLBM_QMAX];
+    real wg[SLLBM_QMAX];          // w_i (2 c_v - D)
+    real sA[SLLBM_SMAX], sB[SLLBM_SMAX], sC[SLLBM_SMAX], sE[SLLBM_SMAX], s2[SLLBM_SMAX];
+    real cv, gfac;                // c_v and (2 c_v - D)
+    real dt, inv_Pr;
+    real mu_ref, inv_T_ref, mu_exp;
+    int  var_mu;                  // mu_exp != 0
+    int  quasi;                   // Pr != 1
+    // boundary constants per boundary id: equilibrium deviations and moving-wall term
+    real eqf[2][SLLBM_QMAX];
+    real eqg[2][SLLBM_QMAX];
+    real mw[2][SLLBM_QMAX];
+    int opp[SLLBM_QMAX];
+};
+
+// ------------------------------------------------------------ compensated sum
+template <typename real>
+struct Acc {
+    real s, c;
+    __device__ __forceinline__ Acc() : s(0), c(0) {}
+    __device__ __forceinline__ void add(real x) { s += x; }
+    __device__ __forceinline__ real get() const { return s; }
+};
+template <>
+struct Acc<float> {   // Kahan summation (no fast-math: the compensation survives)
+    float s, c;
+    __device__ __forceinline__ Acc() : s(0.f), c(0.f) {}
+    __device__ __forceinline__ void add(float x) {
+        float y = __fsub_rn(x, c);
+        float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ float get() const { return s; }
+};
+
+// ------------------------------------------------------------ equilibrium
+// Shell coefficients of P_i - 1 = ((c/24 + 1/6) c + k2) c^2 ... evaluated as
+// P1 = (((c * (1/24) + 1/6) * c + k2) * c + k1) * c + k0.
+template <typename real, int NS>
+struct EqCoef {
+    real k0[NS], k1[NS], k2[NS];
+    __device__ __forceinline__ void build(const CollideConst<real>& C, real U, real t) {
+        const real tU = t * U;
+        const real t2 = t * t;
+#pragma unroll
+        for (int h = 0; h < NS; ++h) {
+            k2[h] = real(0.5) - real(0.25) * U + real(0.25) * t * C.sC[h];
+            k1[h] = real(1.0) - real(0.5) * U + real(0.5) * t * C.sB[h];
+            k0[h] = -real(0.5) * U + real(0.125) * U * U + real(0.5) * t * C.sA[h]
+                    - real(0.25) * tU * C.sB[h] + real(0.125) * t2 * C.sE[h];
+        }
+    }
+};
+
+template <typename real>
+__device__ __forceinline__ real eq_poly1(real c, real k0, real k1, real k2) {
+    return (((c * real(1.0 / 24.0) + real(1.0 / 6.0)) * c + k2) * c + k1) * c + k0;
+}
+
+// f^eq and g^eq deviations of one velocity for the node state (rho, u, T):
+//   fdev = w (rho P1 + (rho - 1)),  gdev = wg (rho T P1 + (rho T - 1))
+template <class VSET, typename real, int I>
+__device__ __forceinline__ void eq_dev(const CollideConst<real>& C, const EqCoef<real, VSET::NS>& K,
+                                       const real (&u)[3], real rho, real rho_d, real rhoT, real rhoT_d,
+                                       real& fdev, real& gdev, real& cdot) {
+    constexpr int h = VSET::shell(I);
+    real c = C.xi[I][0] * u[0] + C.xi[I][1] * u[1];
+    if (VSET::D == 3) c += C.xi[I][2] * u[2];
+    const real P1 = eq_poly1(c, K.k0[h], K.k1[h], K.k2[h]);
+    fdev = C.w[I] * (rho * P1 + rho_d);
+    gdev = C.wg[I] * (rhoT * P1 + rhoT_d);
+    cdot = c;
+}
+
+template <int I, int N>
+struct Unroll {
+    template <class F>
+    __device__ __forceinline__ static void run(F&& f) {
+        f(std::integral_constant<int, I>());
+        Unroll<I + 1, N>::run(f);
+    }
+};
+template <int N>
+struct Unroll<N, N> {
+    template <class F>
+    __device__ __forceinline__ static void run(F&&) {}
+};
+
+// ------------------------------------------------------------ collide
+// In: streamed deviations f[Q], g[Q]; Tw = wall temperature of the node's
+// isothermal correction (Eq. thermalBC) or NaN.  Out: post-collision
+// deviations (Eq. 1).  Returns the node density (for diagnostics).
+template <class VSET, typename real>
+__device__ __forceinline__ void collide_node(const CollideConst<real>& C, real (&f)[VSET::Q],
+                                             real (&g)[VSET::Q], real Tw) {
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    // ---- moments (compensated in FP32)
+    Acc<real> arho, aj0, aj1, aj2, ae;
+    Unroll<0, Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        arho.add(f[i]);
+        aj0.add(C.xi[i][0] * f[i]);
+        aj1.add(C.xi[i][1] * f[i]);
+        if (D == 3) aj2.add(C.xi[i][2] * f[i]);
+        ae.add(C.s2[VSET::shell(i)] * f[i]);
+        ae.add(g[i]);
+    });
+    const real rho_d = arho.get();
+    const real rho = real(1) + rho_d;
+    const real inv_rho = real(1) / rho;
+    real u[3] = {aj0.get() * inv_rho, aj1.get() * inv_rho, D == 3 ? aj2.get() * inv_rho : real(0)};
+    const real U = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    // 2 rho c_v T = e + 2 c_v - rho U  ->  t = T - 1 = (e - rho U - 2 c_v rho_d) / (2 rho c_v)
+    real t = (ae.get() - rho * U - real(2) * C.cv * rho_d) * inv_rho / (real(2) * C.cv);
+
+    // ---- isothermal wall correction (Eq. thermalBC): f += f^eq(T_w) - f^eq(T)
+    if (!(Tw != Tw)) {
+        const real tw = Tw - real(1);
+        EqCoef<real, VSET::NS> K0, K1;
+        K0.build(C, U, t);
+        K1.build(C, U, tw);
+        const real rhoT0 = rho * (real(1) + t), rhoT1 = rho * (real(1) + tw);
+        Unroll<0, Q>::run([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            real f0, g0, f1, g1, cd;
+            eq_dev<VSET, real, i>(C, K0, u, rho, rho_d, rhoT0, rhoT0 - real(1), f0, g0, cd);
+            eq_dev<VSET, real, i>(C, K1, u, rho, rho_d, rhoT1, rhoT1 - real(1), f1, g1, cd);
+            f[i] += f1 - f0;
+            g[i] += g1 - g0;
+        });
+        t = tw;
+    }
+    const real T = real(1) + t;
+    // ---- relaxation times (tau = mu / (p dt) + 1/2, tau_Pr = (tau - 1/2)/Pr + 1/2)
+    real mu = C.mu_ref;
+    if (C.var_mu) mu *= pow(T * C.inv_T_ref, C.mu_exp);
+    const real tau = mu / (rho * T * C.dt) + real(0.5);
+    const real om = real(1) / tau;
+    const real om_pr = real(1) / ((tau - real(0.5)) * C.inv_Pr + real(0.5));
+
+    EqCoef<real, VSET::NS> K;
+    K.build(C, U, t);
+    const real rhoT = rho * T;
+    const real rhoT_d = rho_d + rho * t;
+    real q0 = 0, q1 = 0, q2 = 0;
+    Unroll<0, Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        real fe, ge, cd;
+        eq_dev<VSET, real, i>(C, K, u, rho, rho_d, rhoT, rhoT_d, fe, ge, cd);
+        const real fn = f[i] - fe;
+        const real gn = g[i] - ge;
+        // central heat flux (times 2): sum (xi - u) (|xi - u|^2 f^neq + g^neq)
+        const real cu2 = C.s2[VSET::shell(i)] - real(2) * cd + U;
+        const real h = cu2 * fn + gn;
+        q0 += (C.xi[i][0] - u[0]) * h;
+        q1 += (C.xi[i][1] - u[1]) * h;
+        if (D == 3) q2 += (C.xi[i][2] - u[2]) * h;
+        f[i] -= om * fn;
+        g[i] -= om * gn;
+    });
+    if (C.quasi) {
+        // g*_i = w_i xi_i . (2 q^neq), weighted by (1/tau - 1/tau_Pr)
+        const real a = om - om_pr;
+        q0 *= a;
+        q1 *= a;
+        q2 *= a;
+        Unroll<0, Q>::run([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            real d = C.xi[i][0] * q0 + C.xi[i][1] * q1;
+            if (D == 3) d += C.xi[i][2] * q2;
+            g[i] += C.w[i] * d;
+        });
+    }
+}
+
+// ------------------------------------------------------------ Lagrange basis
+// 1D Lagrange polynomials of order P on the GLC nodes at x (nodes / inverse
+// denominators supplied by the caller).
+template <int P, typename real>
+__device__ __forceinline__ void lagrange_w(real x, const real* xh, const real* inv_den, real (&L)[P + 1]) {
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+        real v = inv_den[a];
+#pragma unroll
+        for (int m = 0; m <= P; ++m)
+            if (m != a) v *= (x - xh[m]);
+        L[a] = v;
+    }
+}
+
+}  // namespace sllbm

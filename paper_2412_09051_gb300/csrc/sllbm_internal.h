@@ -1,0 +1,124 @@
+// Internal structures of the SLLBM library (host side + kernel argument blocks).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sllbm.h"
+#include "sllbm_device.cuh"
+
+namespace sllbm {
+
+// record kinds (departure records)
+enum { REC_INTERIOR = 0, REC_EQ = 1, REC_BB = 2, REC_BB_ISO = 3, REC_OUTLET = 4 };
+
+// ------------------------------------------------------------ host geometry
+struct HostVelSet {
+    int Q = 0, D = 0;
+    std::vector<double> xi;   // Q*D
+    std::vector<double> w;    // Q
+    std::vector<int> opp;     // Q
+    std::vector<double> shell_s;   // |xi|^2 per shell (compile-time shell map)
+};
+int build_velocity_set(int kind, HostVelSet& vs, std::string& err);
+
+struct HostMesh {
+    int kind = 0, D = 0, p = 0;
+    int cells[3] = {1, 1, 1};
+    int N[3] = {1, 1, 1};
+    int periodic[3] = {1, 1, 1};
+    double length[3] = {1, 1, 1};
+    double stretch = 1.0, thickness = 0.12;
+    int central = 0;
+    int64_t n_nodes = 0, n_cells = 0;
+    std::vector<double> V[3];     // cell vertices per dimension (axis-aligned kinds)
+    std::vector<double> X;        // node coordinates [N][D]
+    std::vector<double> glc;      // p+1 reference nodes
+};
+int build_mesh(const sllbm_mesh_desc& d, HostMesh& m, std::string& err);
+
+// ------------------------------------------------------------ device mesh view
+struct MeshView {
+    int kind, D, p;
+    int cells[3], N[3], periodic[3];
+    double length[3];
+    const double* V[3];       // device vertex arrays (axis-aligned kinds)
+    const double* X;          // device node coordinates (curved kinds)
+    double glc[5], glc_inv_den[5];
+    int bc_kind[2];
+    double R;                 // NACA far-field radius
+};
+
+struct TraceArgs {            // setup kernel arguments
+    MeshView M;
+    double xi[SLLBM_QMAX][3];
+    int opp[SLLBM_QMAX];
+    int Q;
+    double dt;
+    int max_newton, max_walk;
+};
+
+// FP64 departure record (setup output), one per (velocity, node) or (velocity, class)
+struct Rec64 {
+    int32_t cell;             // linear cell, -1 for equilibrium records
+    int32_t meta;             // kind | bid << 4 (bid 15 = none) | src << 8
+    double xi[3];
+    double xsrc[3];
+};
+
+template <typename real>
+struct ClassRec {             // structured-mode record (per velocity and class)
+    int32_t cell[3];          // periodic dims: offset from the home cell; else absolute
+    int32_t meta;             // kind | bid << 4 | src << 8
+    real wt[3][4];            // 1D Lagrange weights per dimension
+};
+
+struct StepGeom {             // structured / gather kernel geometry
+    int N[3], cells[3], periodic[3];
+    int ncls[3];              // classes per dimension (p if periodic, else N)
+    int64_t n_nodes;
+    int n_classes;
+};
+
+}  // namespace sllbm
+
+struct sllbm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string last_error;
+    sllbm_mesh_desc desc{};
+    sllbm_params params{};
+    int velset = 0;
+    sllbm::HostVelSet vs;
+    sllbm::HostMesh mesh;
+    int mode = SLLBM_STREAM_GATHER;      // resolved
+    int precision = SLLBM_FP32;
+    // device geometry
+    double* dV[3] = {nullptr, nullptr, nullptr};
+    double* dX = nullptr;
+    // FP64 setup records
+    sllbm::Rec64* rec64 = nullptr;       // [Q][n_rec_units]
+    int64_t n_rec_units = 0;             // nodes (gather) or classes (structured)
+    // step tables
+    void* cls_tab = nullptr;             // ClassRec<real>[Q][n_classes]
+    int32_t* g_code = nullptr;           // gather: [Q][N] cell | kind<<24 | bid<<28
+    void* g_xi = nullptr;                // gather: real [Q][D][N]
+    void* tw_tab = nullptr;              // real: per class (structured) or node (gather); NaN none
+    int64_t table_bytes = 0;
+    int64_t n_boundary_records = 0, n_isothermal_nodes = 0;
+    // state
+    void* f[2] = {nullptr, nullptr};
+    void* g[2] = {nullptr, nullptr};
+    int cur = 0;
+    bool initialised = false;
+    int64_t steps = 0;
+    // scratch
+    double* d_red = nullptr;             // reduction partials
+    int* d_flag = nullptr;
+    sllbm::StepGeom geom{};
+    sllbm::CollideConst<float> cc32{};
+    sllbm::CollideConst<double> cc64{};
+};

@@ -1,0 +1,8 @@
+// FP32 instantiations of the fused step kernels.
+#include "step_kernels.cuh"
+namespace sllbm {
+SLLBM_INSTANTIATE_STEP(0, 2, float)
+SLLBM_INSTANTIATE_STEP(1, 2, float)
+SLLBM_INSTANTIATE_STEP(1, 3, float)
+SLLBM_INSTANTIATE_STEP(2, 2, float)
+}  // namespace sllbm

@@ -1,0 +1,5 @@
+// FP32 instantiations of the fused step kernels, 3D velocity set.
+#include "step_kernels.cuh"
+namespace sllbm {
+SLLBM_INSTANTIATE_STEP(3, 2, float)
+}  // namespace sllbm

@@ -1,0 +1,200 @@
+// Initialisation, state conversion, moment readout and FP64 conservation sums.
+#include "sllbm_internal.h"
+
+namespace sllbm {
+
+// equilibrium deviations (Sec. 3.1) of node fields, in FP64, stored as real
+template <int VS, typename real>
+__global__ void k_init(const double* __restrict__ rho, const double* __restrict__ u, const double* __restrict__ T,
+                       int64_t N, const CollideConst<double> C, real* __restrict__ f, real* __restrict__ g) {
+    using VSET = VelSet<VS>;
+    constexpr int D = VSET::D;
+    const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double r = rho[n];
+    double uu[3] = {u[n * D + 0], u[n * D + 1], D == 3 ? u[n * D + 2] : 0.0};
+    const double U = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+    const double t = T[n] - 1.0;
+    EqCoef<double, VSET::NS> K;
+    K.build(C, U, t);
+    const double rT = r * (1.0 + t);
+    Unroll<0, VSET::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        double fe, ge, cd;
+        eq_dev<VSET, double, i>(C, K, uu, r, r - 1.0, rT, rT - 1.0, fe, ge, cd);
+        f[int64_t(i) * N + n] = real(fe);
+        g[int64_t(i) * N + n] = real(ge);
+    });
+}
+
+// full <-> deviation conversion; dir = 0: dev -> full, 1: full -> dev
+template <typename real>
+__global__ void k_convert(real* __restrict__ fd, real* __restrict__ gd, double* __restrict__ ff,
+                          double* __restrict__ gf, int64_t N, int Q, const double* __restrict__ w,
+                          const double* __restrict__ wg, int dir) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= N * Q) return;
+    const int i = int(t / N);
+    if (dir == 0) {
+        ff[t] = double(fd[t]) + w[i];
+        gf[t] = double(gd[t]) + wg[i];
+    } else {
+        fd[t] = real(ff[t] - w[i]);
+        gd[t] = real(gf[t] - wg[i]);
+    }
+}
+
+// per-node moments (Sec. 3.1) in FP64 from the stored deviations
+template <int VS, typename real>
+__device__ __forceinline__ void node_moments(const real* f, const real* g, int64_t N, int64_t n,
+                                             const CollideConst<double>& C, double& rho, double (&j)[3], double& e2) {
+    using VSET = VelSet<VS>;
+    double rd = 0, e = 0;
+    j[0] = j[1] = j[2] = 0;
+    Unroll<0, VSET::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const double fi = double(f[int64_t(i) * N + n]);
+        const double gi = double(g[int64_t(i) * N + n]);
+        rd += fi;
+        j[0] += C.xi[i][0] * fi;
+        j[1] += C.xi[i][1] * fi;
+        if (VSET::D == 3) j[2] += C.xi[i][2] * fi;
+        e += C.s2[VSET::shell(i)] * fi + gi;
+    });
+    rho = 1.0 + rd;
+    e2 = e + 2.0 * C.cv;
+}
+
+template <int VS, typename real>
+__global__ void k_moments(const real* __restrict__ f, const real* __restrict__ g, int64_t N,
+                          const CollideConst<double> C, double* __restrict__ rho, double* __restrict__ u,
+                          double* __restrict__ T) {
+    using VSET = VelSet<VS>;
+    constexpr int D = VSET::D;
+    const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double r, j[3], e2;
+    node_moments<VS, real>(f, g, N, n, C, r, j, e2);
+    double U = 0;
+    for (int d = 0; d < D; ++d) {
+        const double ud = j[d] / r;
+        U += ud * ud;
+        if (u) u[n * D + d] = ud;
+    }
+    if (rho) rho[n] = r;
+    if (T) T[n] = (e2 - r * U) / (2.0 * r * C.cv);
+}
+
+// block partial sums of (rho, rho u, 2 rho E) and a positivity flag
+template <int VS, typename real>
+__global__ void k_conserve(const real* __restrict__ f, const real* __restrict__ g, int64_t N,
+                           const CollideConst<double> C, double* __restrict__ part, int* __restrict__ flag) {
+    using VSET = VelSet<VS>;
+    constexpr int D = VSET::D;
+    constexpr int K = D + 2;
+    __shared__ double sh[K][256];
+    double acc[K];
+    for (int k = 0; k < K; ++k) acc[k] = 0;
+    int bad = 0;
+    for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < N; n += int64_t(gridDim.x) * blockDim.x) {
+        double r, j[3], e2;
+        node_moments<VS, real>(f, g, N, n, C, r, j, e2);
+        acc[0] += r;
+        double U = 0;
+        for (int d = 0; d < D; ++d) {
+            acc[1 + d] += j[d];
+            U += (j[d] / r) * (j[d] / r);
+        }
+        acc[D + 1] += e2;
+        const double T = (e2 - r * U) / (2.0 * r * C.cv);
+        if (!(r > 0.0) || !(T > 0.0) || !isfinite(e2)) bad = 1;
+    }
+    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < K; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < K; ++k) part[blockIdx.x * K + k] = sh[k][0];
+    if (bad) atomicOr(flag, 1);
+}
+
+__global__ void k_reduce_parts(const double* __restrict__ part, int nblk, int K, double* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= K) return;
+    double s = 0;
+    for (int b = 0; b < nblk; ++b) s += part[b * K + k];
+    out[k] = s;
+}
+
+// ------------------------------------------------------------ launchers
+template <typename real>
+int launch_init(int vs, const double* rho, const double* u, const double* T, int64_t N, const CollideConst<double>& C,
+                real* f, real* g, cudaStream_t s) {
+    const int bs = 128;
+    const unsigned grid = unsigned((N + bs - 1) / bs);
+    switch (vs) {
+        case 0: k_init<0, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, f, g); break;
+        case 1: k_init<1, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, f, g); break;
+        case 2: k_init<2, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, f, g); break;
+        case 3: k_init<3, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, f, g); break;
+        default: return SLLBM_ERR_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
+template <typename real>
+int launch_convert(real* fd, real* gd, double* ff, double* gf, int64_t N, int Q, const double* w, const double* wg,
+                   int dir, cudaStream_t s) {
+    const int bs = 256;
+    k_convert<real><<<unsigned((N * Q + bs - 1) / bs), bs, 0, s>>>(fd, gd, ff, gf, N, Q, w, wg, dir);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
+template <typename real>
+int launch_moments(int vs, const real* f, const real* g, int64_t N, const CollideConst<double>& C, double* rho,
+                   double* u, double* T, cudaStream_t s) {
+    const int bs = 128;
+    const unsigned grid = unsigned((N + bs - 1) / bs);
+    switch (vs) {
+        case 0: k_moments<0, real><<<grid, bs, 0, s>>>(f, g, N, C, rho, u, T); break;
+        case 1: k_moments<1, real><<<grid, bs, 0, s>>>(f, g, N, C, rho, u, T); break;
+        case 2: k_moments<2, real><<<grid, bs, 0, s>>>(f, g, N, C, rho, u, T); break;
+        case 3: k_moments<3, real><<<grid, bs, 0, s>>>(f, g, N, C, rho, u, T); break;
+        default: return SLLBM_ERR_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
+int conserve_blocks() { return 152 * 4; }
+
+template <typename real>
+int launch_conserve(int vs, int D, const real* f, const real* g, int64_t N, const CollideConst<double>& C,
+                    double* part, int* flag, double* out, cudaStream_t s) {
+    const int nb = conserve_blocks();
+    switch (vs) {
+        case 0: k_conserve<0, real><<<nb, 256, 0, s>>>(f, g, N, C, part, flag); break;
+        case 1: k_conserve<1, real><<<nb, 256, 0, s>>>(f, g, N, C, part, flag); break;
+        case 2: k_conserve<2, real><<<nb, 256, 0, s>>>(f, g, N, C, part, flag); break;
+        case 3: k_conserve<3, real><<<nb, 256, 0, s>>>(f, g, N, C, part, flag); break;
+        default: return SLLBM_ERR_ARG;
+    }
+    k_reduce_parts<<<1, 32, 0, s>>>(part, nb, D + 2, out);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
+#define INST(real)                                                                                                 \
+    template int launch_init<real>(int, const double*, const double*, const double*, int64_t,                      \
+                                   const CollideConst<double>&, real*, real*, cudaStream_t);                       \
+    template int launch_convert<real>(real*, real*, double*, double*, int64_t, int, const double*, const double*,  \
+                                      int, cudaStream_t);                                                          \
+    template int launch_moments<real>(int, const real*, const real*, int64_t, const CollideConst<double>&, double*, \
+                                      double*, double*, cudaStream_t);                                             \
+    template int launch_conserve<real>(int, int, const real*, const real*, int64_t, const CollideConst<double>&,   \
+                                       double*, int*, double*, cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace sllbm

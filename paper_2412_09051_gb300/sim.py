@@ -1,0 +1,177 @@
+"""Python-side handle on one SLLBM context (argument marshalling only).
+
+Arrays are numpy (host) or torch CUDA tensors (device); torch is used only to
+own device memory and streams.  All arithmetic happens in libsllbm.so.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import capi
+
+
+def _ptr(a):
+    """(pointer, on_device) for a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data_as(C.c_void_p), 0
+    if a is None:
+        return None, 0
+    assert a.is_contiguous()
+    return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+
+
+def mesh_desc(cfg):
+    m = cfg["mesh"]
+    d = capi.MeshDesc()
+    d.kind = m["kind"]
+    d.dim = len(m["cells"])
+    d.p = m["p"]
+    for k, c in enumerate(m["cells"]):
+        d.cells[k] = c
+        d.length[k] = m["length"][k]
+    d.stretch = m.get("stretch", 1.0)
+    d.central = m.get("central", 0)
+    d.thickness = m.get("thickness", 0.12)
+    for b in range(2):
+        bc = cfg["bcs"][b]
+        d.bc[b].kind = bc["kind"]
+        d.bc[b].rho = bc["rho"]
+        for k in range(3):
+            d.bc[b].u[k] = bc["u"][k] if k < len(bc["u"]) else 0.0
+        d.bc[b].T = bc["T"]
+    return d
+
+
+def params(cfg, precision=None, stream_mode=0, device=0, stream=None):
+    p = capi.Params()
+    p.dt = cfg["dt"]
+    p.gamma = cfg["gamma"]
+    p.Pr = cfg["Pr"]
+    p.mu_ref = cfg["mu_ref"]
+    p.T_ref = cfg["T_ref"]
+    p.mu_exp = cfg["mu_exp"]
+    prec = precision or cfg.get("precision", "fp32")
+    p.precision = capi.FP64 if prec == "fp64" else capi.FP32
+    p.stream_mode = stream_mode
+    p.device = device
+    p.stream = stream
+    return p
+
+
+class Sim:
+    """One library context built from a workload config dict."""
+
+    def __init__(self, cfg, precision=None, stream_mode=0, device=0, stream=None):
+        L = capi.lib()
+        self.cfg = cfg
+        self._desc = mesh_desc(cfg)
+        self._par = params(cfg, precision, stream_mode, device, stream)
+        h = C.c_void_p()
+        rc = L.sllbm_create(C.byref(self._desc), capi.VELSET[cfg["velset"]], C.byref(self._par), C.byref(h))
+        if rc != capi.OK:
+            msg = L.sllbm_last_error(None)
+            raise capi.SllbmError(rc, msg.decode() if msg else "")
+        self.h = h
+        info = capi.Info()
+        capi.check(L.sllbm_info(h, C.byref(info)), h)
+        self.info = info
+        self.N = info.n_nodes
+        self.Q = info.Q
+        self.D = info.dim
+        self.fp64 = info.precision == capi.FP64
+
+    def close(self):
+        if getattr(self, "h", None):
+            capi.lib().sllbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, *args):
+        return capi.check(getattr(capi.lib(), name)(self.h, *args), self.h)
+
+    # ---------------------------------------------------------------- queries
+    def node_coords(self):
+        x = np.zeros((self.N, self.D))
+        self._call("sllbm_node_coords", *_ptr(x))
+        return x
+
+    def velocity_set(self):
+        xi = np.zeros((self.Q, self.D))
+        w = np.zeros(self.Q)
+        opp = np.zeros(self.Q, dtype=np.int32)
+        self._call("sllbm_velocity_set", _ptr(xi)[0], _ptr(w)[0], _ptr(opp)[0])
+        return xi, w, opp
+
+    def stream(self):
+        return capi.lib().sllbm_stream(self.h)
+
+    # ---------------------------------------------------------------- state
+    def init_state(self, rho, u, T):
+        rho = np.ascontiguousarray(rho, dtype=np.float64) if isinstance(rho, np.ndarray) else rho
+        u = np.ascontiguousarray(u, dtype=np.float64) if isinstance(u, np.ndarray) else u
+        T = np.ascontiguousarray(T, dtype=np.float64) if isinstance(T, np.ndarray) else T
+        pr, dev = _ptr(rho)
+        self._call("sllbm_init_state", pr, _ptr(u)[0], _ptr(T)[0], dev)
+
+    def get_state(self):
+        f = np.zeros((self.Q, self.N))
+        g = np.zeros((self.Q, self.N))
+        self._call("sllbm_get_state", _ptr(f)[0], _ptr(g)[0], 0)
+        return f, g
+
+    def set_state(self, f, g):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        self._call("sllbm_set_state", _ptr(f)[0], _ptr(g)[0], 0)
+
+    def get_state_raw(self, f=None, g=None):
+        dt = np.float64 if self.fp64 else np.float32
+        if f is None:
+            f = np.zeros((self.Q, self.N), dtype=dt)
+            g = np.zeros((self.Q, self.N), dtype=dt)
+        pf, dev = _ptr(f)
+        self._call("sllbm_get_state_raw", pf, _ptr(g)[0], dev)
+        return f, g
+
+    def set_state_raw(self, f, g):
+        pf, dev = _ptr(f)
+        self._call("sllbm_set_state_raw", pf, _ptr(g)[0], dev)
+
+    def step(self, n=1):
+        self._call("sllbm_step", C.c_int64(n))
+
+    def sync(self):
+        self._call("sllbm_sync")
+
+    # ---------------------------------------------------------------- readout
+    def moments(self):
+        rho = np.zeros(self.N)
+        u = np.zeros((self.N, self.D))
+        T = np.zeros(self.N)
+        self._call("sllbm_read_moments", _ptr(rho)[0], _ptr(u)[0], _ptr(T)[0], 0)
+        return rho, u, T
+
+    def moments_into(self, rho, u, T):
+        pr, dev = _ptr(rho)
+        self._call("sllbm_read_moments", pr, _ptr(u)[0], _ptr(T)[0], dev)
+
+    def conservation(self, check=True):
+        out = np.zeros(self.D + 2)
+        rc = capi.lib().sllbm_conservation(self.h, _ptr(out)[0])
+        if check:
+            capi.check(rc, self.h)
+        return out, rc
+
+    def departure_records(self):
+        Q, N, D = self.Q, self.N, self.D
+        r = dict(kind=np.zeros((Q, N), np.int32), src=np.zeros((Q, N), np.int32),
+                 bid=np.zeros((Q, N), np.int32), cell=np.zeros((Q, N), np.int32),
+                 xi=np.zeros((Q, N, D)), xsrc=np.zeros((Q, N, D)))
+        self._call("sllbm_departure_records", *[_ptr(r[k])[0] for k in ("kind", "src", "bid", "cell", "xi", "xsrc")])
+        return r

@@ -1,0 +1,191 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 setup quantities (node coordinates, departure points, the
+velocity set) 1e-12; FP64 populations 1e-12 relative to each velocity's
+scale; FP32-offset populations 1e-5 relative (same scale), moments 1e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle import step as ost
+from oracle.departure import REC_EQ
+from tests.oracle_cases import box_cfg, oracle_case
+from workloads import get_config, initial_fields
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "tgv2d_fp64": (lambda: get_config("tgv2d", cells=8), "fp64"),
+    "tgv2d_p3_fp64": (lambda: dict(get_config("tgv2d", cells=6), mesh=dict(kind=0, p=3, cells=(6, 5),
+                                                                            length=(6.2831853, 5.0))), "fp64"),
+    "channel_fp32": (lambda: get_config("channel", cells=(4, 6, 3)), "fp32"),
+    "mixing_fp32": (lambda: get_config("mixing", cells=(3, 8, 2)), "fp32"),
+    "naca_fp32": (lambda: get_config("naca", cells=(16, 6)), "fp32"),
+    "learned_fp32": (lambda: get_config("learned", cells=8), "fp32"),
+}
+
+
+def _naca_small(cfg):
+    cfg["mesh"] = dict(cfg["mesh"], stretch=1.3)
+    cfg["dt"] = 2e-3
+    return cfg
+
+
+def _cfg(name):
+    mk, prec = CASES[name]
+    cfg = mk()
+    if name.startswith("naca"):
+        cfg = _naca_small(cfg)
+    return cfg, prec
+
+
+_cache = {}
+
+
+def _oracle(name):
+    if name not in _cache:
+        cfg, prec = _cfg(name)
+        _cache[name] = (cfg, prec) + oracle_case(cfg)
+    return _cache[name]
+
+
+def _sim(cfg, prec, mode=0):
+    from paper_2412_09051_gb300.sim import Sim
+    return Sim(cfg, precision=prec, stream_mode=mode)
+
+
+def _scale_err(a, b):
+    """max over velocities of max|a - b| / max|b| (per-velocity scale)."""
+    s = np.abs(b).max(axis=1, keepdims=True)
+    return float((np.abs(a - b) / s).max())
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_setup_matches_oracle(built_lib, name):
+    cfg, prec, mesh, xi, w, opp, par, rec = _oracle(name)
+    sim = _sim(cfg, prec)
+    xg, wg, og = sim.velocity_set()
+    assert np.abs(xg - xi).max() < 1e-13 and np.abs(wg - w).max() < 1e-15 and (og == opp).all()
+    X = sim.node_coords()
+    scale = np.abs(mesh.X).max()
+    assert np.abs(X - mesh.X).max() < 1e-13 * scale
+    r = sim.departure_records()
+    assert (r["kind"] == rec["kind"]).all()
+    assert (r["src"] == rec["src"]).all()
+    nb = rec["kind"] != 0
+    assert (r["bid"][nb] == rec["bid"][nb]).all()
+    src = rec["kind"] != REC_EQ
+    # physical source points agree (periodic images identified)
+    d = r["xsrc"][src] - rec["xsrc"][src]
+    if mesh.kind != 3:
+        for k in range(mesh.D):
+            if mesh.periodic[k]:
+                L = mesh.length[k]
+                d[:, k] -= L * np.round(d[:, k] / L)
+    assert np.abs(d).max() < 1e-12 * max(1.0, scale)
+    # cells agree wherever the point is not on a cell face
+    inner = src & (np.abs(rec["xi"]).max(axis=2) < 1 - 1e-9)
+    assert (r["cell"][inner] == rec["cell"][inner]).all()
+    assert np.abs(r["xi"][inner] - rec["xi"][inner]).max() < 1e-10
+    sim.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("mode", [0, 1])
+def test_steps_match_oracle(built_lib, name, mode):
+    cfg, prec, mesh, xi, w, opp, par, rec = _oracle(name)
+    if mode == 1 and mesh.kind == 3:
+        pytest.skip("curved mesh runs gather mode already")
+    sim = _sim(cfg, prec, mode)
+    rho, u, T = initial_fields(cfg, mesh.X)
+    sim.init_state(rho, u, T)
+    f, g = ost.init_equilibrium(rho, u, T, xi, w, par.cv)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    fg, gg = sim.get_state()
+    assert _scale_err(fg, f) < (1e-14 if prec == "fp64" else 1e-7)
+    Tw = ost.isothermal_nodes(rec, par)
+    for k in range(3):
+        f, g = ost.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
+        sim.step(1)
+        fg, gg = sim.get_state()
+        ef, eg = _scale_err(fg, f), _scale_err(gg, g)
+        assert ef < tol and eg < tol, (k, ef, eg)
+    r0, u0, T0 = ost.moments(f, g, xi, par.cv)
+    r1, u1, T1 = sim.moments()
+    assert np.abs(r1 - r0).max() < tol and np.abs(T1 - T0).max() < tol
+    assert np.abs(u1 - u0).max() < tol * max(1.0, np.abs(u0).max())
+    sim.close()
+
+
+def test_gather_equals_structured(built_lib):
+    """The two streaming modes compute the same step (FP32, channel with walls)."""
+    cfg = get_config("channel", cells=(4, 6, 3))
+    a, b = _sim(cfg, "fp32", 2), _sim(cfg, "fp32", 1)
+    X = a.node_coords()
+    rho, u, T = initial_fields(cfg, X)
+    for s in (a, b):
+        s.init_state(rho, u, T)
+        s.step(5)
+    fa, ga = a.get_state()
+    fb, gb = b.get_state()
+    assert _scale_err(fa, fb) < 1e-6 and _scale_err(ga, gb) < 1e-6
+
+
+def test_checkpoint_resume_bitwise(built_lib):
+    cfg = get_config("mixing", cells=(3, 8, 2))
+    s = _sim(cfg, "fp32")
+    rho, u, T = initial_fields(cfg, s.node_coords())
+    s.init_state(rho, u, T)
+    s.step(3)
+    f0, g0 = s.get_state_raw()
+    s.step(4)
+    f1, g1 = s.get_state_raw()
+    s.set_state_raw(f0, g0)
+    s.step(4)
+    f2, g2 = s.get_state_raw()
+    assert np.array_equal(f1, f2) and np.array_equal(g1, g2)
+
+
+def test_conservation_periodic(built_lib):
+    """Periodic FP32 box: mass, momentum, energy drift only through the
+    interpolation (Sec. 4.3 reports ~1e-6 per step), reported in FP64."""
+    cfg = get_config("tgv2d", cells=16)
+    s = _sim(cfg, "fp32")
+    rho, u, T = initial_fields(cfg, s.node_coords())
+    s.init_state(rho, u, T)
+    c0, _ = s.conservation()
+    s.step(20)
+    c1, rc = s.conservation()
+    assert rc == 0
+    assert abs(c1[0] - c0[0]) / c0[0] < 1e-4
+    assert abs(c1[-1] - c0[-1]) / c0[-1] < 1e-4
+
+
+def test_isothermal_wall_temperature(built_lib):
+    """After a step, nodes with an isothermal-wall trajectory sit at T_w before
+    collision; collision conserves energy so their post-step T equals T_w."""
+    cfg = get_config("channel", cells=(4, 6, 3))
+    s = _sim(cfg, "fp64")
+    rho, u, T = initial_fields(cfg, s.node_coords())
+    T = T * 1.2
+    s.init_state(rho, u, T)
+    s.step(1)
+    r = s.departure_records()
+    iso = (r["kind"] == 3).any(axis=0)
+    _, _, T1 = s.moments()
+    assert iso.sum() > 0
+    assert np.abs(T1[iso] - 1.0).max() < 1e-12
+
+
+def test_errors_are_status_codes(built_lib):
+    from paper_2412_09051_gb300.capi import SllbmError
+    cfg = get_config("tgv2d", cells=4)
+    cfg["dt"] = -1.0
+    with pytest.raises(SllbmError) as e:
+        _sim(cfg, "fp64")
+    assert e.value.code == -1
+    cfg = get_config("tgv2d", cells=4)
+    s = _sim(cfg, "fp64")
+    with pytest.raises(SllbmError) as e:
+        s.step(1)     # before init
+    assert e.value.code == -7
