@@ -197,7 +197,8 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
-                    ctx->tw_tab, ctx->f[0], ctx->f[1], ctx->g[0], ctx->g[1], ctx->d_red, ctx->d_flag};
+                    ctx->tw_tab, ctx->f[0], ctx->f[1], ctx->g[0], ctx->g[1], ctx->d_red, ctx->d_flag,
+                    ctx->d_mom};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -641,7 +642,8 @@ int sllbm_read_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int32_
     cudaStream_t s = ctx->stream;
     double *dr = rho, *du = u, *dT = T, *tmp = nullptr;
     if (!on_device) {
-        CK(cudaMalloc(&tmp, sizeof(double) * N * (D + 2)));
+        if (!ctx->d_mom) CK(cudaMalloc(&ctx->d_mom, sizeof(double) * N * (D + 2)));
+        tmp = ctx->d_mom;
         dr = rho ? tmp : nullptr;
         du = u ? tmp + N : nullptr;
         dT = T ? tmp + N * (D + 1) : nullptr;
@@ -658,7 +660,6 @@ int sllbm_read_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int32_
         if (u) CK(cudaMemcpyAsync(u, du, sizeof(double) * N * D, cudaMemcpyDeviceToHost, s));
         if (T) CK(cudaMemcpyAsync(T, dT, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        cudaFree(tmp);
     }
     return SLLBM_OK;
 }

@@ -117,6 +117,7 @@ struct sllbm_ctx {
     int64_t steps = 0;
     // scratch
     double* d_red = nullptr;             // reduction partials
+    double* d_mom = nullptr;             // scratch for host moment reads (N (D+2))
     int* d_flag = nullptr;
     sllbm::StepGeom geom{};
     sllbm::CollideConst<float> cc32{};
