@@ -156,7 +156,8 @@ def run_gpu(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    cfg = get_config(args.config)
+    cfg = get_config(args.config, cells=tuple(int(c) for c in args.cells.split(","))) if args.cells \
+        else get_config(args.config)
     stream = torch.cuda.Stream()
     sim = Sim(cfg, device=local, stream=stream.cuda_stream)
     N, Q = sim.N, sim.Q
@@ -247,7 +248,8 @@ def run_gpu(args, ws, rank, local):
                          "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                          "peak_source": f"{psrc} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "kernel": "k_step_structured<D3Q45,P=2,float>" if args.config == "channel" else "k_step"},
+                         "kernel": {2: "k_step_tiled", 3: "k_step_structured", 1: "k_step_gather"}.get(
+                             sim.info.stream_mode, "k_step") + f"<{cfg['velset']}>"},
             "e2e": {"value": round(N / e2e_s / 1e6, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
@@ -270,6 +272,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", default=None, help="override the cell counts, e.g. 32,48,24 (profiling runs)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

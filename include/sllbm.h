@@ -103,7 +103,10 @@ extern "C" {
 
 #define SLLBM_STREAM_AUTO        0  /* structured kernel where cells are axis-aligned, else gather */
 #define SLLBM_STREAM_GATHER      1  /* one departure record per (node, velocity)                  */
-#define SLLBM_STREAM_STRUCTURED  2  /* one record per (velocity, translation class of nodes)     */
+#define SLLBM_STREAM_STRUCTURED  2  /* one record per (velocity, translation class of nodes); the
+                                       warp-tiled kernel where eligible (p = 2, periodic x, x taps
+                                       within +-3 nodes), else one thread per node               */
+#define SLLBM_STREAM_STRUCTURED_NODE 3  /* class records, always one thread per node              */
 
 /* ------------------------------------------------------------------ descriptors */
 typedef struct {

@@ -2,6 +2,7 @@
 // dispatch and readouts.  See include/sllbm.h for the contract of each call.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -40,6 +41,14 @@ SLLBM_EXTERN_STEP(1, 2, double)
 SLLBM_EXTERN_STEP(1, 3, double)
 SLLBM_EXTERN_STEP(2, 2, double)
 SLLBM_EXTERN_STEP(3, 2, double)
+SLLBM_EXTERN_TILED(0, float)
+SLLBM_EXTERN_TILED(1, float)
+SLLBM_EXTERN_TILED(2, float)
+SLLBM_EXTERN_TILED(3, float)
+SLLBM_EXTERN_TILED(0, double)
+SLLBM_EXTERN_TILED(1, double)
+SLLBM_EXTERN_TILED(2, double)
+SLLBM_EXTERN_TILED(3, double)
 }  // namespace sllbm
 
 using namespace sllbm;
@@ -169,7 +178,15 @@ void build_class_table(const sllbm_ctx* c, const std::vector<Rec64>& rec, std::v
 template <typename real>
 int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const int vs = ctx->velset, p = ctx->mesh.p;
-    const bool st = ctx->mode == SLLBM_STREAM_STRUCTURED;
+    const bool st = ctx->mode != SLLBM_STREAM_GATHER;
+    if (st && ctx->tiled) {
+        switch (vs) {
+            case 0: return launch_step_tiled<0, real>(L);
+            case 1: return launch_step_tiled<1, real>(L);
+            case 2: return launch_step_tiled<2, real>(L);
+            case 3: return launch_step_tiled<3, real>(L);
+        }
+    }
 #define CASE(VS, P)                                                                      \
     if (vs == VS && p == P) return st ? launch_step_structured<VS, P, real>(L) : launch_step_gather<VS, P, real>(L);
     CASE(0, 2)
@@ -182,6 +199,41 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
 }
 
 bool supported(int vs, int p) { return p == 2 || (vs == SLLBM_D2Q19 && p == 3); }
+
+// The warp-tiled kernel needs p = 2, periodic x, x-tap offsets within +-3
+// nodes, and y/z factors (and record kinds) independent of the x parity.
+bool tiled_eligible(const sllbm_ctx* c, const std::vector<Rec64>& rec) {
+    const HostMesh& m = c->mesh;
+    if (m.p != 2 || !m.periodic[0] || m.N[0] < 8) return false;
+    if (int64_t(c->vs.Q) * m.n_nodes >= (int64_t(1) << 31)) return false;
+    if (m.D == 3 && !m.periodic[2]) return false;
+    const StepGeom& G = c->geom;
+    const int64_t U = c->n_rec_units;
+    for (int i = 0; i < c->vs.Q; ++i)
+        for (int64_t u = 0; u < U; u += 2) {     // x parity is the fastest class index
+            const Rec64& a = rec[size_t(i * U + u)];
+            const Rec64& b = rec[size_t(i * U + u + 1)];
+            if (a.meta != b.meta || (a.cell < 0) != (b.cell < 0)) return false;
+            if (a.cell < 0) continue;
+            const int64_t ya = (a.cell / m.cells[0]) % m.cells[1], yb = (b.cell / m.cells[0]) % m.cells[1];
+            const int64_t za = a.cell / (int64_t(m.cells[0]) * m.cells[1]), zb = b.cell / (int64_t(m.cells[0]) * m.cells[1]);
+            if (ya != yb || za != zb) return false;
+            for (int d = 1; d < m.D; ++d)
+                if (a.xi[d] != b.xi[d]) return false;
+            for (int par = 0; par < 2; ++par) {
+                const Rec64& r = par ? b : a;
+                const int cx = int(r.cell % m.cells[0]);
+                for (int t = 0; t <= 2; ++t) {
+                    int d = cx * 2 + t - par;
+                    if (d > m.N[0] / 2) d -= m.N[0];
+                    if (d < -m.N[0] / 2) d += m.N[0];
+                    if (d < -3 || d > 3) return false;
+                }
+            }
+        }
+    (void)G;
+    return true;
+}
 
 }  // namespace
 
@@ -263,11 +315,11 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
     const bool axis = ctx->mesh.kind != SLLBM_MESH_NACA;
     int mode = params->stream_mode;
     if (mode == SLLBM_STREAM_AUTO) mode = axis ? SLLBM_STREAM_STRUCTURED : SLLBM_STREAM_GATHER;
-    if (mode == SLLBM_STREAM_STRUCTURED && !axis) {
+    if ((mode == SLLBM_STREAM_STRUCTURED || mode == SLLBM_STREAM_STRUCTURED_NODE) && !axis) {
         ctx->last_error = "structured streaming needs axis-aligned cells";
         return bail(SLLBM_ERR_ARG);
     }
-    if (mode != SLLBM_STREAM_STRUCTURED && mode != SLLBM_STREAM_GATHER) {
+    if (mode != SLLBM_STREAM_STRUCTURED && mode != SLLBM_STREAM_GATHER && mode != SLLBM_STREAM_STRUCTURED_NODE) {
         ctx->last_error = "bad stream mode";
         return bail(SLLBM_ERR_ARG);
     }
@@ -347,7 +399,7 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
             G.ncls[d] = d < D ? (m.periodic[d] ? m.p : m.N[d]) : 1;
             G.n_classes *= G.ncls[d];
         }
-        const bool st = ctx->mode == SLLBM_STREAM_STRUCTURED;
+        const bool st = ctx->mode != SLLBM_STREAM_GATHER;
         ctx->n_rec_units = st ? G.n_classes : N;
         const int64_t U = ctx->n_rec_units;
         // ---- FP64 trace
@@ -409,6 +461,7 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
             std::vector<Rec64> rec(size_t(U * Q));
             CK(cudaMemcpyAsync(rec.data(), ctx->rec64, sizeof(Rec64) * U * Q, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
+            ctx->tiled = ctx->mode == SLLBM_STREAM_STRUCTURED && tiled_eligible(ctx, rec);
             if (rs == 8) {
                 std::vector<ClassRec<double>> t;
                 build_class_table(ctx, rec, t);
@@ -460,7 +513,7 @@ int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
         o->cells[d] = ctx->mesh.cells[d];
     }
     o->precision = ctx->precision;
-    o->stream_mode = ctx->mode;
+    o->stream_mode = (ctx->mode == SLLBM_STREAM_STRUCTURED && !ctx->tiled) ? SLLBM_STREAM_STRUCTURED_NODE : ctx->mode;
     o->state_bytes = int64_t(2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q);
     o->table_bytes = ctx->table_bytes;
     o->n_records = int64_t(ctx->mesh.n_nodes) * ctx->vs.Q;
@@ -699,7 +752,7 @@ int sllbm_departure_records(sllbm_ctx* ctx, int32_t* kind, int32_t* src, int32_t
     std::vector<Rec64> rec(size_t(U * Q));
     CK(cudaMemcpyAsync(rec.data(), ctx->rec64, sizeof(Rec64) * U * Q, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    const bool st = ctx->mode == SLLBM_STREAM_STRUCTURED;
+    const bool st = ctx->mode != SLLBM_STREAM_GATHER;
     for (int i = 0; i < Q; ++i)
         for (int64_t n = 0; n < N; ++n) {
             int k[3] = {0, 0, 0};

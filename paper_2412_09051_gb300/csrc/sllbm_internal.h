@@ -95,6 +95,7 @@ struct sllbm_ctx {
     sllbm::HostVelSet vs;
     sllbm::HostMesh mesh;
     int mode = SLLBM_STREAM_GATHER;      // resolved
+    bool tiled = false;                  // structured mode runs the warp-tiled kernel
     int precision = SLLBM_FP32;
     // device geometry
     double* dV[3] = {nullptr, nullptr, nullptr};

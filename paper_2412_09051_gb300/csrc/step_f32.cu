@@ -5,4 +5,7 @@ SLLBM_INSTANTIATE_STEP(0, 2, float)
 SLLBM_INSTANTIATE_STEP(1, 2, float)
 SLLBM_INSTANTIATE_STEP(1, 3, float)
 SLLBM_INSTANTIATE_STEP(2, 2, float)
+SLLBM_INSTANTIATE_TILED(0, float)
+SLLBM_INSTANTIATE_TILED(1, float)
+SLLBM_INSTANTIATE_TILED(2, float)
 }  // namespace sllbm

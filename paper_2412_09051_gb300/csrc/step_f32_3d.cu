@@ -2,4 +2,5 @@
 #include "step_kernels.cuh"
 namespace sllbm {
 SLLBM_INSTANTIATE_STEP(3, 2, float)
+SLLBM_INSTANTIATE_TILED(3, float)
 }  // namespace sllbm

@@ -6,4 +6,8 @@ SLLBM_INSTANTIATE_STEP(1, 2, double)
 SLLBM_INSTANTIATE_STEP(1, 3, double)
 SLLBM_INSTANTIATE_STEP(2, 2, double)
 SLLBM_INSTANTIATE_STEP(3, 2, double)
+SLLBM_INSTANTIATE_TILED(0, double)
+SLLBM_INSTANTIATE_TILED(1, double)
+SLLBM_INSTANTIATE_TILED(2, double)
+SLLBM_INSTANTIATE_TILED(3, double)
 }  // namespace sllbm

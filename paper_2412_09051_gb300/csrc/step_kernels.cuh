@@ -235,6 +235,156 @@ __global__ void __launch_bounds__(128) k_step_gather(const real* __restrict__ f,
     });
 }
 
+// ------------------------------------------------------------ warp-tiled (P = 2)
+// One warp owns W = 32 - 2H consecutive x-nodes of one (y, z) row plus H halo
+// nodes on each side.  For every velocity the y and z factors of the
+// tensor-product Lagrange stencil are the same for the whole warp (x is
+// periodic and uniform, the class differs only by the x parity), so each lane
+// loads its own x-column of the (P+1)^(D-1) source rows (coalesced) and
+// contracts them with the y/z weights; the x factor is then applied with warp
+// shuffles from the neighbouring lanes (offsets within [-H, H], checked at
+// setup).  Only lanes H .. H+W-1 store.
+template <typename real>
+__device__ __forceinline__ void load_rec(const ClassRec<real>* p, ClassRec<real>& r) {
+    static_assert(sizeof(ClassRec<real>) % 16 == 0, "record must be a multiple of 16 bytes");
+    const int4* s = reinterpret_cast<const int4*>(p);
+    int4* d = reinterpret_cast<int4*>(&r);
+#pragma unroll
+    for (int k = 0; k < int(sizeof(ClassRec<real>) / 16); ++k) d[k] = __ldg(s + k);
+}
+
+template <int VS, int H, typename real>
+__global__ void __launch_bounds__(128) k_step_tiled(const real* __restrict__ f, const real* __restrict__ g,
+                                                    real* __restrict__ fo, real* __restrict__ go,
+                                                    const ClassRec<real>* __restrict__ tab,
+                                                    const real* __restrict__ twt, const StepGeom G,
+                                                    const CollideConst<real> C) {
+    using VSET = VelSet<VS>;
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    constexpr int P = 2;
+    constexpr int W = 32 - 2 * H;
+    const int lane = threadIdx.x & 31;
+    const int gw = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    const int Nx = G.N[0], N1 = G.N[1];
+    const int tiles = (Nx + W - 1) / W;
+    const int rows = D == 3 ? N1 * G.N[2] : N1;
+    if (gw >= tiles * rows) return;              // whole warps only
+    const int row = gw / tiles;
+    const int x0 = (gw - row * tiles) * W;
+    const int ky = row % N1;
+    const int kz = D == 3 ? row / N1 : 0;
+    int kx = (x0 - H + lane) % Nx;
+    if (kx < 0) kx += Nx;
+    const bool store = lane >= H && lane < H + W && (x0 + lane - H) < Nx;
+    const int NN = int(G.n_nodes);
+    const int plane = Nx * N1;
+    const int n = kx + Nx * ky + plane * kz;
+    const bool py = G.periodic[1] != 0;
+    const int cls = (kx & 1) + G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));
+    const int hx = kx >> 1, hy = py ? (ky >> 1) : 0, hz = kz >> 1;
+    real fs[Q], gs[Q];
+    Unroll<0, Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        ClassRec<real> r;
+        load_rec(tab + i * G.n_classes + cls, r);
+        const int kind = r.meta & 15;
+        const int bid = (r.meta >> 4) & 15;
+        if (kind == REC_EQ) {
+            fs[i] = C.eqf[bid][i];
+            gs[i] = C.eqg[bid][i];
+            return;
+        }
+        const int src = r.meta >> 8;
+        // x taps as lane offsets
+        int cx = r.cell[0] + hx;
+        cx -= (cx >= G.cells[0]) ? G.cells[0] : 0;
+        cx += (cx < 0) ? G.cells[0] : 0;
+        int dl[P + 1];
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+            int d = cx * P + a - kx;
+            d -= (d > (Nx >> 1)) ? Nx : 0;
+            d += (d < -(Nx >> 1)) ? Nx : 0;
+            dl[a] = min(31, max(0, lane + d));
+        }
+        // y/z rows (warp-uniform)
+        int cy = r.cell[1] + hy;
+        if (py) {
+            cy -= (cy >= G.cells[1]) ? G.cells[1] : 0;
+            cy += (cy < 0) ? G.cells[1] : 0;
+        }
+        int tyr[P + 1];
+#pragma unroll
+        for (int b = 0; b <= P; ++b) {
+            int ty = cy * P + b;
+            if (py) ty -= (ty >= N1) ? N1 : 0;
+            tyr[b] = ty * Nx;
+        }
+        int ro[(P + 1) * (D == 3 ? P + 1 : 1)];
+        real rw[(P + 1) * (D == 3 ? P + 1 : 1)];
+        if (D == 3) {
+            int cz = r.cell[2] + hz;
+            cz -= (cz >= G.cells[2]) ? G.cells[2] : 0;
+            cz += (cz < 0) ? G.cells[2] : 0;
+#pragma unroll
+            for (int c3 = 0; c3 <= P; ++c3) {
+                int tz = cz * P + c3;
+                tz -= (tz >= G.N[2]) ? G.N[2] : 0;
+#pragma unroll
+                for (int b = 0; b <= P; ++b) {
+                    ro[c3 * (P + 1) + b] = tyr[b] + tz * plane;
+                    rw[c3 * (P + 1) + b] = r.wt[1][b] * r.wt[2][c3];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                ro[b] = tyr[b];
+                rw[b] = r.wt[1][b];
+            }
+        }
+        const real* fp = f + src * NN + kx;
+        const real* gp = g + src * NN + kx;
+        real sf = 0, sg = 0;
+#pragma unroll
+        for (int k = 0; k < int(sizeof(ro) / sizeof(int)); ++k) {
+            sf += rw[k] * __ldg(fp + ro[k]);
+            sg += rw[k] * __ldg(gp + ro[k]);
+        }
+        real of = 0, og = 0;
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+            of += r.wt[0][a] * __shfl_sync(0xffffffffu, sf, dl[a]);
+            og += r.wt[0][a] * __shfl_sync(0xffffffffu, sg, dl[a]);
+        }
+        if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+        fs[i] = of;
+        gs[i] = og;
+    });
+    collide_node<VSET, real>(C, fs, gs, twt[cls]);
+    if (store) {
+        Unroll<0, Q>::run([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            fo[i * NN + n] = fs[i];
+            go[i * NN + n] = gs[i];
+        });
+    }
+}
+
+template <int VS, typename real>
+int launch_step_tiled(const StepLaunch<real>& L) {
+    constexpr int H = 3, W = 32 - 2 * H;
+    const int D = VelSet<VS>::D;
+    const int tiles = (L.G.N[0] + W - 1) / W;
+    const int64_t rows = D == 3 ? int64_t(L.G.N[1]) * L.G.N[2] : L.G.N[1];
+    const int64_t threads = int64_t(tiles) * rows * 32;
+    const int bs = 128;
+    k_step_tiled<VS, H, real><<<unsigned((threads + bs - 1) / bs), bs, 0, L.stream>>>(L.f, L.g, L.fo, L.go, L.cls,
+                                                                                    L.tw, L.G, *L.C);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
 template <int VS, int P, typename real>
 int launch_step_structured(const StepLaunch<real>& L) {
     const int bs = 128;
@@ -255,6 +405,8 @@ int launch_step_gather(const StepLaunch<real>& L) {
 #define SLLBM_EXTERN_STEP(VS, P, real)                                                   \
     extern template int launch_step_structured<VS, P, real>(const StepLaunch<real>&);    \
     extern template int launch_step_gather<VS, P, real>(const StepLaunch<real>&);
+#define SLLBM_EXTERN_TILED(VS, real) extern template int launch_step_tiled<VS, real>(const StepLaunch<real>&);
+#define SLLBM_INSTANTIATE_TILED(VS, real) template int launch_step_tiled<VS, real>(const StepLaunch<real>&);
 
 #define SLLBM_INSTANTIATE_STEP(VS, P, real)                                              \
     template int launch_step_structured<VS, P, real>(const StepLaunch<real>&);           \

@@ -35,6 +35,6 @@ def test_fullsize_sampled_step(built_lib, name):
     fg, gg = sim.get_state()
     tol = 1e-12 if cfg["precision"] == "fp64" else 1e-5
     for a, b in ((fg[:, nodes], f1), (gg[:, nodes], g1)):
-        s = np.abs(b).max(axis=1, keepdims=True)
+        s = np.maximum(np.abs(b).max(axis=1, keepdims=True), w[:, None])
         assert (np.abs(a - b) / s).max() < tol
     sim.close()

@@ -30,6 +30,7 @@ def initial_fields(cfg, X, seed=None):
         u[:, 1] = 0.1 * U * np.sin(1.3 * X[:, 1] + 0.1)
     elif kind == "channel_laminar":
         ub, amp = ini["ub"], ini["amp"]
+        T = np.full(N, ini.get("T", 1.0))
         y = X[:, 1]
         shape = 1.0 - (y - 1.0) ** 2
         u[:, 0] = 1.5 * ub * shape
