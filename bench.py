@@ -191,9 +191,8 @@ def run_gpu(args, ws, rank, local):
 
     # end to end through the C ABI with host buffers: H2D of the step's input
     # state from pinned memory, one step, D2H of the moments
-    raw_f = torch.empty((Q, N), dtype=torch.float32 if real_bytes == 4 else torch.float64).pin_memory()
-    raw_g = torch.empty_like(raw_f).pin_memory()
-    sim.get_state_raw(raw_f, raw_g)
+    raw = torch.empty((Q, N, 2), dtype=torch.float32 if real_bytes == 4 else torch.float64).pin_memory()
+    sim.get_state_raw(raw)
     sim.sync()
     mr = torch.empty(N, dtype=torch.float64).pin_memory()
     mu_ = torch.empty((N, sim.D), dtype=torch.float64).pin_memory()
@@ -202,7 +201,7 @@ def run_gpu(args, ws, rank, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(ke):
-        sim.set_state_raw(raw_f, raw_g)
+        sim.set_state_raw(raw)
         sim.step(1)
         sim.moments_into(mr, mu_, mT)
     torch.cuda.synchronize()

@@ -198,10 +198,13 @@ int sllbm_init_state(sllbm_ctx* ctx, const double* rho, const double* u, const d
 int sllbm_get_state(sllbm_ctx* ctx, double* f, double* g, int32_t on_device);
 int sllbm_set_state(sllbm_ctx* ctx, const double* f, const double* g, int32_t on_device);
 
-/* Native storage (deviations, FP32 or FP64 per the context's precision),
- * bitwise checkpoint / restore of the current step's populations. */
-int sllbm_get_state_raw(sllbm_ctx* ctx, void* f, void* g, int32_t on_device);
-int sllbm_set_state_raw(sllbm_ctx* ctx, const void* f, const void* g, int32_t on_device);
+/* Native storage, bitwise checkpoint / restore of the current step's
+ * populations: deviations from the reference values, FP32 or FP64 per the
+ * context's precision, interleaved per population and node as (f, g) pairs:
+ * element [i][n][0] = f_i(n) - w_i, [i][n][1] = g_i(n) - w_i (2 c_v - D).
+ * Size 2 Q N elements. */
+int sllbm_get_state_raw(sllbm_ctx* ctx, void* fg, int32_t on_device);
+int sllbm_set_state_raw(sllbm_ctx* ctx, const void* fg, int32_t on_device);
 
 /* ------------------------------------------------------------------ stepping */
 

@@ -56,8 +56,8 @@ _SIGS = {
     "sllbm_init_state": (C.c_int, [_P, _P, _P, _P, C.c_int32]),
     "sllbm_get_state": (C.c_int, [_P, _P, _P, C.c_int32]),
     "sllbm_set_state": (C.c_int, [_P, _P, _P, C.c_int32]),
-    "sllbm_get_state_raw": (C.c_int, [_P, _P, _P, C.c_int32]),
-    "sllbm_set_state_raw": (C.c_int, [_P, _P, _P, C.c_int32]),
+    "sllbm_get_state_raw": (C.c_int, [_P, _P, C.c_int32]),
+    "sllbm_set_state_raw": (C.c_int, [_P, _P, C.c_int32]),
     "sllbm_step": (C.c_int, [_P, C.c_int64]),
     "sllbm_step_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "sllbm_read_moments": (C.c_int, [_P, _P, _P, _P, C.c_int32]),

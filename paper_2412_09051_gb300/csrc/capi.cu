@@ -20,15 +20,15 @@ template <typename real>
 int launch_pack_gather(const Rec64* rec, int64_t N, int Q, int D, int32_t* code, real* xi, cudaStream_t s);
 template <typename real>
 int launch_init(int vs, const double* rho, const double* u, const double* T, int64_t N, const CollideConst<double>& C,
-                real* f, real* g, cudaStream_t s);
+                typename Vec2<real>::T* fg, cudaStream_t s);
 template <typename real>
-int launch_convert(real* fd, real* gd, double* ff, double* gf, int64_t N, int Q, const double* w, const double* wg,
-                   int dir, cudaStream_t s);
+int launch_convert(typename Vec2<real>::T* fgd, double* ff, double* gf, int64_t N, int Q, const double* w,
+                   const double* wg, int dir, cudaStream_t s);
 template <typename real>
-int launch_moments(int vs, const real* f, const real* g, int64_t N, const CollideConst<double>& C, double* rho,
+int launch_moments(int vs, const typename Vec2<real>::T* fg, int64_t N, const CollideConst<double>& C, double* rho,
                    double* u, double* T, cudaStream_t s);
 template <typename real>
-int launch_conserve(int vs, int D, const real* f, const real* g, int64_t N, const CollideConst<double>& C,
+int launch_conserve(int vs, int D, const typename Vec2<real>::T* fg, int64_t N, const CollideConst<double>& C,
                     double* part, int* flag, double* out, cudaStream_t s);
 int conserve_blocks();
 SLLBM_EXTERN_STEP(0, 2, float)
@@ -175,6 +175,62 @@ void build_class_table(const sllbm_ctx* c, const std::vector<Rec64>& rec, std::v
         }
 }
 
+// Warp-tiled records: per (velocity, class) the (y, z) source-row offsets
+// relative to the arrival node (no periodic wrap; the kernel recomputes them
+// near a seam from the packed dy / dz), the weight products and the x taps as
+// lane offsets.
+template <typename real>
+void build_tile_table(const sllbm_ctx* c, const std::vector<Rec64>& rec, std::vector<TileRec<real>>& out) {
+    const HostMesh& m = c->mesh;
+    const StepGeom& G = c->geom;
+    const int Q = c->vs.Q, D = m.D;
+    const int64_t U = c->n_rec_units;
+    out.assign(size_t(Q * U), TileRec<real>());
+    const int Nx = m.N[0], N1 = m.N[1];
+    for (int i = 0; i < Q; ++i)
+        for (int64_t u = 0; u < U; ++u) {
+            const Rec64& r = rec[size_t(i * U + u)];
+            TileRec<real>& o = out[size_t(i * U + u)];
+            std::memset(&o, 0, sizeof(o));
+            o.meta = r.meta;
+            if (r.cell < 0) continue;
+            // representative node of the class
+            const int k0 = int(u % G.ncls[0]);
+            const int k1 = int((u / G.ncls[0]) % G.ncls[1]);
+            const int k2 = int(u / (int64_t(G.ncls[0]) * G.ncls[1]));
+            const int cc0 = int(r.cell % m.cells[0]);
+            const int cc1 = int((r.cell / m.cells[0]) % m.cells[1]);
+            const int cc2 = int(r.cell / (int64_t(m.cells[0]) * m.cells[1]));
+            double L[3][3];
+            for (int d = 0; d < D; ++d)
+                for (int a = 0; a <= 2; ++a) {
+                    double v = 1.0;
+                    for (int q = 0; q <= 2; ++q)
+                        if (q != a) v *= (r.xi[d] - m.glc[q]) / (m.glc[a] - m.glc[q]);
+                    L[d][a] = v;
+                }
+            int dx[3], dy[3], dz[3] = {0, 0, 0};
+            for (int a = 0; a <= 2; ++a) {
+                int d = cc0 * 2 + a - k0;
+                if (d > Nx / 2) d -= Nx;
+                if (d < -Nx / 2) d += Nx;
+                dx[a] = d;
+                dy[a] = cc1 * 2 + a - k1;     // periodic y: offsets from the representative (home cell 0)
+                if (D == 3) dz[a] = cc2 * 2 + a - k2;
+            }
+            o.dxp = (dx[0] + 8) | ((dx[1] + 8) << 4) | ((dx[2] + 8) << 8);
+            o.dyzp = (dy[0] + 8) | ((dy[1] + 8) << 4) | ((dy[2] + 8) << 8) | ((dz[0] + 8) << 12) |
+                     ((dz[1] + 8) << 16) | ((dz[2] + 8) << 20);
+            const int NR = D == 3 ? 9 : 3;
+            for (int k = 0; k < NR; ++k) {
+                const int b = k % 3, cz = k / 3;
+                o.rel[k] = dy[b] * Nx + (D == 3 ? dz[cz] * Nx * N1 : 0);
+                o.rw[k] = real(L[1][b] * (D == 3 ? L[2][cz] : 1.0));
+            }
+            for (int a = 0; a <= 2; ++a) o.wx[a] = real(L[0][a]);
+        }
+}
+
 template <typename real>
 int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const int vs = ctx->velset, p = ctx->mesh.p;
@@ -220,6 +276,15 @@ bool tiled_eligible(const sllbm_ctx* c, const std::vector<Rec64>& rec) {
             if (ya != yb || za != zb) return false;
             for (int d = 1; d < m.D; ++d)
                 if (a.xi[d] != b.xi[d]) return false;
+            for (int d = 1; d < m.D; ++d) {
+                const int64_t cd = d == 1 ? ya : za;
+                const int kd = int((u / (d == 1 ? G.ncls[0] : int64_t(G.ncls[0]) * G.ncls[1])) % G.ncls[d]);
+                for (int t = 0; t <= 2; ++t) {
+                    const int64_t off = cd * 2 + t - kd;
+                    if (m.periodic[d] && (off < -3 || off > 3)) return false;   // seam logic covers +-3
+                    if (off < -7 || off > 7) return false;                       // 4-bit packing
+                }
+            }
             for (int par = 0; par < 2; ++par) {
                 const Rec64& r = par ? b : a;
                 const int cx = int(r.cell % m.cells[0]);
@@ -249,7 +314,7 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
-                    ctx->tw_tab, ctx->f[0], ctx->f[1], ctx->g[0], ctx->g[1], ctx->d_red, ctx->d_flag,
+                    ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->d_red, ctx->d_flag,
                     ctx->d_mom};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -462,6 +527,22 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
             CK(cudaMemcpyAsync(rec.data(), ctx->rec64, sizeof(Rec64) * U * Q, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             ctx->tiled = ctx->mode == SLLBM_STREAM_STRUCTURED && tiled_eligible(ctx, rec);
+            if (ctx->tiled) {
+                if (rs == 8) {
+                    std::vector<TileRec<double>> t;
+                    build_tile_table(ctx, rec, t);
+                    CK(cudaMalloc(&ctx->tile_tab, sizeof(TileRec<double>) * t.size()));
+                    CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(TileRec<double>) * t.size(),
+                                       cudaMemcpyHostToDevice, s));
+                } else {
+                    std::vector<TileRec<float>> t;
+                    build_tile_table(ctx, rec, t);
+                    CK(cudaMalloc(&ctx->tile_tab, sizeof(TileRec<float>) * t.size()));
+                    CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(TileRec<float>) * t.size(),
+                                       cudaMemcpyHostToDevice, s));
+                }
+                CK(cudaStreamSynchronize(s));
+            }
             if (rs == 8) {
                 std::vector<ClassRec<double>> t;
                 build_class_table(ctx, rec, t);
@@ -489,8 +570,7 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
         }
         // ---- state buffers
         for (int b = 0; b < 2; ++b) {
-            CK(cudaMalloc(&ctx->f[b], rs * N * Q));
-            CK(cudaMalloc(&ctx->g[b], rs * N * Q));
+            CK(cudaMalloc(&ctx->fg[b], 2 * rs * N * Q));
         }
         CK(cudaMalloc(&ctx->d_red, sizeof(double) * (conserve_blocks() * 5 + 8)));
         CK(cudaStreamSynchronize(s));
@@ -560,8 +640,8 @@ int sllbm_init_state(sllbm_ctx* ctx, const double* rho, const double* u, const d
         dT = tmp + N * (D + 1);
     }
     int rc = ctx->precision == SLLBM_FP64
-                 ? launch_init<double>(ctx->velset, dr, du, dT, N, ctx->cc64, (double*)ctx->f[0], (double*)ctx->g[0], s)
-                 : launch_init<float>(ctx->velset, dr, du, dT, N, ctx->cc64, (float*)ctx->f[0], (float*)ctx->g[0], s);
+                 ? launch_init<double>(ctx->velset, dr, du, dT, N, ctx->cc64, (double2*)ctx->fg[0], s)
+                 : launch_init<float>(ctx->velset, dr, du, dT, N, ctx->cc64, (float2*)ctx->fg[0], s);
     if (tmp) {
         CK(cudaStreamSynchronize(s));
         cudaFree(tmp);
@@ -598,10 +678,8 @@ int state_io(sllbm_ctx* ctx, double* f, double* g, const double* cf, const doubl
     }
     const int c = ctx->cur;
     int rc = ctx->precision == SLLBM_FP64
-                 ? launch_convert<double>((double*)ctx->f[c], (double*)ctx->g[c], buf, buf + N * Q, N, Q, dw, dw + Q,
-                                          dir, s)
-                 : launch_convert<float>((float*)ctx->f[c], (float*)ctx->g[c], buf, buf + N * Q, N, Q, dw, dw + Q,
-                                         dir, s);
+                 ? launch_convert<double>((double2*)ctx->fg[c], buf, buf + N * Q, N, Q, dw, dw + Q, dir, s)
+                 : launch_convert<float>((float2*)ctx->fg[c], buf, buf + N * Q, N, Q, dw, dw + Q, dir, s);
     if (rc == SLLBM_OK && dir == 0) {
         if (f) CK(cudaMemcpyAsync(f, buf, bytes, k_out, s));
         if (g) CK(cudaMemcpyAsync(g, buf + N * Q, bytes, k_out, s));
@@ -628,26 +706,24 @@ int sllbm_set_state(sllbm_ctx* ctx, const double* f, const double* g, int32_t on
     return SLLBM_OK;
 }
 
-int sllbm_get_state_raw(sllbm_ctx* ctx, void* f, void* g, int32_t on_device) {
-    if (!ctx) return SLLBM_ERR_ARG;
+int sllbm_get_state_raw(sllbm_ctx* ctx, void* fg, int32_t on_device) {
+    if (!ctx || !fg) return SLLBM_ERR_ARG;
     if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
     cudaSetDevice(ctx->device);
-    const size_t bytes = real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q;
+    const size_t bytes = 2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (f) CK(cudaMemcpyAsync(f, ctx->f[ctx->cur], bytes, k, ctx->stream));
-    if (g) CK(cudaMemcpyAsync(g, ctx->g[ctx->cur], bytes, k, ctx->stream));
+    CK(cudaMemcpyAsync(fg, ctx->fg[ctx->cur], bytes, k, ctx->stream));
     if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
     return SLLBM_OK;
 }
 
-int sllbm_set_state_raw(sllbm_ctx* ctx, const void* f, const void* g, int32_t on_device) {
-    if (!ctx || !f || !g) return SLLBM_ERR_ARG;
+int sllbm_set_state_raw(sllbm_ctx* ctx, const void* fg, int32_t on_device) {
+    if (!ctx || !fg) return SLLBM_ERR_ARG;
     cudaSetDevice(ctx->device);
-    const size_t bytes = real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q;
+    const size_t bytes = 2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     ctx->cur = 0;
-    CK(cudaMemcpyAsync(ctx->f[0], f, bytes, k, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->g[0], g, bytes, k, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->fg[0], fg, bytes, k, ctx->stream));
     ctx->steps = 0;
     ctx->initialised = true;
     return SLLBM_OK;
@@ -661,14 +737,16 @@ int sllbm_step(sllbm_ctx* ctx, int64_t n) {
         const int a = ctx->cur, b = 1 - a;
         int rc;
         if (ctx->precision == SLLBM_FP64) {
-            StepLaunch<double> L{(const double*)ctx->f[a], (const double*)ctx->g[a], (double*)ctx->f[b],
-                                 (double*)ctx->g[b], (const ClassRec<double>*)ctx->cls_tab, ctx->g_code,
+            StepLaunch<double> L{(const double2*)ctx->fg[a], (double2*)ctx->fg[b],
+                                 (const ClassRec<double>*)ctx->cls_tab, (const TileRec<double>*)ctx->tile_tab,
+                                 ctx->g_code,
                                  (const double*)ctx->g_xi, (const double*)ctx->tw_tab, ctx->geom, &ctx->cc64,
                                  ctx->stream};
             rc = dispatch_step<double>(ctx, L);
         } else {
-            StepLaunch<float> L{(const float*)ctx->f[a], (const float*)ctx->g[a], (float*)ctx->f[b],
-                                (float*)ctx->g[b], (const ClassRec<float>*)ctx->cls_tab, ctx->g_code,
+            StepLaunch<float> L{(const float2*)ctx->fg[a], (float2*)ctx->fg[b],
+                                (const ClassRec<float>*)ctx->cls_tab, (const TileRec<float>*)ctx->tile_tab,
+                                ctx->g_code,
                                 (const float*)ctx->g_xi, (const float*)ctx->tw_tab, ctx->geom, &ctx->cc32,
                                 ctx->stream};
             rc = dispatch_step<float>(ctx, L);
@@ -703,10 +781,8 @@ int sllbm_read_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int32_
     }
     const int c = ctx->cur;
     int rc = ctx->precision == SLLBM_FP64
-                 ? launch_moments<double>(ctx->velset, (double*)ctx->f[c], (double*)ctx->g[c], N, ctx->cc64, dr, du,
-                                          dT, s)
-                 : launch_moments<float>(ctx->velset, (float*)ctx->f[c], (float*)ctx->g[c], N, ctx->cc64, dr, du, dT,
-                                         s);
+                 ? launch_moments<double>(ctx->velset, (double2*)ctx->fg[c], N, ctx->cc64, dr, du, dT, s)
+                 : launch_moments<float>(ctx->velset, (float2*)ctx->fg[c], N, ctx->cc64, dr, du, dT, s);
     if (rc) return fail(ctx, rc, "moments launch failed");
     if (!on_device) {
         if (rho) CK(cudaMemcpyAsync(rho, dr, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
@@ -729,9 +805,9 @@ int sllbm_conservation(sllbm_ctx* ctx, double* out) {
     CK(cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s));
     const int c = ctx->cur;
     int rc = ctx->precision == SLLBM_FP64
-                 ? launch_conserve<double>(ctx->velset, D, (double*)ctx->f[c], (double*)ctx->g[c], N, ctx->cc64, part,
+                 ? launch_conserve<double>(ctx->velset, D, (double2*)ctx->fg[c], N, ctx->cc64, part,
                                            ctx->d_flag + 1, dout, s)
-                 : launch_conserve<float>(ctx->velset, D, (float*)ctx->f[c], (float*)ctx->g[c], N, ctx->cc64, part,
+                 : launch_conserve<float>(ctx->velset, D, (float2*)ctx->fg[c], N, ctx->cc64, part,
                                           ctx->d_flag + 1, dout, s);
     if (rc) return fail(ctx, rc, "conservation launch failed");
     int flag = 0;

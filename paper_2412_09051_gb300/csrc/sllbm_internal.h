@@ -75,6 +75,28 @@ struct ClassRec {             // structured-mode record (per velocity and class)
     real wt[3][4];            // 1D Lagrange weights per dimension
 };
 
+template <typename real>
+struct TileRec {              // warp-tiled record (per velocity and class), 16-byte aligned
+    int32_t meta;             // kind | bid << 4 | src << 8
+    int32_t dxp;              // lane offsets of the 3 x taps, (dx + 8) in 4-bit fields
+    int32_t dyzp;             // dy[3] (bits 0..11) and dz[3] (bits 12..23), (d + 8) in 4-bit fields
+    int32_t pad0;
+    int32_t rel[9];           // node offsets of the (y, z) source rows, no periodic wrap
+    int32_t pad1[3];
+    real rw[9];               // y x z weight products
+    real wx[3];               // x weights
+};
+
+template <typename real> struct Vec2;
+template <> struct Vec2<float> {
+    using T = float2;
+    __host__ __device__ static float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Vec2<double> {
+    using T = double2;
+    __host__ __device__ static double2 make(double a, double b) { return make_double2(a, b); }
+};
+
 struct StepGeom {             // structured / gather kernel geometry
     int N[3], cells[3], periodic[3];
     int ncls[3];              // classes per dimension (p if periodic, else N)
@@ -105,14 +127,14 @@ struct sllbm_ctx {
     int64_t n_rec_units = 0;             // nodes (gather) or classes (structured)
     // step tables
     void* cls_tab = nullptr;             // ClassRec<real>[Q][n_classes]
+    void* tile_tab = nullptr;            // TileRec<real>[Q][n_classes] (warp-tiled kernel)
     int32_t* g_code = nullptr;           // gather: [Q][N] cell | kind<<24 | bid<<28
     void* g_xi = nullptr;                // gather: real [Q][D][N]
     void* tw_tab = nullptr;              // real: per class (structured) or node (gather); NaN none
     int64_t table_bytes = 0;
     int64_t n_boundary_records = 0, n_isothermal_nodes = 0;
     // state
-    void* f[2] = {nullptr, nullptr};
-    void* g[2] = {nullptr, nullptr};
+    void* fg[2] = {nullptr, nullptr};     // interleaved (f, g) deviations, [Q][N] pairs
     int cur = 0;
     bool initialised = false;
     int64_t steps = 0;

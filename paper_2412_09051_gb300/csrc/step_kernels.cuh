@@ -9,11 +9,10 @@ namespace sllbm {
 
 template <typename real>
 struct StepLaunch {
-    const real* f;
-    const real* g;
-    real* fo;
-    real* go;
+    const typename Vec2<real>::T* fg;    // interleaved (f, g) per population, [Q][N]
+    typename Vec2<real>::T* fgo;
     const ClassRec<real>* cls;      // structured mode
+    const TileRec<real>* tile;      // warp-tiled mode
     const int32_t* code;            // gather mode
     const real* gxi;                // gather mode
     const real* tw;                 // per class / per node wall temperature (NaN: none)
@@ -26,8 +25,8 @@ __device__ __forceinline__ int wrapi(int k, int N) { return k >= N ? k - N : k; 
 
 // ------------------------------------------------------------ structured
 template <int VS, int P, typename real>
-__global__ void __launch_bounds__(128) k_step_structured(const real* __restrict__ f, const real* __restrict__ g,
-                                                         real* __restrict__ fo, real* __restrict__ go,
+__global__ void __launch_bounds__(128) k_step_structured(const typename Vec2<real>::T* __restrict__ fg,
+                                                         typename Vec2<real>::T* __restrict__ fgo,
                                                          const ClassRec<real>* __restrict__ tab,
                                                          const real* __restrict__ twt, const StepGeom G,
                                                          const CollideConst<real> C) {
@@ -81,8 +80,7 @@ __global__ void __launch_bounds__(128) k_step_structured(const real* __restrict_
                 wt[d][a] = __ldg(&r.wt[d][a]);
             }
         }
-        const real* fp = f + int64_t(src) * NN;
-        const real* gp = g + int64_t(src) * NN;
+        const typename Vec2<real>::T* p = fg + int64_t(src) * NN;
         real sf = 0, sg = 0;
         if (D == 2) {
 #pragma unroll
@@ -90,9 +88,9 @@ __global__ void __launch_bounds__(128) k_step_structured(const real* __restrict_
                 real tf = 0, tg = 0;
 #pragma unroll
                 for (int a = 0; a <= P; ++a) {
-                    const int64_t o = off[0][a] + off[1][b];
-                    tf += wt[0][a] * __ldg(fp + o);
-                    tg += wt[0][a] * __ldg(gp + o);
+                    const auto v = __ldg(p + off[0][a] + off[1][b]);
+                    tf += wt[0][a] * v.x;
+                    tg += wt[0][a] * v.y;
                 }
                 sf += wt[1][b] * tf;
                 sg += wt[1][b] * tg;
@@ -106,9 +104,9 @@ __global__ void __launch_bounds__(128) k_step_structured(const real* __restrict_
                     real tf = 0, tg = 0;
 #pragma unroll
                     for (int a = 0; a <= P; ++a) {
-                        const int64_t o = off[0][a] + off[1][b] + off[2][c3];
-                        tf += wt[0][a] * __ldg(fp + o);
-                        tg += wt[0][a] * __ldg(gp + o);
+                        const auto v = __ldg(p + off[0][a] + off[1][b] + off[2][c3]);
+                        tf += wt[0][a] * v.x;
+                        tg += wt[0][a] * v.y;
                     }
                     uf += wt[1][b] * tf;
                     ug += wt[1][b] * tg;
@@ -124,15 +122,14 @@ __global__ void __launch_bounds__(128) k_step_structured(const real* __restrict_
     collide_node<VSET, real>(C, fs, gs, twt[cls]);
     Unroll<0, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        fo[int64_t(i) * NN + n] = fs[i];
-        go[int64_t(i) * NN + n] = gs[i];
+        fgo[int64_t(i) * NN + n] = Vec2<real>::make(fs[i], gs[i]);
     });
 }
 
 // ------------------------------------------------------------ gather
 template <int VS, int P, typename real>
-__global__ void __launch_bounds__(128) k_step_gather(const real* __restrict__ f, const real* __restrict__ g,
-                                                     real* __restrict__ fo, real* __restrict__ go,
+__global__ void __launch_bounds__(128) k_step_gather(const typename Vec2<real>::T* __restrict__ fg,
+                                                     typename Vec2<real>::T* __restrict__ fgo,
                                                      const int32_t* __restrict__ code,
                                                      const real* __restrict__ gxi, const real* __restrict__ twt,
                                                      const StepGeom G, const CollideConst<real> C,
@@ -187,8 +184,7 @@ __global__ void __launch_bounds__(128) k_step_gather(const real* __restrict__ f,
             }
         }
         const int src = (kind == REC_BB || kind == REC_BB_ISO) ? C.opp[i] : i;
-        const real* fp = f + int64_t(src) * NN;
-        const real* gp = g + int64_t(src) * NN;
+        const typename Vec2<real>::T* p = fg + int64_t(src) * NN;
         real sf = 0, sg = 0;
         if (D == 2) {
 #pragma unroll
@@ -196,9 +192,9 @@ __global__ void __launch_bounds__(128) k_step_gather(const real* __restrict__ f,
                 real tf = 0, tg = 0;
 #pragma unroll
                 for (int a = 0; a <= P; ++a) {
-                    const int64_t o = off[0][a] + off[1][b];
-                    tf += wt[0][a] * __ldg(fp + o);
-                    tg += wt[0][a] * __ldg(gp + o);
+                    const auto v = __ldg(p + off[0][a] + off[1][b]);
+                    tf += wt[0][a] * v.x;
+                    tg += wt[0][a] * v.y;
                 }
                 sf += wt[1][b] * tf;
                 sg += wt[1][b] * tg;
@@ -212,9 +208,9 @@ __global__ void __launch_bounds__(128) k_step_gather(const real* __restrict__ f,
                     real tf = 0, tg = 0;
 #pragma unroll
                     for (int a = 0; a <= P; ++a) {
-                        const int64_t o = off[0][a] + off[1][b] + off[2][c3];
-                        tf += wt[0][a] * __ldg(fp + o);
-                        tg += wt[0][a] * __ldg(gp + o);
+                        const auto v = __ldg(p + off[0][a] + off[1][b] + off[2][c3]);
+                        tf += wt[0][a] * v.x;
+                        tg += wt[0][a] * v.y;
                     }
                     uf += wt[1][b] * tf;
                     ug += wt[1][b] * tg;
@@ -230,8 +226,7 @@ __global__ void __launch_bounds__(128) k_step_gather(const real* __restrict__ f,
     collide_node<VSET, real>(C, fs, gs, twt[n]);
     Unroll<0, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        fo[int64_t(i) * NN + n] = fs[i];
-        go[int64_t(i) * NN + n] = gs[i];
+        fgo[int64_t(i) * NN + n] = Vec2<real>::make(fs[i], gs[i]);
     });
 }
 
@@ -254,16 +249,17 @@ __device__ __forceinline__ void load_rec(const ClassRec<real>* p, ClassRec<real>
 }
 
 template <int VS, int H, typename real>
-__global__ void __launch_bounds__(128) k_step_tiled(const real* __restrict__ f, const real* __restrict__ g,
-                                                    real* __restrict__ fo, real* __restrict__ go,
-                                                    const ClassRec<real>* __restrict__ tab,
+__global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T* __restrict__ fg,
+                                                    typename Vec2<real>::T* __restrict__ fgo,
+                                                    const TileRec<real>* __restrict__ tab,
                                                     const real* __restrict__ twt, const StepGeom G,
                                                     const CollideConst<real> C) {
     using VSET = VelSet<VS>;
+    using V2 = typename Vec2<real>::T;
     constexpr int Q = VSET::Q;
     constexpr int D = VSET::D;
-    constexpr int P = 2;
     constexpr int W = 32 - 2 * H;
+    constexpr int NR = D == 3 ? 9 : 3;
     const int lane = threadIdx.x & 31;
     const int gw = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
     const int Nx = G.N[0], N1 = G.N[1];
@@ -282,81 +278,57 @@ __global__ void __launch_bounds__(128) k_step_tiled(const real* __restrict__ f, 
     const int n = kx + Nx * ky + plane * kz;
     const bool py = G.periodic[1] != 0;
     const int cls = (kx & 1) + G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));
-    const int hx = kx >> 1, hy = py ? (ky >> 1) : 0, hz = kz >> 1;
+    // rows near a periodic y / z seam need wrapped offsets (warp-uniform)
+    const bool seam = (py && (ky < 3 || ky >= N1 - 3)) || (D == 3 && (kz < 3 || kz >= G.N[2] - 3));
     real fs[Q], gs[Q];
     Unroll<0, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        ClassRec<real> r;
-        load_rec(tab + i * G.n_classes + cls, r);
-        const int kind = r.meta & 15;
-        const int bid = (r.meta >> 4) & 15;
+        const TileRec<real>* r = tab + i * G.n_classes + cls;
+        const int4 h0 = __ldg(reinterpret_cast<const int4*>(r));
+        const int kind = h0.x & 15;
+        const int bid = (h0.x >> 4) & 15;
         if (kind == REC_EQ) {
             fs[i] = C.eqf[bid][i];
             gs[i] = C.eqg[bid][i];
             return;
         }
-        const int src = r.meta >> 8;
-        // x taps as lane offsets
-        int cx = r.cell[0] + hx;
-        cx -= (cx >= G.cells[0]) ? G.cells[0] : 0;
-        cx += (cx < 0) ? G.cells[0] : 0;
-        int dl[P + 1];
-#pragma unroll
-        for (int a = 0; a <= P; ++a) {
-            int d = cx * P + a - kx;
-            d -= (d > (Nx >> 1)) ? Nx : 0;
-            d += (d < -(Nx >> 1)) ? Nx : 0;
-            dl[a] = min(31, max(0, lane + d));
+        const int src = h0.x >> 8;
+        int rel[9];
+        {
+            const int4 a0 = __ldg(reinterpret_cast<const int4*>(r) + 1);
+            const int4 a1 = __ldg(reinterpret_cast<const int4*>(r) + 2);
+            const int4 a2 = __ldg(reinterpret_cast<const int4*>(r) + 3);
+            rel[0] = a0.x; rel[1] = a0.y; rel[2] = a0.z; rel[3] = a0.w;
+            rel[4] = a1.x; rel[5] = a1.y; rel[6] = a1.z; rel[7] = a1.w;
+            rel[8] = a2.x;
         }
-        // y/z rows (warp-uniform)
-        int cy = r.cell[1] + hy;
-        if (py) {
-            cy -= (cy >= G.cells[1]) ? G.cells[1] : 0;
-            cy += (cy < 0) ? G.cells[1] : 0;
-        }
-        int tyr[P + 1];
+        if (seam) {   // recompute with periodic wrap of y and z
 #pragma unroll
-        for (int b = 0; b <= P; ++b) {
-            int ty = cy * P + b;
-            if (py) ty -= (ty >= N1) ? N1 : 0;
-            tyr[b] = ty * Nx;
-        }
-        int ro[(P + 1) * (D == 3 ? P + 1 : 1)];
-        real rw[(P + 1) * (D == 3 ? P + 1 : 1)];
-        if (D == 3) {
-            int cz = r.cell[2] + hz;
-            cz -= (cz >= G.cells[2]) ? G.cells[2] : 0;
-            cz += (cz < 0) ? G.cells[2] : 0;
-#pragma unroll
-            for (int c3 = 0; c3 <= P; ++c3) {
-                int tz = cz * P + c3;
-                tz -= (tz >= G.N[2]) ? G.N[2] : 0;
-#pragma unroll
-                for (int b = 0; b <= P; ++b) {
-                    ro[c3 * (P + 1) + b] = tyr[b] + tz * plane;
-                    rw[c3 * (P + 1) + b] = r.wt[1][b] * r.wt[2][c3];
-                }
-            }
-        } else {
-#pragma unroll
-            for (int b = 0; b <= P; ++b) {
-                ro[b] = tyr[b];
-                rw[b] = r.wt[1][b];
+            for (int k = 0; k < NR; ++k) {
+                const int dy = ((h0.z >> (4 * (k % 3))) & 15) - 8;
+                const int dz = D == 3 ? ((h0.z >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+                int ty = ky + dy, tz = kz + dz;
+                if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
+                if (D == 3) { tz += tz < 0 ? G.N[2] : 0; tz -= tz >= G.N[2] ? G.N[2] : 0; }
+                rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
             }
         }
-        const real* fp = f + src * NN + kx;
-        const real* gp = g + src * NN + kx;
+        const V2* p = fg + src * NN + n;
         real sf = 0, sg = 0;
 #pragma unroll
-        for (int k = 0; k < int(sizeof(ro) / sizeof(int)); ++k) {
-            sf += rw[k] * __ldg(fp + ro[k]);
-            sg += rw[k] * __ldg(gp + ro[k]);
+        for (int k = 0; k < NR; ++k) {
+            const V2 v = __ldg(p + rel[k]);
+            const real wk = r->rw[k];
+            sf += wk * v.x;
+            sg += wk * v.y;
         }
         real of = 0, og = 0;
 #pragma unroll
-        for (int a = 0; a <= P; ++a) {
-            of += r.wt[0][a] * __shfl_sync(0xffffffffu, sf, dl[a]);
-            og += r.wt[0][a] * __shfl_sync(0xffffffffu, sg, dl[a]);
+        for (int a = 0; a < 3; ++a) {
+            const int dl = min(31, max(0, lane + ((h0.y >> (4 * a)) & 15) - 8));
+            const real wx = r->wx[a];
+            of += wx * __shfl_sync(0xffffffffu, sf, dl);
+            og += wx * __shfl_sync(0xffffffffu, sg, dl);
         }
         if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
         fs[i] = of;
@@ -366,8 +338,7 @@ __global__ void __launch_bounds__(128) k_step_tiled(const real* __restrict__ f, 
     if (store) {
         Unroll<0, Q>::run([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            fo[i * NN + n] = fs[i];
-            go[i * NN + n] = gs[i];
+            fgo[i * NN + n] = Vec2<real>::make(fs[i], gs[i]);
         });
     }
 }
@@ -380,8 +351,8 @@ int launch_step_tiled(const StepLaunch<real>& L) {
     const int64_t rows = D == 3 ? int64_t(L.G.N[1]) * L.G.N[2] : L.G.N[1];
     const int64_t threads = int64_t(tiles) * rows * 32;
     const int bs = 128;
-    k_step_tiled<VS, H, real><<<unsigned((threads + bs - 1) / bs), bs, 0, L.stream>>>(L.f, L.g, L.fo, L.go, L.cls,
-                                                                                    L.tw, L.G, *L.C);
+    k_step_tiled<VS, H, real><<<unsigned((threads + bs - 1) / bs), bs, 0, L.stream>>>(L.fg, L.fgo, L.tile, L.tw,
+                                                                                    L.G, *L.C);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
@@ -389,7 +360,7 @@ template <int VS, int P, typename real>
 int launch_step_structured(const StepLaunch<real>& L) {
     const int bs = 128;
     const int64_t grid = (L.G.n_nodes + bs - 1) / bs;
-    k_step_structured<VS, P, real><<<unsigned(grid), bs, 0, L.stream>>>(L.f, L.g, L.fo, L.go, L.cls, L.tw, L.G, *L.C);
+    k_step_structured<VS, P, real><<<unsigned(grid), bs, 0, L.stream>>>(L.fg, L.fgo, L.cls, L.tw, L.G, *L.C);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
@@ -397,8 +368,8 @@ template <int VS, int P, typename real>
 int launch_step_gather(const StepLaunch<real>& L) {
     const int bs = 128;
     const int64_t grid = (L.G.n_nodes + bs - 1) / bs;
-    k_step_gather<VS, P, real><<<unsigned(grid), bs, 0, L.stream>>>(L.f, L.g, L.fo, L.go, L.code, L.gxi, L.tw, L.G,
-                                                                     *L.C, nullptr);
+    k_step_gather<VS, P, real><<<unsigned(grid), bs, 0, L.stream>>>(L.fg, L.fgo, L.code, L.gxi, L.tw, L.G, *L.C,
+                                                                     nullptr);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 

@@ -6,7 +6,7 @@ namespace sllbm {
 // equilibrium deviations (Sec. 3.1) of node fields, in FP64, stored as real
 template <int VS, typename real>
 __global__ void k_init(const double* __restrict__ rho, const double* __restrict__ u, const double* __restrict__ T,
-                       int64_t N, const CollideConst<double> C, real* __restrict__ f, real* __restrict__ g) {
+                       int64_t N, const CollideConst<double> C, typename Vec2<real>::T* __restrict__ fg) {
     using VSET = VelSet<VS>;
     constexpr int D = VSET::D;
     const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -22,39 +22,39 @@ __global__ void k_init(const double* __restrict__ rho, const double* __restrict_
         constexpr int i = decltype(ic)::value;
         double fe, ge, cd;
         eq_dev<VSET, double, i>(C, K, uu, r, r - 1.0, rT, rT - 1.0, fe, ge, cd);
-        f[int64_t(i) * N + n] = real(fe);
-        g[int64_t(i) * N + n] = real(ge);
+        fg[int64_t(i) * N + n] = Vec2<real>::make(real(fe), real(ge));
     });
 }
 
 // full <-> deviation conversion; dir = 0: dev -> full, 1: full -> dev
 template <typename real>
-__global__ void k_convert(real* __restrict__ fd, real* __restrict__ gd, double* __restrict__ ff,
+__global__ void k_convert(typename Vec2<real>::T* __restrict__ fgd, double* __restrict__ ff,
                           double* __restrict__ gf, int64_t N, int Q, const double* __restrict__ w,
                           const double* __restrict__ wg, int dir) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= N * Q) return;
     const int i = int(t / N);
     if (dir == 0) {
-        ff[t] = double(fd[t]) + w[i];
-        gf[t] = double(gd[t]) + wg[i];
+        const auto v = fgd[t];
+        ff[t] = double(v.x) + w[i];
+        gf[t] = double(v.y) + wg[i];
     } else {
-        fd[t] = real(ff[t] - w[i]);
-        gd[t] = real(gf[t] - wg[i]);
+        fgd[t] = Vec2<real>::make(real(ff[t] - w[i]), real(gf[t] - wg[i]));
     }
 }
 
 // per-node moments (Sec. 3.1) in FP64 from the stored deviations
 template <int VS, typename real>
-__device__ __forceinline__ void node_moments(const real* f, const real* g, int64_t N, int64_t n,
+__device__ __forceinline__ void node_moments(const typename Vec2<real>::T* fg, int64_t N, int64_t n,
                                              const CollideConst<double>& C, double& rho, double (&j)[3], double& e2) {
     using VSET = VelSet<VS>;
     double rd = 0, e = 0;
     j[0] = j[1] = j[2] = 0;
     Unroll<0, VSET::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        const double fi = double(f[int64_t(i) * N + n]);
-        const double gi = double(g[int64_t(i) * N + n]);
+        const auto v = fg[int64_t(i) * N + n];
+        const double fi = double(v.x);
+        const double gi = double(v.y);
         rd += fi;
         j[0] += C.xi[i][0] * fi;
         j[1] += C.xi[i][1] * fi;
@@ -66,7 +66,7 @@ __device__ __forceinline__ void node_moments(const real* f, const real* g, int64
 }
 
 template <int VS, typename real>
-__global__ void k_moments(const real* __restrict__ f, const real* __restrict__ g, int64_t N,
+__global__ void k_moments(const typename Vec2<real>::T* __restrict__ fg, int64_t N,
                           const CollideConst<double> C, double* __restrict__ rho, double* __restrict__ u,
                           double* __restrict__ T) {
     using VSET = VelSet<VS>;
@@ -74,7 +74,7 @@ __global__ void k_moments(const real* __restrict__ f, const real* __restrict__ g
     const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (n >= N) return;
     double r, j[3], e2;
-    node_moments<VS, real>(f, g, N, n, C, r, j, e2);
+    node_moments<VS, real>(fg, N, n, C, r, j, e2);
     double U = 0;
     for (int d = 0; d < D; ++d) {
         const double ud = j[d] / r;
@@ -87,7 +87,7 @@ __global__ void k_moments(const real* __restrict__ f, const real* __restrict__ g
 
 // block partial sums of (rho, rho u, 2 rho E) and a positivity flag
 template <int VS, typename real>
-__global__ void k_conserve(const real* __restrict__ f, const real* __restrict__ g, int64_t N,
+__global__ void k_conserve(const typename Vec2<real>::T* __restrict__ fg, int64_t N,
                            const CollideConst<double> C, double* __restrict__ part, int* __restrict__ flag) {
     using VSET = VelSet<VS>;
     constexpr int D = VSET::D;
@@ -98,7 +98,7 @@ __global__ void k_conserve(const real* __restrict__ f, const real* __restrict__ 
     int bad = 0;
     for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < N; n += int64_t(gridDim.x) * blockDim.x) {
         double r, j[3], e2;
-        node_moments<VS, real>(f, g, N, n, C, r, j, e2);
+        node_moments<VS, real>(fg, N, n, C, r, j, e2);
         acc[0] += r;
         double U = 0;
         for (int d = 0; d < D; ++d) {
@@ -132,37 +132,37 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nblk, int K,
 // ------------------------------------------------------------ launchers
 template <typename real>
 int launch_init(int vs, const double* rho, const double* u, const double* T, int64_t N, const CollideConst<double>& C,
-                real* f, real* g, cudaStream_t s) {
+                typename Vec2<real>::T* fg, cudaStream_t s) {
     const int bs = 128;
     const unsigned grid = unsigned((N + bs - 1) / bs);
     switch (vs) {
-        case 0: k_init<0, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, f, g); break;
-        case 1: k_init<1, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, f, g); break;
-        case 2: k_init<2, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, f, g); break;
-        case 3: k_init<3, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, f, g); break;
+        case 0: k_init<0, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, fg); break;
+        case 1: k_init<1, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, fg); break;
+        case 2: k_init<2, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, fg); break;
+        case 3: k_init<3, real><<<grid, bs, 0, s>>>(rho, u, T, N, C, fg); break;
         default: return SLLBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
 template <typename real>
-int launch_convert(real* fd, real* gd, double* ff, double* gf, int64_t N, int Q, const double* w, const double* wg,
-                   int dir, cudaStream_t s) {
+int launch_convert(typename Vec2<real>::T* fgd, double* ff, double* gf, int64_t N, int Q, const double* w,
+                   const double* wg, int dir, cudaStream_t s) {
     const int bs = 256;
-    k_convert<real><<<unsigned((N * Q + bs - 1) / bs), bs, 0, s>>>(fd, gd, ff, gf, N, Q, w, wg, dir);
+    k_convert<real><<<unsigned((N * Q + bs - 1) / bs), bs, 0, s>>>(fgd, ff, gf, N, Q, w, wg, dir);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
 template <typename real>
-int launch_moments(int vs, const real* f, const real* g, int64_t N, const CollideConst<double>& C, double* rho,
+int launch_moments(int vs, const typename Vec2<real>::T* fg, int64_t N, const CollideConst<double>& C, double* rho,
                    double* u, double* T, cudaStream_t s) {
     const int bs = 128;
     const unsigned grid = unsigned((N + bs - 1) / bs);
     switch (vs) {
-        case 0: k_moments<0, real><<<grid, bs, 0, s>>>(f, g, N, C, rho, u, T); break;
-        case 1: k_moments<1, real><<<grid, bs, 0, s>>>(f, g, N, C, rho, u, T); break;
-        case 2: k_moments<2, real><<<grid, bs, 0, s>>>(f, g, N, C, rho, u, T); break;
-        case 3: k_moments<3, real><<<grid, bs, 0, s>>>(f, g, N, C, rho, u, T); break;
+        case 0: k_moments<0, real><<<grid, bs, 0, s>>>(fg, N, C, rho, u, T); break;
+        case 1: k_moments<1, real><<<grid, bs, 0, s>>>(fg, N, C, rho, u, T); break;
+        case 2: k_moments<2, real><<<grid, bs, 0, s>>>(fg, N, C, rho, u, T); break;
+        case 3: k_moments<3, real><<<grid, bs, 0, s>>>(fg, N, C, rho, u, T); break;
         default: return SLLBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
@@ -171,14 +171,14 @@ int launch_moments(int vs, const real* f, const real* g, int64_t N, const Collid
 int conserve_blocks() { return 152 * 4; }
 
 template <typename real>
-int launch_conserve(int vs, int D, const real* f, const real* g, int64_t N, const CollideConst<double>& C,
+int launch_conserve(int vs, int D, const typename Vec2<real>::T* fg, int64_t N, const CollideConst<double>& C,
                     double* part, int* flag, double* out, cudaStream_t s) {
     const int nb = conserve_blocks();
     switch (vs) {
-        case 0: k_conserve<0, real><<<nb, 256, 0, s>>>(f, g, N, C, part, flag); break;
-        case 1: k_conserve<1, real><<<nb, 256, 0, s>>>(f, g, N, C, part, flag); break;
-        case 2: k_conserve<2, real><<<nb, 256, 0, s>>>(f, g, N, C, part, flag); break;
-        case 3: k_conserve<3, real><<<nb, 256, 0, s>>>(f, g, N, C, part, flag); break;
+        case 0: k_conserve<0, real><<<nb, 256, 0, s>>>(fg, N, C, part, flag); break;
+        case 1: k_conserve<1, real><<<nb, 256, 0, s>>>(fg, N, C, part, flag); break;
+        case 2: k_conserve<2, real><<<nb, 256, 0, s>>>(fg, N, C, part, flag); break;
+        case 3: k_conserve<3, real><<<nb, 256, 0, s>>>(fg, N, C, part, flag); break;
         default: return SLLBM_ERR_ARG;
     }
     k_reduce_parts<<<1, 32, 0, s>>>(part, nb, D + 2, out);
@@ -187,12 +187,12 @@ int launch_conserve(int vs, int D, const real* f, const real* g, int64_t N, cons
 
 #define INST(real)                                                                                                 \
     template int launch_init<real>(int, const double*, const double*, const double*, int64_t,                      \
-                                   const CollideConst<double>&, real*, real*, cudaStream_t);                       \
-    template int launch_convert<real>(real*, real*, double*, double*, int64_t, int, const double*, const double*,  \
-                                      int, cudaStream_t);                                                          \
-    template int launch_moments<real>(int, const real*, const real*, int64_t, const CollideConst<double>&, double*, \
+                                   const CollideConst<double>&, Vec2<real>::T*, cudaStream_t);                     \
+    template int launch_convert<real>(Vec2<real>::T*, double*, double*, int64_t, int, const double*,               \
+                                      const double*, int, cudaStream_t);                                           \
+    template int launch_moments<real>(int, const Vec2<real>::T*, int64_t, const CollideConst<double>&, double*,    \
                                       double*, double*, cudaStream_t);                                             \
-    template int launch_conserve<real>(int, int, const real*, const real*, int64_t, const CollideConst<double>&,   \
+    template int launch_conserve<real>(int, int, const Vec2<real>::T*, int64_t, const CollideConst<double>&,       \
                                        double*, int*, double*, cudaStream_t);
 INST(float)
 INST(double)

@@ -130,18 +130,18 @@ class Sim:
         g = np.ascontiguousarray(g, dtype=np.float64)
         self._call("sllbm_set_state", _ptr(f)[0], _ptr(g)[0], 0)
 
-    def get_state_raw(self, f=None, g=None):
+    def get_state_raw(self, fg=None):
+        """Native storage: deviations, interleaved (f, g) per population and node, [Q, N, 2]."""
         dt = np.float64 if self.fp64 else np.float32
-        if f is None:
-            f = np.zeros((self.Q, self.N), dtype=dt)
-            g = np.zeros((self.Q, self.N), dtype=dt)
-        pf, dev = _ptr(f)
-        self._call("sllbm_get_state_raw", pf, _ptr(g)[0], dev)
-        return f, g
+        if fg is None:
+            fg = np.zeros((self.Q, self.N, 2), dtype=dt)
+        p, dev = _ptr(fg)
+        self._call("sllbm_get_state_raw", p, dev)
+        return fg
 
-    def set_state_raw(self, f, g):
-        pf, dev = _ptr(f)
-        self._call("sllbm_set_state_raw", pf, _ptr(g)[0], dev)
+    def set_state_raw(self, fg):
+        p, dev = _ptr(fg)
+        self._call("sllbm_set_state_raw", p, dev)
 
     def step(self, n=1):
         self._call("sllbm_step", C.c_int64(n))
