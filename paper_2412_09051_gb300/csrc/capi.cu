@@ -216,7 +216,15 @@ void build_tile_table(const sllbm_ctx* c, const std::vector<Rec64>& rec, std::ve
                 if (d < -Nx / 2) d += Nx;
                 dx[a] = d;
                 dy[a] = cc1 * 2 + a - k1;     // periodic y: offsets from the representative (home cell 0)
-                if (D == 3) dz[a] = cc2 * 2 + a - k2;
+                if (m.periodic[1]) {
+                    if (dy[a] > N1 / 2) dy[a] -= N1;
+                    if (dy[a] < -N1 / 2) dy[a] += N1;
+                }
+                if (D == 3) {
+                    dz[a] = cc2 * 2 + a - k2;
+                    if (dz[a] > m.N[2] / 2) dz[a] -= m.N[2];
+                    if (dz[a] < -m.N[2] / 2) dz[a] += m.N[2];
+                }
             }
             o.dxp = (dx[0] + 8) | ((dx[1] + 8) << 4) | ((dx[2] + 8) << 8);
             o.dyzp = (dy[0] + 8) | ((dy[1] + 8) << 4) | ((dy[2] + 8) << 8) | ((dz[0] + 8) << 12) |
@@ -280,7 +288,11 @@ bool tiled_eligible(const sllbm_ctx* c, const std::vector<Rec64>& rec) {
                 const int64_t cd = d == 1 ? ya : za;
                 const int kd = int((u / (d == 1 ? G.ncls[0] : int64_t(G.ncls[0]) * G.ncls[1])) % G.ncls[d]);
                 for (int t = 0; t <= 2; ++t) {
-                    const int64_t off = cd * 2 + t - kd;
+                    int64_t off = cd * 2 + t - kd;
+                    if (m.periodic[d]) {                                         // nearest periodic image
+                        if (off > m.N[d] / 2) off -= m.N[d];
+                        if (off < -m.N[d] / 2) off += m.N[d];
+                    }
                     if (m.periodic[d] && (off < -3 || off > 3)) return false;   // seam logic covers +-3
                     if (off < -7 || off > 7) return false;                       // 4-bit packing
                 }
