@@ -242,6 +242,59 @@ int sllbm_conservation(sllbm_ctx* ctx, double* out);
 int sllbm_departure_records(sllbm_ctx* ctx, int32_t* kind, int32_t* src, int32_t* bid,
                             int32_t* cell, double* xi, double* xsrc);
 
+/* ------------------------------------------------------------------ learned collision */
+/* Not in the paper: a small MLP (Q -> 64 -> 64 -> Q, tanh, BF16 weights, FP32
+ * activations and accumulation) corrects the post-collision f of a coarse run.
+ *   z_k = sum_i Phi_ki f^neq_i    non-equilibrium moments of the streamed state
+ *                                 (Phi: weighted-orthonormal moment basis, see
+ *                                 sllbm_moment_basis)
+ *   x = s_in (.) z, h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), o = W3 h2 + b3
+ *   delta f_i = w_i sigma (P o)_i  (P: projection off {1, xi, |xi|^2} in the
+ *                                 weighted inner product -> mass, momentum and
+ *                                 energy conserved exactly)
+ * Available for FP32 D2Q19 contexts that run the warp-tiled structured kernel;
+ * otherwise SLLBM_ERR_UNSUPPORTED. */
+#define SLLBM_MLP_HIDDEN 64
+
+/* Install (enable = 1) or disable (enable = 0) the correction.  Host
+ * pointers: w_bf16 = W1[64][Q] | W2[64][64] | W3[Q][64] as bfloat16 bit
+ * patterns, biases = b1[64] | b2[64] | b3[Q], s_in[Q], sigma > 0. */
+int sllbm_mlp_set(sllbm_ctx* ctx, const uint16_t* w_bf16, const float* biases, const float* s_in, float sigma,
+                  int32_t enable);
+
+/* One plain step (no correction) that also writes the non-equilibrium
+ * moments z [N][Q] (FP32) of the step's streamed state. */
+int sllbm_step_features(sllbm_ctx* ctx, float* z, int32_t on_device);
+
+/* Phi[Q][Q] (rows: Gram-Schmidt in sum_i w_i a_i b_i of the graded monomials
+ * xi^m: total degree, then decreasing power of xi_0, then of xi_1) and the
+ * projection P[Q][Q] = I - C^T G^-1 C W (C: rows 1, xi_a, |xi|^2).  Host. */
+int sllbm_moment_basis(const sllbm_ctx* ctx, double* Phi, double* P);
+
+/* Trainer of the correction on the device: FP32 master parameters
+ * (flattened W1 | b1 | W2 | b2 | W3 | b3, 128 Q + 4224 + Q floats), forward
+ * pass on BF16-rounded weights, loss L = (1/B) sum_samples sum_i w_i (P(o - y))_i^2,
+ * Adam (0.9, 0.999, 1e-8). */
+typedef struct sllbm_trainer sllbm_trainer;
+int sllbm_train_create(const sllbm_ctx* ctx, const float* init_params, sllbm_trainer** out);
+int sllbm_train_destroy(sllbm_trainer* tr);
+const char* sllbm_train_last_error(const sllbm_trainer* tr);
+/* Data: Z [M][Q] moments (sllbm_step_features) and R [M][Q] = (f_target - f_plain)/w.
+ * Sets s_in_k = 1/rms(z_k) (0 for moments without signal) and
+ * sigma = rms over samples of |P R|_w, then stores x = s_in z and y = R / sigma. */
+int sllbm_train_set_data(sllbm_trainer* tr, const float* Z, const float* R, int64_t M, int32_t on_device);
+int sllbm_train_scales(const sllbm_trainer* tr, float* s_in, float* sigma);
+/* One pass over the data in consecutive minibatches of `batch` samples (the
+ * caller shuffles); *loss = mean minibatch loss. */
+int sllbm_train_epoch(sllbm_trainer* tr, int32_t batch, float lr, float* loss);
+/* Gradient (host, flattened like the parameters) and loss of the samples
+ * [offset, offset + count) as one minibatch, without an update. */
+int sllbm_train_grads(sllbm_trainer* tr, int64_t offset, int32_t count, float* grads, float* loss);
+int sllbm_train_params(const sllbm_trainer* tr, float* params);
+int sllbm_train_set_params(sllbm_trainer* tr, const float* params);
+/* BF16 weights (layout of sllbm_mlp_set) and FP32 biases. */
+int sllbm_train_export(const sllbm_trainer* tr, uint16_t* w_bf16, float* biases);
+
 /* Synchronise the context stream. */
 int sllbm_sync(sllbm_ctx* ctx);
 

@@ -65,6 +65,19 @@ _SIGS = {
     "sllbm_departure_records": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "sllbm_sync": (C.c_int, [_P]),
     "sllbm_stream": (C.c_void_p, [_P]),
+    "sllbm_mlp_set": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_int32]),
+    "sllbm_step_features": (C.c_int, [_P, _P, C.c_int32]),
+    "sllbm_moment_basis": (C.c_int, [_P, _P, _P]),
+    "sllbm_train_create": (C.c_int, [_P, _P, C.POINTER(_P)]),
+    "sllbm_train_destroy": (C.c_int, [_P]),
+    "sllbm_train_last_error": (C.c_char_p, [_P]),
+    "sllbm_train_set_data": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32]),
+    "sllbm_train_scales": (C.c_int, [_P, _P, _P]),
+    "sllbm_train_epoch": (C.c_int, [_P, C.c_int32, C.c_float, _P]),
+    "sllbm_train_grads": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P]),
+    "sllbm_train_params": (C.c_int, [_P, _P]),
+    "sllbm_train_set_params": (C.c_int, [_P, _P]),
+    "sllbm_train_export": (C.c_int, [_P, _P, _P]),
 }
 EXPORTED = sorted(_SIGS)
 

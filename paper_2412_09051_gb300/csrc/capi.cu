@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "sllbm_internal.h"
+#include "mlp.cuh"
 #include "step_kernels.cuh"
 
 namespace sllbm {
@@ -49,6 +50,9 @@ SLLBM_EXTERN_TILED(0, double)
 SLLBM_EXTERN_TILED(1, double)
 SLLBM_EXTERN_TILED(2, double)
 SLLBM_EXTERN_TILED(3, double)
+SLLBM_EXTERN_TILED_MLP(1, float)
+void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
+                        std::vector<double>& P);
 }  // namespace sllbm
 
 using namespace sllbm;
@@ -173,6 +177,32 @@ void build_class_table(const sllbm_ctx* c, const std::vector<Rec64>& rec, std::v
                 }
             }
         }
+}
+
+// Builds the constant part of the learned-collision image (moment basis,
+// inverse Gram matrix) on first use; weights arrive with sllbm_mlp_set.
+int ensure_mlp_image(sllbm_ctx* ctx) {
+    if (ctx->mlp_img) return SLLBM_OK;
+    if (ctx->precision != SLLBM_FP32 || !(ctx->tiled && ctx->velset == SLLBM_D2Q19))
+        return fail(ctx, SLLBM_ERR_UNSUPPORTED,
+                    "learned collision is built for FP32 D2Q19 contexts with the warp-tiled structured kernel");
+    const int Q = ctx->vs.Q, D = ctx->vs.D;
+    std::vector<double> Phi, Ginv, P;
+    build_moment_basis(ctx->vs, Phi, Ginv, P);
+    const int n = mlp_image_floats(Q, D);
+    std::vector<float> img(n, 0.0f);
+    const int H = MLP_H;
+    const int o_sin = H * Q + H * H + Q * H + 2 * H + Q;
+    const int o_phi = o_sin + Q;
+    const int o_gi = o_phi + Q * Q;
+    for (int k = 0; k < Q * Q; ++k) img[o_phi + k] = float(Phi[k]);
+    for (int k = 0; k < (D + 2) * (D + 2); ++k) img[o_gi + k] = float(Ginv[k]);
+    img[n - 1] = 1.0f;
+    ctx->mlp_host = img;
+    CK(cudaMalloc(&ctx->mlp_img, sizeof(float) * n));
+    CK(cudaMemcpyAsync(ctx->mlp_img, img.data(), sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SLLBM_OK;
 }
 
 // Warp-tiled records: per (velocity, class) the (y, z) source-row offsets
@@ -327,7 +357,7 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->d_red, ctx->d_flag,
-                    ctx->d_mom};
+                    ctx->d_mom, ctx->mlp_img, ctx->d_feat};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -741,32 +771,109 @@ int sllbm_set_state_raw(sllbm_ctx* ctx, const void* fg, int32_t on_device) {
     return SLLBM_OK;
 }
 
+namespace {
+// one launch of the fused step; mlpm: 0 plain (or learned if enabled), 2 export features
+int step_once(sllbm_ctx* ctx, float* feat) {
+    const int a = ctx->cur, b = 1 - a;
+    const int mlpm = feat ? 2 : (ctx->mlp_enabled ? 1 : 0);
+    int rc;
+    if (ctx->precision == SLLBM_FP64) {
+        if (mlpm) return fail(ctx, SLLBM_ERR_UNSUPPORTED, "learned collision runs in FP32");
+        StepLaunch<double> L{(const double2*)ctx->fg[a], (double2*)ctx->fg[b], (const ClassRec<double>*)ctx->cls_tab,
+                             (const TileRec<double>*)ctx->tile_tab, ctx->g_code, (const double*)ctx->g_xi,
+                             (const double*)ctx->tw_tab, nullptr, nullptr, ctx->geom, &ctx->cc64, ctx->stream};
+        rc = dispatch_step<double>(ctx, L);
+    } else {
+        StepLaunch<float> L{(const float2*)ctx->fg[a], (float2*)ctx->fg[b], (const ClassRec<float>*)ctx->cls_tab,
+                            (const TileRec<float>*)ctx->tile_tab, ctx->g_code, (const float*)ctx->g_xi,
+                            (const float*)ctx->tw_tab, ctx->mlp_img, feat, ctx->geom, &ctx->cc32, ctx->stream};
+        if (mlpm) {
+            if (!(ctx->tiled && ctx->velset == SLLBM_D2Q19))
+                return fail(ctx, SLLBM_ERR_UNSUPPORTED,
+                            "learned collision is built for D2Q19 with the warp-tiled structured kernel");
+            rc = mlpm == 1 ? launch_step_tiled<1, float, 1>(L) : launch_step_tiled<1, float, 2>(L);
+        } else {
+            rc = dispatch_step<float>(ctx, L);
+        }
+    }
+    if (rc) return rc == SLLBM_ERR_CUDA ? fail(ctx, rc, "step launch failed") : rc;
+    ctx->cur = b;
+    ++ctx->steps;
+    return SLLBM_OK;
+}
+}  // namespace
+
 int sllbm_step(sllbm_ctx* ctx, int64_t n) {
     if (!ctx || n < 0) return SLLBM_ERR_ARG;
     if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
     cudaSetDevice(ctx->device);
     for (int64_t k = 0; k < n; ++k) {
-        const int a = ctx->cur, b = 1 - a;
-        int rc;
-        if (ctx->precision == SLLBM_FP64) {
-            StepLaunch<double> L{(const double2*)ctx->fg[a], (double2*)ctx->fg[b],
-                                 (const ClassRec<double>*)ctx->cls_tab, (const TileRec<double>*)ctx->tile_tab,
-                                 ctx->g_code,
-                                 (const double*)ctx->g_xi, (const double*)ctx->tw_tab, ctx->geom, &ctx->cc64,
-                                 ctx->stream};
-            rc = dispatch_step<double>(ctx, L);
-        } else {
-            StepLaunch<float> L{(const float2*)ctx->fg[a], (float2*)ctx->fg[b],
-                                (const ClassRec<float>*)ctx->cls_tab, (const TileRec<float>*)ctx->tile_tab,
-                                ctx->g_code,
-                                (const float*)ctx->g_xi, (const float*)ctx->tw_tab, ctx->geom, &ctx->cc32,
-                                ctx->stream};
-            rc = dispatch_step<float>(ctx, L);
-        }
-        if (rc) return rc == SLLBM_ERR_CUDA ? fail(ctx, rc, "step launch failed") : rc;
-        ctx->cur = b;
-        ++ctx->steps;
+        const int rc = step_once(ctx, nullptr);
+        if (rc) return rc;
     }
+    return SLLBM_OK;
+}
+
+int sllbm_step_features(sllbm_ctx* ctx, float* z, int32_t on_device) {
+    if (!ctx || !z) return SLLBM_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    cudaSetDevice(ctx->device);
+    int rc = ensure_mlp_image(ctx);
+    if (rc) return rc;
+    const size_t bytes = sizeof(float) * ctx->mesh.n_nodes * ctx->vs.Q;
+    float* dz = z;
+    if (!on_device) {
+        if (!ctx->d_feat) CK(cudaMalloc(&ctx->d_feat, bytes));
+        dz = ctx->d_feat;
+    }
+    rc = step_once(ctx, dz);
+    if (rc) return rc;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(z, dz, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return SLLBM_OK;
+}
+
+int sllbm_mlp_set(sllbm_ctx* ctx, const uint16_t* w_bf16, const float* biases, const float* s_in, float sigma,
+                  int32_t enable) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (!enable) {
+        ctx->mlp_enabled = false;
+        return SLLBM_OK;
+    }
+    if (!w_bf16 || !biases || !s_in || !(sigma > 0)) return SLLBM_ERR_ARG;
+    if (ctx->precision != SLLBM_FP32 || !(ctx->tiled && ctx->velset == SLLBM_D2Q19))
+        return fail(ctx, SLLBM_ERR_UNSUPPORTED,
+                    "learned collision is built for FP32 D2Q19 contexts with the warp-tiled structured kernel");
+    int rc = ensure_mlp_image(ctx);
+    if (rc) return rc;
+    const int Q = ctx->vs.Q, H = MLP_H;
+    std::vector<float> img(ctx->mlp_host);
+    auto f32 = [](uint16_t b) {
+        const uint32_t u = uint32_t(b) << 16;
+        float f;
+        std::memcpy(&f, &u, 4);
+        return f;
+    };
+    int k = 0;
+    for (int p = 0; p < H * Q + H * H + Q * H; ++p) img[k++] = f32(w_bf16[p]);
+    for (int p = 0; p < 2 * H + Q; ++p) img[k++] = biases[p];
+    for (int q = 0; q < Q; ++q) img[k++] = s_in[q];
+    img[img.size() - 1] = sigma;
+    CK(cudaMemcpyAsync(ctx->mlp_img, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->mlp_enabled = true;
+    return SLLBM_OK;
+}
+
+int sllbm_moment_basis(const sllbm_ctx* ctx, double* Phi, double* P) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    std::vector<double> ph, gi, pp;
+    build_moment_basis(ctx->vs, ph, gi, pp);
+    if (Phi) std::memcpy(Phi, ph.data(), sizeof(double) * ph.size());
+    if (P) std::memcpy(P, pp.data(), sizeof(double) * pp.size());
     return SLLBM_OK;
 }
 

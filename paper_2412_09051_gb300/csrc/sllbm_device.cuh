@@ -151,7 +151,7 @@ struct Unroll<N, N> {
 // deviations (Eq. 1).  Returns the node density (for diagnostics).
 template <class VSET, typename real>
 __device__ __forceinline__ void collide_node(const CollideConst<real>& C, real (&f)[VSET::Q],
-                                             real (&g)[VSET::Q], real Tw) {
+                                             real (&g)[VSET::Q], real Tw, real* fneq = nullptr) {
     constexpr int Q = VSET::Q;
     constexpr int D = VSET::D;
     // ---- moments (compensated in FP32)
@@ -209,6 +209,7 @@ __device__ __forceinline__ void collide_node(const CollideConst<real>& C, real (
         eq_dev<VSET, real, i>(C, K, u, rho, rho_d, rhoT, rhoT_d, fe, ge, cd);
         const real fn = f[i] - fe;
         const real gn = g[i] - ge;
+        if (fneq) fneq[i] = fn;
         // central heat flux (times 2): sum (xi - u) (|xi - u|^2 f^neq + g^neq)
         const real cu2 = C.s2[VSET::shell(i)] - real(2) * cd + U;
         const real h = cu2 * fn + gn;

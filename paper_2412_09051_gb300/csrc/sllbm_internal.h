@@ -141,6 +141,10 @@ struct sllbm_ctx {
     // scratch
     double* d_red = nullptr;             // reduction partials
     double* d_mom = nullptr;             // scratch for host moment reads (N (D+2))
+    float* mlp_img = nullptr;            // learned-collision image (device)
+    std::vector<float> mlp_host;         // its host copy (constant part)
+    bool mlp_enabled = false;
+    float* d_feat = nullptr;             // scratch for host feature reads
     int* d_flag = nullptr;
     sllbm::StepGeom geom{};
     sllbm::CollideConst<float> cc32{};

@@ -8,4 +8,5 @@ SLLBM_INSTANTIATE_STEP(2, 2, float)
 SLLBM_INSTANTIATE_TILED(0, float)
 SLLBM_INSTANTIATE_TILED(1, float)
 SLLBM_INSTANTIATE_TILED(2, float)
+SLLBM_INSTANTIATE_TILED_MLP(1, float)
 }  // namespace sllbm

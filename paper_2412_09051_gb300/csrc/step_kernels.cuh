@@ -3,6 +3,7 @@
 // moments, isothermal correction (Eq. thermalBC) and collision (Eq. 1), one
 // thread per arrival node, all 2Q streamed values held in registers.
 #pragma once
+#include "mlp.cuh"
 #include "sllbm_internal.h"
 
 namespace sllbm {
@@ -16,6 +17,8 @@ struct StepLaunch {
     const int32_t* code;            // gather mode
     const real* gxi;                // gather mode
     const real* tw;                 // per class / per node wall temperature (NaN: none)
+    const float* mlp_img;           // learned-collision image (mlp.cuh) or nullptr
+    float* feat;                    // feature export [N][Q] or nullptr
     StepGeom G;
     const CollideConst<real>* C;    // host copy, passed by value to the kernel
     cudaStream_t stream;
@@ -239,94 +242,106 @@ __global__ void __launch_bounds__(128) k_step_gather(const typename Vec2<real>::
 // contracts them with the y/z weights; the x factor is then applied with warp
 // shuffles from the neighbouring lanes (offsets within [-H, H], checked at
 // setup).  Only lanes H .. H+W-1 store.
-template <typename real>
-__device__ __forceinline__ void load_rec(const ClassRec<real>* p, ClassRec<real>& r) {
-    static_assert(sizeof(ClassRec<real>) % 16 == 0, "record must be a multiple of 16 bytes");
-    const int4* s = reinterpret_cast<const int4*>(p);
-    int4* d = reinterpret_cast<int4*>(&r);
-#pragma unroll
-    for (int k = 0; k < int(sizeof(ClassRec<real>) / 16); ++k) d[k] = __ldg(s + k);
-}
-
-template <int VS, int H, typename real>
-__global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T* __restrict__ fg,
+template <int VS, int H, typename real, int MLPM>
+__global__ void __launch_bounds__(256) k_step_tiled(const typename Vec2<real>::T* __restrict__ fg,
                                                     typename Vec2<real>::T* __restrict__ fgo,
                                                     const TileRec<real>* __restrict__ tab,
                                                     const real* __restrict__ twt, const StepGeom G,
-                                                    const CollideConst<real> C) {
+                                                    const CollideConst<real> C, const float* __restrict__ mlp_img,
+                                                    float* __restrict__ feat) {
     using VSET = VelSet<VS>;
     using V2 = typename Vec2<real>::T;
     constexpr int Q = VSET::Q;
     constexpr int D = VSET::D;
     constexpr int W = 32 - 2 * H;
     constexpr int NR = D == 3 ? 9 : 3;
+    // block = up to 8 warps covering consecutive x tiles of one (y, z) row; the
+    // row's records (both x parities) are staged in shared memory
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    TileRec<real>* srec = reinterpret_cast<TileRec<real>*>(dyn_smem);
     const int lane = threadIdx.x & 31;
-    const int gw = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
     const int Nx = G.N[0], N1 = G.N[1];
     const int tiles = (Nx + W - 1) / W;
-    const int rows = D == 3 ? N1 * G.N[2] : N1;
-    if (gw >= tiles * rows) return;              // whole warps only
-    const int row = gw / tiles;
-    const int x0 = (gw - row * tiles) * W;
+    const int bpr = (tiles + 7) / 8;                  // blocks per row
+    const int row = blockIdx.x / bpr;
+    const int tile = (blockIdx.x - row * bpr) * 8 + (threadIdx.x >> 5);
     const int ky = row % N1;
     const int kz = D == 3 ? row / N1 : 0;
+    const bool py = G.periodic[1] != 0;
+    const int crow = G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));
+    {
+        constexpr int words = int(sizeof(TileRec<real>) / 16);
+        for (int k = threadIdx.x; k < 2 * Q * words; k += blockDim.x) {
+            const int rec = k / words, wd = k - rec * words;
+            const int i = rec >> 1, par = rec & 1;
+            reinterpret_cast<int4*>(srec + rec)[wd] =
+                __ldg(reinterpret_cast<const int4*>(tab + i * G.n_classes + crow + par) + wd);
+        }
+    }
+    float* mlp_s = reinterpret_cast<float*>(dyn_smem + sizeof(TileRec<real>) * 2 * Q);
+    if (MLPM) mlp_load<Q, D>(mlp_img, mlp_s);
+    __syncthreads();
+    if (tile >= tiles) return;                        // whole warps only
+    const int x0 = tile * W;
     int kx = (x0 - H + lane) % Nx;
     if (kx < 0) kx += Nx;
     const bool store = lane >= H && lane < H + W && (x0 + lane - H) < Nx;
     const int NN = int(G.n_nodes);
     const int plane = Nx * N1;
     const int n = kx + Nx * ky + plane * kz;
-    const bool py = G.periodic[1] != 0;
-    const int cls = (kx & 1) + G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));
+    const int par = kx & 1;
     // rows near a periodic y / z seam need wrapped offsets (warp-uniform)
     const bool seam = (py && (ky < 3 || ky >= N1 - 3)) || (D == 3 && (kz < 3 || kz >= G.N[2] - 3));
+    const V2* base = fg + n;
     real fs[Q], gs[Q];
+    V2 buf[2][NR];
+    // issue the source-row loads of velocity I into buf[I & 1]
+    auto issue = [&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const TileRec<real>& r = srec[2 * i + par];
+        const int meta = r.meta;
+        if ((meta & 15) == REC_EQ) return;
+        const V2* p = base + (meta >> 8) * NN;
+        if (!seam) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) buf[i & 1][k] = __ldg(p + r.rel[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                const int dy = ((r.dyzp >> (4 * (k % 3))) & 15) - 8;
+                const int dz = D == 3 ? ((r.dyzp >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+                int ty = ky + dy, tz = kz + dz;
+                if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
+                if (D == 3) { tz += tz < 0 ? G.N[2] : 0; tz -= tz >= G.N[2] ? G.N[2] : 0; }
+                buf[i & 1][k] = __ldg(p + (ty - ky) * Nx + (tz - kz) * plane);
+            }
+        }
+    };
+    issue(std::integral_constant<int, 0>());
     Unroll<0, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        const TileRec<real>* r = tab + i * G.n_classes + cls;
-        const int4 h0 = __ldg(reinterpret_cast<const int4*>(r));
-        const int kind = h0.x & 15;
-        const int bid = (h0.x >> 4) & 15;
+        if (i + 1 < Q) issue(std::integral_constant<int, (i + 1 < Q ? i + 1 : i)>());
+        const TileRec<real>& r = srec[2 * i + par];
+        const int meta = r.meta;
+        const int kind = meta & 15;
+        const int bid = (meta >> 4) & 15;
         if (kind == REC_EQ) {
             fs[i] = C.eqf[bid][i];
             gs[i] = C.eqg[bid][i];
             return;
         }
-        const int src = h0.x >> 8;
-        int rel[9];
-        {
-            const int4 a0 = __ldg(reinterpret_cast<const int4*>(r) + 1);
-            const int4 a1 = __ldg(reinterpret_cast<const int4*>(r) + 2);
-            const int4 a2 = __ldg(reinterpret_cast<const int4*>(r) + 3);
-            rel[0] = a0.x; rel[1] = a0.y; rel[2] = a0.z; rel[3] = a0.w;
-            rel[4] = a1.x; rel[5] = a1.y; rel[6] = a1.z; rel[7] = a1.w;
-            rel[8] = a2.x;
-        }
-        if (seam) {   // recompute with periodic wrap of y and z
-#pragma unroll
-            for (int k = 0; k < NR; ++k) {
-                const int dy = ((h0.z >> (4 * (k % 3))) & 15) - 8;
-                const int dz = D == 3 ? ((h0.z >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
-                int ty = ky + dy, tz = kz + dz;
-                if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
-                if (D == 3) { tz += tz < 0 ? G.N[2] : 0; tz -= tz >= G.N[2] ? G.N[2] : 0; }
-                rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
-            }
-        }
-        const V2* p = fg + src * NN + n;
         real sf = 0, sg = 0;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            const V2 v = __ldg(p + rel[k]);
-            const real wk = r->rw[k];
-            sf += wk * v.x;
-            sg += wk * v.y;
+            const real wk = r.rw[k];
+            sf += wk * buf[i & 1][k].x;
+            sg += wk * buf[i & 1][k].y;
         }
         real of = 0, og = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const int dl = min(31, max(0, lane + ((h0.y >> (4 * a)) & 15) - 8));
-            const real wx = r->wx[a];
+            const int dl = min(31, max(0, lane + ((r.dxp >> (4 * a)) & 15) - 8));
+            const real wx = r.wx[a];
             of += wx * __shfl_sync(0xffffffffu, sf, dl);
             og += wx * __shfl_sync(0xffffffffu, sg, dl);
         }
@@ -334,7 +349,23 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
         fs[i] = of;
         gs[i] = og;
     });
-    collide_node<VSET, real>(C, fs, gs, twt[cls]);
+    const int cls = par + crow;
+    if (MLPM) {
+        real fneq[Q];
+        collide_node<VSET, real>(C, fs, gs, twt[cls], fneq);
+        const MlpView<Q, D> M(mlp_s);
+        float z[Q];
+        mlp_moments<Q, D, real>(M, fneq, z);
+        if (MLPM == 2) {
+            if (store)
+#pragma unroll
+                for (int k = 0; k < Q; ++k) feat[int64_t(n) * Q + k] = z[k];
+        } else {
+            mlp_correct<Q, D, real>(M, C, z, fs);
+        }
+    } else {
+        collide_node<VSET, real>(C, fs, gs, twt[cls]);
+    }
     if (store) {
         Unroll<0, Q>::run([&](auto ic) {
             constexpr int i = decltype(ic)::value;
@@ -343,16 +374,20 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
     }
 }
 
-template <int VS, typename real>
+template <int VS, typename real, int MLPM = 0>
 int launch_step_tiled(const StepLaunch<real>& L) {
     constexpr int H = 3, W = 32 - 2 * H;
-    const int D = VelSet<VS>::D;
+    constexpr int Q = VelSet<VS>::Q, D = VelSet<VS>::D;
     const int tiles = (L.G.N[0] + W - 1) / W;
+    const int bpr = (tiles + 7) / 8;
     const int64_t rows = D == 3 ? int64_t(L.G.N[1]) * L.G.N[2] : L.G.N[1];
-    const int64_t threads = int64_t(tiles) * rows * 32;
-    const int bs = 128;
-    k_step_tiled<VS, H, real><<<unsigned((threads + bs - 1) / bs), bs, 0, L.stream>>>(L.fg, L.fgo, L.tile, L.tw,
-                                                                                    L.G, *L.C);
+    const int threads = 32 * (tiles < 8 ? tiles : 8);
+    size_t smem = sizeof(TileRec<real>) * 2 * Q;
+    if (MLPM) smem += sizeof(float) * mlp_image_floats(Q, D);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_step_tiled<VS, H, real, MLPM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_step_tiled<VS, H, real, MLPM><<<unsigned(rows * bpr), threads, smem, L.stream>>>(
+        L.fg, L.fgo, L.tile, L.tw, L.G, *L.C, L.mlp_img, L.feat);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
@@ -376,8 +411,14 @@ int launch_step_gather(const StepLaunch<real>& L) {
 #define SLLBM_EXTERN_STEP(VS, P, real)                                                   \
     extern template int launch_step_structured<VS, P, real>(const StepLaunch<real>&);    \
     extern template int launch_step_gather<VS, P, real>(const StepLaunch<real>&);
-#define SLLBM_EXTERN_TILED(VS, real) extern template int launch_step_tiled<VS, real>(const StepLaunch<real>&);
-#define SLLBM_INSTANTIATE_TILED(VS, real) template int launch_step_tiled<VS, real>(const StepLaunch<real>&);
+#define SLLBM_EXTERN_TILED(VS, real) extern template int launch_step_tiled<VS, real, 0>(const StepLaunch<real>&);
+#define SLLBM_INSTANTIATE_TILED(VS, real) template int launch_step_tiled<VS, real, 0>(const StepLaunch<real>&);
+#define SLLBM_EXTERN_TILED_MLP(VS, real)                                          \
+    extern template int launch_step_tiled<VS, real, 1>(const StepLaunch<real>&);  \
+    extern template int launch_step_tiled<VS, real, 2>(const StepLaunch<real>&);
+#define SLLBM_INSTANTIATE_TILED_MLP(VS, real)                              \
+    template int launch_step_tiled<VS, real, 1>(const StepLaunch<real>&);  \
+    template int launch_step_tiled<VS, real, 2>(const StepLaunch<real>&);
 
 #define SLLBM_INSTANTIATE_STEP(VS, P, real)                                              \
     template int launch_step_structured<VS, P, real>(const StepLaunch<real>&);           \

@@ -1,0 +1,158 @@
+"""GPU tests of the learned collision correction: features, corrected step and
+training gradients against the FP64 oracle, exact conservation, and the gain
+of the trained network over the plain coarse method."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from oracle import step as ost
+from oracle.equilibrium import feq
+from tests.oracle_cases import oracle_case
+from workloads import get_config, initial_fields
+
+pytestmark = pytest.mark.gpu
+
+
+def _small():
+    cfg = get_config("learned", cells=8)
+    cfg["init"] = dict(kind="isentropic_vortex", mach=0.6, seed=3)
+    return cfg
+
+
+def _oracle_stream(cfg):
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    rho, u, T = initial_fields(cfg, mesh.X)
+    f, g = ost.init_equilibrium(rho, u, T, xi, w, par.cv)
+    fs, gs = ost.stream(mesh, rec, f, g, xi, w, par)
+    r, uu, TT = ost.moments(fs, gs, xi, par.cv)
+    fneq = fs - feq(r, uu, TT, xi, w)
+    f1, g1 = ost.collide(fs, gs, xi, w, par)
+    return mesh, xi, w, par, (rho, u, T), fneq, f1, g1
+
+
+def _random_model(Q, seed):
+    from paper_2412_09051_gb300.learned import init_params
+    p = init_params(Q, seed).astype(np.float64)
+    r = np.random.default_rng(seed)
+    p += r.normal(0, 0.05, p.shape)        # non-zero biases too
+    return p
+
+
+def _split(p, Q):
+    H = 64
+    o = np.cumsum([0, H * Q, H, H * H, H, Q * H, Q])
+    W1 = p[o[0]:o[1]].reshape(H, Q)
+    b1 = p[o[1]:o[2]]
+    W2 = p[o[2]:o[3]].reshape(H, H)
+    b2 = p[o[3]:o[4]]
+    W3 = p[o[4]:o[5]].reshape(Q, H)
+    b3 = p[o[5]:o[6]]
+    return W1, b1, W2, b2, W3, b3
+
+
+def test_moment_basis_matches_oracle(built_lib):
+    import ctypes as C
+    from paper_2412_09051_gb300.sim import Sim, _ptr
+    s = Sim(_small())
+    Phi = np.zeros((s.Q, s.Q))
+    P = np.zeros((s.Q, s.Q))
+    s._call("sllbm_moment_basis", _ptr(Phi)[0], _ptr(P)[0])
+    xi, w, _ = s.velocity_set()
+    assert np.abs(Phi - omlp.moment_basis(xi, w)).max() < 1e-10
+    assert np.abs(P - omlp.projector(xi, w)).max() < 1e-12
+
+
+def test_features_match_oracle(built_lib):
+    from paper_2412_09051_gb300.learned import step_features
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = _small()
+    mesh, xi, w, par, (rho, u, T), fneq, f1, g1 = _oracle_stream(cfg)
+    s = Sim(cfg)
+    s.init_state(rho, u, T)
+    z = step_features(s)
+    zr = (omlp.moment_basis(xi, w) @ fneq).T
+    assert np.abs(z - zr).max() < 1e-5 * max(np.abs(zr).max(), 1e-6) + 2e-7
+    fg, gg = s.get_state()                  # the export step is a plain step
+    assert np.abs(fg - f1).max() < 1e-5 * np.abs(f1).max()
+
+
+def test_corrected_step_matches_oracle_and_conserves(built_lib):
+    from paper_2412_09051_gb300.learned import set_mlp
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = _small()
+    mesh, xi, w, par, (rho, u, T), fneq, f1, g1 = _oracle_stream(cfg)
+    Q = len(w)
+    p = _random_model(Q, 5)
+    W1, b1, W2, b2, W3, b3 = _split(p, Q)
+    W1r, W2r, W3r = (omlp.bf16_round(a) for a in (W1, W2, W3))
+    s_in = np.abs(np.random.default_rng(1).normal(50, 10, Q)).astype(np.float32)
+    sigma = 3e-4
+    bits = np.concatenate([a.astype(np.float32).ravel().view(np.uint32) >> 16 for a in (W1r, W2r, W3r)])
+    s = Sim(cfg)
+    set_mlp(s, bits.astype(np.uint16), np.concatenate([b1, b2, b3]).astype(np.float32), s_in, sigma)
+    s.init_state(rho, u, T)
+    c0, _ = s.conservation()
+    s.step(1)
+    fg, gg = s.get_state()
+    net = omlp.MLP(W1r, np.float32(b1), W2r, np.float32(b2), W3r, np.float32(b3), s_in, sigma)
+    df = net.correction(fneq, xi, w, omlp.moment_basis(xi, w), omlp.projector(xi, w))
+    ref = f1 + df
+    assert np.abs(df).max() > 1e-6                       # the correction is not negligible
+    assert np.abs(fg - ref).max() < 1e-5 * np.abs(ref).max()
+    # exact conservation: the learned step conserves what the plain step conserves
+    plain = Sim(cfg)
+    plain.init_state(rho, u, T)
+    plain.step(1)
+    c_plain, _ = plain.conservation()
+    c1, _ = s.conservation()
+    assert np.abs(c1 - c_plain).max() < 1e-9 * np.abs(c0).max()
+
+
+def test_training_gradients_match_oracle(built_lib):
+    from paper_2412_09051_gb300.learned import Trainer
+    from paper_2412_09051_gb300.sim import Sim
+    s = Sim(_small())
+    xi, w, _ = s.velocity_set()
+    Q = len(w)
+    r = np.random.default_rng(7)
+    M = 100
+    Z = r.normal(0, 1e-3, (M, Q)).astype(np.float32)
+    Z[:, :3] = 0.0                                     # conserved moments carry no signal
+    R = r.normal(0, 2e-3, (M, Q)).astype(np.float32)
+    p = _random_model(Q, 9).astype(np.float32)
+    tr = Trainer(s, p)
+    tr.set_data(Z, R)
+    s_in, sigma = tr.scales()
+    # oracle definitions of the data scales
+    rms = np.sqrt((Z.astype(np.float64) ** 2).mean(0))
+    s_ref = np.where(rms > 1e-6 * rms.max(), 1.0 / np.maximum(rms, 1e-300), 0.0)
+    P = omlp.projector(xi, w)
+    pr = R.astype(np.float64) @ P.T
+    sig_ref = np.sqrt(((pr ** 2) * w).sum(1).mean())
+    assert np.abs(s_in - s_ref).max() < 1e-4 * s_ref.max() and abs(sigma - sig_ref) < 1e-5 * sig_ref
+    g, loss = tr.grads(10, 64)
+    W1, b1, W2, b2, W3, b3 = _split(p.astype(np.float64), Q)
+    net = omlp.MLP(omlp.bf16_round(W1), b1, omlp.bf16_round(W2), b2, omlp.bf16_round(W3), b3, s_ref, sig_ref)
+    x = Z[10:74].astype(np.float64) * s_in.astype(np.float64)
+    y = R[10:74].astype(np.float64) / sigma
+    lref, gref = net.loss_and_grads(x, y, P, w)
+    gref = np.concatenate([a.ravel() for a in gref])
+    assert abs(loss - lref) < 1e-4 * lref
+    assert np.abs(g - gref).max() < 1e-4 * np.abs(gref).max()
+
+
+def test_learned_beats_plain(built_lib):
+    """Trained on fine/coarse pairs of vortex and shear-layer runs, the learned
+    coarse run is closer to the fine FP64 reference than the plain coarse run."""
+    from paper_2412_09051_gb300 import learned as L
+    train_cases = [("isentropic_vortex", m, s) for m in (0.3, 0.6, 0.9, 1.2) for s in (0, 1)] + \
+                  [("shear_layer", m, s) for m in (0.3, 0.6, 0.9, 1.2) for s in (0,)]
+    Z, R = L.generate_pairs(train_cases, fine_cells=128, snapshots=6, stride=6)
+    from paper_2412_09051_gb300.sim import Sim
+    sim = Sim(get_config("learned", cells=64))
+    model = L.train(sim, Z, R, epochs=40)
+    assert model["losses"][-1] < model["losses"][0]
+    res = L.evaluate(model, ("isentropic_vortex", 0.75, 11), steps=20)
+    print(res)
+    assert res["learned"]["err_f"] < res["plain"]["err_f"]
+    assert res["learned"]["err_u"] < res["plain"]["err_u"]

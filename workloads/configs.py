@@ -70,7 +70,7 @@ def _learned(cells=128, p=2, precision="fp32"):
     return dict(
         name=f"learned2d_{cells}x{cells}_p{p}", velset="D2Q19",
         mesh=dict(kind=0, p=p, cells=(cells, cells), length=(L, L), stretch=1.0, central=0),
-        dt=0.04 * 128 / cells, gamma=1.4, Pr=1.0, mu_ref=2.0e-3, T_ref=1.0, mu_exp=0.0,
+        dt=0.012 * 64 / cells, gamma=1.4, Pr=1.0, mu_ref=2.0e-3, T_ref=1.0, mu_exp=0.0,
         bcs=[_bc(0), _bc(0)], precision=precision, steps=200,
         init=dict(kind="isentropic_vortex", mach=0.6, seed=0))
 
