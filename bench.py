@@ -159,7 +159,7 @@ def run_gpu(args, ws, rank, local):
     cfg = get_config(args.config, cells=tuple(int(c) for c in args.cells.split(","))) if args.cells \
         else get_config(args.config)
     stream = torch.cuda.Stream()
-    sim = Sim(cfg, device=local, stream=stream.cuda_stream)
+    sim = Sim(cfg, device=local, stream=stream.cuda_stream, stream_mode=args.mode)
     N, Q = sim.N, sim.Q
     X = sim.node_coords()
     rho, u, T = initial_fields(cfg, X)
@@ -247,7 +247,8 @@ def run_gpu(args, ws, rank, local):
                          "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                          "peak_source": f"{psrc} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "kernel": {2: "k_step_tiled", 3: "k_step_structured", 1: "k_step_gather"}.get(
+                         "kernel": {2: "k_step_tiled_smem", 4: "k_step_tiled", 3: "k_step_structured",
+                                    1: "k_step_gather"}.get(
                              sim.info.stream_mode, "k_step") + f"<{cfg['velset']}>"},
             "e2e": {"value": round(N / e2e_s / 1e6, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -272,6 +273,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", default=None, help="override the cell counts, e.g. 32,48,24 (profiling runs)")
+    ap.add_argument("--mode", type=int, default=0, help="streaming mode (include/sllbm.h SLLBM_STREAM_*)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

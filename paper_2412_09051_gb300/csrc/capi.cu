@@ -116,6 +116,13 @@ void fill_collide_const(sllbm_ctx* c, CollideConst<real>& C) {
         C.w[i] = real(vs.w[i]);
         C.wg[i] = real(vs.w[i] * gf);
         C.opp[i] = vs.opp[i];
+        double s = 0;
+        for (int d = 0; d < D; ++d) s += vs.xi[i * D + d] * vs.xi[i * D + d];
+        C.s2v[i] = real(s);
+        C.sAv[i] = real(s - D);
+        C.sBv[i] = real(s - D - 2);
+        C.sCv[i] = real(s - D - 4);
+        C.sEv[i] = real(s * s - 2.0 * (D + 2) * s + D * (D + 2.0));
     }
     for (size_t h = 0; h < vs.shell_s.size(); ++h) {
         const double s = vs.shell_s[h];
@@ -274,11 +281,12 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const int vs = ctx->velset, p = ctx->mesh.p;
     const bool st = ctx->mode != SLLBM_STREAM_GATHER;
     if (st && ctx->tiled) {
+        const bool reg = ctx->mode == SLLBM_STREAM_TILED_REG;
         switch (vs) {
-            case 0: return launch_step_tiled<0, real>(L);
-            case 1: return launch_step_tiled<1, real>(L);
-            case 2: return launch_step_tiled<2, real>(L);
-            case 3: return launch_step_tiled<3, real>(L);
+            case 0: return reg ? launch_step_tiled<0, real>(L) : launch_step_tiled_smem<0, real>(L);
+            case 1: return reg ? launch_step_tiled<1, real>(L) : launch_step_tiled_smem<1, real>(L);
+            case 2: return reg ? launch_step_tiled<2, real>(L) : launch_step_tiled_smem<2, real>(L);
+            case 3: return reg ? launch_step_tiled<3, real>(L) : launch_step_tiled_smem<3, real>(L);
         }
     }
 #define CASE(VS, P)                                                                      \
@@ -422,11 +430,13 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
     const bool axis = ctx->mesh.kind != SLLBM_MESH_NACA;
     int mode = params->stream_mode;
     if (mode == SLLBM_STREAM_AUTO) mode = axis ? SLLBM_STREAM_STRUCTURED : SLLBM_STREAM_GATHER;
-    if ((mode == SLLBM_STREAM_STRUCTURED || mode == SLLBM_STREAM_STRUCTURED_NODE) && !axis) {
+    if ((mode == SLLBM_STREAM_STRUCTURED || mode == SLLBM_STREAM_STRUCTURED_NODE || mode == SLLBM_STREAM_TILED_REG) &&
+        !axis) {
         ctx->last_error = "structured streaming needs axis-aligned cells";
         return bail(SLLBM_ERR_ARG);
     }
-    if (mode != SLLBM_STREAM_STRUCTURED && mode != SLLBM_STREAM_GATHER && mode != SLLBM_STREAM_STRUCTURED_NODE) {
+    if (mode != SLLBM_STREAM_STRUCTURED && mode != SLLBM_STREAM_GATHER && mode != SLLBM_STREAM_STRUCTURED_NODE &&
+        mode != SLLBM_STREAM_TILED_REG) {
         ctx->last_error = "bad stream mode";
         return bail(SLLBM_ERR_ARG);
     }
@@ -568,7 +578,8 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
             std::vector<Rec64> rec(size_t(U * Q));
             CK(cudaMemcpyAsync(rec.data(), ctx->rec64, sizeof(Rec64) * U * Q, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            ctx->tiled = ctx->mode == SLLBM_STREAM_STRUCTURED && tiled_eligible(ctx, rec);
+            ctx->tiled = (ctx->mode == SLLBM_STREAM_STRUCTURED || ctx->mode == SLLBM_STREAM_TILED_REG) &&
+                         tiled_eligible(ctx, rec);
             if (ctx->tiled) {
                 if (rs == 8) {
                     std::vector<TileRec<double>> t;
@@ -635,7 +646,9 @@ int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
         o->cells[d] = ctx->mesh.cells[d];
     }
     o->precision = ctx->precision;
-    o->stream_mode = (ctx->mode == SLLBM_STREAM_STRUCTURED && !ctx->tiled) ? SLLBM_STREAM_STRUCTURED_NODE : ctx->mode;
+    o->stream_mode = ((ctx->mode == SLLBM_STREAM_STRUCTURED || ctx->mode == SLLBM_STREAM_TILED_REG) && !ctx->tiled)
+                         ? SLLBM_STREAM_STRUCTURED_NODE
+                         : ctx->mode;
     o->state_bytes = int64_t(2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q);
     o->table_bytes = ctx->table_bytes;
     o->n_records = int64_t(ctx->mesh.n_nodes) * ctx->vs.Q;

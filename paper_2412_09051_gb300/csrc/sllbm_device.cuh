@@ -15,10 +15,22 @@
 #include <cstdint>
 #include <type_traits>
 
+#include <cuda_runtime.h>
+
 #define SLLBM_QMAX 45
 #define SLLBM_SMAX 6
 
 namespace sllbm {
+
+template <typename real> struct Vec2;
+template <> struct Vec2<float> {
+    using T = float2;
+    __host__ __device__ static float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Vec2<double> {
+    using T = double2;
+    __host__ __device__ static double2 make(double a, double b) { return make_double2(a, b); }
+};
 
 // ------------------------------------------------------------ velocity sets
 // Compile-time structure (Q, D, shell of each index); numeric values arrive
@@ -69,6 +81,8 @@ struct CollideConst {
     real eqg[2][SLLBM_QMAX];
     real mw[2][SLLBM_QMAX];
     int opp[SLLBM_QMAX];
+    // per-velocity copies of the shell constants (runtime-indexed loops)
+    real s2v[SLLBM_QMAX], sAv[SLLBM_QMAX], sBv[SLLBM_QMAX], sCv[SLLBM_QMAX], sEv[SLLBM_QMAX];
 };
 
 // ------------------------------------------------------------ compensated sum
@@ -246,6 +260,105 @@ __device__ __forceinline__ void lagrange_w(real x, const real* xh, const real* i
         for (int m = 0; m <= P; ++m)
             if (m != a) v *= (x - xh[m]);
         L[a] = v;
+    }
+}
+
+}  // namespace sllbm
+
+namespace sllbm {
+
+// ------------------------------------------------------------ collide, state in shared memory
+// Same arithmetic as collide_node with runtime velocity loops: the streamed
+// deviations of the thread's node sit at Sf[i * stride], Sg[i * stride]; the
+// post-collision pair of velocity i is written to out[i * NN] (out == nullptr:
+// no store).
+template <class VSET, typename real, typename V2>
+__device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* Sf, real* Sg, int stride, real Tw,
+                                             V2* out, int NN) {
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    Acc<real> arho, aj0, aj1, aj2, ae;
+#pragma unroll 3
+    for (int i = 0; i < Q; ++i) {
+        const real f = Sf[i * stride], g = Sg[i * stride];
+        arho.add(f);
+        aj0.add(C.xi[i][0] * f);
+        aj1.add(C.xi[i][1] * f);
+        if (D == 3) aj2.add(C.xi[i][2] * f);
+        ae.add(C.s2v[i] * f);
+        ae.add(g);
+    }
+    const real rho_d = arho.get();
+    const real rho = real(1) + rho_d;
+    const real inv_rho = real(1) / rho;
+    const real u0 = aj0.get() * inv_rho, u1 = aj1.get() * inv_rho, u2 = D == 3 ? aj2.get() * inv_rho : real(0);
+    const real U = u0 * u0 + u1 * u1 + u2 * u2;
+    real t = (ae.get() - rho * U - real(2) * C.cv * rho_d) * inv_rho / (real(2) * C.cv);
+    // P1 of velocity i for temperature offset tt
+    auto p1 = [&](int i, real tt, real& cd) {
+        real c = C.xi[i][0] * u0 + C.xi[i][1] * u1;
+        if (D == 3) c += C.xi[i][2] * u2;
+        cd = c;
+        const real k2 = real(0.5) - real(0.25) * U + real(0.25) * tt * C.sCv[i];
+        const real k1 = real(1.0) - real(0.5) * U + real(0.5) * tt * C.sBv[i];
+        const real k0 = -real(0.5) * U + real(0.125) * U * U + real(0.5) * tt * C.sAv[i] -
+                        real(0.25) * tt * U * C.sBv[i] + real(0.125) * tt * tt * C.sEv[i];
+        return eq_poly1(c, k0, k1, k2);
+    };
+    if (!(Tw != Tw)) {   // isothermal wall correction (Eq. thermalBC)
+        const real tw = Tw - real(1);
+        const real rT0 = rho * (real(1) + t), rT1 = rho * (real(1) + tw);
+#pragma unroll 3
+        for (int i = 0; i < Q; ++i) {
+            real cd;
+            const real a0 = p1(i, t, cd), a1 = p1(i, tw, cd);
+            Sf[i * stride] += C.w[i] * rho * (a1 - a0);
+            Sg[i * stride] += C.wg[i] * ((rT1 * a1 + (rT1 - real(1))) - (rT0 * a0 + (rT0 - real(1))));
+        }
+        t = tw;
+    }
+    const real T = real(1) + t;
+    real mu = C.mu_ref;
+    if (C.var_mu) mu *= pow(T * C.inv_T_ref, C.mu_exp);
+    const real tau = mu / (rho * T * C.dt) + real(0.5);
+    const real om = real(1) / tau;
+    const real om_pr = real(1) / ((tau - real(0.5)) * C.inv_Pr + real(0.5));
+    const real rhoT = rho * T;
+    const real rhoT_d = rho_d + rho * t;
+    real q0 = 0, q1 = 0, q2 = 0;
+#pragma unroll 3
+    for (int i = 0; i < Q; ++i) {
+        real cd;
+        const real P1 = p1(i, t, cd);
+        const real fe = C.w[i] * (rho * P1 + rho_d);
+        const real ge = C.wg[i] * (rhoT * P1 + rhoT_d);
+        const real f = Sf[i * stride], g = Sg[i * stride];
+        const real fn = f - fe, gn = g - ge;
+        const real h = (C.s2v[i] - real(2) * cd + U) * fn + gn;
+        q0 += (C.xi[i][0] - u0) * h;
+        q1 += (C.xi[i][1] - u1) * h;
+        if (D == 3) q2 += (C.xi[i][2] - u2) * h;
+        const real fo = f - om * fn, go = g - om * gn;
+        if (C.quasi) {
+            Sf[i * stride] = fo;
+            Sg[i * stride] = go;
+        } else if (out) {
+            out[i * NN] = Vec2<real>::make(fo, go);
+        }
+    }
+    if (C.quasi) {
+        const real a = om - om_pr;
+        q0 *= a;
+        q1 *= a;
+        q2 *= a;
+        if (out) {
+#pragma unroll 3
+            for (int i = 0; i < Q; ++i) {
+                real dq = C.xi[i][0] * q0 + C.xi[i][1] * q1;
+                if (D == 3) dq += C.xi[i][2] * q2;
+                out[i * NN] = Vec2<real>::make(Sf[i * stride], Sg[i * stride] + C.w[i] * dq);
+            }
+        }
     }
 }
 

@@ -87,16 +87,6 @@ struct TileRec {              // warp-tiled record (per velocity and class), 16-
     real wx[3];               // x weights
 };
 
-template <typename real> struct Vec2;
-template <> struct Vec2<float> {
-    using T = float2;
-    __host__ __device__ static float2 make(float a, float b) { return make_float2(a, b); }
-};
-template <> struct Vec2<double> {
-    using T = double2;
-    __host__ __device__ static double2 make(double a, double b) { return make_double2(a, b); }
-};
-
 struct StepGeom {             // structured / gather kernel geometry
     int N[3], cells[3], periodic[3];
     int ncls[3];              // classes per dimension (p if periodic, else N)

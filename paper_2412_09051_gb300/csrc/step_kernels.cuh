@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(128) k_step_gather(const typename Vec2<real>::
 // shuffles from the neighbouring lanes (offsets within [-H, H], checked at
 // setup).  Only lanes H .. H+W-1 store.
 template <int VS, int H, typename real, int MLPM>
-__global__ void __launch_bounds__(256) k_step_tiled(const typename Vec2<real>::T* __restrict__ fg,
+__global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T* __restrict__ fg,
                                                     typename Vec2<real>::T* __restrict__ fgo,
                                                     const TileRec<real>* __restrict__ tab,
                                                     const real* __restrict__ twt, const StepGeom G,
@@ -255,93 +255,76 @@ __global__ void __launch_bounds__(256) k_step_tiled(const typename Vec2<real>::T
     constexpr int D = VSET::D;
     constexpr int W = 32 - 2 * H;
     constexpr int NR = D == 3 ? 9 : 3;
-    // block = up to 8 warps covering consecutive x tiles of one (y, z) row; the
-    // row's records (both x parities) are staged in shared memory
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    TileRec<real>* srec = reinterpret_cast<TileRec<real>*>(dyn_smem);
+    float* mlp_s = reinterpret_cast<float*>(dyn_smem);
+    if (MLPM) mlp_load<Q, D>(mlp_img, mlp_s);        // whole block, before any early exit
     const int lane = threadIdx.x & 31;
+    const int gw = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
     const int Nx = G.N[0], N1 = G.N[1];
     const int tiles = (Nx + W - 1) / W;
-    const int bpr = (tiles + 7) / 8;                  // blocks per row
-    const int row = blockIdx.x / bpr;
-    const int tile = (blockIdx.x - row * bpr) * 8 + (threadIdx.x >> 5);
+    const int rows = D == 3 ? N1 * G.N[2] : N1;
+    if (gw >= tiles * rows) return;              // whole warps only
+    const int row = gw / tiles;
+    const int x0 = (gw - row * tiles) * W;
     const int ky = row % N1;
     const int kz = D == 3 ? row / N1 : 0;
-    const bool py = G.periodic[1] != 0;
-    const int crow = G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));
-    {
-        constexpr int words = int(sizeof(TileRec<real>) / 16);
-        for (int k = threadIdx.x; k < 2 * Q * words; k += blockDim.x) {
-            const int rec = k / words, wd = k - rec * words;
-            const int i = rec >> 1, par = rec & 1;
-            reinterpret_cast<int4*>(srec + rec)[wd] =
-                __ldg(reinterpret_cast<const int4*>(tab + i * G.n_classes + crow + par) + wd);
-        }
-    }
-    float* mlp_s = reinterpret_cast<float*>(dyn_smem + sizeof(TileRec<real>) * 2 * Q);
-    if (MLPM) mlp_load<Q, D>(mlp_img, mlp_s);
-    __syncthreads();
-    if (tile >= tiles) return;                        // whole warps only
-    const int x0 = tile * W;
     int kx = (x0 - H + lane) % Nx;
     if (kx < 0) kx += Nx;
     const bool store = lane >= H && lane < H + W && (x0 + lane - H) < Nx;
     const int NN = int(G.n_nodes);
     const int plane = Nx * N1;
     const int n = kx + Nx * ky + plane * kz;
-    const int par = kx & 1;
+    const bool py = G.periodic[1] != 0;
+    const int cls = (kx & 1) + G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));
     // rows near a periodic y / z seam need wrapped offsets (warp-uniform)
     const bool seam = (py && (ky < 3 || ky >= N1 - 3)) || (D == 3 && (kz < 3 || kz >= G.N[2] - 3));
     const V2* base = fg + n;
     real fs[Q], gs[Q];
-    V2 buf[2][NR];
-    // issue the source-row loads of velocity I into buf[I & 1]
-    auto issue = [&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        const TileRec<real>& r = srec[2 * i + par];
-        const int meta = r.meta;
-        if ((meta & 15) == REC_EQ) return;
-        const V2* p = base + (meta >> 8) * NN;
-        if (!seam) {
-#pragma unroll
-            for (int k = 0; k < NR; ++k) buf[i & 1][k] = __ldg(p + r.rel[k]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < NR; ++k) {
-                const int dy = ((r.dyzp >> (4 * (k % 3))) & 15) - 8;
-                const int dz = D == 3 ? ((r.dyzp >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
-                int ty = ky + dy, tz = kz + dz;
-                if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
-                if (D == 3) { tz += tz < 0 ? G.N[2] : 0; tz -= tz >= G.N[2] ? G.N[2] : 0; }
-                buf[i & 1][k] = __ldg(p + (ty - ky) * Nx + (tz - kz) * plane);
-            }
-        }
-    };
-    issue(std::integral_constant<int, 0>());
     Unroll<0, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        if (i + 1 < Q) issue(std::integral_constant<int, (i + 1 < Q ? i + 1 : i)>());
-        const TileRec<real>& r = srec[2 * i + par];
-        const int meta = r.meta;
-        const int kind = meta & 15;
-        const int bid = (meta >> 4) & 15;
+        const TileRec<real>* r = tab + i * G.n_classes + cls;
+        const int4 h0 = __ldg(reinterpret_cast<const int4*>(r));
+        const int kind = h0.x & 15;
+        const int bid = (h0.x >> 4) & 15;
         if (kind == REC_EQ) {
             fs[i] = C.eqf[bid][i];
             gs[i] = C.eqg[bid][i];
             return;
         }
+        int rel[12];
+        {
+            const int4 a0 = __ldg(reinterpret_cast<const int4*>(r) + 1);
+            const int4 a1 = __ldg(reinterpret_cast<const int4*>(r) + 2);
+            const int4 a2 = __ldg(reinterpret_cast<const int4*>(r) + 3);
+            rel[0] = a0.x; rel[1] = a0.y; rel[2] = a0.z; rel[3] = a0.w;
+            rel[4] = a1.x; rel[5] = a1.y; rel[6] = a1.z; rel[7] = a1.w;
+            rel[8] = a2.x;
+        }
+        if (seam) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                const int dy = ((h0.z >> (4 * (k % 3))) & 15) - 8;
+                const int dz = D == 3 ? ((h0.z >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+                int ty = ky + dy, tz = kz + dz;
+                if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
+                if (D == 3) { tz += tz < 0 ? G.N[2] : 0; tz -= tz >= G.N[2] ? G.N[2] : 0; }
+                rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
+            }
+        }
+        const V2* p = base + (h0.x >> 8) * NN;
         real sf = 0, sg = 0;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            const real wk = r.rw[k];
-            sf += wk * buf[i & 1][k].x;
-            sg += wk * buf[i & 1][k].y;
+            const V2 v = __ldg(p + rel[k]);
+            const real wk = __ldg(&r->rw[k]);
+            sf += wk * v.x;
+            sg += wk * v.y;
         }
         real of = 0, og = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const int dl = min(31, max(0, lane + ((r.dxp >> (4 * a)) & 15) - 8));
-            const real wx = r.wx[a];
+            const int dl = min(31, max(0, lane + ((h0.y >> (4 * a)) & 15) - 8));
+            const real wx = __ldg(&r->wx[a]);
             of += wx * __shfl_sync(0xffffffffu, sf, dl);
             og += wx * __shfl_sync(0xffffffffu, sg, dl);
         }
@@ -349,7 +332,6 @@ __global__ void __launch_bounds__(256) k_step_tiled(const typename Vec2<real>::T
         fs[i] = of;
         gs[i] = og;
     });
-    const int cls = par + crow;
     if (MLPM) {
         real fneq[Q];
         collide_node<VSET, real>(C, fs, gs, twt[cls], fneq);
@@ -374,19 +356,135 @@ __global__ void __launch_bounds__(256) k_step_tiled(const typename Vec2<real>::T
     }
 }
 
+// ------------------------------------------------------------ warp-tiled, state in shared memory
+// Same streaming as k_step_tiled, but with runtime velocity loops and the
+// node's 2Q streamed values in shared memory ([2][Q][blockDim] per block): a
+// compact kernel body and a small register footprint, so more warps per SM
+// hide the load latency.  Warps are independent (no block barrier).
+template <int VS, typename real>
+__global__ void __launch_bounds__(128) k_step_tiled_smem(const typename Vec2<real>::T* __restrict__ fg,
+                                                         typename Vec2<real>::T* __restrict__ fgo,
+                                                         const TileRec<real>* __restrict__ tab,
+                                                         const real* __restrict__ twt, const StepGeom G,
+                                                         const CollideConst<real> C) {
+    using VSET = VelSet<VS>;
+    using V2 = typename Vec2<real>::T;
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    constexpr int H = 3, W = 32 - 2 * H;
+    constexpr int NR = D == 3 ? 9 : 3;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    real* S = reinterpret_cast<real*>(dyn_smem);
+    const int lane = threadIdx.x & 31;
+    const int gw = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    const int Nx = G.N[0], N1 = G.N[1];
+    const int tiles = (Nx + W - 1) / W;
+    const int rows = D == 3 ? N1 * G.N[2] : N1;
+    if (gw >= tiles * rows) return;              // whole warps only
+    const int row = gw / tiles;
+    const int x0 = (gw - row * tiles) * W;
+    const int ky = row % N1;
+    const int kz = D == 3 ? row / N1 : 0;
+    int kx = (x0 - H + lane) % Nx;
+    if (kx < 0) kx += Nx;
+    const bool store = lane >= H && lane < H + W && (x0 + lane - H) < Nx;
+    const int NN = int(G.n_nodes);
+    const int plane = Nx * N1;
+    const int n = kx + Nx * ky + plane * kz;
+    const bool py = G.periodic[1] != 0;
+    const int cls = (kx & 1) + G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));
+    const bool seam = (py && (ky < 3 || ky >= N1 - 3)) || (D == 3 && (kz < 3 || kz >= G.N[2] - 3));
+    const int stride = blockDim.x;
+    real* Sf = S + threadIdx.x;
+    real* Sg = S + Q * stride + threadIdx.x;
+    const V2* base = fg + n;
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) {
+        const TileRec<real>* r = tab + i * G.n_classes + cls;
+        const int4 h0 = __ldg(reinterpret_cast<const int4*>(r));
+        const int kind = h0.x & 15;
+        const int bid = (h0.x >> 4) & 15;
+        real of, og;
+        if (kind == REC_EQ) {
+            of = C.eqf[bid][i];
+            og = C.eqg[bid][i];
+        } else {
+            int rel[12];
+            {
+                const int4 a0 = __ldg(reinterpret_cast<const int4*>(r) + 1);
+                const int4 a1 = __ldg(reinterpret_cast<const int4*>(r) + 2);
+                const int4 a2 = __ldg(reinterpret_cast<const int4*>(r) + 3);
+                rel[0] = a0.x; rel[1] = a0.y; rel[2] = a0.z; rel[3] = a0.w;
+                rel[4] = a1.x; rel[5] = a1.y; rel[6] = a1.z; rel[7] = a1.w;
+                rel[8] = a2.x;
+            }
+            if (seam) {
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const int dy = ((h0.z >> (4 * (k % 3))) & 15) - 8;
+                    const int dz = D == 3 ? ((h0.z >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+                    int ty = ky + dy, tz = kz + dz;
+                    if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
+                    if (D == 3) { tz += tz < 0 ? G.N[2] : 0; tz -= tz >= G.N[2] ? G.N[2] : 0; }
+                    rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
+                }
+            }
+            const V2* p = base + (h0.x >> 8) * NN;
+            V2 v[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) v[k] = __ldg(p + rel[k]);
+            real sf = 0, sg = 0;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                const real wk = __ldg(&r->rw[k]);
+                sf += wk * v[k].x;
+                sg += wk * v[k].y;
+            }
+            of = 0;
+            og = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int dl = min(31, max(0, lane + ((h0.y >> (4 * a)) & 15) - 8));
+                const real wx = __ldg(&r->wx[a]);
+                of += wx * __shfl_sync(0xffffffffu, sf, dl);
+                og += wx * __shfl_sync(0xffffffffu, sg, dl);
+            }
+            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+        }
+        Sf[i * stride] = of;
+        Sg[i * stride] = og;
+    }
+    collide_smem<VSET, real, V2>(C, Sf, Sg, stride, twt[cls], store ? fgo + n : nullptr, NN);
+}
+
+template <int VS, typename real>
+int launch_step_tiled_smem(const StepLaunch<real>& L) {
+    constexpr int H = 3, W = 32 - 2 * H;
+    constexpr int Q = VelSet<VS>::Q, D = VelSet<VS>::D;
+    const int tiles = (L.G.N[0] + W - 1) / W;
+    const int64_t rows = D == 3 ? int64_t(L.G.N[1]) * L.G.N[2] : L.G.N[1];
+    const int64_t threads = int64_t(tiles) * rows * 32;
+    const int bs = 128;
+    const size_t smem = sizeof(real) * 2 * Q * bs;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_step_tiled_smem<VS, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_step_tiled_smem<VS, real><<<unsigned((threads + bs - 1) / bs), bs, smem, L.stream>>>(L.fg, L.fgo, L.tile, L.tw,
+                                                                                         L.G, *L.C);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
 template <int VS, typename real, int MLPM = 0>
 int launch_step_tiled(const StepLaunch<real>& L) {
     constexpr int H = 3, W = 32 - 2 * H;
     constexpr int Q = VelSet<VS>::Q, D = VelSet<VS>::D;
     const int tiles = (L.G.N[0] + W - 1) / W;
-    const int bpr = (tiles + 7) / 8;
     const int64_t rows = D == 3 ? int64_t(L.G.N[1]) * L.G.N[2] : L.G.N[1];
-    const int threads = 32 * (tiles < 8 ? tiles : 8);
-    size_t smem = sizeof(TileRec<real>) * 2 * Q;
-    if (MLPM) smem += sizeof(float) * mlp_image_floats(Q, D);
+    const int64_t threads = int64_t(tiles) * rows * 32;
+    const int bs = 128;
+    const size_t smem = MLPM ? sizeof(float) * mlp_image_floats(Q, D) : 0;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_step_tiled<VS, H, real, MLPM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    k_step_tiled<VS, H, real, MLPM><<<unsigned(rows * bpr), threads, smem, L.stream>>>(
+    k_step_tiled<VS, H, real, MLPM><<<unsigned((threads + bs - 1) / bs), bs, smem, L.stream>>>(
         L.fg, L.fgo, L.tile, L.tw, L.G, *L.C, L.mlp_img, L.feat);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
@@ -411,8 +509,12 @@ int launch_step_gather(const StepLaunch<real>& L) {
 #define SLLBM_EXTERN_STEP(VS, P, real)                                                   \
     extern template int launch_step_structured<VS, P, real>(const StepLaunch<real>&);    \
     extern template int launch_step_gather<VS, P, real>(const StepLaunch<real>&);
-#define SLLBM_EXTERN_TILED(VS, real) extern template int launch_step_tiled<VS, real, 0>(const StepLaunch<real>&);
-#define SLLBM_INSTANTIATE_TILED(VS, real) template int launch_step_tiled<VS, real, 0>(const StepLaunch<real>&);
+#define SLLBM_EXTERN_TILED(VS, real)                                              \
+    extern template int launch_step_tiled<VS, real, 0>(const StepLaunch<real>&);  \
+    extern template int launch_step_tiled_smem<VS, real>(const StepLaunch<real>&);
+#define SLLBM_INSTANTIATE_TILED(VS, real)                                  \
+    template int launch_step_tiled<VS, real, 0>(const StepLaunch<real>&);  \
+    template int launch_step_tiled_smem<VS, real>(const StepLaunch<real>&);
 #define SLLBM_EXTERN_TILED_MLP(VS, real)                                          \
     extern template int launch_step_tiled<VS, real, 1>(const StepLaunch<real>&);  \
     extern template int launch_step_tiled<VS, real, 2>(const StepLaunch<real>&);

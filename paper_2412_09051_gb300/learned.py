@@ -41,7 +41,6 @@ def inject(f, n_fine):
 
 
 def case_cfg(base, cells, kind, mach, seed):
-    cfg = dict(base)
     from workloads.configs import get_config
     cfg = get_config("learned", cells=cells)
     cfg["init"] = dict(kind=kind, mach=mach, seed=seed)

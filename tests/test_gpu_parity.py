@@ -99,10 +99,11 @@ def test_setup_matches_oracle(built_lib, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_steps_match_oracle(built_lib, name, mode):
-    """Every streaming mode (0 auto: warp-tiled where eligible, 1 gather,
-    3 one thread per node with class records) against the oracle."""
+    """Every streaming mode (0 auto: warp-tiled with shared-memory state where
+    eligible, 1 gather, 3 one thread per node with class records, 4 warp-tiled
+    with register state) against the oracle."""
     cfg, prec, mesh, xi, w, opp, par, rec = _oracle(name)
     if mode != 0 and mesh.kind == 3:
         pytest.skip("curved mesh runs gather mode already")
@@ -127,7 +128,7 @@ def test_steps_match_oracle(built_lib, name, mode):
     sim.close()
 
 
-@pytest.mark.parametrize("modes", [(2, 1), (2, 3)])
+@pytest.mark.parametrize("modes", [(2, 1), (2, 3), (2, 4)])
 def test_streaming_modes_agree(built_lib, modes):
     """The streaming modes compute the same step (FP32, channel with walls)."""
     cfg = get_config("channel", cells=(4, 6, 3))
