@@ -283,9 +283,12 @@ int sllbm_train_create(const sllbm_ctx* ctx, const float* init_params, sllbm_tra
 int sllbm_train_destroy(sllbm_trainer* tr);
 const char* sllbm_train_last_error(const sllbm_trainer* tr);
 /* Data: Z [M][Q] moments (sllbm_step_features) and R [M][Q] = (f_target - f_plain)/w.
- * Sets s_in_k = 1/rms(z_k) (0 for moments without signal) and
- * sigma = rms over samples of |P R|_w, then stores x = s_in z and y = R / sigma. */
-int sllbm_train_set_data(sllbm_trainer* tr, const float* Z, const float* R, int64_t M, int32_t on_device);
+ * max_degree > 0 first keeps only the moments of R (in the basis Phi) of
+ * polynomial degree <= max_degree (0 keeps all).  Sets s_in_k = 1/rms(z_k)
+ * (0 for moments without signal) and sigma = rms over samples of |P R|_w,
+ * then stores x = s_in z and y = R / sigma. */
+int sllbm_train_set_data(sllbm_trainer* tr, const float* Z, const float* R, int64_t M, int32_t max_degree,
+                         int32_t on_device);
 int sllbm_train_scales(const sllbm_trainer* tr, float* s_in, float* sigma);
 /* One pass over the data in consecutive minibatches of `batch` samples (the
  * caller shuffles); *loss = mean minibatch loss. */

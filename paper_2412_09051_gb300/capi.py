@@ -71,7 +71,7 @@ _SIGS = {
     "sllbm_train_create": (C.c_int, [_P, _P, C.POINTER(_P)]),
     "sllbm_train_destroy": (C.c_int, [_P]),
     "sllbm_train_last_error": (C.c_char_p, [_P]),
-    "sllbm_train_set_data": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32]),
+    "sllbm_train_set_data": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_int32]),
     "sllbm_train_scales": (C.c_int, [_P, _P, _P]),
     "sllbm_train_epoch": (C.c_int, [_P, C.c_int32, C.c_float, _P]),
     "sllbm_train_grads": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P]),

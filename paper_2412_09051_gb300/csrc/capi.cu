@@ -53,6 +53,8 @@ SLLBM_EXTERN_TILED(3, double)
 SLLBM_EXTERN_TILED_MLP(1, float)
 void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
                         std::vector<double>& P);
+void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
+                        std::vector<double>& P, std::vector<int>* degree);
 }  // namespace sllbm
 
 using namespace sllbm;

@@ -20,9 +20,10 @@ namespace sllbm {
 // Phi: modified Gram-Schmidt of graded monomials in <a,b> = sum w a b;
 // Ginv: inverse Gram matrix of {1, xi, |xi|^2}; P = I - C^T Ginv C W.
 void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
-                        std::vector<double>& P) {
+                        std::vector<double>& P, std::vector<int>* degree) {
     const int Q = vs.Q, D = vs.D;
     std::vector<std::vector<double>> rows;
+    if (degree) degree->clear();
     auto dot = [&](const std::vector<double>& a, const std::vector<double>& b) {
         double s = 0;
         for (int i = 0; i < Q; ++i) s += vs.w[i] * a[i] * b[i];
@@ -54,6 +55,7 @@ void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vec
             if (n > 1e-9 * std::max(n0, 1.0)) {
                 for (int i = 0; i < Q; ++i) v[i] /= n;
                 rows.push_back(v);
+                if (degree) degree->push_back(deg);
             }
         }
     }
@@ -107,6 +109,11 @@ void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vec
                 for (int l = 0; l < K; ++l) s -= Cm[k * Q + i] * Ginv[k * K + l] * Cm[l * Q + j] * vs.w[j];
             P[i * Q + j] = s;
         }
+}
+
+void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
+                        std::vector<double>& P) {
+    build_moment_basis(vs, Phi, Ginv, P, nullptr);
 }
 
 // ------------------------------------------------------------ device kernels
@@ -286,6 +293,20 @@ __global__ void k_round_params(const float* __restrict__ p, float* __restrict__ 
 
 // data normalisation: per-feature mean square of z, and the weighted
 // mean square of the projected targets
+// target filter: R <- F R in place (F = Phi_K^T Phi_K W keeps the moments of
+// the selected degrees; identity when all are kept)
+__global__ void k_filter_targets(float* __restrict__ R, int64_t M, int Q, const float* __restrict__ F) {
+    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    float r[64];
+    for (int j = 0; j < Q; ++j) r[j] = R[s * Q + j];
+    for (int i = 0; i < Q; ++i) {
+        float a = 0.f;
+        for (int j = 0; j < Q; ++j) a += F[i * Q + j] * r[j];
+        R[s * Q + i] = a;
+    }
+}
+
 __global__ void k_data_stats(const float* __restrict__ Z, const float* __restrict__ R, int64_t M, int Q,
                              const float* __restrict__ P, const float* __restrict__ w, double* __restrict__ acc) {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -322,6 +343,7 @@ struct sllbm_trainer {
     cudaStream_t stream = nullptr;
     std::string last_error;
     std::vector<double> w, Phi, Ginv, P;
+    std::vector<int> degree;          // polynomial degree of each moment-basis row
     float *d_p = nullptr, *d_pr = nullptr, *d_grad = nullptr, *d_m = nullptr, *d_v = nullptr;
     float *d_P = nullptr, *d_w = nullptr, *d_loss = nullptr;
     float *d_X = nullptr, *d_Y = nullptr, *d_sin = nullptr;
@@ -383,7 +405,7 @@ int sllbm_train_create(const sllbm_ctx* ctx, const float* init_params, sllbm_tra
     tr->D = ctx->vs.D;
     tr->stream = ctx->stream;
     cudaSetDevice(tr->device);
-    build_moment_basis(ctx->vs, tr->Phi, tr->Ginv, tr->P);
+    build_moment_basis(ctx->vs, tr->Phi, tr->Ginv, tr->P, &tr->degree);
     tr->w = ctx->vs.w;
     const int n = n_params(tr->Q);
     auto bail = [&](int rc) {
@@ -426,8 +448,9 @@ int sllbm_train_destroy(sllbm_trainer* tr) {
 
 const char* sllbm_train_last_error(const sllbm_trainer* tr) { return tr ? tr->last_error.c_str() : ""; }
 
-int sllbm_train_set_data(sllbm_trainer* tr, const float* Z, const float* R, int64_t M, int32_t on_device) {
-    if (!tr || !Z || !R || M <= 0) return SLLBM_ERR_ARG;
+int sllbm_train_set_data(sllbm_trainer* tr, const float* Z, const float* R, int64_t M, int32_t max_degree,
+                         int32_t on_device) {
+    if (!tr || !Z || !R || M <= 0 || max_degree < 0 || tr->Q > 64) return SLLBM_ERR_ARG;
     cudaSetDevice(tr->device);
     const int Q = tr->Q;
     if (tr->d_X) cudaFree(tr->d_X);
@@ -444,6 +467,22 @@ int sllbm_train_set_data(sllbm_trainer* tr, const float* Z, const float* R, int6
     TCK(cudaMemcpyAsync(dZ, Z, sizeof(float) * M * Q, k, tr->stream));
     TCK(cudaMemcpyAsync(dR, R, sizeof(float) * M * Q, k, tr->stream));
     TCK(cudaMemsetAsync(acc, 0, sizeof(double) * (Q + 1), tr->stream));
+    if (max_degree > 0) {   // keep only the target moments of degree <= max_degree
+        std::vector<float> F(size_t(Q) * Q, 0.0f);
+        for (int i = 0; i < Q; ++i)
+            for (int j = 0; j < Q; ++j) {
+                double a = 0;
+                for (int k = 0; k < Q; ++k)
+                    if (tr->degree[k] <= max_degree) a += tr->Phi[k * Q + i] * tr->Phi[k * Q + j];
+                F[i * Q + j] = float(a * tr->w[j]);
+            }
+        float* dF = nullptr;
+        TCK(cudaMalloc(&dF, sizeof(float) * Q * Q));
+        TCK(cudaMemcpyAsync(dF, F.data(), sizeof(float) * Q * Q, cudaMemcpyHostToDevice, tr->stream));
+        k_filter_targets<<<unsigned((M + 127) / 128), 128, 0, tr->stream>>>(dR, M, Q, dF);
+        TCK(cudaStreamSynchronize(tr->stream));
+        cudaFree(dF);
+    }
     k_data_stats<<<unsigned((M + 255) / 256), 256, 0, tr->stream>>>(dZ, dR, M, Q, tr->d_P, tr->d_w, acc);
     std::vector<double> a(Q + 1);
     TCK(cudaMemcpyAsync(a.data(), acc, sizeof(double) * (Q + 1), cudaMemcpyDeviceToHost, tr->stream));

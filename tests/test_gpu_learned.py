@@ -121,7 +121,7 @@ def test_training_gradients_match_oracle(built_lib):
     R = r.normal(0, 2e-3, (M, Q)).astype(np.float32)
     p = _random_model(Q, 9).astype(np.float32)
     tr = Trainer(s, p)
-    tr.set_data(Z, R)
+    tr.set_data(Z, R, 0)
     s_in, sigma = tr.scales()
     # oracle definitions of the data scales
     rms = np.sqrt((Z.astype(np.float64) ** 2).mean(0))
@@ -153,6 +153,6 @@ def test_learned_beats_plain(built_lib):
     model = L.train(sim, Z, R, epochs=40)
     assert model["losses"][-1] < model["losses"][0]
     res = L.evaluate(model, ("isentropic_vortex", 0.75, 11), steps=20)
-    print(res)
+    print(model["losses"][0], model["losses"][-1], res)
     assert res["learned"]["err_f"] < res["plain"]["err_f"]
     assert res["learned"]["err_u"] < res["plain"]["err_u"]
