@@ -230,6 +230,30 @@ int sllbm_read_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int32_
  * rho <= 0 or T <= 0 or a non-finite value (out is still filled). */
 int sllbm_conservation(sllbm_ctx* ctx, double* out);
 
+/* Allocation-free variant of sllbm_conservation (the paper has no
+ * counterpart; this is a service of the library).  Same sums, same outputs,
+ * same SLLBM_ERR_UNSTABLE check, but the per-block partial sums live in a
+ * fixed 1 MiB device array compiled into the library instead of in scratch
+ * that the context allocates.  It is meant for callers that must not call
+ * cudaMalloc / cudaFree at the point where they check conservation: code
+ * whose device memory budget is owned by another framework's pool (a raw
+ * cudaMalloc there can fail or fragment it), or a time loop that cannot
+ * afford the device synchronisation a cudaFree implies.  The call allocates
+ * nothing; it writes D + 2 doubles to the caller's host buffer `out`.
+ *   - Limit: one partial per 256 nodes, at most 26,211 blocks in 3D
+ *     (6,710,016 nodes) and 32,764 blocks in 2D (8,387,584 nodes); larger
+ *     meshes get SLLBM_ERR_ARG with the limit in sllbm_last_error().
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - Every call on a device shares the one array and leaves the last
+ *     call's sums in it; the positivity flag is cleared at the start of each
+ *     call.  Calls that overlap on the GPU (different streams or contexts of
+ *     the same device at the same time) race on the array: serialise them.
+ *   - Every GPU that loads the library holds the array until the process
+ *     exits. */
+int sllbm_conservation_static(sllbm_ctx* ctx, double* out);
+
 /* ------------------------------------------------------------------ setup data */
 
 /* FP64 departure records as produced by the setup pass, one per

@@ -62,6 +62,7 @@ _SIGS = {
     "sllbm_step_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "sllbm_read_moments": (C.c_int, [_P, _P, _P, _P, C.c_int32]),
     "sllbm_conservation": (C.c_int, [_P, _P]),
+    "sllbm_conservation_static": (C.c_int, [_P, _P]),
     "sllbm_departure_records": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "sllbm_sync": (C.c_int, [_P]),
     "sllbm_stream": (C.c_void_p, [_P]),

@@ -1,4 +1,7 @@
 // Initialisation, state conversion, moment readout and FP64 conservation sums.
+#include <mutex>
+#include <string>
+
 #include "sllbm_internal.h"
 
 namespace sllbm {
@@ -198,3 +201,150 @@ INST(float)
 INST(double)
 
 }  // namespace sllbm
+
+// ====================================================================== allocation-free conservation
+// sllbm_conservation_static: the conservation sums of sllbm_conservation with
+// the per-block partial sums in a fixed device array compiled into this
+// library instead of scratch owned by the context, for callers that must not
+// allocate device memory themselves (see include/sllbm.h).
+namespace sllbm {
+
+// Layout (doubles): [0] positivity flag (as int), [8, 8 + D + 2) final sums,
+// [16, 16 + blocks (D + 2)) block partials.  Fixed size: 2^17 doubles (1 MiB)
+// on every device that loads the library, held until the process exits.
+constexpr int kStaticScratchDoubles = 1 << 17;
+constexpr int kStaticHead = 16;
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+
+// one block per 256 nodes (no grid-stride loop): partial sums of
+// (rho, rho u, 2 rho E) and the positivity flag
+template <int VS, typename real>
+__global__ void k_conserve_blocks(const typename Vec2<real>::T* __restrict__ fg, int64_t N,
+                                  const CollideConst<double> C, double* __restrict__ part, int* __restrict__ flag) {
+    using VSET = VelSet<VS>;
+    constexpr int D = VSET::D;
+    constexpr int K = D + 2;
+    __shared__ double sh[K][256];
+    double acc[K];
+    for (int k = 0; k < K; ++k) acc[k] = 0;
+    int bad = 0;
+    const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n < N) {
+        double r, j[3], e2;
+        node_moments<VS, real>(fg, N, n, C, r, j, e2);
+        acc[0] = r;
+        double U = 0;
+        for (int d = 0; d < D; ++d) {
+            acc[1 + d] = j[d];
+            U += (j[d] / r) * (j[d] / r);
+        }
+        acc[D + 1] = e2;
+        const double T = (e2 - r * U) / (2.0 * r * C.cv);
+        if (!(r > 0.0) || !(T > 0.0) || !isfinite(e2)) bad = 1;
+    }
+    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < K; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < K; ++k) part[blockIdx.x * K + k] = sh[k][0];
+    if (bad) atomicOr(flag, 1);
+}
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {};   // device address of g_static_scratch, per device ordinal
+
+template <typename real>
+int launch_conserve_blocks(int vs, const typename Vec2<real>::T* fg, int64_t N, const CollideConst<double>& C,
+                           double* part, int* flag, unsigned blocks, cudaStream_t s) {
+    switch (vs) {
+        case 0: k_conserve_blocks<0, real><<<blocks, 256, 0, s>>>(fg, N, C, part, flag); break;
+        case 1: k_conserve_blocks<1, real><<<blocks, 256, 0, s>>>(fg, N, C, part, flag); break;
+        case 2: k_conserve_blocks<2, real><<<blocks, 256, 0, s>>>(fg, N, C, part, flag); break;
+        case 3: k_conserve_blocks<3, real><<<blocks, 256, 0, s>>>(fg, N, C, part, flag); break;
+        default: return SLLBM_ERR_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+}  // namespace
+}  // namespace sllbm
+
+extern "C" int sllbm_conservation_static(sllbm_ctx* ctx, double* out) {
+    using namespace sllbm;
+    if (!ctx || !out) return SLLBM_ERR_ARG;
+    if (!ctx->initialised) {
+        ctx->last_error = "state not initialised";
+        return SLLBM_ERR_STATE;
+    }
+    const int dev = ctx->device;
+    if (dev < 0 || dev >= 64) {
+        ctx->last_error = "device ordinal out of range for the static scratch table";
+        return SLLBM_ERR_ARG;
+    }
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        ctx->last_error = "cudaSetDevice failed";
+        return SLLBM_ERR_CUDA;
+    }
+    const int64_t N = ctx->mesh.n_nodes;
+    const int D = ctx->mesh.D;
+    const int64_t blocks = (N + 255) / 256;
+    if (kStaticHead + blocks * (D + 2) > kStaticScratchDoubles) {
+        ctx->last_error = "mesh too large for the static scratch of sllbm_conservation_static: at most " +
+                          std::to_string(int64_t(kStaticScratchDoubles - kStaticHead) / (D + 2) * 256) +
+                          " nodes for D = " + std::to_string(D) + " (this mesh has " + std::to_string(N) + ")";
+        return SLLBM_ERR_ARG;
+    }
+    // first call on this device: look up the device address of the array
+    double* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+            if (e != cudaSuccess || !p) {
+                ctx->last_error = std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+                return SLLBM_ERR_CUDA;
+            }
+            g_static_ptr[dev] = p;
+        }
+        base = static_cast<double*>(g_static_ptr[dev]);
+    }
+    int* flag = reinterpret_cast<int*>(base);
+    double* sums = base + 8;
+    double* part = base + kStaticHead;
+    cudaStream_t s = ctx->stream;
+    if (cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) {
+        ctx->last_error = "cudaMemsetAsync failed";
+        return SLLBM_ERR_CUDA;
+    }
+    const int c = ctx->cur;
+    int rc = ctx->precision == SLLBM_FP64
+                 ? launch_conserve_blocks<double>(ctx->velset, (const double2*)ctx->fg[c], N, ctx->cc64, part, flag,
+                                                  unsigned(blocks), s)
+                 : launch_conserve_blocks<float>(ctx->velset, (const float2*)ctx->fg[c], N, ctx->cc64, part, flag,
+                                                 unsigned(blocks), s);
+    if (rc == SLLBM_OK) {
+        k_reduce_parts<<<1, 32, 0, s>>>(part, int(blocks), D + 2, sums);
+        if (cudaGetLastError() != cudaSuccess) rc = SLLBM_ERR_CUDA;
+    }
+    if (rc) {
+        ctx->last_error = "conservation launch failed";
+        return rc;
+    }
+    int hflag = 0;
+    if (cudaMemcpyAsync(out, sums, sizeof(double) * (D + 2), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        ctx->last_error = "copy of the conservation sums failed";
+        return SLLBM_ERR_CUDA;
+    }
+    if (hflag) {
+        ctx->last_error = "non-positive density or temperature, or non-finite state";
+        return SLLBM_ERR_UNSTABLE;
+    }
+    return SLLBM_OK;
+}
