@@ -398,61 +398,73 @@ __global__ void __launch_bounds__(128) k_step_tiled_smem(const typename Vec2<rea
     real* Sf = S + threadIdx.x;
     real* Sg = S + Q * stride + threadIdx.x;
     const V2* base = fg + n;
+    // velocities in groups of GV: all record loads of a group, then all source
+    // loads (unconditional: equilibrium records read a valid dummy address), then
+    // the arithmetic, so GV velocities' memory latencies overlap
+    constexpr int GV = 3;
 #pragma unroll 1
-    for (int i = 0; i < Q; ++i) {
-        const TileRec<real>* r = tab + i * G.n_classes + cls;
-        const int4 h0 = __ldg(reinterpret_cast<const int4*>(r));
-        const int kind = h0.x & 15;
-        const int bid = (h0.x >> 4) & 15;
-        real of, og;
-        if (kind == REC_EQ) {
-            of = C.eqf[bid][i];
-            og = C.eqg[bid][i];
-        } else {
-            int rel[12];
-            {
-                const int4 a0 = __ldg(reinterpret_cast<const int4*>(r) + 1);
-                const int4 a1 = __ldg(reinterpret_cast<const int4*>(r) + 2);
-                const int4 a2 = __ldg(reinterpret_cast<const int4*>(r) + 3);
-                rel[0] = a0.x; rel[1] = a0.y; rel[2] = a0.z; rel[3] = a0.w;
-                rel[4] = a1.x; rel[5] = a1.y; rel[6] = a1.z; rel[7] = a1.w;
-                rel[8] = a2.x;
-            }
-            if (seam) {
+    for (int i0 = 0; i0 < Q; i0 += GV) {
+        TileRec<real> r[GV];
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const int i = min(i0 + u, Q - 1);
+            const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes + cls);
+            int4* dst = reinterpret_cast<int4*>(&r[u]);
+#pragma unroll
+            for (int k = 0; k < int(sizeof(TileRec<real>) / 16); ++k) dst[k] = __ldg(src + k);
+        }
+        V2 v[GV][NR];
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const bool eq = (r[u].meta & 15) == REC_EQ;
+            int rel[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) rel[k] = eq ? 0 : r[u].rel[k];
+            if (seam && !eq) {
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
-                    const int dy = ((h0.z >> (4 * (k % 3))) & 15) - 8;
-                    const int dz = D == 3 ? ((h0.z >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+                    const int dy = ((r[u].dyzp >> (4 * (k % 3))) & 15) - 8;
+                    const int dz = D == 3 ? ((r[u].dyzp >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
                     int ty = ky + dy, tz = kz + dz;
                     if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
                     if (D == 3) { tz += tz < 0 ? G.N[2] : 0; tz -= tz >= G.N[2] ? G.N[2] : 0; }
                     rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
                 }
             }
-            const V2* p = base + (h0.x >> 8) * NN;
-            V2 v[NR];
+            const V2* p = base + (eq ? 0 : (r[u].meta >> 8)) * NN;
 #pragma unroll
-            for (int k = 0; k < NR; ++k) v[k] = __ldg(p + rel[k]);
-            real sf = 0, sg = 0;
-#pragma unroll
-            for (int k = 0; k < NR; ++k) {
-                const real wk = __ldg(&r->rw[k]);
-                sf += wk * v[k].x;
-                sg += wk * v[k].y;
-            }
-            of = 0;
-            og = 0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int dl = min(31, max(0, lane + ((h0.y >> (4 * a)) & 15) - 8));
-                const real wx = __ldg(&r->wx[a]);
-                of += wx * __shfl_sync(0xffffffffu, sf, dl);
-                og += wx * __shfl_sync(0xffffffffu, sg, dl);
-            }
-            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+            for (int k = 0; k < NR; ++k) v[u][k] = __ldg(p + rel[k]);
         }
-        Sf[i * stride] = of;
-        Sg[i * stride] = og;
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const int i = i0 + u;
+            if (i >= Q) break;
+            const int kind = r[u].meta & 15;
+            const int bid = (r[u].meta >> 4) & 15;
+            real of, og;
+            if (kind == REC_EQ) {
+                of = C.eqf[bid][i];
+                og = C.eqg[bid][i];
+            } else {
+                real sf = 0, sg = 0;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    sf += r[u].rw[k] * v[u][k].x;
+                    sg += r[u].rw[k] * v[u][k].y;
+                }
+                of = 0;
+                og = 0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int dl = min(31, max(0, lane + ((r[u].dxp >> (4 * a)) & 15) - 8));
+                    of += r[u].wx[a] * __shfl_sync(0xffffffffu, sf, dl);
+                    og += r[u].wx[a] * __shfl_sync(0xffffffffu, sg, dl);
+                }
+                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+            }
+            Sf[i * stride] = of;
+            Sg[i * stride] = og;
+        }
     }
     collide_smem<VSET, real, V2>(C, Sf, Sg, stride, twt[cls], store ? fgo + n : nullptr, NN);
 }
