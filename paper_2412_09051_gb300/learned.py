@@ -156,9 +156,12 @@ def generate_pairs(cases, fine_cells=128, snapshots=8, stride=4, spinup=4):
     return np.concatenate(Zs), np.concatenate(Rs)
 
 
-def train(sim, Z, R, epochs=60, batch=512, lr=2e-3, seed=0, max_degree=3):
+def train(sim, Z, R, epochs=60, batch=512, lr=2e-3, seed=0, max_degree=3, apply_scale=0.5):
     """Train on (Z, R); the target keeps its stress and heat-flux moments
-    (degree <= max_degree) so the network does not fit high-order noise."""
+    (degree <= max_degree) so the network does not fit high-order noise.
+    The installed correction is apply_scale times the one-step prediction:
+    a full-strength correction overshoots in multi-step rollouts (chosen on
+    validation vortex / shear-layer cases that the tests do not evaluate)."""
     r = np.random.Generator(np.random.Philox(seed))
     perm = r.permutation(len(Z))
     tr = Trainer(sim, init_params(sim.Q, seed))
@@ -170,7 +173,7 @@ def train(sim, Z, R, epochs=60, batch=512, lr=2e-3, seed=0, max_degree=3):
     w, b = tr.export()
     s_in, sigma = tr.scales()
     tr.close()
-    return dict(w=w, b=b, s_in=s_in, sigma=sigma, losses=losses)
+    return dict(w=w, b=b, s_in=s_in, sigma=sigma * apply_scale, losses=losses)
 
 
 def evaluate(model, case, fine_cells=128, steps=20, spinup=4):
