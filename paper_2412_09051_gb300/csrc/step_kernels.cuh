@@ -501,6 +501,159 @@ int launch_step_tiled(const StepLaunch<real>& L) {
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
+// ------------------------------------------------------------ gather, state in shared memory
+// One departure record per (velocity, node) as in k_step_gather, with the
+// node state in shared memory, runtime velocity loops and the records and
+// source loads of GV velocities issued together (GV = 2 for up to 16 taps).
+template <int VS, int P, typename real>
+__global__ void __launch_bounds__(128) k_step_gather_smem(const typename Vec2<real>::T* __restrict__ fg,
+                                                          typename Vec2<real>::T* __restrict__ fgo,
+                                                          const int32_t* __restrict__ code,
+                                                          const real* __restrict__ gxi, const real* __restrict__ twt,
+                                                          const StepGeom G, const CollideConst<real> C) {
+    using VSET = VelSet<VS>;
+    using V2 = typename Vec2<real>::T;
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    constexpr int T1 = P + 1;
+    constexpr int NT = D == 3 ? T1 * T1 * T1 : T1 * T1;
+    constexpr int GV = NT <= 16 ? 2 : 1;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    real* S = reinterpret_cast<real*>(dyn_smem);
+    const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n >= G.n_nodes) return;                   // no block barrier in this kernel
+    const int64_t NN = G.n_nodes;
+    const int N0 = G.N[0], N1 = G.N[1];
+    const int C0 = G.cells[0], C1 = G.cells[1];
+    real xh[T1], inv_den[T1];
+#pragma unroll
+    for (int a = 0; a <= P; ++a) xh[a] = real(-cospi(double(a) / P));
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+        double den = 1.0;
+        for (int m = 0; m <= P; ++m)
+            if (m != a) den *= (-cospi(double(a) / P) + cospi(double(m) / P));
+        inv_den[a] = real(1.0 / den);
+    }
+    const int stride = blockDim.x;
+    real* Sf = S + threadIdx.x;
+    real* Sg = S + Q * stride + threadIdx.x;
+#pragma unroll 1
+    for (int i0 = 0; i0 < Q; i0 += GV) {
+        int cw[GV];
+        real xr[GV][D];
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const int i = min(i0 + u, Q - 1);
+            cw[u] = __ldg(code + int64_t(i) * NN + n);
+#pragma unroll
+            for (int d = 0; d < D; ++d) xr[u][d] = __ldg(gxi + (int64_t(i) * D + d) * NN + n);
+        }
+        V2 v[GV][NT];
+        real wt[GV][D][T1];
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const int i = min(i0 + u, Q - 1);
+            const int kind = (cw[u] >> 24) & 15;
+            const bool eq = kind == REC_EQ;
+            const int cell = eq ? 0 : (cw[u] & 0xFFFFFF);
+            int cc[3];
+            cc[0] = cell % C0;
+            cc[1] = (cell / C0) % C1;
+            cc[2] = cell / (C0 * C1);
+            int64_t off[3][T1];
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                lagrange_w<P, real>(xr[u][d], xh, inv_den, wt[u][d]);
+                const int64_t st = d == 0 ? 1 : (d == 1 ? int64_t(N0) : int64_t(N0) * N1);
+#pragma unroll
+                for (int a = 0; a <= P; ++a) {
+                    int kk = cc[d] * P + a;
+                    if (G.periodic[d]) kk = wrapi(kk, G.N[d]);
+                    off[d][a] = kk * st;
+                }
+            }
+            const int src = eq ? 0 : ((kind == REC_BB || kind == REC_BB_ISO) ? C.opp[i] : i);
+            const V2* p = fg + int64_t(src) * NN;
+            if (D == 2) {
+#pragma unroll
+                for (int b = 0; b <= P; ++b)
+#pragma unroll
+                    for (int a = 0; a <= P; ++a) v[u][b * T1 + a] = __ldg(p + off[0][a] + off[1][b]);
+            } else {
+#pragma unroll
+                for (int c3 = 0; c3 <= P; ++c3)
+#pragma unroll
+                    for (int b = 0; b <= P; ++b)
+#pragma unroll
+                        for (int a = 0; a <= P; ++a)
+                            v[u][(c3 * T1 + b) * T1 + a] = __ldg(p + off[0][a] + off[1][b] + off[2][c3]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const int i = i0 + u;
+            if (i >= Q) break;
+            const int kind = (cw[u] >> 24) & 15;
+            const int bid = (cw[u] >> 28) & 15;
+            real of = 0, og = 0;
+            if (kind == REC_EQ) {
+                of = C.eqf[bid][i];
+                og = C.eqg[bid][i];
+            } else {
+                if (D == 2) {
+#pragma unroll
+                    for (int b = 0; b <= P; ++b) {
+                        real tf = 0, tg = 0;
+#pragma unroll
+                        for (int a = 0; a <= P; ++a) {
+                            tf += wt[u][0][a] * v[u][b * T1 + a].x;
+                            tg += wt[u][0][a] * v[u][b * T1 + a].y;
+                        }
+                        of += wt[u][1][b] * tf;
+                        og += wt[u][1][b] * tg;
+                    }
+                } else {
+#pragma unroll
+                    for (int c3 = 0; c3 <= P; ++c3) {
+                        real uf = 0, ug = 0;
+#pragma unroll
+                        for (int b = 0; b <= P; ++b) {
+                            real tf = 0, tg = 0;
+#pragma unroll
+                            for (int a = 0; a <= P; ++a) {
+                                tf += wt[u][0][a] * v[u][(c3 * T1 + b) * T1 + a].x;
+                                tg += wt[u][0][a] * v[u][(c3 * T1 + b) * T1 + a].y;
+                            }
+                            uf += wt[u][1][b] * tf;
+                            ug += wt[u][1][b] * tg;
+                        }
+                        of += wt[u][2][c3] * uf;
+                        og += wt[u][2][c3] * ug;
+                    }
+                }
+                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+            }
+            Sf[i * stride] = of;
+            Sg[i * stride] = og;
+        }
+    }
+    collide_smem<VSET, real, V2>(C, Sf, Sg, stride, twt[n], fgo + n, int(NN));
+}
+
+template <int VS, int P, typename real>
+int launch_step_gather_smem(const StepLaunch<real>& L) {
+    constexpr int Q = VelSet<VS>::Q;
+    const int bs = 128;
+    const int64_t grid = (L.G.n_nodes + bs - 1) / bs;
+    const size_t smem = sizeof(real) * 2 * Q * bs;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_step_gather_smem<VS, P, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_step_gather_smem<VS, P, real><<<unsigned(grid), bs, smem, L.stream>>>(L.fg, L.fgo, L.code, L.gxi, L.tw, L.G,
+                                                                          *L.C);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
 template <int VS, int P, typename real>
 int launch_step_structured(const StepLaunch<real>& L) {
     const int bs = 128;
@@ -520,7 +673,8 @@ int launch_step_gather(const StepLaunch<real>& L) {
 
 #define SLLBM_EXTERN_STEP(VS, P, real)                                                   \
     extern template int launch_step_structured<VS, P, real>(const StepLaunch<real>&);    \
-    extern template int launch_step_gather<VS, P, real>(const StepLaunch<real>&);
+    extern template int launch_step_gather<VS, P, real>(const StepLaunch<real>&);        \
+    extern template int launch_step_gather_smem<VS, P, real>(const StepLaunch<real>&);
 #define SLLBM_EXTERN_TILED(VS, real)                                              \
     extern template int launch_step_tiled<VS, real, 0>(const StepLaunch<real>&);  \
     extern template int launch_step_tiled_smem<VS, real>(const StepLaunch<real>&);
@@ -536,6 +690,7 @@ int launch_step_gather(const StepLaunch<real>& L) {
 
 #define SLLBM_INSTANTIATE_STEP(VS, P, real)                                              \
     template int launch_step_structured<VS, P, real>(const StepLaunch<real>&);           \
-    template int launch_step_gather<VS, P, real>(const StepLaunch<real>&);
+    template int launch_step_gather<VS, P, real>(const StepLaunch<real>&);               \
+    template int launch_step_gather_smem<VS, P, real>(const StepLaunch<real>&);
 
 }  // namespace sllbm

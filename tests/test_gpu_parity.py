@@ -99,14 +99,15 @@ def test_setup_matches_oracle(built_lib, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("mode", [0, 1, 3, 4])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5])
 def test_steps_match_oracle(built_lib, name, mode):
     """Every streaming mode (0 auto: warp-tiled with shared-memory state where
-    eligible, 1 gather, 3 one thread per node with class records, 4 warp-tiled
-    with register state) against the oracle."""
+    eligible, 1 gather with shared-memory state, 3 one thread per node with
+    class records, 4 warp-tiled with register state, 5 gather with register
+    state) against the oracle."""
     cfg, prec, mesh, xi, w, opp, par, rec = _oracle(name)
-    if mode != 0 and mesh.kind == 3:
-        pytest.skip("curved mesh runs gather mode already")
+    if mode not in (0, 5) and mesh.kind == 3:
+        pytest.skip("curved mesh runs the gather modes (0 = 1)")
     sim = _sim(cfg, prec, mode)
     rho, u, T = initial_fields(cfg, mesh.X)
     sim.init_state(rho, u, T)
@@ -128,13 +129,14 @@ def test_steps_match_oracle(built_lib, name, mode):
     sim.close()
 
 
-@pytest.mark.parametrize("modes", [(2, 1), (2, 3), (2, 4)])
+@pytest.mark.parametrize("modes", [(2, 1), (2, 3), (2, 4), (1, 5)])
 def test_streaming_modes_agree(built_lib, modes):
     """The streaming modes compute the same step (FP32, channel with walls)."""
     cfg = get_config("channel", cells=(4, 6, 3))
     a, b = _sim(cfg, "fp32", modes[0]), _sim(cfg, "fp32", modes[1])
     if modes[0] == 2:
         assert a.info.stream_mode == 2          # the warp-tiled kernel is eligible here
+    assert b.info.stream_mode == modes[1]
     X = a.node_coords()
     rho, u, T = initial_fields(cfg, X)
     for s in (a, b):
