@@ -248,7 +248,7 @@ def run_gpu(args, ws, rank, local):
                          "peak_source": f"{psrc} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "kernel": {2: "k_step_tiled_smem", 4: "k_step_tiled", 3: "k_step_structured",
-                                    1: "k_step_gather_smem", 5: "k_step_gather"}.get(
+                                    1: "k_step_gather", 5: "k_step_gather_smem"}.get(
                              sim.info.stream_mode, "k_step") + f"<{cfg['velset']}>"},
             "e2e": {"value": round(N / e2e_s / 1e6, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -102,8 +102,8 @@ extern "C" {
                            and w_i rho0 T0 (2 c_v - D) (g); compensated FP32 moments  */
 
 #define SLLBM_STREAM_AUTO        0  /* structured kernel where cells are axis-aligned, else gather */
-#define SLLBM_STREAM_GATHER      1  /* one departure record per (node, velocity); node state in
-                                       shared memory                                             */
+#define SLLBM_STREAM_GATHER      1  /* one departure record per (node, velocity), node state in
+                                       registers                                                 */
 #define SLLBM_STREAM_STRUCTURED  2  /* one record per (velocity, translation class of nodes); the
                                        warp-tiled kernel with the node state in shared memory
                                        where eligible (p = 2, periodic x, taps within +-3 nodes),
@@ -111,7 +111,7 @@ extern "C" {
 #define SLLBM_STREAM_STRUCTURED_NODE 3  /* class records, always one thread per node              */
 #define SLLBM_STREAM_TILED_REG   4  /* warp-tiled kernel with the node state in registers (the
                                        kernel that carries the learned collision)                */
-#define SLLBM_STREAM_GATHER_REG  5  /* per-record gather with the node state in registers        */
+#define SLLBM_STREAM_GATHER_SMEM 5  /* per-record gather with the node state in shared memory    */
 
 /* ------------------------------------------------------------------ descriptors */
 typedef struct {

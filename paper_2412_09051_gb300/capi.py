@@ -17,7 +17,7 @@ ERRORS = {-1: "SLLBM_ERR_ARG", -2: "SLLBM_ERR_CUDA", -3: "SLLBM_ERR_ARCH", -4: "
 MESH = dict(box=0, channel=1, mixing=2, naca=3)
 VELSET = dict(D2Q9=0, D2Q19=1, D2Q25=2, D3Q45=3)
 FP64, FP32 = 0, 1
-STREAM_AUTO, STREAM_GATHER, STREAM_STRUCTURED, STREAM_STRUCTURED_NODE, STREAM_TILED_REG, STREAM_GATHER_REG = \
+STREAM_AUTO, STREAM_GATHER, STREAM_STRUCTURED, STREAM_STRUCTURED_NODE, STREAM_TILED_REG, STREAM_GATHER_SMEM = \
     0, 1, 2, 3, 4, 5
 
 

@@ -281,7 +281,7 @@ void build_tile_table(const sllbm_ctx* c, const std::vector<Rec64>& rec, std::ve
 template <typename real>
 int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const int vs = ctx->velset, p = ctx->mesh.p;
-    const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_REG;
+    const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_SMEM;
     if (st && ctx->tiled) {
         const bool reg = ctx->mode == SLLBM_STREAM_TILED_REG;
         switch (vs) {
@@ -291,11 +291,11 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
             case 3: return reg ? launch_step_tiled<3, real>(L) : launch_step_tiled_smem<3, real>(L);
         }
     }
-    const bool greg = ctx->mode == SLLBM_STREAM_GATHER_REG;
+    const bool gsm = ctx->mode == SLLBM_STREAM_GATHER_SMEM;
 #define CASE(VS, P)                                                                                    \
     if (vs == VS && p == P)                                                                            \
         return st ? launch_step_structured<VS, P, real>(L)                                             \
-                  : (greg ? launch_step_gather<VS, P, real>(L) : launch_step_gather_smem<VS, P, real>(L));
+                  : (gsm ? launch_step_gather_smem<VS, P, real>(L) : launch_step_gather<VS, P, real>(L));
     CASE(0, 2)
     CASE(1, 2)
     CASE(1, 3)
@@ -441,7 +441,7 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
         return bail(SLLBM_ERR_ARG);
     }
     if (mode != SLLBM_STREAM_STRUCTURED && mode != SLLBM_STREAM_GATHER && mode != SLLBM_STREAM_STRUCTURED_NODE &&
-        mode != SLLBM_STREAM_TILED_REG && mode != SLLBM_STREAM_GATHER_REG) {
+        mode != SLLBM_STREAM_TILED_REG && mode != SLLBM_STREAM_GATHER_SMEM) {
         ctx->last_error = "bad stream mode";
         return bail(SLLBM_ERR_ARG);
     }
@@ -521,7 +521,7 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
             G.ncls[d] = d < D ? (m.periodic[d] ? m.p : m.N[d]) : 1;
             G.n_classes *= G.ncls[d];
         }
-        const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_REG;
+        const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_SMEM;
         ctx->n_rec_units = st ? G.n_classes : N;
         const int64_t U = ctx->n_rec_units;
         // ---- FP64 trace
@@ -965,7 +965,7 @@ int sllbm_departure_records(sllbm_ctx* ctx, int32_t* kind, int32_t* src, int32_t
     std::vector<Rec64> rec(size_t(U * Q));
     CK(cudaMemcpyAsync(rec.data(), ctx->rec64, sizeof(Rec64) * U * Q, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_REG;
+    const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_SMEM;
     for (int i = 0; i < Q; ++i)
         for (int64_t n = 0; n < N; ++n) {
             int k[3] = {0, 0, 0};

@@ -272,13 +272,13 @@ namespace sllbm {
 // deviations of the thread's node sit at Sf[i * stride], Sg[i * stride]; the
 // post-collision pair of velocity i is written to out[i * NN] (out == nullptr:
 // no store).
-template <class VSET, typename real, typename V2>
-__device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* Sf, real* Sg, int stride, real Tw,
+template <class VSET, typename real, typename V2, int stride>
+__device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* Sf, real* Sg, real Tw,
                                              V2* out, int NN) {
     constexpr int Q = VSET::Q;
     constexpr int D = VSET::D;
     Acc<real> arho, aj0, aj1, aj2, ae;
-#pragma unroll 3
+#pragma unroll
     for (int i = 0; i < Q; ++i) {
         const real f = Sf[i * stride], g = Sg[i * stride];
         arho.add(f);
@@ -308,7 +308,7 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
     if (!(Tw != Tw)) {   // isothermal wall correction (Eq. thermalBC)
         const real tw = Tw - real(1);
         const real rT0 = rho * (real(1) + t), rT1 = rho * (real(1) + tw);
-#pragma unroll 3
+#pragma unroll
         for (int i = 0; i < Q; ++i) {
             real cd;
             const real a0 = p1(i, t, cd), a1 = p1(i, tw, cd);
@@ -326,7 +326,7 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
     const real rhoT = rho * T;
     const real rhoT_d = rho_d + rho * t;
     real q0 = 0, q1 = 0, q2 = 0;
-#pragma unroll 3
+#pragma unroll
     for (int i = 0; i < Q; ++i) {
         real cd;
         const real P1 = p1(i, t, cd);
@@ -352,7 +352,7 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
         q1 *= a;
         q2 *= a;
         if (out) {
-#pragma unroll 3
+#pragma unroll
             for (int i = 0; i < Q; ++i) {
                 real dq = C.xi[i][0] * q0 + C.xi[i][1] * q1;
                 if (D == 3) dq += C.xi[i][2] * q2;

@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
 // compact kernel body and a small register footprint, so more warps per SM
 // hide the load latency.  Warps are independent (no block barrier).
 template <int VS, typename real>
-__global__ void __launch_bounds__(128) k_step_tiled_smem(const typename Vec2<real>::T* __restrict__ fg,
+__global__ void __launch_bounds__(128, 4) k_step_tiled_smem(const typename Vec2<real>::T* __restrict__ fg,
                                                          typename Vec2<real>::T* __restrict__ fgo,
                                                          const TileRec<real>* __restrict__ tab,
                                                          const real* __restrict__ twt, const StepGeom G,
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(128) k_step_tiled_smem(const typename Vec2<rea
     const bool py = G.periodic[1] != 0;
     const int cls = (kx & 1) + G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));
     const bool seam = (py && (ky < 3 || ky >= N1 - 3)) || (D == 3 && (kz < 3 || kz >= G.N[2] - 3));
-    const int stride = blockDim.x;
+    constexpr int stride = 128;                  // the launch block size
     real* Sf = S + threadIdx.x;
     real* Sg = S + Q * stride + threadIdx.x;
     const V2* base = fg + n;
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(128) k_step_tiled_smem(const typename Vec2<rea
             Sg[i * stride] = og;
         }
     }
-    collide_smem<VSET, real, V2>(C, Sf, Sg, stride, twt[cls], store ? fgo + n : nullptr, NN);
+    collide_smem<VSET, real, V2, 128>(C, Sf, Sg, twt[cls], store ? fgo + n : nullptr, NN);
 }
 
 template <int VS, typename real>
@@ -506,7 +506,7 @@ int launch_step_tiled(const StepLaunch<real>& L) {
 // node state in shared memory, runtime velocity loops and the records and
 // source loads of GV velocities issued together (GV = 2 for up to 16 taps).
 template <int VS, int P, typename real>
-__global__ void __launch_bounds__(128) k_step_gather_smem(const typename Vec2<real>::T* __restrict__ fg,
+__global__ void __launch_bounds__(128, 4) k_step_gather_smem(const typename Vec2<real>::T* __restrict__ fg,
                                                           typename Vec2<real>::T* __restrict__ fgo,
                                                           const int32_t* __restrict__ code,
                                                           const real* __restrict__ gxi, const real* __restrict__ twt,
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(128) k_step_gather_smem(const typename Vec2<re
             if (m != a) den *= (-cospi(double(a) / P) + cospi(double(m) / P));
         inv_den[a] = real(1.0 / den);
     }
-    const int stride = blockDim.x;
+    constexpr int stride = 128;                  // the launch block size
     real* Sf = S + threadIdx.x;
     real* Sg = S + Q * stride + threadIdx.x;
 #pragma unroll 1
@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(128) k_step_gather_smem(const typename Vec2<re
             Sg[i * stride] = og;
         }
     }
-    collide_smem<VSET, real, V2>(C, Sf, Sg, stride, twt[n], fgo + n, int(NN));
+    collide_smem<VSET, real, V2, 128>(C, Sf, Sg, twt[n], fgo + n, int(NN));
 }
 
 template <int VS, int P, typename real>

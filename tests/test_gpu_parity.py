@@ -102,9 +102,9 @@ def test_setup_matches_oracle(built_lib, name):
 @pytest.mark.parametrize("mode", [0, 1, 3, 4, 5])
 def test_steps_match_oracle(built_lib, name, mode):
     """Every streaming mode (0 auto: warp-tiled with shared-memory state where
-    eligible, 1 gather with shared-memory state, 3 one thread per node with
-    class records, 4 warp-tiled with register state, 5 gather with register
-    state) against the oracle."""
+    eligible, 1 gather with register state, 3 one thread per node with
+    class records, 4 warp-tiled with register state, 5 gather with
+    shared-memory state) against the oracle."""
     cfg, prec, mesh, xi, w, opp, par, rec = _oracle(name)
     if mode not in (0, 5) and mesh.kind == 3:
         pytest.skip("curved mesh runs the gather modes (0 = 1)")
