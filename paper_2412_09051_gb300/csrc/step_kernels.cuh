@@ -416,10 +416,12 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem(const typename Vec2<
         V2 v[GV][NR];
 #pragma unroll
         for (int u = 0; u < GV; ++u) {
+            // equilibrium records carry zero offsets and their own velocity as
+            // source, so their (unused) loads read a valid row
             const bool eq = (r[u].meta & 15) == REC_EQ;
             int rel[NR];
 #pragma unroll
-            for (int k = 0; k < NR; ++k) rel[k] = eq ? 0 : r[u].rel[k];
+            for (int k = 0; k < NR; ++k) rel[k] = r[u].rel[k];
             if (seam && !eq) {
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
@@ -431,7 +433,7 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem(const typename Vec2<
                     rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
                 }
             }
-            const V2* p = base + (eq ? 0 : (r[u].meta >> 8)) * NN;
+            const V2* p = base + (r[u].meta >> 8) * NN;
 #pragma unroll
             for (int k = 0; k < NR; ++k) v[u][k] = __ldg(p + rel[k]);
         }
@@ -456,7 +458,9 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem(const typename Vec2<
                 og = 0;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const int dl = min(31, max(0, lane + ((r[u].dxp >> (4 * a)) & 15) - 8));
+                    // source lane; halo lanes may point outside the warp (the
+                    // shuffle wraps) but their results are never stored
+                    const int dl = lane + ((r[u].dxp >> (4 * a)) & 15) - 8;
                     of += r[u].wx[a] * __shfl_sync(0xffffffffu, sf, dl);
                     og += r[u].wx[a] * __shfl_sync(0xffffffffu, sg, dl);
                 }
