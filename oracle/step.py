@@ -29,13 +29,14 @@ from .equilibrium import feq, geq
 
 
 class Params:
-    def __init__(self, dt, gamma=1.4, Pr=1.0, mu_ref=1e-3, T_ref=1.0, mu_exp=0.0, bcs=None):
+    def __init__(self, dt, gamma=1.4, Pr=1.0, mu_ref=1e-3, T_ref=1.0, mu_exp=0.0, bcs=None, force=None):
         self.dt = float(dt)
         self.gamma = float(gamma)
         self.cv = 1.0 / (self.gamma - 1.0)
         self.Pr = float(Pr)
         self.mu_ref, self.T_ref, self.mu_exp = float(mu_ref), float(T_ref), float(mu_exp)
         self.bcs = bcs or [dict(kind=0, rho=1.0, u=(0.0, 0.0, 0.0), T=1.0)] * 2
+        self.force = None if force is None else np.asarray(force, dtype=np.float64)
 
 
 def init_equilibrium(rho, u, T, xi, w, cv):
@@ -132,7 +133,19 @@ def collide(fs, gs, xi, w, par):
     gstar = w[:, None] * (xi @ (2.0 * q).T)
     f1 = fs - om[None, :] * (fs - fe)
     g1 = gs - om[None, :] * (gs - ge) + (om - om_pr)[None, :] * gstar
+    if par.force is not None and np.any(par.force != 0.0):
+        # Kupershtokh exact-difference forcing after the collision (Sec. 4.3):
+        # delta f_i = f_i^eq(rho, u + du, T) - f_i^eq(rho, u, T), du = F dt / rho
+        du = par.force[None, : xi.shape[1]] * par.dt / rho[:, None]
+        f1 = f1 + feq(rho, u + du, T, xi, w) - fe
     return f1, g1
+
+
+def rescale_mass(f, g, target_mass):
+    """Sec. 4.3: scale every population by target / current total mass (the
+    nodal sum of rho); velocity and temperature are unchanged."""
+    s = target_mass / f.sum()
+    return f * s, g * s
 
 
 def step(mesh, rec, f, g, xi, w, par, Tw=None, mlp=None):

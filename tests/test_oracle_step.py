@@ -225,3 +225,55 @@ def test_couette_temperature_rise_scales_with_prandtl():
     assert uerr < 0.03                                  # linear velocity profile
     assert abs(rise05 / rise1 - 0.5) < 0.025
     assert abs(rise1 - exact1) < 0.15 * exact1
+
+
+def test_forcing_moments():
+    """Kupershtokh forcing (Sec. 4.3): mass unchanged, momentum raised by F dt,
+    total energy by the kinetic work rho(|u + du|^2 - |u|^2), temperature unchanged."""
+    xi, w, _ = velocity_set("D3Q45")
+    F = np.array([0.03, -0.01, 0.02])
+    par0 = st.Params(dt=0.01, Pr=0.7, mu_ref=0.02)
+    parF = st.Params(dt=0.01, Pr=0.7, mu_ref=0.02, force=F)
+    f, g = random_neq_state(xi, w, parF.cv, 16, seed=4)
+    a0, b0 = st.collide(f, g, xi, w, par0)
+    a1, b1 = st.collide(f, g, xi, w, parF)
+    rho, u, T = st.moments(f, g, xi, parF.cv)
+    df = a1 - a0
+    assert np.abs(b1 - b0).max() == 0.0
+    assert np.abs(df.sum(0)).max() < 1e-14
+    assert np.abs(xi.T @ df - (F * parF.dt)[:, None]).max() < 1e-14
+    du = F[None] * parF.dt / rho[:, None]
+    e = (xi ** 2).sum(1) @ df
+    assert np.abs(e - rho * (((u + du) ** 2).sum(1) - (u ** 2).sum(1))).max() < 1e-13
+    _, _, T1 = st.moments(a1, b1, xi, parF.cv)
+    _, _, T0 = st.moments(a0, b0, xi, parF.cv)
+    assert np.abs(T1 - T0).max() < 1e-13
+
+
+def test_uniform_acceleration():
+    """A uniform state under a constant force density in a periodic box
+    accelerates as u(t) = u0 + F t / rho and keeps its temperature."""
+    F = np.array([0.02, 0.005])
+    cfg = box_cfg(cells=(3, 3), L=(1.0, 1.0), dt=0.02)
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    par.force = F
+    N = mesh.n_nodes
+    rho0, u0, T0 = 1.1, np.array([0.3, -0.2]), 0.9
+    f, g = st.init_equilibrium(np.full(N, rho0), np.tile(u0, (N, 1)), np.full(N, T0), xi, w, par.cv)
+    n = 7
+    for _ in range(n):
+        f, g = st.step(mesh, rec, f, g, xi, w, par)
+    r, u, T = st.moments(f, g, xi, par.cv)
+    assert np.abs(u - (u0 + n * F * par.dt / rho0)).max() < 1e-13
+    assert np.abs(T - T0).max() < 1e-13 and np.abs(r - rho0).max() < 1e-13
+
+
+def test_mass_rescaling():
+    xi, w, _ = velocity_set("D2Q19")
+    par = st.Params(dt=0.01)
+    f, g = random_neq_state(xi, w, par.cv, 12, seed=8)
+    f1, g1 = st.rescale_mass(f, g, 11.5)
+    r0, u0, T0 = st.moments(f, g, xi, par.cv)
+    r1, u1, T1 = st.moments(f1, g1, xi, par.cv)
+    assert abs(r1.sum() - 11.5) < 1e-12
+    assert np.abs(u1 - u0).max() < 1e-14 and np.abs(T1 - T0).max() < 1e-13
