@@ -221,6 +221,37 @@ int sllbm_step(sllbm_ctx* ctx, int64_t n);
 /* Number of steps taken since the last init / set_state. */
 int sllbm_step_count(const sllbm_ctx* ctx, int64_t* out);
 
+/* ------------------------------------------------------------------ forcing and control */
+
+/* Body force density F[3] (host pointer, D components used) applied after the
+ * collision with Kupershtokh's exact-difference method (Sec. 4.3):
+ * f_i += f_i^eq(rho, u + du, T) - f_i^eq(rho, u, T) with du = F dt / rho; g is
+ * unchanged, so momentum grows by F dt and energy by the kinetic work.
+ * F = 0 switches the term off.  Takes effect from the next step. */
+int sllbm_set_force(sllbm_ctx* ctx, const double* F);
+
+/* Mass rescaling (Sec. 4.3): scale every population (f and g) by
+ * target_mass / sum_n rho_n, which leaves u and T unchanged. */
+int sllbm_rescale_mass(sllbm_ctx* ctx, double target_mass);
+
+typedef struct {
+    double  target_momentum;  /* target nodal mean of rho u_x                         */
+    double  force0;           /* base force density F_x (e.g. rho_w Re_tau^2 mu_w^2 / delta^3) */
+    double  kp, ki;           /* PI gains on the momentum error                       */
+    int32_t control_every;    /* steps between force updates (0: no control)          */
+    int32_t rescale_every;    /* steps between mass rescalings (0: none); Sec. 4.3 uses 10 */
+    double  target_mass;      /* sum_n rho_n kept by the rescaling                    */
+} sllbm_control;
+
+/* Advance n steps with the volume force of Sec. 4.3 adjusted by a PI
+ * controller on the mean streamwise momentum: every control_every steps,
+ * e = target_momentum - mean(rho u_x) (FP64 reduction), I += e * control_every * dt,
+ * F_x = force0 + kp e + ki I; every rescale_every steps the mass is rescaled.
+ * The controller state persists in the context.  force_out (host, 3 doubles,
+ * may be NULL) receives the force in effect at the end.  The reductions
+ * synchronise the context stream. */
+int sllbm_step_controlled(sllbm_ctx* ctx, int64_t n, const sllbm_control* control, double* force_out);
+
 /* ------------------------------------------------------------------ readout */
 
 /* Per-node moments (Sec. 3.1): rho[N], u[N][D], T[N] in FP64. */

@@ -38,6 +38,11 @@ class Params(C.Structure):
                 ("max_walk", C.c_int32), ("stream", C.c_void_p)]
 
 
+class Control(C.Structure):
+    _fields_ = [("target_momentum", C.c_double), ("force0", C.c_double), ("kp", C.c_double), ("ki", C.c_double),
+                ("control_every", C.c_int32), ("rescale_every", C.c_int32), ("target_mass", C.c_double)]
+
+
 class Info(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("Q", C.c_int32), ("dim", C.c_int32), ("p", C.c_int32),
                 ("nodes", C.c_int32 * 3), ("cells", C.c_int32 * 3), ("precision", C.c_int32),
@@ -64,6 +69,9 @@ _SIGS = {
     "sllbm_read_moments": (C.c_int, [_P, _P, _P, _P, C.c_int32]),
     "sllbm_conservation": (C.c_int, [_P, _P]),
     "sllbm_conservation_static": (C.c_int, [_P, _P]),
+    "sllbm_set_force": (C.c_int, [_P, _P]),
+    "sllbm_rescale_mass": (C.c_int, [_P, C.c_double]),
+    "sllbm_step_controlled": (C.c_int, [_P, C.c_int64, C.POINTER(Control), _P]),
     "sllbm_departure_records": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "sllbm_sync": (C.c_int, [_P]),
     "sllbm_stream": (C.c_void_p, [_P]),

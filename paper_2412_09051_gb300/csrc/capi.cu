@@ -32,6 +32,9 @@ template <typename real>
 int launch_conserve(int vs, int D, const typename Vec2<real>::T* fg, int64_t N, const CollideConst<double>& C,
                     double* part, int* flag, double* out, cudaStream_t s);
 int conserve_blocks();
+template <typename real>
+int launch_scale_state(typename Vec2<real>::T* fg, int64_t N, int Q, const double* w, const double* wg, double s,
+                       cudaStream_t st);
 SLLBM_EXTERN_STEP(0, 2, float)
 SLLBM_EXTERN_STEP(1, 2, float)
 SLLBM_EXTERN_STEP(1, 3, float)
@@ -143,6 +146,8 @@ void fill_collide_const(sllbm_ctx* c, CollideConst<real>& C) {
     C.mu_exp = real(c->params.mu_exp);
     C.var_mu = c->params.mu_exp != 0.0;
     C.quasi = c->params.Pr != 1.0;
+    C.forced = (c->force[0] != 0.0 || c->force[1] != 0.0 || c->force[2] != 0.0) ? 1 : 0;
+    for (int d = 0; d < 3; ++d) C.force_dt[d] = real(d < D ? c->force[d] * c->params.dt : 0.0);
     for (int b = 0; b < 2; ++b) {
         const sllbm_bc& bc = c->desc.bc[b];
         double fe[SLLBM_QMAX], ge[SLLBM_QMAX];
@@ -370,7 +375,7 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->d_red, ctx->d_flag,
-                    ctx->d_mom, ctx->mlp_img, ctx->d_feat};
+                    ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -1028,5 +1033,80 @@ int sllbm_sync(sllbm_ctx* ctx) {
 }
 
 void* sllbm_stream(const sllbm_ctx* ctx) { return ctx ? static_cast<void*>(ctx->stream) : nullptr; }
+
+}  // extern "C"
+
+// ====================================================================== forcing, mass rescaling, control
+extern "C" {
+
+int sllbm_set_force(sllbm_ctx* ctx, const double* F) {
+    if (!ctx || !F) return SLLBM_ERR_ARG;
+    for (int d = 0; d < 3; ++d) {
+        if (!std::isfinite(F[d])) return fail(ctx, SLLBM_ERR_ARG, "force must be finite");
+        ctx->force[d] = d < ctx->mesh.D ? F[d] : 0.0;
+    }
+    fill_collide_const(ctx, ctx->cc32);
+    fill_collide_const(ctx, ctx->cc64);
+    return SLLBM_OK;
+}
+
+int sllbm_rescale_mass(sllbm_ctx* ctx, double target_mass) {
+    if (!ctx || !(target_mass > 0)) return SLLBM_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    double sums[5];
+    int rc = sllbm_conservation(ctx, sums);
+    if (rc) return rc;
+    const double s = target_mass / sums[0];
+    cudaSetDevice(ctx->device);
+    const int64_t N = ctx->mesh.n_nodes;
+    const int Q = ctx->vs.Q;
+    if (!ctx->d_wref) {
+        std::vector<double> wv(2 * Q);
+        const double gf = 2.0 / (ctx->params.gamma - 1.0) - ctx->mesh.D;
+        for (int i = 0; i < Q; ++i) {
+            wv[i] = ctx->vs.w[i];
+            wv[Q + i] = ctx->vs.w[i] * gf;
+        }
+        CK(cudaMalloc(&ctx->d_wref, sizeof(double) * 2 * Q));
+        CK(cudaMemcpy(ctx->d_wref, wv.data(), sizeof(double) * 2 * Q, cudaMemcpyHostToDevice));
+    }
+    const int c = ctx->cur;
+    rc = ctx->precision == SLLBM_FP64
+             ? launch_scale_state<double>((double2*)ctx->fg[c], N, Q, ctx->d_wref, ctx->d_wref + Q, s, ctx->stream)
+             : launch_scale_state<float>((float2*)ctx->fg[c], N, Q, ctx->d_wref, ctx->d_wref + Q, s, ctx->stream);
+    return rc ? fail(ctx, rc, "rescale launch failed") : SLLBM_OK;
+}
+
+int sllbm_step_controlled(sllbm_ctx* ctx, int64_t n, const sllbm_control* cfg, double* force_out) {
+    if (!ctx || !cfg || n < 0) return SLLBM_ERR_ARG;
+    if (cfg->control_every < 0 || cfg->rescale_every < 0) return SLLBM_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    const int D = ctx->mesh.D;
+    const double Nn = double(ctx->mesh.n_nodes);
+    for (int64_t k = 0; k < n; ++k) {
+        int rc = sllbm_step(ctx, 1);
+        if (rc) return rc;
+        const int64_t s = ctx->steps;
+        if (cfg->control_every > 0 && s % cfg->control_every == 0) {
+            double sums[5];
+            rc = sllbm_conservation(ctx, sums);
+            if (rc) return rc;
+            // PI control of the mean streamwise momentum density (nodal mean of rho u_x)
+            const double err = cfg->target_momentum - sums[1] / Nn;
+            ctx->ctl_integral += err * cfg->control_every * ctx->params.dt;
+            double F[3] = {ctx->force[0], ctx->force[1], D == 3 ? ctx->force[2] : 0.0};
+            F[0] = cfg->force0 + cfg->kp * err + cfg->ki * ctx->ctl_integral;
+            rc = sllbm_set_force(ctx, F);
+            if (rc) return rc;
+        }
+        if (cfg->rescale_every > 0 && s % cfg->rescale_every == 0) {
+            rc = sllbm_rescale_mass(ctx, cfg->target_mass);
+            if (rc) return rc;
+        }
+    }
+    if (force_out)
+        for (int d = 0; d < 3; ++d) force_out[d] = ctx->force[d];
+    return SLLBM_OK;
+}
 
 }  // extern "C"

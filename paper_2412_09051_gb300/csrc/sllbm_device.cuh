@@ -76,6 +76,8 @@ struct CollideConst {
     real mu_ref, inv_T_ref, mu_exp;
     int  var_mu;                  // mu_exp != 0
     int  quasi;                   // Pr != 1
+    int  forced;                  // body force present
+    real force_dt[3];             // F dt (force density times time step)
     // boundary constants per boundary id: equilibrium deviations and moving-wall term
     real eqf[2][SLLBM_QMAX];
     real eqg[2][SLLBM_QMAX];
@@ -246,6 +248,22 @@ __device__ __forceinline__ void collide_node(const CollideConst<real>& C, real (
             g[i] += C.w[i] * d;
         });
     }
+    if (C.forced) {
+        // Kupershtokh exact-difference forcing (Sec. 4.3):
+        // f_i += f_i^eq(rho, u + du, T) - f_i^eq(rho, u, T), du = F dt / rho
+        real v[3] = {u[0] + C.force_dt[0] * inv_rho, u[1] + C.force_dt[1] * inv_rho,
+                     D == 3 ? u[2] + C.force_dt[2] * inv_rho : real(0)};
+        const real V = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        EqCoef<real, VSET::NS> K1;
+        K1.build(C, V, t);
+        Unroll<0, Q>::run([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            real fa, ga, fb, gb, cd;
+            eq_dev<VSET, real, i>(C, K1, v, rho, rho_d, rhoT, rhoT_d, fa, ga, cd);
+            eq_dev<VSET, real, i>(C, K, u, rho, rho_d, rhoT, rhoT_d, fb, gb, cd);
+            f[i] += fa - fb;
+        });
+    }
 }
 
 // ------------------------------------------------------------ Lagrange basis
@@ -339,24 +357,40 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
         q1 += (C.xi[i][1] - u1) * h;
         if (D == 3) q2 += (C.xi[i][2] - u2) * h;
         const real fo = f - om * fn, go = g - om * gn;
-        if (C.quasi) {
+        if (C.quasi || C.forced) {
             Sf[i * stride] = fo;
             Sg[i * stride] = go;
         } else if (out) {
             out[i * NN] = Vec2<real>::make(fo, go);
         }
     }
-    if (C.quasi) {
+    if (C.quasi || C.forced) {
         const real a = om - om_pr;
-        q0 *= a;
-        q1 *= a;
-        q2 *= a;
+        q0 *= C.quasi ? a : real(0);
+        q1 *= C.quasi ? a : real(0);
+        q2 *= C.quasi ? a : real(0);
+        // Kupershtokh exact-difference forcing (Sec. 4.3), du = F dt / rho
+        const real v0 = u0 + C.force_dt[0] * inv_rho, v1 = u1 + C.force_dt[1] * inv_rho;
+        const real v2 = D == 3 ? u2 + C.force_dt[2] * inv_rho : real(0);
+        const real V = v0 * v0 + v1 * v1 + v2 * v2;
         if (out) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 real dq = C.xi[i][0] * q0 + C.xi[i][1] * q1;
                 if (D == 3) dq += C.xi[i][2] * q2;
-                out[i * NN] = Vec2<real>::make(Sf[i * stride], Sg[i * stride] + C.w[i] * dq);
+                real fo = Sf[i * stride];
+                if (C.forced) {
+                    real cd;
+                    const real pa = p1(i, t, cd);
+                    real c = C.xi[i][0] * v0 + C.xi[i][1] * v1;
+                    if (D == 3) c += C.xi[i][2] * v2;
+                    const real k2 = real(0.5) - real(0.25) * V + real(0.25) * t * C.sCv[i];
+                    const real k1 = real(1.0) - real(0.5) * V + real(0.5) * t * C.sBv[i];
+                    const real k0 = -real(0.5) * V + real(0.125) * V * V + real(0.5) * t * C.sAv[i] -
+                                    real(0.25) * t * V * C.sBv[i] + real(0.125) * t * t * C.sEv[i];
+                    fo += C.w[i] * rho * (eq_poly1(c, k0, k1, k2) - pa);
+                }
+                out[i * NN] = Vec2<real>::make(fo, Sg[i * stride] + C.w[i] * dq);
             }
         }
     }

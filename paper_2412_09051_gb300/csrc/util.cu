@@ -200,7 +200,32 @@ int launch_conserve(int vs, int D, const typename Vec2<real>::T* fg, int64_t N, 
 INST(float)
 INST(double)
 
+// mass rescaling (Sec. 4.3): full populations scaled by s; in deviation
+// storage dev' = s dev + (s - 1) ref
+template <typename real>
+__global__ void k_scale_state(typename Vec2<real>::T* __restrict__ fg, int64_t N, int Q, const double* __restrict__ w,
+                              const double* __restrict__ wg, double s) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= N * Q) return;
+    const int i = int(t / N);
+    auto v = fg[t];
+    v.x = real(s * double(v.x) + (s - 1.0) * w[i]);
+    v.y = real(s * double(v.y) + (s - 1.0) * wg[i]);
+    fg[t] = v;
+}
+
+template <typename real>
+int launch_scale_state(typename Vec2<real>::T* fg, int64_t N, int Q, const double* w, const double* wg, double s,
+                       cudaStream_t st) {
+    const int bs = 256;
+    k_scale_state<real><<<unsigned((N * Q + bs - 1) / bs), bs, 0, st>>>(fg, N, Q, w, wg, s);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+template int launch_scale_state<float>(float2*, int64_t, int, const double*, const double*, double, cudaStream_t);
+template int launch_scale_state<double>(double2*, int64_t, int, const double*, const double*, double, cudaStream_t);
+
 }  // namespace sllbm
+
 
 // ====================================================================== allocation-free conservation
 // sllbm_conservation_static: the conservation sums of sllbm_conservation with

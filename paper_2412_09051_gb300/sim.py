@@ -146,6 +146,21 @@ class Sim:
     def step(self, n=1):
         self._call("sllbm_step", C.c_int64(n))
 
+    def set_force(self, F):
+        F = np.zeros(3) if F is None else np.ascontiguousarray(list(F) + [0.0] * (3 - len(F)), dtype=np.float64)
+        self._call("sllbm_set_force", _ptr(F)[0])
+
+    def rescale_mass(self, target):
+        self._call("sllbm_rescale_mass", C.c_double(target))
+
+    def step_controlled(self, n, target_momentum, force0, kp, ki, control_every=10, rescale_every=10,
+                        target_mass=None):
+        c = capi.Control(target_momentum, force0, kp, ki, control_every, rescale_every,
+                         target_mass if target_mass is not None else float(self.N))
+        F = np.zeros(3)
+        self._call("sllbm_step_controlled", C.c_int64(n), C.byref(c), _ptr(F)[0])
+        return F
+
     def sync(self):
         self._call("sllbm_sync")
 

@@ -1,0 +1,95 @@
+"""GPU tests of the Sec. 4.3 additions: Kupershtokh forcing against the
+oracle and the closed-form uniform acceleration, mass rescaling, and the PI
+controller on the mean streamwise momentum."""
+import numpy as np
+import pytest
+
+from oracle import step as ost
+from tests.oracle_cases import box_cfg, oracle_case
+from workloads import get_config, initial_fields
+
+pytestmark = pytest.mark.gpu
+
+
+def _sim(cfg, prec, mode=0):
+    from paper_2412_09051_gb300.sim import Sim
+    return Sim(cfg, precision=prec, stream_mode=mode)
+
+
+@pytest.mark.parametrize("name,over,prec,F", [("channel", dict(cells=(4, 6, 3)), "fp32", (0.05, 0.0, 0.01)),
+                                              ("tgv2d", dict(cells=6), "fp64", (0.02, -0.01))])
+@pytest.mark.parametrize("mode", [0, 1, 4])
+def test_forced_steps_match_oracle(built_lib, name, over, prec, F, mode):
+    cfg = get_config(name, **over)
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    par.force = np.array(F[:mesh.D])
+    sim = _sim(cfg, prec, mode)
+    sim.set_force(F)
+    rho, u, T = initial_fields(cfg, mesh.X)
+    sim.init_state(rho, u, T)
+    f, g = ost.init_equilibrium(rho, u, T, xi, w, par.cv)
+    Tw = ost.isothermal_nodes(rec, par)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for _ in range(3):
+        f, g = ost.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
+    sim.step(3)
+    fg, gg = sim.get_state()
+    for a, b in ((fg, f), (gg, g)):
+        s = np.maximum(np.abs(b).max(axis=1, keepdims=True), w[:, None])
+        assert (np.abs(a - b) / s).max() < tol
+
+
+def test_uniform_acceleration(built_lib):
+    """Closed form: u(t) = u0 + F t / rho for a uniform state in a periodic box."""
+    F = np.array([0.02, 0.005])
+    cfg = box_cfg(cells=(4, 4), L=(1.0, 1.0), dt=0.02)
+    sim = _sim(cfg, "fp64")
+    N = sim.N
+    rho0, u0, T0 = 1.1, np.array([0.3, -0.2]), 0.9
+    sim.init_state(np.full(N, rho0), np.tile(u0, (N, 1)), np.full(N, T0))
+    sim.set_force(F)
+    sim.step(9)
+    r, u, T = sim.moments()
+    assert np.abs(u - (u0 + 9 * F * cfg["dt"] / rho0)).max() < 1e-12
+    assert np.abs(T - T0).max() < 1e-12 and np.abs(r - rho0).max() < 1e-12
+
+
+def test_mass_rescaling(built_lib):
+    cfg = get_config("channel", cells=(4, 6, 3))
+    sim = _sim(cfg, "fp64")
+    rho, u, T = initial_fields(cfg, sim.node_coords())
+    sim.init_state(rho, u, T)
+    sim.step(5)
+    r0, u0, T0 = sim.moments()
+    target = 1.02 * r0.sum()
+    sim.rescale_mass(target)
+    c, _ = sim.conservation()
+    r1, u1, T1 = sim.moments()
+    assert abs(c[0] - target) < 1e-12 * target
+    assert np.abs(u1 - u0).max() < 1e-12 and np.abs(T1 - T0).max() < 1e-12
+
+
+def test_pi_controller_holds_bulk_momentum(built_lib):
+    """Wall friction decelerates the channel; the PI-controlled volume force
+    (Sec. 4.3) keeps the mean streamwise momentum near its target, and mass
+    rescaling every 10 steps keeps the total mass."""
+    cfg = get_config("channel", cells=(4, 12, 3))
+    free = _sim(cfg, "fp32")
+    ctl = _sim(cfg, "fp32")
+    X = free.node_coords()
+    rho, u, T = initial_fields(cfg, X)
+    for s in (free, ctl):
+        s.init_state(rho, u, T)
+    c0, _ = free.conservation()
+    N = free.N
+    target = c0[1] / N
+    free.step(300)
+    F = ctl.step_controlled(300, target, 0.0, kp=2.0, ki=20.0, control_every=5, rescale_every=10,
+                            target_mass=c0[0])
+    cf, _ = free.conservation()
+    cc, _ = ctl.conservation()
+    err_free = abs(cf[1] / N - target)
+    err_ctl = abs(cc[1] / N - target)
+    assert F[0] > 0
+    assert err_ctl < 0.25 * err_free
+    assert abs(cc[0] - c0[0]) < 1e-4 * c0[0]
