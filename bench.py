@@ -86,6 +86,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def aggregate(ms_total, nodes, steps, e2e_s, dist=None, device="cpu"):
+    """Whole-job numbers over the replicas: the slowest rank's time (max over
+    ranks) and all ranks' nodes (sum).  Returns (ms_max, nodes_total,
+    MLUPS, e2e MLUPS)."""
+    import torch
+    t = torch.tensor([float(ms_total), float(e2e_s)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(nodes)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    ms_max, e2e_max = (float(v) for v in t.tolist())
+    total = float(n.item())
+    return ms_max, total, total * steps / (ms_max / 1e3) / 1e6, total / e2e_max / 1e6
+
+
 def algorithmic_bytes_per_node(Q, real_bytes):
     """Every population of f and g read once and written once."""
     return 2 * 2 * Q * real_bytes
@@ -183,10 +198,6 @@ def run_gpu(args, ws, rank, local):
         dist.barrier()
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     ms_total = ev[0].elapsed_time(ev[-1])
-    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     cons, rc = sim.conservation(check=False)
 
     # end to end through the C ABI with host buffers: H2D of the step's input
@@ -209,9 +220,8 @@ def run_gpu(args, ws, rank, local):
     h2d = 2 * Q * N * real_bytes
     d2h = N * (sim.D + 2) * 8
 
-    mlups_rank = N * args.steps / (ms_max / 1e3) / 1e6
-    total_nodes = N * ws
-    value = total_nodes * args.steps / (ms_max / 1e3) / 1e6
+    ms_max, total_nodes, value, e2e_value = aggregate(ms_total, N, args.steps, e2e_s, dist, "cuda")
+    mlups_rank = N * args.steps / (ms_total / 1e3) / 1e6
     avg_launch_ms = statistics.mean(per)
     peaks, psrc = _peaks()
     alg_bytes = algorithmic_bytes_per_node(Q, real_bytes) * N
@@ -250,8 +260,8 @@ def run_gpu(args, ws, rank, local):
                          "kernel": {2: "k_step_tiled_smem", 4: "k_step_tiled", 3: "k_step_structured",
                                     1: "k_step_gather", 5: "k_step_gather_smem"}.get(
                              sim.info.stream_mode, "k_step") + f"<{cfg['velset']}>"},
-            "e2e": {"value": round(N / e2e_s / 1e6, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+            "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d * ws,
+                    "d2h_bytes_per_step": d2h * ws},
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "conservation_rc": rc,
