@@ -101,6 +101,23 @@ def aggregate(ms_total, nodes, steps, e2e_s, dist=None, device="cpu"):
     return ms_max, total, total * steps / (ms_max / 1e3) / 1e6, total / e2e_max / 1e6
 
 
+def workload_config(cfg, ws=1):
+    """The `config` object of the JSON line (shared by both arms)."""
+    m = cfg["mesh"]
+    periodic = {0: (1, 1, 1), 1: (1, 0, 1), 2: (1, 0, 1), 3: (1, 0)}[m["kind"]]
+    N = 1
+    for d, c in enumerate(m["cells"]):
+        N *= c * m["p"] + (0 if periodic[d] else 1)
+    Q = {"D2Q9": 9, "D2Q19": 19, "D2Q25": 25, "D3Q45": 45}[cfg["velset"]]
+    rb = 8 if cfg.get("precision") == "fp64" else 4
+    return {"workload": f"{cfg['name']} ({cfg['velset']}, {'FP32-offset' if rb == 4 else 'FP64'}, "
+                        f"{'gather' if m['kind'] == 3 else 'structured'} streaming)",
+            "nodes": N, "Q": Q, "replicas": ws,
+            "l2": (f"inputs larger than L2: state {2 * Q * N * rb / 1e6:.0f} MB per buffer pair"
+                   if 2 * Q * N * rb > 129e6 else
+                   f"inputs smaller than L2 ({2 * Q * N * rb / 1e6:.0f} MB per buffer pair): no flush, L2-warm")}
+
+
 def algorithmic_bytes_per_node(Q, real_bytes):
     """Every population of f and g read once and written once."""
     return 2 * 2 * Q * real_bytes
@@ -148,6 +165,12 @@ def oracle_sample_rate(cfg_name, target_s=10.0, cores=1):
     return {"value": total_nodes / total_t / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{total_nodes} random arrival nodes of {cfg['name']}, one step each "
                       f"(stream + thermal correction + collision, FP64 numpy), {total_t:.1f} s"}
+
+
+def _cfg_of(args):
+    from workloads import get_config
+    return get_config(args.config, cells=tuple(int(c) for c in args.cells.split(","))) if args.cells \
+        else get_config(args.config)
 
 
 def run_oracle_subprocess(cfg_name, target_s):
@@ -249,10 +272,7 @@ def run_gpu(args, ws, rank, local):
             "dtype": "f32" if real_bytes == 4 else "f64",
             "data": "synthetic (seeded laminar profile + 10% Philox perturbation)" if args.config == "channel"
                     else "synthetic (seeded)",
-            "config": {"workload": f"{cfg['name']} ({cfg['velset']}, "
-                                   f"{'FP32-offset' if real_bytes == 4 else 'FP64'}, structured streaming)",
-                       "nodes": N, "Q": Q, "replicas": ws,
-                       "l2": f"inputs larger than L2: state {2 * Q * N * real_bytes / 1e6:.0f} MB per buffer pair"},
+            "config": workload_config(cfg, ws),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                          "peak_source": f"{psrc} (copy bandwidth)",
@@ -293,7 +313,7 @@ def main():
         line = {"impl": "reference", "metric": "MLUPS (node updates/s, all Q of f and g)", "value": cb["value"],
                 "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic (seeded)", "config": {"workload": args.config},
+                "data": "synthetic (seeded)", "config": workload_config(_cfg_of(args)),
                 "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                                             "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
