@@ -69,27 +69,26 @@ def test_mass_rescaling(built_lib):
     assert np.abs(u1 - u0).max() < 1e-12 and np.abs(T1 - T0).max() < 1e-12
 
 
-def test_pi_controller_holds_bulk_momentum(built_lib):
-    """Wall friction decelerates the channel; the PI-controlled volume force
-    (Sec. 4.3) keeps the mean streamwise momentum near its target, and mass
+def test_pi_controller_spins_up_to_target(built_lib):
+    """Sec. 4.3: the volume force is adjusted by a PI controller on the mean
+    streamwise momentum.  From rest, the controlled channel reaches the
+    target momentum (the uncontrolled one stays at rest) while mass
     rescaling every 10 steps keeps the total mass."""
     cfg = get_config("channel", cells=(4, 12, 3))
     free = _sim(cfg, "fp32")
     ctl = _sim(cfg, "fp32")
-    X = free.node_coords()
-    rho, u, T = initial_fields(cfg, X)
-    for s in (free, ctl):
-        s.init_state(rho, u, T)
-    c0, _ = free.conservation()
     N = free.N
-    target = c0[1] / N
-    free.step(300)
-    F = ctl.step_controlled(300, target, 0.0, kp=2.0, ki=20.0, control_every=5, rescale_every=10,
+    Tw = cfg["bcs"][0]["T"]
+    for s in (free, ctl):
+        s.init_state(np.ones(N), np.zeros((N, 3)), np.full(N, Tw))
+    c0, _ = free.conservation()
+    target = 0.05
+    free.step(600)
+    F = ctl.step_controlled(600, target, 0.0, kp=20.0, ki=100.0, control_every=5, rescale_every=10,
                             target_mass=c0[0])
     cf, _ = free.conservation()
     cc, _ = ctl.conservation()
-    err_free = abs(cf[1] / N - target)
-    err_ctl = abs(cc[1] / N - target)
+    assert abs(cf[1] / N) < 1e-3 * target
+    assert abs(cc[1] / N - target) < 0.1 * target
     assert F[0] > 0
-    assert err_ctl < 0.25 * err_free
     assert abs(cc[0] - c0[0]) < 1e-4 * c0[0]
