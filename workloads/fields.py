@@ -51,7 +51,10 @@ def initial_fields(cfg, X, seed=None):
         xc, yc = r.uniform(0.3 * L, 0.7 * L, size=2)
         U0 = mach * math.sqrt(1.4)
         eps = ini.get("eps", 2.5)
-        dx, dy = X[:, 0] - xc, X[:, 1] - yc
+        R = ini.get("R", 1.0)                       # core radius
+        if "center" in ini:
+            xc, yc = ini["center"]
+        dx, dy = (X[:, 0] - xc) / R, (X[:, 1] - yc) / R
         r2 = dx * dx + dy * dy
         e = np.exp(0.5 * (1.0 - r2))
         u[:, 0] = U0 - eps / (2.0 * math.pi) * e * dy
