@@ -16,8 +16,12 @@ Modules and the passage each follows:
   step           Sec. 3.1 Eq. (1), moment definitions, Sec. 3.3 boundary schemes
   mlp            learned collision correction (not in the paper)
 
-Parity status: every function is pinned by tests in tests/test_oracle_*.py
-except the quasi-equilibrium term for Pr != 1 (pinned only by its defining
-invariants) and the curved-wall / outlet boundary schemes (pinned by
-invariants and special cases, not by printed values): "parity partly unpinned".
+Parity status: the velocity sets, equilibrium, interpolation, inverse maps,
+collision, thermal correction, forcing and mass rescaling are pinned by
+closed forms, invariants and special cases (tests/test_oracle_*.py); the
+quasi-equilibrium term (Pr != 1) by its relaxation-rate invariants, the
+Prandtl scaling of the compressible Couette temperature rise and the
+thermal part of the sound attenuation.  The curved-wall bounce-back and the
+outlet scheme are pinned only geometrically (source points, populations
+read): "parity partly unpinned" for those two boundary schemes.
 """
