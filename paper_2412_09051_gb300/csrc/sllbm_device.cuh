@@ -286,49 +286,53 @@ __device__ __forceinline__ void lagrange_w(real x, const real* xh, const real* i
 namespace sllbm {
 
 // ------------------------------------------------------------ collide, state in shared memory
-// Same arithmetic as collide_node: the streamed deviations of the thread's
-// node sit at Sf[i * stride], Sg[i * stride]; the post-collision pair of
-// velocity i is written to out[i * NN] (out == nullptr: no store).  Loops are
-// unrolled at compile time (constant operands, per-shell equilibrium
-// coefficients).  Density and energy sums are compensated (Kahan); the
-// momentum sums are plain (their FP32 error on the stored deviations is far
-// below the parity tolerance and nothing cancels in them).
+// Same arithmetic as collide_node with runtime velocity loops: the streamed
+// deviations of the thread's node sit at Sf[i * stride], Sg[i * stride]; the
+// post-collision pair of velocity i is written to out[i * NN] (out == nullptr:
+// no store).
 template <class VSET, typename real, typename V2, int stride>
 __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* Sf, real* Sg, real Tw,
                                              V2* out, int NN) {
     constexpr int Q = VSET::Q;
     constexpr int D = VSET::D;
-    Acc<real> arho, ae;
-    real j0 = 0, j1 = 0, j2 = 0;
-    Unroll<0, Q>::run([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
+    Acc<real> arho, aj0, aj1, aj2, ae;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
         const real f = Sf[i * stride], g = Sg[i * stride];
         arho.add(f);
-        j0 += C.xi[i][0] * f;
-        j1 += C.xi[i][1] * f;
-        if (D == 3) j2 += C.xi[i][2] * f;
-        ae.add(C.s2[VSET::shell(i)] * f + g);
-    });
+        aj0.add(C.xi[i][0] * f);
+        aj1.add(C.xi[i][1] * f);
+        if (D == 3) aj2.add(C.xi[i][2] * f);
+        ae.add(C.s2v[i] * f);
+        ae.add(g);
+    }
     const real rho_d = arho.get();
     const real rho = real(1) + rho_d;
     const real inv_rho = real(1) / rho;
-    real u[3] = {j0 * inv_rho, j1 * inv_rho, D == 3 ? j2 * inv_rho : real(0)};
-    const real U = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const real u0 = aj0.get() * inv_rho, u1 = aj1.get() * inv_rho, u2 = D == 3 ? aj2.get() * inv_rho : real(0);
+    const real U = u0 * u0 + u1 * u1 + u2 * u2;
     real t = (ae.get() - rho * U - real(2) * C.cv * rho_d) * inv_rho / (real(2) * C.cv);
+    // P1 of velocity i for temperature offset tt
+    auto p1 = [&](int i, real tt, real& cd) {
+        real c = C.xi[i][0] * u0 + C.xi[i][1] * u1;
+        if (D == 3) c += C.xi[i][2] * u2;
+        cd = c;
+        const real k2 = real(0.5) - real(0.25) * U + real(0.25) * tt * C.sCv[i];
+        const real k1 = real(1.0) - real(0.5) * U + real(0.5) * tt * C.sBv[i];
+        const real k0 = -real(0.5) * U + real(0.125) * U * U + real(0.5) * tt * C.sAv[i] -
+                        real(0.25) * tt * U * C.sBv[i] + real(0.125) * tt * tt * C.sEv[i];
+        return eq_poly1(c, k0, k1, k2);
+    };
     if (!(Tw != Tw)) {   // isothermal wall correction (Eq. thermalBC)
         const real tw = Tw - real(1);
-        EqCoef<real, VSET::NS> K0, K1;
-        K0.build(C, U, t);
-        K1.build(C, U, tw);
         const real rT0 = rho * (real(1) + t), rT1 = rho * (real(1) + tw);
-        Unroll<0, Q>::run([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            real f0, g0, f1, g1, cd;
-            eq_dev<VSET, real, i>(C, K0, u, rho, rho_d, rT0, rT0 - real(1), f0, g0, cd);
-            eq_dev<VSET, real, i>(C, K1, u, rho, rho_d, rT1, rT1 - real(1), f1, g1, cd);
-            Sf[i * stride] += f1 - f0;
-            Sg[i * stride] += g1 - g0;
-        });
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            real cd;
+            const real a0 = p1(i, t, cd), a1 = p1(i, tw, cd);
+            Sf[i * stride] += C.w[i] * rho * (a1 - a0);
+            Sg[i * stride] += C.wg[i] * ((rT1 * a1 + (rT1 - real(1))) - (rT0 * a0 + (rT0 - real(1))));
+        }
         t = tw;
     }
     const real T = real(1) + t;
@@ -339,53 +343,56 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
     const real om_pr = real(1) / ((tau - real(0.5)) * C.inv_Pr + real(0.5));
     const real rhoT = rho * T;
     const real rhoT_d = rho_d + rho * t;
-    EqCoef<real, VSET::NS> K;
-    K.build(C, U, t);
-    const bool later = C.quasi || C.forced;
     real q0 = 0, q1 = 0, q2 = 0;
-    Unroll<0, Q>::run([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        real fe, ge, cd;
-        eq_dev<VSET, real, i>(C, K, u, rho, rho_d, rhoT, rhoT_d, fe, ge, cd);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        real cd;
+        const real P1 = p1(i, t, cd);
+        const real fe = C.w[i] * (rho * P1 + rho_d);
+        const real ge = C.wg[i] * (rhoT * P1 + rhoT_d);
         const real f = Sf[i * stride], g = Sg[i * stride];
         const real fn = f - fe, gn = g - ge;
-        if (C.quasi) {
-            const real h = (C.s2[VSET::shell(i)] - real(2) * cd + U) * fn + gn;
-            q0 += (C.xi[i][0] - u[0]) * h;
-            q1 += (C.xi[i][1] - u[1]) * h;
-            if (D == 3) q2 += (C.xi[i][2] - u[2]) * h;
-        }
+        const real h = (C.s2v[i] - real(2) * cd + U) * fn + gn;
+        q0 += (C.xi[i][0] - u0) * h;
+        q1 += (C.xi[i][1] - u1) * h;
+        if (D == 3) q2 += (C.xi[i][2] - u2) * h;
         const real fo = f - om * fn, go = g - om * gn;
-        if (later) {
+        if (C.quasi || C.forced) {
             Sf[i * stride] = fo;
             Sg[i * stride] = go;
         } else if (out) {
             out[i * NN] = Vec2<real>::make(fo, go);
         }
-    });
-    if (later && out) {
-        const real a = C.quasi ? om - om_pr : real(0);
-        q0 *= a;
-        q1 *= a;
-        q2 *= a;
+    }
+    if (C.quasi || C.forced) {
+        const real a = om - om_pr;
+        q0 *= C.quasi ? a : real(0);
+        q1 *= C.quasi ? a : real(0);
+        q2 *= C.quasi ? a : real(0);
         // Kupershtokh exact-difference forcing (Sec. 4.3), du = F dt / rho
-        real v[3] = {u[0] + C.force_dt[0] * inv_rho, u[1] + C.force_dt[1] * inv_rho,
-                     D == 3 ? u[2] + C.force_dt[2] * inv_rho : real(0)};
-        EqCoef<real, VSET::NS> K1;
-        K1.build(C, v[0] * v[0] + v[1] * v[1] + v[2] * v[2], t);
-        Unroll<0, Q>::run([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            real dq = C.xi[i][0] * q0 + C.xi[i][1] * q1;
-            if (D == 3) dq += C.xi[i][2] * q2;
-            real fo = Sf[i * stride];
-            if (C.forced) {
-                real fa, ga, fb, gb, cd;
-                eq_dev<VSET, real, i>(C, K1, v, rho, rho_d, rhoT, rhoT_d, fa, ga, cd);
-                eq_dev<VSET, real, i>(C, K, u, rho, rho_d, rhoT, rhoT_d, fb, gb, cd);
-                fo += fa - fb;
+        const real v0 = u0 + C.force_dt[0] * inv_rho, v1 = u1 + C.force_dt[1] * inv_rho;
+        const real v2 = D == 3 ? u2 + C.force_dt[2] * inv_rho : real(0);
+        const real V = v0 * v0 + v1 * v1 + v2 * v2;
+        if (out) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                real dq = C.xi[i][0] * q0 + C.xi[i][1] * q1;
+                if (D == 3) dq += C.xi[i][2] * q2;
+                real fo = Sf[i * stride];
+                if (C.forced) {
+                    real cd;
+                    const real pa = p1(i, t, cd);
+                    real c = C.xi[i][0] * v0 + C.xi[i][1] * v1;
+                    if (D == 3) c += C.xi[i][2] * v2;
+                    const real k2 = real(0.5) - real(0.25) * V + real(0.25) * t * C.sCv[i];
+                    const real k1 = real(1.0) - real(0.5) * V + real(0.5) * t * C.sBv[i];
+                    const real k0 = -real(0.5) * V + real(0.125) * V * V + real(0.5) * t * C.sAv[i] -
+                                    real(0.25) * t * V * C.sBv[i] + real(0.125) * t * t * C.sEv[i];
+                    fo += C.w[i] * rho * (eq_poly1(c, k0, k1, k2) - pa);
+                }
+                out[i * NN] = Vec2<real>::make(fo, Sg[i * stride] + C.w[i] * dq);
             }
-            out[i * NN] = Vec2<real>::make(fo, Sg[i * stride] + C.w[i] * dq);
-        });
+        }
     }
 }
 

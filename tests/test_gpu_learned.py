@@ -100,7 +100,7 @@ def test_corrected_step_matches_oracle_and_conserves(built_lib):
     assert np.abs(df).max() > 1e-6                       # the correction is not negligible
     assert np.abs(fg - ref).max() < 1e-5 * np.abs(ref).max()
     # exact conservation: the learned step conserves what the plain step conserves
-    plain = Sim(cfg)
+    plain = Sim(cfg, stream_mode=4)          # the kernel that carries the correction
     plain.init_state(rho, u, T)
     plain.step(1)
     c_plain, _ = plain.conservation()
