@@ -167,6 +167,12 @@ def oracle_sample_rate(cfg_name, target_s=10.0, cores=1):
                       f"(stream + thermal correction + collision, FP64 numpy), {total_t:.1f} s"}
 
 
+def mlp_flops_per_node(Q, H=64):
+    """Flops of the learned correction's network per node (Q -> H -> H -> Q),
+    2 per multiply-add; the moment transform and projection not counted."""
+    return 2 * (Q * H + H * H + H * Q)
+
+
 def _cfg_of(args):
     from workloads import get_config
     return get_config(args.config, cells=tuple(int(c) for c in args.cells.split(","))) if args.cells \
@@ -203,6 +209,13 @@ def run_gpu(args, ws, rank, local):
     rho, u, T = initial_fields(cfg, X)
     sim.init_state(rho, u, T)
     real_bytes = 8 if sim.fp64 else 4
+    if args.learned != "none":
+        # the learned collision correction with a seeded random network of the
+        # trained shape (timing does not depend on the weights' values)
+        from paper_2412_09051_gb300 import capi
+        from paper_2412_09051_gb300.learned import init_params, install_params
+        install_params(sim, init_params(Q, 0), np.ones(Q, np.float32), 1e-3)
+        sim.mlp_path(capi.MLP_TENSOR if args.learned == "tensor" else capi.MLP_SIMT)
     # warm-up
     sim.step(args.warmup)
     sim.sync()
@@ -222,6 +235,7 @@ def run_gpu(args, ws, rank, local):
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     ms_total = ev[0].elapsed_time(ev[-1])
     cons, rc = sim.conservation(check=False)
+    dev_status = sim.device_status() if args.learned != "none" else 0
 
     # end to end through the C ABI with host buffers: H2D of the step's input
     # state from pinned memory, one step, D2H of the moments
@@ -277,14 +291,19 @@ def run_gpu(args, ws, rank, local):
                          "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                          "peak_source": f"{psrc} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "kernel": {2: "k_step_tiled_smem", 4: "k_step_tiled", 3: "k_step_structured",
-                                    1: "k_step_gather", 5: "k_step_gather_smem"}.get(
-                             sim.info.stream_mode, "k_step") + f"<{cfg['velset']}>"},
+                         "kernel": ({2: "k_step_tiled_smem", 4: "k_step_tiled", 3: "k_step_structured",
+                                     1: "k_step_gather", 5: "k_step_gather_smem"}.get(
+                             sim.info.stream_mode, "k_step") if args.learned == "none"
+                             else f"k_step_tiled (learned, MLP on {'tensor' if args.learned == 'tensor' else 'CUDA'}"
+                                  " cores)") + f"<{cfg['velset']}>"},
             "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d * ws,
                     "d2h_bytes_per_step": d2h * ws},
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "conservation_rc": rc,
+            **({"learned": {"mlp": args.learned, "device_status": dev_status,
+                            "mlp_tflops": round(mlp_flops_per_node(Q) * N / (avg_launch_ms / 1e3) / 1e12, 2)}}
+               if args.learned != "none" else {}),
             "per_rank_mlups": round(mlups_rank, 2),
         }
     sim.close()
@@ -304,6 +323,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", default=None, help="override the cell counts, e.g. 32,48,24 (profiling runs)")
     ap.add_argument("--mode", type=int, default=0, help="streaming mode (include/sllbm.h SLLBM_STREAM_*)")
+    ap.add_argument("--learned", default="none", choices=["none", "tensor", "simt"],
+                    help="time the learned-correction step (config learned): MLP on tensor or CUDA cores")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

@@ -322,6 +322,27 @@ int sllbm_departure_records(sllbm_ctx* ctx, int32_t* kind, int32_t* src, int32_t
 int sllbm_mlp_set(sllbm_ctx* ctx, const uint16_t* w_bf16, const float* biases, const float* s_in, float sigma,
                   int32_t enable);
 
+/* Which units evaluate the installed correction inside sllbm_step:
+ *   SLLBM_MLP_TENSOR (default)  5th-generation tensor cores: per block of
+ *       128 nodes three M = 128 BF16 products with FP32 accumulation in
+ *       tensor memory; each FP32 activation enters as the sum of two BF16
+ *       parts (hi + lo), so the result equals the CUDA-core evaluation to
+ *       FP32 rounding.
+ *   SLLBM_MLP_SIMT              CUDA cores, FP32 fused multiply-adds.
+ * Both compute the network defined above.  Any other value: SLLBM_ERR_ARG.
+ * The tensor-core kernel bounds each wait for its products (about a second);
+ * if one runs out it leaves that block's f uncorrected and records
+ * SLLBM_DEV_TC_TIMEOUT in the status word read by sllbm_device_status. */
+#define SLLBM_MLP_TENSOR 0
+#define SLLBM_MLP_SIMT   1
+int sllbm_mlp_path(sllbm_ctx* ctx, int32_t path);
+
+/* Device status word of the context: synchronises the context's stream,
+ * writes the word to *code (0: nothing recorded, SLLBM_DEV_TC_TIMEOUT: a
+ * tensor-core wait ran out) and clears it.  Host pointer. */
+#define SLLBM_DEV_TC_TIMEOUT 1
+int sllbm_device_status(sllbm_ctx* ctx, int32_t* code);
+
 /* One plain step (no correction) that also writes the non-equilibrium
  * moments z [N][Q] (FP32) of the step's streamed state. */
 int sllbm_step_features(sllbm_ctx* ctx, float* z, int32_t on_device);

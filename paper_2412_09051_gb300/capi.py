@@ -16,6 +16,8 @@ ERRORS = {-1: "SLLBM_ERR_ARG", -2: "SLLBM_ERR_CUDA", -3: "SLLBM_ERR_ARCH", -4: "
           -8: "SLLBM_ERR_UNSUPPORTED"}
 MESH = dict(box=0, channel=1, mixing=2, naca=3)
 VELSET = dict(D2Q9=0, D2Q19=1, D2Q25=2, D3Q45=3)
+MLP_TENSOR, MLP_SIMT = 0, 1
+DEV_TC_TIMEOUT = 1
 FP64, FP32 = 0, 1
 STREAM_AUTO, STREAM_GATHER, STREAM_STRUCTURED, STREAM_STRUCTURED_NODE, STREAM_TILED_REG, STREAM_GATHER_SMEM = \
     0, 1, 2, 3, 4, 5
@@ -77,6 +79,8 @@ _SIGS = {
     "sllbm_stream": (C.c_void_p, [_P]),
     "sllbm_mlp_set": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_int32]),
     "sllbm_step_features": (C.c_int, [_P, _P, C.c_int32]),
+    "sllbm_mlp_path": (C.c_int, [_P, C.c_int32]),
+    "sllbm_device_status": (C.c_int, [_P, _P]),
     "sllbm_moment_basis": (C.c_int, [_P, _P, _P]),
     "sllbm_train_create": (C.c_int, [_P, _P, C.POINTER(_P)]),
     "sllbm_train_destroy": (C.c_int, [_P]),

@@ -375,7 +375,7 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->d_red, ctx->d_flag,
-                    ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref};
+                    ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -814,7 +814,15 @@ int step_once(sllbm_ctx* ctx, float* feat) {
             if (!(ctx->tiled && ctx->velset == SLLBM_D2Q19))
                 return fail(ctx, SLLBM_ERR_UNSUPPORTED,
                             "learned collision is built for D2Q19 with the warp-tiled structured kernel");
-            rc = mlpm == 1 ? launch_step_tiled<1, float, 1>(L) : launch_step_tiled<1, float, 2>(L);
+            if (mlpm == 2) {
+                rc = launch_step_tiled<1, float, 2>(L);
+            } else if (ctx->mlp_tensor) {
+                L.mlp_tc = ctx->mlp_tc;
+                L.status = ctx->d_status;
+                rc = launch_step_tiled<1, float, 3>(L);
+            } else {
+                rc = launch_step_tiled<1, float, 1>(L);
+            }
         } else {
             rc = dispatch_step<float>(ctx, L);
         }
@@ -885,9 +893,50 @@ int sllbm_mlp_set(sllbm_ctx* ctx, const uint16_t* w_bf16, const float* biases, c
     for (int p = 0; p < 2 * H + Q; ++p) img[k++] = biases[p];
     for (int q = 0; q < Q; ++q) img[k++] = s_in[q];
     img[img.size() - 1] = sigma;
+    // the same weights as BF16 operand tiles of the tensor-core path:
+    // W1 [64][K1], W2 [64][64], W3 [N3][64], zero padded, canonical K-major
+    using TC = MlpTc<19, 2>;
+    std::vector<uint16_t> tiles(TC::B_BYTES / 2, 0);
+    auto put = [&](int base_bytes, int r, int kk, int K, uint16_t v) {
+        tiles[(base_bytes + tc_canon_offset(r, kk, K)) / 2] = v;
+    };
+    const uint16_t* W1 = w_bf16;
+    const uint16_t* W2 = W1 + H * Q;
+    const uint16_t* W3 = W2 + H * H;
+    for (int j = 0; j < H; ++j)
+        for (int q = 0; q < Q; ++q) put(0, j, q, TC::K1, W1[j * Q + q]);
+    for (int j = 0; j < H; ++j)
+        for (int q = 0; q < H; ++q) put(TC::B1, j, q, H, W2[j * H + q]);
+    for (int i = 0; i < Q; ++i)
+        for (int q = 0; q < H; ++q) put(TC::B1 + TC::B2, i, q, H, W3[i * H + q]);
+    if (!ctx->mlp_tc) CK(cudaMalloc(&ctx->mlp_tc, TC::B_BYTES));
+    if (!ctx->d_status) {
+        CK(cudaMalloc(&ctx->d_status, sizeof(int)));
+        CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+    }
+    CK(cudaMemcpyAsync(ctx->mlp_tc, tiles.data(), TC::B_BYTES, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->mlp_img, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->mlp_enabled = true;
+    return SLLBM_OK;
+}
+
+int sllbm_mlp_path(sllbm_ctx* ctx, int32_t path) {
+    if (!ctx || (path != SLLBM_MLP_TENSOR && path != SLLBM_MLP_SIMT)) return SLLBM_ERR_ARG;
+    ctx->mlp_tensor = path == SLLBM_MLP_TENSOR;
+    return SLLBM_OK;
+}
+
+int sllbm_device_status(sllbm_ctx* ctx, int32_t* code) {
+    if (!ctx || !code) return SLLBM_ERR_ARG;
+    *code = 0;
+    cudaSetDevice(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->d_status) return SLLBM_OK;
+    int v = 0;
+    CK(cudaMemcpy(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    *code = v;
     return SLLBM_OK;
 }
 

@@ -23,6 +23,9 @@ __host__ __device__ constexpr int mlp_image_floats(int Q, int D) {
     return MLP_H * Q + MLP_H * MLP_H + Q * MLP_H + 2 * MLP_H + Q + Q + Q * Q + (D + 2) * (D + 2) + 1;
 }
 
+// floats of the three weight matrices at the head of the image
+__host__ __device__ constexpr int mlp_weight_floats(int Q) { return MLP_H * Q + MLP_H * MLP_H + Q * MLP_H; }
+
 template <int Q, int D>
 struct MlpView {
     const float* W1;
@@ -40,6 +43,19 @@ struct MlpView {
         W2 = W1 + MLP_H * Q;
         W3 = W2 + MLP_H * MLP_H;
         b1 = W3 + Q * MLP_H;
+        b2 = b1 + MLP_H;
+        b3 = b2 + MLP_H;
+        s_in = b3 + Q;
+        phi = s_in + Q;
+        ginv = phi + Q * Q;
+        sigma = ginv[(D + 2) * (D + 2)];
+    }
+    // view of the image's tail only (biases onward): the tensor-core path keeps
+    // the weights as BF16 operand tiles instead
+    struct TailOnly {};
+    __device__ __forceinline__ MlpView(const float* tail, TailOnly) {
+        W1 = W2 = W3 = nullptr;
+        b1 = tail;
         b2 = b1 + MLP_H;
         b3 = b2 + MLP_H;
         s_in = b3 + Q;
@@ -69,6 +85,10 @@ __device__ __forceinline__ void mlp_moments(const MlpView<Q, D>& M, const real (
     }
 }
 
+template <int Q, int D, typename real>
+__device__ __forceinline__ void mlp_project_add(const MlpView<Q, D>& M, const CollideConst<real>& C,
+                                                const float (&o)[Q], real (&f)[Q]);
+
 // correction of the post-collision f (deviation storage: adds delta f)
 template <int Q, int D, typename real>
 __device__ __forceinline__ void mlp_correct(const MlpView<Q, D>& M, const CollideConst<real>& C, const float (&z)[Q],
@@ -96,7 +116,14 @@ __device__ __forceinline__ void mlp_correct(const MlpView<Q, D>& M, const Collid
 #pragma unroll
         for (int i = 0; i < Q; ++i) o[i] += M.W3[i * MLP_H + j] * h;
     }
-    // weighted moments of o along {1, xi, |xi|^2}, then remove them
+    mlp_project_add<Q, D, real>(M, C, o, f);
+}
+
+// f += w_i sigma (P o)_i: removes from o its weighted moments along
+// {1, xi, |xi|^2} (inverse Gram matrix), so mass, momentum and energy are unchanged
+template <int Q, int D, typename real>
+__device__ __forceinline__ void mlp_project_add(const MlpView<Q, D>& M, const CollideConst<real>& C,
+                                                const float (&o)[Q], real (&f)[Q]) {
     float m[D + 2];
 #pragma unroll
     for (int l = 0; l < D + 2; ++l) m[l] = 0.f;

@@ -4,6 +4,7 @@
 // thread per arrival node, all 2Q streamed values held in registers.
 #pragma once
 #include "mlp.cuh"
+#include "mlp_tc.cuh"
 #include "sllbm_internal.h"
 
 namespace sllbm {
@@ -22,6 +23,8 @@ struct StepLaunch {
     StepGeom G;
     const CollideConst<real>* C;    // host copy, passed by value to the kernel
     cudaStream_t stream;
+    const uint16_t* mlp_tc = nullptr;   // BF16 weight tiles of the tensor-core MLP (mlp_tc.cuh)
+    int* status = nullptr;              // device status word (tensor-core MLP)
 };
 
 __device__ __forceinline__ int wrapi(int k, int N) { return k >= N ? k - N : k; }
@@ -242,28 +245,36 @@ __global__ void __launch_bounds__(128) k_step_gather(const typename Vec2<real>::
 // contracts them with the y/z weights; the x factor is then applied with warp
 // shuffles from the neighbouring lanes (offsets within [-H, H], checked at
 // setup).  Only lanes H .. H+W-1 store.
+// MLPM: 0 plain collision, 1 learned correction on CUDA cores, 2 export of
+// the MLP features, 3 learned correction on the tensor cores (mlp_tc.cuh:
+// every thread of the block takes part, idle warps included).
 template <int VS, int H, typename real, int MLPM>
 __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T* __restrict__ fg,
                                                     typename Vec2<real>::T* __restrict__ fgo,
                                                     const TileRec<real>* __restrict__ tab,
                                                     const real* __restrict__ twt, const StepGeom G,
                                                     const CollideConst<real> C, const float* __restrict__ mlp_img,
-                                                    float* __restrict__ feat) {
+                                                    float* __restrict__ feat, const uint16_t* __restrict__ mlp_tc,
+                                                    int* __restrict__ status) {
     using VSET = VelSet<VS>;
     using V2 = typename Vec2<real>::T;
     constexpr int Q = VSET::Q;
     constexpr int D = VSET::D;
     constexpr int W = 32 - 2 * H;
     constexpr int NR = D == 3 ? 9 : 3;
-    extern __shared__ __align__(16) unsigned char dyn_smem[];
-    float* mlp_s = reinterpret_cast<float*>(dyn_smem);
-    if (MLPM) mlp_load<Q, D>(mlp_img, mlp_s);        // whole block, before any early exit
+    constexpr bool TC = MLPM == 3;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    float* mlp_s = reinterpret_cast<float*>(dyn_smem + (TC ? MlpTc<Q, D>::OFF_TAIL : 0));
+    if (MLPM == 1 || MLPM == 2) mlp_load<Q, D>(mlp_img, mlp_s);   // whole block, before any early exit
+    uint32_t tbase = 0;
+    if (TC) tbase = mlp_tc_setup<Q, D>(mlp_img, mlp_tc, dyn_smem);
     const int lane = threadIdx.x & 31;
     const int gw = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
     const int Nx = G.N[0], N1 = G.N[1];
     const int tiles = (Nx + W - 1) / W;
     const int rows = D == 3 ? N1 * G.N[2] : N1;
-    if (gw >= tiles * rows) return;              // whole warps only
+    const bool live = gw < tiles * rows;         // whole warps
+    if (!TC && !live) return;
     const int row = gw / tiles;
     const int x0 = (gw - row * tiles) * W;
     const int ky = row % N1;
@@ -280,7 +291,10 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
     const bool seam = (py && (ky < 3 || ky >= N1 - 3)) || (D == 3 && (kz < 3 || kz >= G.N[2] - 3));
     const V2* base = fg + n;
     real fs[Q], gs[Q];
-    Unroll<0, Q>::run([&](auto ic) {
+    if (TC && !live) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fs[i] = gs[i] = real(0);
+    } else Unroll<0, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         const TileRec<real>* r = tab + i * G.n_classes + cls;
         const int4 h0 = __ldg(reinterpret_cast<const int4*>(r));
@@ -332,7 +346,20 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
         fs[i] = of;
         gs[i] = og;
     });
-    if (MLPM) {
+    if (TC) {
+        float z[Q];
+        const MlpView<Q, D> M(mlp_s, typename MlpView<Q, D>::TailOnly{});
+        if (live) {
+            real fneq[Q];
+            collide_node<VSET, real>(C, fs, gs, twt[cls], fneq);
+            mlp_moments<Q, D, real>(M, fneq, z);
+        } else {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) z[k] = 0.f;
+        }
+        mlp_correct_tc<Q, D, real>(M, C, dyn_smem, tbase, z, fs, status);   // whole block; frees TMEM
+        if (!live) return;
+    } else if (MLPM) {
         real fneq[Q];
         collide_node<VSET, real>(C, fs, gs, twt[cls], fneq);
         const MlpView<Q, D> M(mlp_s);
@@ -496,12 +523,13 @@ int launch_step_tiled(const StepLaunch<real>& L) {
     const int tiles = (L.G.N[0] + W - 1) / W;
     const int64_t rows = D == 3 ? int64_t(L.G.N[1]) * L.G.N[2] : L.G.N[1];
     const int64_t threads = int64_t(tiles) * rows * 32;
-    const int bs = 128;
-    const size_t smem = MLPM ? sizeof(float) * mlp_image_floats(Q, D) : 0;
+    const int bs = 128;   // = TC_M: the tensor-core MLP takes one node per TMEM lane
+    const size_t smem = MLPM == 3 ? size_t(MlpTc<Q, D>::SMEM) : MLPM ? sizeof(float) * mlp_image_floats(Q, D) : 0;
+    if (MLPM == 3 && (!L.mlp_tc || !L.status)) return SLLBM_ERR_ARG;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_step_tiled<VS, H, real, MLPM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     k_step_tiled<VS, H, real, MLPM><<<unsigned((threads + bs - 1) / bs), bs, smem, L.stream>>>(
-        L.fg, L.fgo, L.tile, L.tw, L.G, *L.C, L.mlp_img, L.feat);
+        L.fg, L.fgo, L.tile, L.tw, L.G, *L.C, L.mlp_img, L.feat, L.mlp_tc, L.status);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
@@ -687,10 +715,12 @@ int launch_step_gather(const StepLaunch<real>& L) {
     template int launch_step_tiled_smem<VS, real>(const StepLaunch<real>&);
 #define SLLBM_EXTERN_TILED_MLP(VS, real)                                          \
     extern template int launch_step_tiled<VS, real, 1>(const StepLaunch<real>&);  \
-    extern template int launch_step_tiled<VS, real, 2>(const StepLaunch<real>&);
+    extern template int launch_step_tiled<VS, real, 2>(const StepLaunch<real>&);  \
+    extern template int launch_step_tiled<VS, real, 3>(const StepLaunch<real>&);
 #define SLLBM_INSTANTIATE_TILED_MLP(VS, real)                              \
     template int launch_step_tiled<VS, real, 1>(const StepLaunch<real>&);  \
-    template int launch_step_tiled<VS, real, 2>(const StepLaunch<real>&);
+    template int launch_step_tiled<VS, real, 2>(const StepLaunch<real>&);  \
+    template int launch_step_tiled<VS, real, 3>(const StepLaunch<real>&);
 
 #define SLLBM_INSTANTIATE_STEP(VS, P, real)                                              \
     template int launch_step_structured<VS, P, real>(const StepLaunch<real>&);           \

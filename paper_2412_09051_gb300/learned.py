@@ -120,6 +120,15 @@ def set_mlp(sim, w_bf16, biases, s_in, sigma, enable=True):
               1 if enable else 0)
 
 
+def install_params(sim, params, s_in, sigma):
+    """Installs flattened FP32 parameters (W1|b1|W2|b2|W3|b3) as the correction:
+    the library's trainer rounds the weights to BF16."""
+    tr = Trainer(sim, params)
+    w, b = tr.export()
+    tr.close()
+    set_mlp(sim, w, b, s_in, sigma)
+
+
 def step_features(sim):
     z = np.zeros((sim.N, sim.Q), np.float32)
     sim._call("sllbm_step_features", _ptr(z)[0], 0)

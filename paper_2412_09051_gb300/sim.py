@@ -164,6 +164,16 @@ class Sim:
     def sync(self):
         self._call("sllbm_sync")
 
+    def mlp_path(self, path):
+        """capi.MLP_TENSOR (tensor cores, default) or capi.MLP_SIMT (CUDA cores)."""
+        self._call("sllbm_mlp_path", C.c_int32(path))
+
+    def device_status(self):
+        """Synchronise and return (and clear) the context's device status word."""
+        v = C.c_int32(0)
+        self._call("sllbm_device_status", C.byref(v))
+        return v.value
+
     # ---------------------------------------------------------------- readout
     def moments(self):
         rho = np.zeros(self.N)

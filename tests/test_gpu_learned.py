@@ -76,7 +76,21 @@ def test_features_match_oracle(built_lib):
     assert np.abs(fg - f1).max() < 1e-5 * np.abs(f1).max()
 
 
-def test_corrected_step_matches_oracle_and_conserves(built_lib):
+def _random_install(s, Q, seed=5, sigma=3e-4):
+    """Installs a seeded random network on Sim s; returns (W1r, b1, W2r, b2, W3r, b3, s_in, sigma)."""
+    from paper_2412_09051_gb300.learned import set_mlp
+    p = _random_model(Q, seed)
+    W1, b1, W2, b2, W3, b3 = _split(p, Q)
+    W1r, W2r, W3r = (omlp.bf16_round(a) for a in (W1, W2, W3))
+    s_in = np.abs(np.random.default_rng(1).normal(50, 10, Q)).astype(np.float32)
+    bits = np.concatenate([a.astype(np.float32).ravel().view(np.uint32) >> 16 for a in (W1r, W2r, W3r)])
+    set_mlp(s, bits.astype(np.uint16), np.concatenate([b1, b2, b3]).astype(np.float32), s_in, sigma)
+    return W1r, b1, W2r, b2, W3r, b3, s_in, sigma
+
+
+@pytest.mark.parametrize("path", ["tensor", "simt"])
+def test_corrected_step_matches_oracle_and_conserves(built_lib, path):
+    from paper_2412_09051_gb300 import capi
     from paper_2412_09051_gb300.learned import set_mlp
     from paper_2412_09051_gb300.sim import Sim
     cfg = _small()
@@ -90,9 +104,11 @@ def test_corrected_step_matches_oracle_and_conserves(built_lib):
     bits = np.concatenate([a.astype(np.float32).ravel().view(np.uint32) >> 16 for a in (W1r, W2r, W3r)])
     s = Sim(cfg)
     set_mlp(s, bits.astype(np.uint16), np.concatenate([b1, b2, b3]).astype(np.float32), s_in, sigma)
+    s.mlp_path(capi.MLP_TENSOR if path == "tensor" else capi.MLP_SIMT)
     s.init_state(rho, u, T)
     c0, _ = s.conservation()
     s.step(1)
+    assert s.device_status() == 0
     fg, gg = s.get_state()
     net = omlp.MLP(W1r, np.float32(b1), W2r, np.float32(b2), W3r, np.float32(b3), s_in, sigma)
     df = net.correction(fneq, xi, w, omlp.moment_basis(xi, w), omlp.projector(xi, w))
@@ -106,6 +122,40 @@ def test_corrected_step_matches_oracle_and_conserves(built_lib):
     c_plain, _ = plain.conservation()
     c1, _ = s.conservation()
     assert np.abs(c1 - c_plain).max() < 1e-9 * np.abs(c0).max()
+
+
+def test_tensor_core_path_matches_cuda_cores(built_lib):
+    """The tensor-core evaluation (BF16 hi + lo activations, FP32 accumulation
+    in tensor memory) against the CUDA-core one over 20 corrected steps on a
+    178 x 178 node grid: 7 tiles of 26 nodes per row, the last one ragged,
+    1246 warps in 312 blocks of 128 threads, the last block with two idle
+    warps.  Both compute the same network; they differ by FP32 summation
+    order only, far less than the correction itself (plain run)."""
+    from paper_2412_09051_gb300 import capi
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = get_config("learned", cells=89)
+    cfg["init"] = dict(kind="isentropic_vortex", mach=0.9, seed=4)
+    plain = Sim(cfg, stream_mode=4)
+    plain.init_state(*initial_fields(cfg, plain.node_coords()))
+    plain.step(20)
+    fp, _ = plain.get_state()
+    out = {}
+    for path in (capi.MLP_TENSOR, capi.MLP_SIMT):
+        s = Sim(cfg)
+        _random_install(s, s.Q, seed=11, sigma=1e-3)
+        s.mlp_path(path)
+        s.init_state(*initial_fields(cfg, s.node_coords()))
+        f0, _ = s.get_state()
+        s.step(20)
+        assert s.device_status() == 0
+        out[path] = s.get_state()
+    ft, gt = out[capi.MLP_TENSOR]
+    fs, gs = out[capi.MLP_SIMT]
+    assert np.abs(ft - f0).max() > 1e-3 * np.abs(f0).max()   # the run moved
+    d = np.abs(ft - fs).max()
+    assert d < 2e-6 * np.abs(fs).max()
+    assert np.abs(gt - gs).max() < 2e-6 * np.abs(gs).max()
+    assert np.abs(ft - fp).max() > 100 * d
 
 
 def test_training_gradients_match_oracle(built_lib):
