@@ -45,6 +45,14 @@ SLLBM_EXTERN_STEP(1, 2, double)
 SLLBM_EXTERN_STEP(1, 3, double)
 SLLBM_EXTERN_STEP(2, 2, double)
 SLLBM_EXTERN_STEP(3, 2, double)
+SLLBM_EXTERN_STEP(0, 4, float)
+SLLBM_EXTERN_STEP(1, 4, float)
+SLLBM_EXTERN_STEP(2, 4, float)
+SLLBM_EXTERN_STEP_COMPACT(3, 4, float)
+SLLBM_EXTERN_STEP(0, 4, double)
+SLLBM_EXTERN_STEP(1, 4, double)
+SLLBM_EXTERN_STEP(2, 4, double)
+SLLBM_EXTERN_STEP_COMPACT(3, 4, double)
 SLLBM_EXTERN_TILED(0, float)
 SLLBM_EXTERN_TILED(1, float)
 SLLBM_EXTERN_TILED(2, float)
@@ -306,11 +314,17 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     CASE(1, 3)
     CASE(2, 2)
     CASE(3, 2)
+    CASE(0, 4)
+    CASE(1, 4)
+    CASE(2, 4)
 #undef CASE
-    return fail(ctx, SLLBM_ERR_UNSUPPORTED, "velocity set / order combination not built (p must be 2, or 3 for D2Q19)");
+    if (vs == 3 && p == 4)
+        return st ? launch_step_structured_smem<3, 4, real>(L) : launch_step_gather_smem<3, 4, real>(L);
+    return fail(ctx, SLLBM_ERR_UNSUPPORTED,
+                "velocity set / order combination not built (p must be 2 or 4, or 3 for D2Q19)");
 }
 
-bool supported(int vs, int p) { return p == 2 || (vs == SLLBM_D2Q19 && p == 3); }
+bool supported(int vs, int p) { return p == 2 || p == 4 || (vs == SLLBM_D2Q19 && p == 3); }
 
 // The warp-tiled kernel needs p = 2, periodic x, x-tap offsets within +-3
 // nodes, and y/z factors (and record kinds) independent of the x parity.

@@ -72,7 +72,7 @@ template <typename real>
 struct ClassRec {             // structured-mode record (per velocity and class)
     int32_t cell[3];          // periodic dims: offset from the home cell; else absolute
     int32_t meta;             // kind | bid << 4 | src << 8
-    real wt[3][4];            // 1D Lagrange weights per dimension
+    real wt[3][5];            // 1D Lagrange weights per dimension (p <= 4)
 };
 
 template <typename real>

@@ -29,6 +29,40 @@ struct StepLaunch {
 
 __device__ __forceinline__ int wrapi(int k, int N) { return k >= N ? k - N : k; }
 
+// sum-factorised tensor-product interpolation of one (f, g) population from
+// the (P+1)^D source nodes at p + off[0][a] + off[1][b] (+ off[2][c]):
+// x first, then y, then z; loads and multiply-adds interleaved (no staging)
+template <int D, int P, typename real, typename V2>
+__device__ __forceinline__ void interp_direct(const V2* __restrict__ p, const int64_t (&off)[3][P + 1],
+                                              const real (&wt)[3][P + 1], real& of, real& og) {
+    real sf = 0, sg = 0;
+#pragma unroll
+    for (int c3 = 0; c3 <= (D == 3 ? P : 0); ++c3) {
+        real uf = 0, ug = 0;
+#pragma unroll
+        for (int b = 0; b <= P; ++b) {
+            real tf = 0, tg = 0;
+#pragma unroll
+            for (int a = 0; a <= P; ++a) {
+                const V2 v = __ldg(p + off[0][a] + off[1][b] + (D == 3 ? off[2][c3] : 0));
+                tf += wt[0][a] * v.x;
+                tg += wt[0][a] * v.y;
+            }
+            uf += wt[1][b] * tf;
+            ug += wt[1][b] * tg;
+        }
+        if (D == 3) {
+            sf += wt[2][c3] * uf;
+            sg += wt[2][c3] * ug;
+        } else {
+            sf = uf;
+            sg = ug;
+        }
+    }
+    of = sf;
+    og = sg;
+}
+
 // ------------------------------------------------------------ structured
 template <int VS, int P, typename real>
 __global__ void __launch_bounds__(128) k_step_structured(const typename Vec2<real>::T* __restrict__ fg,
@@ -130,6 +164,80 @@ __global__ void __launch_bounds__(128) k_step_structured(const typename Vec2<rea
         constexpr int i = decltype(ic)::value;
         fgo[int64_t(i) * NN + n] = Vec2<real>::make(fs[i], gs[i]);
     });
+}
+
+// ------------------------------------------------------------ structured, state in shared memory
+// The per-class records of k_step_structured with a runtime velocity loop and
+// the node's 2Q streamed values in shared memory ([2][Q][128] per block), for
+// orders whose (P+1)^D taps per population make a fully unrolled body too
+// large (3D, p = 4: 125 taps).  No block barrier: threads are independent.
+template <int VS, int P, typename real>
+__global__ void __launch_bounds__(128, 4) k_step_structured_smem(const typename Vec2<real>::T* __restrict__ fg,
+                                                              typename Vec2<real>::T* __restrict__ fgo,
+                                                              const ClassRec<real>* __restrict__ tab,
+                                                              const real* __restrict__ twt, const StepGeom G,
+                                                              const CollideConst<real> C) {
+    using VSET = VelSet<VS>;
+    using V2 = typename Vec2<real>::T;
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    real* S = reinterpret_cast<real*>(dyn_smem);
+    const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n >= G.n_nodes) return;
+    const int N0 = G.N[0], N1 = G.N[1];
+    int k[3];
+    k[0] = int(n % N0);
+    k[1] = int((n / N0) % N1);
+    k[2] = D == 3 ? int(n / (int64_t(N0) * N1)) : 0;
+    int cl[3], home[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        cl[d] = (d < D && G.periodic[d]) ? k[d] % P : (d < D ? k[d] : 0);
+        home[d] = k[d] / P;
+    }
+    const int cls = cl[0] + G.ncls[0] * (cl[1] + G.ncls[1] * cl[2]);
+    const int64_t NN = G.n_nodes;
+    constexpr int stride = 128;                  // the launch block size
+    real* Sf = S + threadIdx.x;
+    real* Sg = S + Q * stride + threadIdx.x;
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) {
+        const ClassRec<real>& r = tab[i * G.n_classes + cls];
+        const int meta = __ldg(&r.meta);
+        const int kind = meta & 15;
+        const int bid = (meta >> 4) & 15;
+        real of, og;
+        if (kind == REC_EQ) {
+            of = C.eqf[bid][i];
+            og = C.eqg[bid][i];
+        } else {
+            int64_t off[3][P + 1];
+            real wt[3][P + 1];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                int c = d < D ? __ldg(&r.cell[d]) : 0;
+                if (d < D && G.periodic[d]) {
+                    c += home[d];
+                    c %= G.cells[d];
+                    if (c < 0) c += G.cells[d];
+                }
+                const int64_t st = d == 0 ? 1 : (d == 1 ? int64_t(N0) : int64_t(N0) * N1);
+#pragma unroll
+                for (int a = 0; a <= P; ++a) {
+                    int kk = c * P + a;
+                    if (d < D && G.periodic[d]) kk = wrapi(kk, G.N[d]);
+                    off[d][a] = d < D ? kk * st : 0;
+                    wt[d][a] = d < D ? __ldg(&r.wt[d][a]) : real(0);
+                }
+            }
+            interp_direct<D, P, real, V2>(fg + int64_t(meta >> 8) * NN, off, wt, of, og);
+            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+        }
+        Sf[i * stride] = of;
+        Sg[i * stride] = og;
+    }
+    collide_smem<VSET, real, V2, 128>(C, Sf, Sg, twt[cls], fgo + n, int(NN));
 }
 
 // ------------------------------------------------------------ gather
@@ -263,7 +371,7 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
     constexpr int W = 32 - 2 * H;
     constexpr int NR = D == 3 ? 9 : 3;
     constexpr bool TC = MLPM == 3;
-    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    extern __shared__ __align__(16) unsigned char dyn_smem[];   // 16 B: enough for the no-swizzle operand tiles
     float* mlp_s = reinterpret_cast<float*>(dyn_smem + (TC ? MlpTc<Q, D>::OFF_TAIL : 0));
     if (MLPM == 1 || MLPM == 2) mlp_load<Q, D>(mlp_img, mlp_s);   // whole block, before any early exit
     uint32_t tbase = 0;
@@ -550,6 +658,7 @@ __global__ void __launch_bounds__(128, 4) k_step_gather_smem(const typename Vec2
     constexpr int T1 = P + 1;
     constexpr int NT = D == 3 ? T1 * T1 * T1 : T1 * T1;
     constexpr int GV = NT <= 16 ? 2 : 1;
+    constexpr bool STAGE = NT <= 32;             // else interpolate while loading (3D, p >= 3)
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     real* S = reinterpret_cast<real*>(dyn_smem);
     const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -570,6 +679,48 @@ __global__ void __launch_bounds__(128, 4) k_step_gather_smem(const typename Vec2
     constexpr int stride = 128;                  // the launch block size
     real* Sf = S + threadIdx.x;
     real* Sg = S + Q * stride + threadIdx.x;
+    if constexpr (!STAGE) {
+#pragma unroll 1
+        for (int i = 0; i < Q; ++i) {
+            const int cw = __ldg(code + int64_t(i) * NN + n);
+            const int kind = (cw >> 24) & 15;
+            const int bid = (cw >> 28) & 15;
+            real of, og;
+            if (kind == REC_EQ) {
+                of = C.eqf[bid][i];
+                og = C.eqg[bid][i];
+            } else {
+                const int cell = cw & 0xFFFFFF;
+                int cc[3];
+                cc[0] = cell % C0;
+                cc[1] = (cell / C0) % C1;
+                cc[2] = cell / (C0 * C1);
+                int64_t off[3][T1];
+                real wt[3][T1];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (d < D) {
+                        lagrange_w<P, real>(__ldg(gxi + (int64_t(i) * D + d) * NN + n), xh, inv_den, wt[d]);
+                    } else {
+#pragma unroll
+                        for (int a = 0; a <= P; ++a) wt[d][a] = real(0);
+                    }
+                    const int64_t st = d == 0 ? 1 : (d == 1 ? int64_t(N0) : int64_t(N0) * N1);
+#pragma unroll
+                    for (int a = 0; a <= P; ++a) {
+                        int kk = cc[d] * P + a;
+                        if (d < D && G.periodic[d]) kk = wrapi(kk, G.N[d]);
+                        off[d][a] = d < D ? kk * st : 0;
+                    }
+                }
+                const int src = (kind == REC_BB || kind == REC_BB_ISO) ? C.opp[i] : i;
+                interp_direct<D, P, real, V2>(fg + int64_t(src) * NN, off, wt, of, og);
+                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+            }
+            Sf[i * stride] = of;
+            Sg[i * stride] = og;
+        }
+    } else
 #pragma unroll 1
     for (int i0 = 0; i0 < Q; i0 += GV) {
         int cw[GV];
@@ -695,6 +846,20 @@ int launch_step_structured(const StepLaunch<real>& L) {
 }
 
 template <int VS, int P, typename real>
+int launch_step_structured_smem(const StepLaunch<real>& L) {
+    constexpr int Q = VelSet<VS>::Q;
+    const int bs = 128;
+    const int64_t grid = (L.G.n_nodes + bs - 1) / bs;
+    const size_t smem = sizeof(real) * 2 * Q * bs;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_step_structured_smem<VS, P, real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem));
+    k_step_structured_smem<VS, P, real><<<unsigned(grid), bs, smem, L.stream>>>(L.fg, L.fgo, L.cls, L.tw, L.G,
+                                                                              *L.C);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
+template <int VS, int P, typename real>
 int launch_step_gather(const StepLaunch<real>& L) {
     const int bs = 128;
     const int64_t grid = (L.G.n_nodes + bs - 1) / bs;
@@ -725,6 +890,14 @@ int launch_step_gather(const StepLaunch<real>& L) {
 #define SLLBM_INSTANTIATE_STEP(VS, P, real)                                              \
     template int launch_step_structured<VS, P, real>(const StepLaunch<real>&);           \
     template int launch_step_gather<VS, P, real>(const StepLaunch<real>&);               \
+    template int launch_step_gather_smem<VS, P, real>(const StepLaunch<real>&);
+// orders whose fully unrolled kernels would be too large (3D, p = 4): the
+// runtime-loop structured and gather kernels only
+#define SLLBM_EXTERN_STEP_COMPACT(VS, P, real)                                                \
+    extern template int launch_step_structured_smem<VS, P, real>(const StepLaunch<real>&);    \
+    extern template int launch_step_gather_smem<VS, P, real>(const StepLaunch<real>&);
+#define SLLBM_INSTANTIATE_STEP_COMPACT(VS, P, real)                                    \
+    template int launch_step_structured_smem<VS, P, real>(const StepLaunch<real>&);    \
     template int launch_step_gather_smem<VS, P, real>(const StepLaunch<real>&);
 
 }  // namespace sllbm

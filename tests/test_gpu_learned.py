@@ -100,7 +100,7 @@ def test_corrected_step_matches_oracle_and_conserves(built_lib, path):
     W1, b1, W2, b2, W3, b3 = _split(p, Q)
     W1r, W2r, W3r = (omlp.bf16_round(a) for a in (W1, W2, W3))
     s_in = np.abs(np.random.default_rng(1).normal(50, 10, Q)).astype(np.float32)
-    sigma = 3e-4
+    sigma = 3e-2                       # max |delta f| ~ 1e-3: FP32 storage keeps it to ~1e-5 relative
     bits = np.concatenate([a.astype(np.float32).ravel().view(np.uint32) >> 16 for a in (W1r, W2r, W3r)])
     s = Sim(cfg)
     set_mlp(s, bits.astype(np.uint16), np.concatenate([b1, b2, b3]).astype(np.float32), s_in, sigma)
@@ -113,12 +113,15 @@ def test_corrected_step_matches_oracle_and_conserves(built_lib, path):
     net = omlp.MLP(W1r, np.float32(b1), W2r, np.float32(b2), W3r, np.float32(b3), s_in, sigma)
     df = net.correction(fneq, xi, w, omlp.moment_basis(xi, w), omlp.projector(xi, w))
     ref = f1 + df
-    assert np.abs(df).max() > 1e-6                       # the correction is not negligible
+    assert np.abs(df).max() > 1e-4                       # the correction is not negligible
     assert np.abs(fg - ref).max() < 1e-5 * np.abs(ref).max()
-    # exact conservation: the learned step conserves what the plain step conserves
     plain = Sim(cfg, stream_mode=4)          # the kernel that carries the correction
     plain.init_state(rho, u, T)
     plain.step(1)
+    # the correction itself: GPU (corrected - plain) against the oracle's delta f
+    fp, _ = plain.get_state()
+    assert np.abs((fg - fp) - df).max() < 2e-4 * np.abs(df).max()
+    # exact conservation: the learned step conserves what the plain step conserves
     c_plain, _ = plain.conservation()
     c1, _ = s.conservation()
     assert np.abs(c1 - c_plain).max() < 1e-9 * np.abs(c0).max()
@@ -126,36 +129,42 @@ def test_corrected_step_matches_oracle_and_conserves(built_lib, path):
 
 def test_tensor_core_path_matches_cuda_cores(built_lib):
     """The tensor-core evaluation (BF16 hi + lo activations, FP32 accumulation
-    in tensor memory) against the CUDA-core one over 20 corrected steps on a
-    178 x 178 node grid: 7 tiles of 26 nodes per row, the last one ragged,
-    1246 warps in 312 blocks of 128 threads, the last block with two idle
-    warps.  Both compute the same network; they differ by FP32 summation
-    order only, far less than the correction itself (plain run)."""
+    in tensor memory) against the CUDA-core one on a 178 x 178 node grid:
+    7 tiles of 26 nodes per row, the last one ragged, 1246 warps in 312
+    blocks of 128 threads, the last block with two idle warps.  Both compute
+    the same network and differ by FP32 summation order: the one-step
+    corrections (corrected - plain) agree to 2e-4 of their size at every
+    node, and 20-step runs stay within FP32 round-off of each other."""
     from paper_2412_09051_gb300 import capi
     from paper_2412_09051_gb300.sim import Sim
     cfg = get_config("learned", cells=89)
     cfg["init"] = dict(kind="isentropic_vortex", mach=0.9, seed=4)
     plain = Sim(cfg, stream_mode=4)
     plain.init_state(*initial_fields(cfg, plain.node_coords()))
-    plain.step(20)
-    fp, _ = plain.get_state()
-    out = {}
+    plain.step(1)
+    fp, gp = plain.get_state()
+    one, many = {}, {}
     for path in (capi.MLP_TENSOR, capi.MLP_SIMT):
         s = Sim(cfg)
-        _random_install(s, s.Q, seed=11, sigma=1e-3)
+        _random_install(s, s.Q, seed=11, sigma=3e-2)
         s.mlp_path(path)
         s.init_state(*initial_fields(cfg, s.node_coords()))
         f0, _ = s.get_state()
-        s.step(20)
+        s.step(1)
+        one[path] = s.get_state()
+        s.step(19)
         assert s.device_status() == 0
-        out[path] = s.get_state()
-    ft, gt = out[capi.MLP_TENSOR]
-    fs, gs = out[capi.MLP_SIMT]
+        many[path] = s.get_state()
+    dt_ = one[capi.MLP_TENSOR][0] - fp
+    ds_ = one[capi.MLP_SIMT][0] - fp
+    assert np.abs(ds_).max() > 1e-4
+    assert np.abs(dt_ - ds_).max() < 2e-4 * np.abs(ds_).max()
+    assert np.abs(one[capi.MLP_TENSOR][1] - gp).max() < 1e-6 * np.abs(gp).max()   # g carries no correction
+    ft, gt = many[capi.MLP_TENSOR]
+    fs, gs = many[capi.MLP_SIMT]
     assert np.abs(ft - f0).max() > 1e-3 * np.abs(f0).max()   # the run moved
-    d = np.abs(ft - fs).max()
-    assert d < 2e-6 * np.abs(fs).max()
-    assert np.abs(gt - gs).max() < 2e-6 * np.abs(gs).max()
-    assert np.abs(ft - fp).max() > 100 * d
+    assert np.abs(ft - fs).max() < 1e-5 * np.abs(fs).max()
+    assert np.abs(gt - gs).max() < 1e-5 * np.abs(gs).max()
 
 
 def test_training_gradients_match_oracle(built_lib):

@@ -22,6 +22,13 @@ CASES = {
     "mixing_fp32": (lambda: get_config("mixing", cells=(3, 8, 2)), "fp32"),
     "naca_fp32": (lambda: get_config("naca", cells=(16, 6)), "fp32"),
     "learned_fp32": (lambda: get_config("learned", cells=8), "fp32"),
+    # order p = 4, the order of every case in Sec. 4
+    "tgv2d_p4_fp64": (lambda: dict(get_config("tgv2d", cells=4), mesh=dict(kind=0, p=4, cells=(4, 3),
+                                                                           length=(6.2831853, 5.0))), "fp64"),
+    "box_d2q25_p4_fp32": (lambda: box_cfg(cells=(3, 4), p=4, velset="D2Q25", dt=0.02, mu=0.02, Pr=0.71,
+                                          mu_exp=0.7), "fp32"),
+    "channel_p4_fp32": (lambda: get_config("channel", cells=(2, 3, 2), p=4), "fp32"),
+    "naca_p4_fp32": (lambda: get_config("naca", cells=(8, 4), p=4), "fp32"),
 }
 
 

@@ -66,6 +66,7 @@ def _mixing(cells=(96, 64, 48), p=2, mac=0.7, precision="fp32"):
 
 
 def _learned(cells=128, p=2, precision="fp32"):
+    cells = int(cells[0]) if isinstance(cells, (tuple, list)) else int(cells)   # square box
     L = 2.0 * math.pi
     return dict(
         name=f"learned2d_{cells}x{cells}_p{p}", velset="D2Q19",
