@@ -175,8 +175,12 @@ def mlp_flops_per_node(Q, H=64):
 
 def _cfg_of(args):
     from workloads import get_config
-    return get_config(args.config, cells=tuple(int(c) for c in args.cells.split(","))) if args.cells \
-        else get_config(args.config)
+    over = {}
+    if args.cells:
+        over["cells"] = tuple(int(c) for c in args.cells.split(","))
+    if args.p:
+        over["p"] = args.p
+    return get_config(args.config, **over)
 
 
 def run_oracle_subprocess(cfg_name, target_s):
@@ -200,8 +204,7 @@ def run_gpu(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    cfg = get_config(args.config, cells=tuple(int(c) for c in args.cells.split(","))) if args.cells \
-        else get_config(args.config)
+    cfg = _cfg_of(args)
     stream = torch.cuda.Stream()
     sim = Sim(cfg, device=local, stream=stream.cuda_stream, stream_mode=args.mode)
     N, Q = sim.N, sim.Q
@@ -322,6 +325,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", default=None, help="override the cell counts, e.g. 32,48,24 (profiling runs)")
+    ap.add_argument("--p", type=int, default=None, help="override the Lagrange order (e.g. 4, the paper's)")
     ap.add_argument("--mode", type=int, default=0, help="streaming mode (include/sllbm.h SLLBM_STREAM_*)")
     ap.add_argument("--learned", default="none", choices=["none", "tensor", "simt"],
                     help="time the learned-correction step (config learned): MLP on tensor or CUDA cores")

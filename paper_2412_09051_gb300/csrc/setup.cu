@@ -133,7 +133,31 @@ __device__ int locate_naca(const TraceArgs& A, const double x[2], int ca0, int c
             cr = nr;
             continue;
         }
-        return -1;   // inside the reference square but Newton did not converge
+        // Newton did not converge yet ended inside the reference square, which
+        // gives no direction (strongly curved cells, e.g. next to the trailing
+        // edge at p = 4): search the 3 x 3 neighbourhood and take the lowest
+        // containing cell index, the brute-force search's tie rule
+        int best = -1;
+        double bxi[2] = {0.0, 0.0};
+        for (int dr = -1; dr <= 1; ++dr)
+            for (int da = -1; da <= 1; ++da) {
+                const int r2 = cr + dr, a2 = (ca + da + M.cells[0]) % M.cells[0];
+                if ((dr == 0 && da == 0) || r2 < 0 || r2 >= M.cells[1]) continue;
+                double xi2[2];
+                if (newton_cell(M, a2, r2, x, xi2, A.max_newton) && fabs(xi2[0]) <= tol && fabs(xi2[1]) <= tol) {
+                    const int idx = r2 * M.cells[0] + a2;
+                    if (best < 0 || idx < best) {
+                        best = idx;
+                        bxi[0] = xi2[0];
+                        bxi[1] = xi2[1];
+                    }
+                }
+            }
+        if (best < 0) return -1;
+        cell = best;
+        xi[0] = bxi[0];
+        xi[1] = bxi[1];
+        return 1;
     }
     return -1;
 }
