@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import step as ost
-from oracle.departure import REC_EQ
+from oracle.departure import REC_BB, REC_BB_ISO, REC_EQ, REC_OUTLET
 from tests.oracle_cases import box_cfg, oracle_case
 from workloads import get_config, initial_fields
 
@@ -89,14 +89,46 @@ def test_setup_matches_oracle(built_lib, name):
     assert (r["src"] == rec["src"]).all()
     nb = rec["kind"] != 0
     assert (r["bid"][nb] == rec["bid"][nb]).all()
-    src = rec["kind"] != REC_EQ
+    # Source points.  A clamped record (the reflected or mirrored point left
+    # the domain, so its source is where the segment from the inside point
+    # crosses the boundary, found by bisection) is determined only as well as
+    # the inside test near the boundary: where the segment leaves a curved
+    # boundary almost tangentially that is far coarser than rounding.  There
+    # the kind, source, boundary id and cell must agree and the GPU point must
+    # be a valid clamp point: on the segment, inside the mesh, and close to
+    # the oracle's.  Every other source point agrees to rounding.
+    def pdiff(x, y):
+        """x - y with periodic images identified (axis-aligned meshes)."""
+        d = x - y
+        if mesh.kind != 3:
+            for k in range(mesh.D):
+                if mesh.periodic[k]:
+                    d[..., k] -= mesh.length[k] * np.round(d[..., k] / mesh.length[k])
+        return d
+
+    st = cfg["dt"] * xi[:, None, :]
+    Xn = mesh.X[None, :, :]
+    xw = Xn - rec["tw"][:, :, None] * st
+    kind = rec["kind"]
+    bb = (kind == REC_BB) | (kind == REC_BB_ISO)
+    free = np.where(bb[:, :, None], 2 * xw - Xn + st, Xn + st)        # unclamped reflected / mirrored point
+    inner_end = np.where(bb[:, :, None], xw, Xn)
+    clamped = ((kind == REC_BB) | (kind == REC_BB_ISO) | (kind == REC_OUTLET)) & \
+        (np.abs(pdiff(rec["xsrc"], free)).max(axis=2) > 1e-13 * max(1.0, scale))
+    src = (kind != REC_EQ) & ~clamped
+    if clamped.any():
+        assert (r["cell"][clamped] == rec["cell"][clamped]).all()
+        a, b, g = inner_end[clamped], free[clamped], r["xsrc"][clamped]
+        u = (b - a) / np.linalg.norm(b - a, axis=1, keepdims=True)
+        ga = pdiff(g, a)
+        off = ga - (ga * u).sum(1, keepdims=True) * u
+        assert np.abs(off).max() < 1e-12 * max(1.0, scale)                # on the segment
+        from oracle.departure import Locator
+        cg, _ = Locator(mesh).locate(g)
+        assert (cg >= 0).all()                                            # inside the mesh
+        assert np.abs(pdiff(g, rec["xsrc"][clamped])).max() < 1e-6 * max(1.0, scale)
     # physical source points agree (periodic images identified)
-    d = r["xsrc"][src] - rec["xsrc"][src]
-    if mesh.kind != 3:
-        for k in range(mesh.D):
-            if mesh.periodic[k]:
-                L = mesh.length[k]
-                d[:, k] -= L * np.round(d[:, k] / L)
+    d = pdiff(r["xsrc"][src], rec["xsrc"][src])
     if np.abs(d).max() >= 1e-12 * max(1.0, scale):
         j = int(np.abs(d).max(axis=1).argmax())
         i, n = (a[j] for a in np.nonzero(src))
@@ -104,7 +136,8 @@ def test_setup_matches_oracle(built_lib, name):
                     f"kind {rec['kind'][i, n]}: GPU {r['xsrc'][i, n]} oracle {rec['xsrc'][i, n]}, "
                     f"cells {r['cell'][i, n]} / {rec['cell'][i, n]}")
     # cells agree wherever the point is not on a cell face
-    inner = src & (np.abs(rec["xi"]).max(axis=2) < 1 - 1e-9)
+    inner = (kind != REC_EQ) & (np.abs(rec["xi"]).max(axis=2) < 1 - 1e-9)
+    inner &= ~clamped | (np.abs(rec["xi"]).max(axis=2) < 1 - 1e-6)
     assert (r["cell"][inner] == rec["cell"][inner]).all()
     assert np.abs(r["xi"][inner] - rec["xi"][inner]).max() < 1e-10
     sim.close()
