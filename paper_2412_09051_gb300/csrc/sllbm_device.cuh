@@ -326,7 +326,10 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
     if (!(Tw != Tw)) {   // isothermal wall correction (Eq. thermalBC)
         const real tw = Tw - real(1);
         const real rT0 = rho * (real(1) + t), rT1 = rho * (real(1) + tw);
-#pragma unroll
+        // runtime loop: only nodes next to an isothermal wall take this
+        // branch, and a compact body keeps it out of the instruction cache's
+        // way on every other node
+#pragma unroll 1
         for (int i = 0; i < Q; ++i) {
             real cd;
             const real a0 = p1(i, t, cd), a1 = p1(i, tw, cd);
@@ -373,7 +376,17 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
         const real v0 = u0 + C.force_dt[0] * inv_rho, v1 = u1 + C.force_dt[1] * inv_rho;
         const real v2 = D == 3 ? u2 + C.force_dt[2] * inv_rho : real(0);
         const real V = v0 * v0 + v1 * v1 + v2 * v2;
-        if (out) {
+        // the forcing test is hoisted out of the unrolled loop: interleaved
+        // with it, the never-taken forcing code filled the instruction cache
+        // lines of the quasi-equilibrium pass
+        if (out && !C.forced) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                real dq = C.xi[i][0] * q0 + C.xi[i][1] * q1;
+                if (D == 3) dq += C.xi[i][2] * q2;
+                out[i * NN] = Vec2<real>::make(Sf[i * stride], Sg[i * stride] + C.w[i] * dq);
+            }
+        } else if (out) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 real dq = C.xi[i][0] * q0 + C.xi[i][1] * q1;
