@@ -296,7 +296,7 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
     constexpr int Q = VSET::Q;
     constexpr int D = VSET::D;
     Acc<real> arho, aj0, aj1, aj2, ae;
-#pragma unroll
+#pragma unroll 5   // partial unrolling: a full one costs more in instruction fetch than it saves
     for (int i = 0; i < Q; ++i) {
         const real f = Sf[i * stride], g = Sg[i * stride];
         arho.add(f);
@@ -347,8 +347,9 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
     const real rhoT = rho * T;
     const real rhoT_d = rho_d + rho * t;
     real q0 = 0, q1 = 0, q2 = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    // BGK relaxation of velocity i; accumulates the heat flux of the
+    // quasi-equilibrium term
+    auto relax = [&](int i, real& fo, real& go) {
         real cd;
         const real P1 = p1(i, t, cd);
         const real fe = C.w[i] * (rho * P1 + rho_d);
@@ -359,11 +360,24 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
         q0 += (C.xi[i][0] - u0) * h;
         q1 += (C.xi[i][1] - u1) * h;
         if (D == 3) q2 += (C.xi[i][2] - u2) * h;
-        const real fo = f - om * fn, go = g - om * gn;
-        if (C.quasi || C.forced) {
+        fo = f - om * fn;
+        go = g - om * gn;
+    };
+    // one loop per destination, chosen once: a per-velocity test in the
+    // unrolled loop costs instruction fetch on every node
+    if (C.quasi || C.forced) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            real fo, go;
+            relax(i, fo, go);
             Sf[i * stride] = fo;
             Sg[i * stride] = go;
-        } else if (out) {
+        }
+    } else if (out) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            real fo, go;
+            relax(i, fo, go);
             out[i * NN] = Vec2<real>::make(fo, go);
         }
     }
