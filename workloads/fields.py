@@ -37,12 +37,12 @@ def initial_fields(cfg, X, seed=None):
         r = _rng(ini["seed"] if seed is None else seed).uniform(-1.0, 1.0, size=(N, D))
         u += amp * ub * shape[:, None] * r
     elif kind == "mixing_layer":
+        # tanh profile with delta_omega0 = 1 (delta_theta0 = 1/4) plus the
+        # solenoidal broadband disturbance of Sec. 4.4, max |u'| = amp * du
         du, amp = ini["du"], ini["amp"]
         y = X[:, 1]
         u[:, 0] = 0.5 * du * np.tanh(-y / 1.0 * 2.0)
-        env = np.exp(-(y / 2.0) ** 2)
-        r = _rng(ini["seed"] if seed is None else seed).uniform(-1.0, 1.0, size=(N, D))
-        u += amp * du * env[:, None] * r
+        u += spectral_broadband(X, amp * du, 0.25, ini["seed"] if seed is None else seed)
     elif kind == "isentropic_vortex":
         # Shu's isentropic vortex of strength eps advected by a uniform stream
         mach = ini["mach"]
@@ -72,6 +72,67 @@ def initial_fields(cfg, X, seed=None):
     else:
         raise ValueError(kind)
     return rho, u, T
+
+
+def _grid_of(X):
+    """Axes and per-node indices of nodes that form a tensor-product grid."""
+    N, D = X.shape
+    axes, idx = [], []
+    for d in range(D):
+        a = np.unique(np.round(X[:, d], 12))
+        axes.append(a)
+        idx.append(np.searchsorted(a, np.round(X[:, d], 12)))
+    if int(np.prod([len(a) for a in axes])) != N:
+        raise ValueError("nodes do not form a tensor-product grid")
+    return axes, idx
+
+
+def spectral_broadband(X, amp_abs, dtheta0, seed, kdecay=24.0):
+    """Solenoidal broadband velocity disturbance after the recipe of Sec. 4.4:
+    a random vector potential with values uniform in [0, 1] on the node grid
+    (one scalar potential in 2D), scaled in spectral space by exp(-|k| / 24)
+    (k: integer wavenumbers of the node grid, one period per grid length in
+    each direction), multiplied by exp(-(x2 / (2 dtheta0))^2) and differentiated:
+    u' = curl(g Xi).  Derivatives are spectral in node-index space times
+    d(index)/dx from the node spacing (the grid may be stretched).  Scaled so
+    that max |u'| = amp_abs.  X: [N, D] nodes on a tensor-product grid."""
+    N, D = X.shape
+    axes, idx = _grid_of(X)
+    shape = tuple(len(a) for a in axes)               # (n0, n1[, n2]) in x, y, z order
+    r = _rng(seed)
+    ncomp = 3 if D == 3 else 1
+    xi0 = r.uniform(0.0, 1.0, size=(ncomp,) + shape)
+    kv = np.meshgrid(*[np.fft.fftfreq(n) * n for n in shape], indexing="ij")
+    kabs = np.sqrt(sum(k * k for k in kv))
+    F = np.fft.fftn(xi0, axes=tuple(range(1, D + 1))) * np.exp(-kabs / kdecay)
+    Xi = np.fft.ifftn(F, axes=tuple(range(1, D + 1))).real
+    # d(Xi)/dx_d: spectral derivative in index space / (dx_d / d index)
+    dXi = []
+    for d in range(D):
+        ik = 2j * np.pi * kv[d] / shape[d]
+        dd = np.fft.ifftn(F * ik, axes=tuple(range(1, D + 1))).real
+        h = np.gradient(axes[d])                      # dx_d per index step
+        sh = [1] * (D + 1)
+        sh[d + 1] = -1
+        dXi.append(dd / h.reshape(sh))
+    y = axes[1]
+    g = np.exp(-(y / (2.0 * dtheta0)) ** 2)
+    gp = -y / (2.0 * dtheta0 ** 2) * g                 # dg/dy
+    sh = [1] * D
+    sh[1] = -1
+    g, gp = g.reshape(sh), gp.reshape(sh)
+    if D == 2:
+        psi, (dpx, dpy) = Xi[0], (dXi[0][0], dXi[1][0])
+        comp = [g * dpy + gp * psi, -g * dpx]
+    else:
+        # curl(g Xi) = g curl(Xi) + grad(g) x Xi, grad(g) = (0, g', 0)
+        Xx, Xy, Xz = Xi
+        comp = [g * (dXi[1][2] - dXi[2][1]) + gp * Xz,
+                g * (dXi[2][0] - dXi[0][2]),
+                g * (dXi[0][1] - dXi[1][0]) - gp * Xx]
+    up = np.stack([c[tuple(idx)] for c in comp], axis=1)
+    m = np.abs(up).max()
+    return up * (amp_abs / m) if m > 0 else up
 
 
 def random_state_perturbation(Q, N, seed, amp):
