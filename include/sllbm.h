@@ -287,6 +287,43 @@ int sllbm_conservation(sllbm_ctx* ctx, double* out);
  *     exits. */
 int sllbm_conservation_static(sllbm_ctx* ctx, double* out);
 
+/* ------------------------------------------------------------------ flow statistics */
+/* Statistics of the paper's experiments, reduced on the device from the
+ * moments of the current state (rho, u, T per node; p = rho T).
+ *
+ * Reynolds averages (Sec. 4.3, Eq. reynolds) are arithmetic means over the
+ * homogeneous directions x and z, i.e. over the nodes of one plane of constant
+ * y index j (N1 planes); Favre averages (Eq. favre) are mean(rho phi) /
+ * mean(rho); the Reynolds stresses (Eq. rij) are
+ *     R_ab = mean(rho u_a'' u_b'') / mean(rho),  u'' = u - u~.
+ * Axis-aligned meshes only (box, channel, mixing layer); SLLBM_ERR_UNSUPPORTED
+ * on the O-grid, SLLBM_ERR_STATE before init.  Host pointers, each may be
+ * NULL: y [N1] (the plane's y coordinate), rho_bar [N1], u_bar [N1][D]
+ * (Reynolds), u_favre [N1][D], T_bar [N1], p_bar [N1], R [N1][D][D]
+ * (symmetric).  Synchronises the context's stream. */
+int sllbm_plane_profiles(sllbm_ctx* ctx, double* y, double* rho_bar, double* u_bar, double* u_favre, double* T_bar,
+                         double* p_bar, double* R);
+
+/* Temporal mixing layer thicknesses (Sec. 4.4) of the current state:
+ *   delta_theta = 1 / (rho0 du^2) * integral over y of
+ *                 rho_bar (du/2 - u1~)(du/2 + u1~) dy
+ *   delta_omega = du / max |d u1_bar / dy|
+ * The integral is that of the order-p Lagrange interpolant of the plane
+ * values over the mesh's y cells (exact per cell); d/dy is the derivative of
+ * the cell's interpolant at its nodes, maximised over every (cell, node).
+ * du != 0, rho0 > 0; either output may be NULL (not both).  Axis-aligned
+ * meshes only, as sllbm_plane_profiles. */
+int sllbm_mixing_thickness(sllbm_ctx* ctx, double du, double rho0, double* delta_theta, double* delta_omega);
+
+/* Pressure coefficient (Sec. 4.2) C_P = (p - p0) / (gamma/2 p0 Ma^2), p = rho T,
+ * at the nodes of the plane y index 0 (side 0) or N1 - 1 (side 1): on the
+ * O-grid the airfoil surface and the far-field ring, on the channel the two
+ * walls.  p0 > 0 and Ma > 0 are the caller's reference (the inlet state);
+ * gamma is the context's.  *count = N0 * N2 nodes (N2 = 1 in 2D), x fastest;
+ * x [count][D] (node coordinates) and cp [count] are host pointers, either
+ * may be NULL (both NULL: only the count, no state needed). */
+int sllbm_plane_cp(sllbm_ctx* ctx, int32_t side, double p0, double mach, double* x, double* cp, int64_t* count);
+
 /* ------------------------------------------------------------------ setup data */
 
 /* FP64 departure records as produced by the setup pass, one per

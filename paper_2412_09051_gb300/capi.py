@@ -80,6 +80,9 @@ _SIGS = {
     "sllbm_mlp_set": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_int32]),
     "sllbm_step_features": (C.c_int, [_P, _P, C.c_int32]),
     "sllbm_mlp_path": (C.c_int, [_P, C.c_int32]),
+    "sllbm_plane_profiles": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "sllbm_mixing_thickness": (C.c_int, [_P, C.c_double, C.c_double, _P, _P]),
+    "sllbm_plane_cp": (C.c_int, [_P, C.c_int32, C.c_double, C.c_double, _P, _P, _P]),
     "sllbm_device_status": (C.c_int, [_P, _P]),
     "sllbm_moment_basis": (C.c_int, [_P, _P, _P]),
     "sllbm_train_create": (C.c_int, [_P, _P, C.POINTER(_P)]),

@@ -1,6 +1,8 @@
 // C ABI of the SLLBM library: context lifecycle, setup orchestration, step
 // dispatch and readouts.  See include/sllbm.h for the contract of each call.
+#include <algorithm>
 #include <cmath>
+#include <limits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -62,6 +64,11 @@ SLLBM_EXTERN_TILED(1, double)
 SLLBM_EXTERN_TILED(2, double)
 SLLBM_EXTERN_TILED(3, double)
 SLLBM_EXTERN_TILED_MLP(1, float)
+int plane_stat_count(int D);
+int launch_plane_sums(const double* rho, const double* u, const double* T, int D, int N0, int N1, int N2,
+                      double* out, cudaStream_t s);
+int launch_plane_cp(const double* rho, const double* T, int N0, int N1, int N2, int j, double p0, double denom,
+                    double* out, cudaStream_t s);
 void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
                         std::vector<double>& P);
 void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
@@ -389,7 +396,8 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->d_red, ctx->d_flag,
-                    ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status};
+                    ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status,
+                    ctx->d_plane, ctx->d_cp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -1173,3 +1181,158 @@ int sllbm_step_controlled(sllbm_ctx* ctx, int64_t n, const sllbm_control* cfg, d
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ flow statistics (Sec. 4.2-4.4)
+namespace {
+// moments of the current state into ctx->d_mom: rho [N] | u [N][D] | T [N]
+int moments_on_device(sllbm_ctx* ctx, double*& r, double*& u, double*& T) {
+    const int64_t N = ctx->mesh.n_nodes;
+    const int D = ctx->mesh.D;
+    if (!ctx->d_mom) CK(cudaMalloc(&ctx->d_mom, sizeof(double) * N * (D + 2)));
+    r = ctx->d_mom;
+    u = ctx->d_mom + N;
+    T = ctx->d_mom + N * (D + 1);
+    return sllbm_read_moments(ctx, r, u, T, 1);
+}
+
+int plane_checks(sllbm_ctx* ctx) {
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    if (ctx->mesh.kind == SLLBM_MESH_NACA)
+        return fail(ctx, SLLBM_ERR_UNSUPPORTED, "plane statistics need an axis-aligned mesh (box, channel, mixing)");
+    return SLLBM_OK;
+}
+
+// plane means S [N1][K] (see stats.cu for the order of the K values)
+int plane_means(sllbm_ctx* ctx, std::vector<double>& S) {
+    int rc = plane_checks(ctx);
+    if (rc) return rc;
+    cudaSetDevice(ctx->device);
+    const HostMesh& m = ctx->mesh;
+    const int K = plane_stat_count(m.D);
+    double *r, *u, *T;
+    rc = moments_on_device(ctx, r, u, T);
+    if (rc) return rc;
+    if (!ctx->d_plane) CK(cudaMalloc(&ctx->d_plane, sizeof(double) * m.N[1] * K));
+    rc = launch_plane_sums(r, u, T, m.D, m.N[0], m.N[1], m.D == 3 ? m.N[2] : 1, ctx->d_plane, ctx->stream);
+    if (rc) return fail(ctx, rc, "plane statistics launch failed");
+    S.assign(size_t(m.N[1]) * K, 0.0);
+    CK(cudaMemcpyAsync(S.data(), ctx->d_plane, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SLLBM_OK;
+}
+
+// increasing-power coefficients of the Lagrange polynomial a on the nodes xh
+std::vector<double> lagrange_coeffs(const std::vector<double>& xh, int a) {
+    std::vector<double> c(1, 1.0);
+    for (int q = 0; q < int(xh.size()); ++q) {
+        if (q == a) continue;
+        const double s = 1.0 / (xh[a] - xh[q]);
+        std::vector<double> nc(c.size() + 1, 0.0);
+        for (size_t k = 0; k < c.size(); ++k) {
+            nc[k + 1] += c[k] * s;
+            nc[k] -= c[k] * xh[q] * s;
+        }
+        c.swap(nc);
+    }
+    return c;
+}
+}  // namespace
+
+int sllbm_plane_profiles(sllbm_ctx* ctx, double* y, double* rho_bar, double* u_bar, double* u_favre, double* T_bar,
+                         double* p_bar, double* R) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    std::vector<double> S;
+    int rc = plane_means(ctx, S);
+    if (rc) return rc;
+    const HostMesh& m = ctx->mesh;
+    const int D = m.D, K = plane_stat_count(D);
+    for (int j = 0; j < m.N[1]; ++j) {
+        const double* s = &S[size_t(j) * K];
+        const double rb = s[0];
+        double uf[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) uf[a] = s[1 + a] / rb;
+        if (y) y[j] = m.X[size_t(m.N[0]) * j * D + 1];
+        if (rho_bar) rho_bar[j] = rb;
+        for (int a = 0; a < D; ++a) {
+            if (u_bar) u_bar[j * D + a] = s[1 + D + a];
+            if (u_favre) u_favre[j * D + a] = uf[a];
+        }
+        if (T_bar) T_bar[j] = s[1 + 2 * D];
+        if (p_bar) p_bar[j] = s[2 + 2 * D];
+        if (R) {
+            int k = 3 + 2 * D;
+            for (int a = 0; a < D; ++a)
+                for (int b = a; b < D; ++b, ++k) {
+                    const double v = s[k] / rb - uf[a] * uf[b];
+                    R[(size_t(j) * D + a) * D + b] = v;
+                    R[(size_t(j) * D + b) * D + a] = v;
+                }
+        }
+    }
+    return SLLBM_OK;
+}
+
+int sllbm_mixing_thickness(sllbm_ctx* ctx, double du, double rho0, double* delta_theta, double* delta_omega) {
+    if (!ctx || !(du != 0.0) || !(rho0 > 0.0) || (!delta_theta && !delta_omega)) return SLLBM_ERR_ARG;
+    std::vector<double> S;
+    int rc = plane_means(ctx, S);
+    if (rc) return rc;
+    const HostMesh& m = ctx->mesh;
+    const int D = m.D, K = plane_stat_count(D), p = m.p, N1 = m.N[1];
+    // integral over [-1, 1] of each basis polynomial, and their derivatives at the nodes
+    std::vector<double> Wint(p + 1, 0.0), dL((p + 1) * (p + 1), 0.0);
+    for (int a = 0; a <= p; ++a) {
+        const std::vector<double> c = lagrange_coeffs(m.glc, a);
+        for (int k = 0; k < int(c.size()); k += 2) Wint[a] += 2.0 * c[k] / (k + 1);
+        for (int q = 0; q <= p; ++q) {
+            double v = 0.0, xp = 1.0;
+            for (int k = 1; k < int(c.size()); ++k, xp *= m.glc[q]) v += k * c[k] * xp;
+            dL[q * (p + 1) + a] = v;
+        }
+    }
+    double theta = 0.0, slope = 0.0;
+    for (int c = 0; c < m.cells[1]; ++c) {
+        const double h = m.V[1][c + 1] - m.V[1][c];
+        for (int q = 0; q <= p; ++q) {
+            const int j = (c * p + q) % N1;
+            const double* s = &S[size_t(j) * K];
+            const double uf = s[1] / s[0];
+            theta += 0.5 * h * Wint[q] * s[0] * (0.5 * du - uf) * (0.5 * du + uf);
+            double d = 0.0;
+            for (int b = 0; b <= p; ++b) d += dL[q * (p + 1) + b] * S[size_t((c * p + b) % N1) * K + 1 + D];
+            slope = std::max(slope, std::fabs(d) * 2.0 / h);
+        }
+    }
+    if (delta_theta) *delta_theta = theta / (rho0 * du * du);
+    if (delta_omega) *delta_omega = slope > 0.0 ? du / slope : std::numeric_limits<double>::infinity();
+    return SLLBM_OK;
+}
+
+int sllbm_plane_cp(sllbm_ctx* ctx, int32_t side, double p0, double mach, double* x, double* cp, int64_t* count) {
+    if (!ctx || (side != 0 && side != 1) || !(p0 > 0.0) || !(mach > 0.0)) return SLLBM_ERR_ARG;
+    const HostMesh& m = ctx->mesh;
+    const int N2 = m.D == 3 ? m.N[2] : 1;
+    const int64_t M = int64_t(m.N[0]) * N2;
+    if (count) *count = M;
+    if (!x && !cp) return SLLBM_OK;
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    cudaSetDevice(ctx->device);
+    const int j = side == 0 ? 0 : m.N[1] - 1;
+    if (x)
+        for (int64_t q = 0; q < M; ++q) {
+            const int64_t n = q % m.N[0] + int64_t(m.N[0]) * (j + int64_t(m.N[1]) * (q / m.N[0]));
+            for (int d = 0; d < m.D; ++d) x[q * m.D + d] = m.X[size_t(n) * m.D + d];
+        }
+    if (cp) {
+        double *r, *u, *T;
+        int rc = moments_on_device(ctx, r, u, T);
+        if (rc) return rc;
+        if (!ctx->d_cp) CK(cudaMalloc(&ctx->d_cp, sizeof(double) * M));
+        const double denom = 0.5 * ctx->params.gamma * p0 * mach * mach;
+        rc = launch_plane_cp(r, T, m.N[0], m.N[1], N2, j, p0, denom, ctx->d_cp, ctx->stream);
+        if (rc) return fail(ctx, rc, "pressure coefficient launch failed");
+        CK(cudaMemcpyAsync(cp, ctx->d_cp, sizeof(double) * M, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return SLLBM_OK;
+}

@@ -137,6 +137,8 @@ struct sllbm_ctx {
     bool mlp_tensor = true;              // SLLBM_MLP_TENSOR (default) or SLLBM_MLP_SIMT
     uint16_t* mlp_tc = nullptr;          // BF16 weight tiles, canonical K-major layout (device)
     int* d_status = nullptr;             // device status word (tensor-core MLP)
+    double* d_plane = nullptr;           // plane statistics [N1][K]
+    double* d_cp = nullptr;              // pressure coefficient of one node plane
     double force[3] = {0.0, 0.0, 0.0};   // body force density (Kupershtokh forcing)
     double ctl_integral = 0.0;           // PI controller state
     double* d_wref = nullptr;            // reference weights w_i, w_i (2 c_v - D) for rescaling

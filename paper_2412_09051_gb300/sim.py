@@ -164,6 +164,32 @@ class Sim:
     def sync(self):
         self._call("sllbm_sync")
 
+    # ---------------------------------------------------------------- statistics
+    def plane_profiles(self):
+        """Reynolds / Favre plane averages (sllbm_plane_profiles): dict of
+        y, rho, u, u_favre, T, p [N1(, D)] and R [N1, D, D]."""
+        N1, D = self.info.nodes[1], self.D
+        out = dict(y=np.zeros(N1), rho=np.zeros(N1), u=np.zeros((N1, D)), u_favre=np.zeros((N1, D)),
+                   T=np.zeros(N1), p=np.zeros(N1), R=np.zeros((N1, D, D)))
+        self._call("sllbm_plane_profiles", *[_ptr(out[k])[0] for k in ("y", "rho", "u", "u_favre", "T", "p", "R")])
+        return out
+
+    def mixing_thickness(self, du, rho0=1.0):
+        """(delta_theta, delta_omega) of the current state (sllbm_mixing_thickness)."""
+        th, om = C.c_double(), C.c_double()
+        self._call("sllbm_mixing_thickness", C.c_double(du), C.c_double(rho0), C.byref(th), C.byref(om))
+        return th.value, om.value
+
+    def plane_cp(self, side, p0, mach):
+        """(x [M, D], C_P [M]) at the nodes of plane y index 0 (side 0) or N1 - 1 (side 1)."""
+        n = C.c_int64()
+        self._call("sllbm_plane_cp", C.c_int32(side), C.c_double(p0), C.c_double(mach), None, None, C.byref(n))
+        x = np.zeros((n.value, self.D))
+        cp = np.zeros(n.value)
+        self._call("sllbm_plane_cp", C.c_int32(side), C.c_double(p0), C.c_double(mach), _ptr(x)[0], _ptr(cp)[0],
+                   C.byref(n))
+        return x, cp
+
     def mlp_path(self, path):
         """capi.MLP_TENSOR (tensor cores, default) or capi.MLP_SIMT (CUDA cores)."""
         self._call("sllbm_mlp_path", C.c_int32(path))
