@@ -64,6 +64,8 @@ SLLBM_EXTERN_TILED(1, double)
 SLLBM_EXTERN_TILED(2, double)
 SLLBM_EXTERN_TILED(3, double)
 SLLBM_EXTERN_TILED_MLP(1, float)
+int launch_moments_f32(int vs, const float2* fg, int64_t N, const CollideConst<float>& C, double cv, double* rho,
+                       double* u, double* T, cudaStream_t s);
 int plane_stat_count(int D);
 int launch_plane_sums(const double* rho, const double* u, const double* T, int D, int N0, int N1, int N2,
                       double* out, cudaStream_t s);
@@ -995,7 +997,7 @@ int sllbm_read_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int32_
     const int c = ctx->cur;
     int rc = ctx->precision == SLLBM_FP64
                  ? launch_moments<double>(ctx->velset, (double2*)ctx->fg[c], N, ctx->cc64, dr, du, dT, s)
-                 : launch_moments<float>(ctx->velset, (float2*)ctx->fg[c], N, ctx->cc64, dr, du, dT, s);
+                 : launch_moments_f32(ctx->velset, (float2*)ctx->fg[c], N, ctx->cc32, ctx->cc64.cv, dr, du, dT, s);
     if (rc) return fail(ctx, rc, "moments launch failed");
     if (!on_device) {
         if (rho) CK(cudaMemcpyAsync(rho, dr, sizeof(double) * N, cudaMemcpyDeviceToHost, s));

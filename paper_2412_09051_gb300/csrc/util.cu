@@ -88,6 +88,41 @@ __global__ void k_moments(const typename Vec2<real>::T* __restrict__ fg, int64_t
     if (T) T[n] = (e2 - r * U) / (2.0 * r * C.cv);
 }
 
+// FP32 contexts: the same moments from compensated FP32 sums of the stored
+// FP32 deviations (the precision the state carries, as in the step kernels);
+// T is formed in FP64.  FP64 accumulation here was bound by the GB300's FP64
+// rate, not by memory.
+template <int VS>
+__global__ void k_moments_f32(const float2* __restrict__ fg, int64_t N, const CollideConst<float> C, double cv,
+                              double* __restrict__ rho, double* __restrict__ u, double* __restrict__ T) {
+    using VSET = VelSet<VS>;
+    constexpr int D = VSET::D;
+    const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    Acc<float> ar, a0, a1, a2, ae;
+    Unroll<0, VSET::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const float2 v = fg[int64_t(i) * N + n];
+        ar.add(v.x);
+        a0.add(C.xi[i][0] * v.x);
+        a1.add(C.xi[i][1] * v.x);
+        if (D == 3) a2.add(C.xi[i][2] * v.x);
+        ae.add(C.s2[VSET::shell(i)] * v.x);
+        ae.add(v.y);
+    });
+    const double r = 1.0 + double(ar.get());
+    const double j[3] = {double(a0.get()), double(a1.get()), D == 3 ? double(a2.get()) : 0.0};
+    const double e2 = double(ae.get()) + 2.0 * cv;
+    double U = 0;
+    for (int d = 0; d < D; ++d) {
+        const double ud = j[d] / r;
+        U += ud * ud;
+        if (u) u[n * D + d] = ud;
+    }
+    if (rho) rho[n] = r;
+    if (T) T[n] = (e2 - r * U) / (2.0 * r * cv);
+}
+
 // block partial sums of (rho, rho u, 2 rho E) and a positivity flag
 template <int VS, typename real>
 __global__ void k_conserve(const typename Vec2<real>::T* __restrict__ fg, int64_t N,
@@ -166,6 +201,20 @@ int launch_moments(int vs, const typename Vec2<real>::T* fg, int64_t N, const Co
         case 1: k_moments<1, real><<<grid, bs, 0, s>>>(fg, N, C, rho, u, T); break;
         case 2: k_moments<2, real><<<grid, bs, 0, s>>>(fg, N, C, rho, u, T); break;
         case 3: k_moments<3, real><<<grid, bs, 0, s>>>(fg, N, C, rho, u, T); break;
+        default: return SLLBM_ERR_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
+int launch_moments_f32(int vs, const float2* fg, int64_t N, const CollideConst<float>& C, double cv, double* rho,
+                       double* u, double* T, cudaStream_t s) {
+    const int bs = 128;
+    const unsigned grid = unsigned((N + bs - 1) / bs);
+    switch (vs) {
+        case 0: k_moments_f32<0><<<grid, bs, 0, s>>>(fg, N, C, cv, rho, u, T); break;
+        case 1: k_moments_f32<1><<<grid, bs, 0, s>>>(fg, N, C, cv, rho, u, T); break;
+        case 2: k_moments_f32<2><<<grid, bs, 0, s>>>(fg, N, C, cv, rho, u, T); break;
+        case 3: k_moments_f32<3><<<grid, bs, 0, s>>>(fg, N, C, cv, rho, u, T); break;
         default: return SLLBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
