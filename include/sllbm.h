@@ -106,11 +106,12 @@ extern "C" {
                                        registers                                                 */
 #define SLLBM_STREAM_STRUCTURED  2  /* one record per (velocity, translation class of nodes); the
                                        warp-tiled kernel with the node state in shared memory
-                                       where eligible (p = 2, periodic x, taps within +-3 nodes),
-                                       else one thread per node                                  */
+                                       where eligible (p = 2 or 4, periodic x (and z in 3D), x
+                                       taps within +-p nodes), else one thread per node          */
 #define SLLBM_STREAM_STRUCTURED_NODE 3  /* class records, always one thread per node              */
 #define SLLBM_STREAM_TILED_REG   4  /* warp-tiled kernel with the node state in registers (the
-                                       kernel that carries the learned collision)                */
+                                       kernel that carries the learned collision); p = 2 only,
+                                       p = 4 runs the order-4 shared-memory warp-tiled kernel    */
 #define SLLBM_STREAM_GATHER_SMEM 5  /* per-record gather with the node state in shared memory    */
 
 /* ------------------------------------------------------------------ descriptors */

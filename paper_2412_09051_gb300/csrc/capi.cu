@@ -55,6 +55,14 @@ SLLBM_EXTERN_STEP(0, 4, double)
 SLLBM_EXTERN_STEP(1, 4, double)
 SLLBM_EXTERN_STEP(2, 4, double)
 SLLBM_EXTERN_STEP_COMPACT(3, 4, double)
+SLLBM_EXTERN_TILED_P(0, 4, float)
+SLLBM_EXTERN_TILED_P(1, 4, float)
+SLLBM_EXTERN_TILED_P(2, 4, float)
+SLLBM_EXTERN_TILED_P(3, 4, float)
+SLLBM_EXTERN_TILED_P(0, 4, double)
+SLLBM_EXTERN_TILED_P(1, 4, double)
+SLLBM_EXTERN_TILED_P(2, 4, double)
+SLLBM_EXTERN_TILED_P(3, 4, double)
 SLLBM_EXTERN_TILED(0, float)
 SLLBM_EXTERN_TILED(1, float)
 SLLBM_EXTERN_TILED(2, float)
@@ -313,6 +321,16 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
             case 3: return reg ? launch_step_tiled<3, real>(L) : launch_step_tiled_smem<3, real>(L);
         }
     }
+    if (st && ctx->tiled_p == 4) {
+        StepLaunch<real> Lp = L;
+        Lp.tilep = ctx->tile_tab;
+        switch (vs) {
+            case 0: return launch_step_tiled_p<0, 4, real>(Lp);
+            case 1: return launch_step_tiled_p<1, 4, real>(Lp);
+            case 2: return launch_step_tiled_p<2, 4, real>(Lp);
+            case 3: return launch_step_tiled_p<3, 4, real>(Lp);
+        }
+    }
     const bool gsm = ctx->mode == SLLBM_STREAM_GATHER_SMEM;
 #define CASE(VS, P)                                                                                    \
     if (vs == VS && p == P)                                                                            \
@@ -381,6 +399,102 @@ bool tiled_eligible(const sllbm_ctx* c, const std::vector<Rec64>& rec) {
         }
     (void)G;
     return true;
+}
+
+// The order-P warp-tiled kernel needs periodic x (and z in 3D), x taps within
+// +-P lanes, (y, z) offsets within the 4-bit packing (+-7, and nearest image
+// on periodic axes), and every x class of a (y, z) class sharing the record's
+// kind, source, y / z cell and y / z reference coordinates.
+template <int P>
+bool tiled_p_eligible(const sllbm_ctx* c, const std::vector<Rec64>& rec) {
+    const HostMesh& m = c->mesh;
+    if (m.p != P || !m.periodic[0] || m.N[0] < 16) return false;
+    if (int64_t(c->vs.Q) * m.n_nodes >= (int64_t(1) << 31)) return false;
+    if (m.D == 3 && !m.periodic[2]) return false;
+    const StepGeom& G = c->geom;
+    if (G.ncls[0] != P) return false;
+    const int64_t U = c->n_rec_units;
+    const int64_t C01 = int64_t(m.cells[0]) * m.cells[1];
+    for (int i = 0; i < c->vs.Q; ++i)
+        for (int64_t u = 0; u < U; u += P) {     // x class is the fastest class index
+            const Rec64& a = rec[size_t(i * U + u)];
+            for (int k0 = 1; k0 < P; ++k0) {
+                const Rec64& b = rec[size_t(i * U + u + k0)];
+                if (a.meta != b.meta || (a.cell < 0) != (b.cell < 0)) return false;
+                if (a.cell < 0) continue;
+                if ((a.cell / m.cells[0]) % m.cells[1] != (b.cell / m.cells[0]) % m.cells[1] ||
+                    a.cell / C01 != b.cell / C01)
+                    return false;
+                for (int d = 1; d < m.D; ++d)
+                    if (a.xi[d] != b.xi[d]) return false;
+            }
+            if (a.cell < 0) continue;
+            for (int d = 1; d < m.D; ++d) {
+                const int64_t cd = d == 1 ? (a.cell / m.cells[0]) % m.cells[1] : a.cell / C01;
+                const int kd = int((u / (d == 1 ? G.ncls[0] : int64_t(G.ncls[0]) * G.ncls[1])) % G.ncls[d]);
+                for (int t = 0; t <= P; ++t) {
+                    int64_t off = cd * P + t - kd;
+                    if (m.periodic[d]) {
+                        if (off > m.N[d] / 2) off -= m.N[d];
+                        if (off < -m.N[d] / 2) off += m.N[d];
+                        if (2 * (off < 0 ? -off : off) >= m.N[d]) return false;
+                    }
+                    if (off < -7 || off > 7) return false;
+                }
+            }
+            for (int k0 = 0; k0 < P; ++k0) {
+                const Rec64& r = rec[size_t(i * U + u + k0)];
+                const int cx = int(r.cell % m.cells[0]);
+                for (int t = 0; t <= P; ++t) {
+                    int d = cx * P + t - k0;
+                    if (d > m.N[0] / 2) d -= m.N[0];
+                    if (d < -m.N[0] / 2) d += m.N[0];
+                    if (d < -P || d > P) return false;
+                }
+            }
+        }
+    return true;
+}
+
+// Order-P warp-tiled records: x taps as lane offsets, (y, z) row offsets from
+// the class's representative node (nearest image on periodic axes), and the
+// factorised 1D Lagrange weights at the departure point's reference coordinates.
+template <typename real, int P>
+void build_tile_table_p(const sllbm_ctx* c, const std::vector<Rec64>& rec, std::vector<TileRecP<real, P>>& out) {
+    const HostMesh& m = c->mesh;
+    const StepGeom& G = c->geom;
+    const int Q = c->vs.Q, D = m.D;
+    const int64_t U = c->n_rec_units;
+    out.assign(size_t(Q * U), TileRecP<real, P>());
+    for (int i = 0; i < Q; ++i)
+        for (int64_t u = 0; u < U; ++u) {
+            const Rec64& r = rec[size_t(i * U + u)];
+            TileRecP<real, P>& o = out[size_t(i * U + u)];
+            std::memset(&o, 0, sizeof(o));
+            o.meta = r.meta;
+            if (r.cell < 0) continue;
+            const int k[3] = {int(u % G.ncls[0]), int((u / G.ncls[0]) % G.ncls[1]),
+                              int(u / (int64_t(G.ncls[0]) * G.ncls[1]))};
+            const int cc[3] = {int(r.cell % m.cells[0]), int((r.cell / m.cells[0]) % m.cells[1]),
+                               int(r.cell / (int64_t(m.cells[0]) * m.cells[1]))};
+            int packed[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d)
+                for (int a = 0; a <= P; ++a) {
+                    double v = 1.0;
+                    for (int q = 0; q <= P; ++q)
+                        if (q != a) v *= (r.xi[d] - m.glc[q]) / (m.glc[a] - m.glc[q]);
+                    (d == 0 ? o.wx : d == 1 ? o.wy : o.wz)[a] = real(v);
+                    int off = cc[d] * P + a - k[d];
+                    if (m.periodic[d]) {
+                        if (off > m.N[d] / 2) off -= m.N[d];
+                        if (off < -m.N[d] / 2) off += m.N[d];
+                    }
+                    packed[d] |= (off + 8) << (4 * a);
+                }
+            o.dxp = packed[0];
+            o.dyp = packed[1];
+            o.dzp = packed[2];
+        }
 }
 
 }  // namespace
@@ -614,6 +728,22 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
             CK(cudaStreamSynchronize(s));
             ctx->tiled = (ctx->mode == SLLBM_STREAM_STRUCTURED || ctx->mode == SLLBM_STREAM_TILED_REG) &&
                          tiled_eligible(ctx, rec);
+            if ((ctx->mode == SLLBM_STREAM_STRUCTURED || ctx->mode == SLLBM_STREAM_TILED_REG) &&
+                ctx->mesh.p == 4 && tiled_p_eligible<4>(ctx, rec)) {
+                if (rs == 8) {
+                    std::vector<TileRecP<double, 4>> t;
+                    build_tile_table_p(ctx, rec, t);
+                    CK(cudaMalloc(&ctx->tile_tab, sizeof(t[0]) * t.size()));
+                    CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(t[0]) * t.size(), cudaMemcpyHostToDevice, s));
+                } else {
+                    std::vector<TileRecP<float, 4>> t;
+                    build_tile_table_p(ctx, rec, t);
+                    CK(cudaMalloc(&ctx->tile_tab, sizeof(t[0]) * t.size()));
+                    CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(t[0]) * t.size(), cudaMemcpyHostToDevice, s));
+                }
+                CK(cudaStreamSynchronize(s));
+                ctx->tiled_p = 4;
+            }
             if (ctx->tiled) {
                 if (rs == 8) {
                     std::vector<TileRec<double>> t;
@@ -680,7 +810,8 @@ int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
         o->cells[d] = ctx->mesh.cells[d];
     }
     o->precision = ctx->precision;
-    o->stream_mode = ((ctx->mode == SLLBM_STREAM_STRUCTURED || ctx->mode == SLLBM_STREAM_TILED_REG) && !ctx->tiled)
+    o->stream_mode = ((ctx->mode == SLLBM_STREAM_STRUCTURED || ctx->mode == SLLBM_STREAM_TILED_REG) && !ctx->tiled &&
+                      !ctx->tiled_p)
                          ? SLLBM_STREAM_STRUCTURED_NODE
                          : ctx->mode;
     o->state_bytes = int64_t(2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q);

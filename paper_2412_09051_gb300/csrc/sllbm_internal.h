@@ -87,6 +87,15 @@ struct TileRec {              // warp-tiled record (per velocity and class), 16-
     real wx[3];               // x weights
 };
 
+template <typename real, int P>
+struct alignas(16) TileRecP {  // warp-tiled record of order P (per velocity and class), factorised
+    int32_t meta;             // kind | bid << 4 | src << 8
+    int32_t dxp;              // lane offsets of the P + 1 x taps, (dx + 8) in 4-bit fields
+    int32_t dyp;              // y offsets of the P + 1 source rows, (dy + 8) in 4-bit fields
+    int32_t dzp;              // z offsets, likewise (3D)
+    real wx[P + 1], wy[P + 1], wz[P + 1];   // 1D Lagrange weights
+};
+
 struct StepGeom {             // structured / gather kernel geometry
     int N[3], cells[3], periodic[3];
     int ncls[3];              // classes per dimension (p if periodic, else N)
@@ -108,6 +117,7 @@ struct sllbm_ctx {
     sllbm::HostMesh mesh;
     int mode = SLLBM_STREAM_GATHER;      // resolved
     bool tiled = false;                  // structured mode runs the warp-tiled kernel
+    int tiled_p = 0;                     // order of the warp-tiled order-P table (4), 0: none
     int precision = SLLBM_FP32;
     // device geometry
     double* dV[3] = {nullptr, nullptr, nullptr};

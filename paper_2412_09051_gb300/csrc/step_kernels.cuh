@@ -23,6 +23,7 @@ struct StepLaunch {
     StepGeom G;
     const CollideConst<real>* C;    // host copy, passed by value to the kernel
     cudaStream_t stream;
+    const void* tilep = nullptr;        // warp-tiled records of order P (TileRecP), P > 2
     const uint16_t* mlp_tc = nullptr;   // BF16 weight tiles of the tensor-core MLP (mlp_tc.cuh)
     int* status = nullptr;              // device status word (tensor-core MLP)
 };
@@ -641,6 +642,122 @@ int launch_step_tiled(const StepLaunch<real>& L) {
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
+// ------------------------------------------------------------ warp-tiled, order P, state in shared memory
+// The warp-tiled streaming of k_step_tiled_smem for order P cells: a warp owns
+// W = 32 - 2P consecutive x-nodes of one (y, z) row plus P halo lanes per side;
+// per velocity each lane loads its x-column of the (P+1)^(D-1) source rows,
+// contracts them with the factorised y then z weights and takes the x factor
+// from the P+1 neighbouring lanes by shuffles.  Source-row offsets are formed
+// from the packed dy / dz with the periodic wrap (no seam special case).
+// Requires every x class of a (y, z) class to share the record's kind, y/z
+// cell and y/z weights (checked at setup), so branches are warp-uniform.
+template <int VS, int P, typename real>
+__global__ void __launch_bounds__(128, 4) k_step_tiled_p(const typename Vec2<real>::T* __restrict__ fg,
+                                                      typename Vec2<real>::T* __restrict__ fgo,
+                                                      const TileRecP<real, P>* __restrict__ tab,
+                                                      const real* __restrict__ twt, const StepGeom G,
+                                                      const CollideConst<real> C) {
+    using VSET = VelSet<VS>;
+    using V2 = typename Vec2<real>::T;
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    constexpr int H = P, W = 32 - 2 * H;
+    constexpr int NZ = D == 3 ? P + 1 : 1;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    real* S = reinterpret_cast<real*>(dyn_smem);
+    const int lane = threadIdx.x & 31;
+    const int gw = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    const int Nx = G.N[0], N1 = G.N[1], N2 = D == 3 ? G.N[2] : 1;
+    const int tiles = (Nx + W - 1) / W;
+    const int rows = N1 * N2;
+    if (gw >= tiles * rows) return;              // whole warps only
+    const int row = gw / tiles;
+    const int x0 = (gw - row * tiles) * W;
+    const int ky = row % N1;
+    const int kz = row / N1;
+    int kx = (x0 - H + lane) % Nx;
+    if (kx < 0) kx += Nx;
+    const bool store = lane >= H && lane < H + W && (x0 + lane - H) < Nx;
+    const int NN = int(G.n_nodes);
+    const int plane = Nx * N1;
+    const int n = kx + Nx * ky + plane * kz;
+    const bool py = G.periodic[1] != 0;
+    const int cls = (kx % P) + G.ncls[0] * ((py ? (ky % P) : ky) + G.ncls[1] * (D == 3 ? (kz % P) : 0));
+    constexpr int stride = 128;                  // the launch block size
+    real* Sf = S + threadIdx.x;
+    real* Sg = S + Q * stride + threadIdx.x;
+    const V2* base = fg + n;
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) {
+        const TileRecP<real, P> r = tab[i * G.n_classes + cls];
+        const int kind = r.meta & 15;
+        const int bid = (r.meta >> 4) & 15;
+        real of = 0, og = 0;
+        if (kind == REC_EQ) {
+            of = C.eqf[bid][i];
+            og = C.eqg[bid][i];
+        } else {
+            int oy[P + 1], oz[NZ];
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                int ty = ky + ((r.dyp >> (4 * b)) & 15) - 8;
+                if (py) ty += ty < 0 ? N1 : (ty >= N1 ? -N1 : 0);
+                oy[b] = (ty - ky) * Nx;
+            }
+#pragma unroll
+            for (int c = 0; c < NZ; ++c) {
+                int tz = kz + ((r.dzp >> (4 * c)) & 15) - 8;
+                tz += tz < 0 ? N2 : (tz >= N2 ? -N2 : 0);
+                oz[c] = D == 3 ? (tz - kz) * plane : 0;
+            }
+            const V2* p = base + (r.meta >> 8) * NN;
+            real sf = 0, sg = 0;
+#pragma unroll
+            for (int c = 0; c < NZ; ++c) {
+                real tf = 0, tg = 0;
+#pragma unroll
+                for (int b = 0; b <= P; ++b) {
+                    const V2 v = __ldg(p + oy[b] + oz[c]);
+                    tf += r.wy[b] * v.x;
+                    tg += r.wy[b] * v.y;
+                }
+                const real wz = D == 3 ? r.wz[c] : real(1);
+                sf += wz * tf;
+                sg += wz * tg;
+            }
+#pragma unroll
+            for (int a = 0; a <= P; ++a) {
+                // halo lanes may read across the warp edge (the shuffle wraps);
+                // their results are never stored
+                const int dl = lane + ((r.dxp >> (4 * a)) & 15) - 8;
+                of += r.wx[a] * __shfl_sync(0xffffffffu, sf, dl);
+                og += r.wx[a] * __shfl_sync(0xffffffffu, sg, dl);
+            }
+            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+        }
+        Sf[i * stride] = of;
+        Sg[i * stride] = og;
+    }
+    collide_smem<VSET, real, V2, 128>(C, Sf, Sg, twt[cls], store ? fgo + n : nullptr, NN);
+}
+
+template <int VS, int P, typename real>
+int launch_step_tiled_p(const StepLaunch<real>& L) {
+    constexpr int W = 32 - 2 * P;
+    constexpr int Q = VelSet<VS>::Q, D = VelSet<VS>::D;
+    if (!L.tilep) return SLLBM_ERR_ARG;
+    const int tiles = (L.G.N[0] + W - 1) / W;
+    const int64_t rows = D == 3 ? int64_t(L.G.N[1]) * L.G.N[2] : L.G.N[1];
+    const int64_t threads = int64_t(tiles) * rows * 32;
+    const int bs = 128;
+    const size_t smem = sizeof(real) * 2 * Q * bs;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_step_tiled_p<VS, P, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_step_tiled_p<VS, P, real><<<unsigned((threads + bs - 1) / bs), bs, smem, L.stream>>>(
+        L.fg, L.fgo, static_cast<const TileRecP<real, P>*>(L.tilep), L.tw, L.G, *L.C);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
 // ------------------------------------------------------------ gather, state in shared memory
 // One departure record per (velocity, node) as in k_step_gather, with the
 // node state in shared memory, runtime velocity loops and the records and
@@ -899,5 +1016,7 @@ int launch_step_gather(const StepLaunch<real>& L) {
 #define SLLBM_INSTANTIATE_STEP_COMPACT(VS, P, real)                                    \
     template int launch_step_structured_smem<VS, P, real>(const StepLaunch<real>&);    \
     template int launch_step_gather_smem<VS, P, real>(const StepLaunch<real>&);
+#define SLLBM_EXTERN_TILED_P(VS, P, real) extern template int launch_step_tiled_p<VS, P, real>(const StepLaunch<real>&);
+#define SLLBM_INSTANTIATE_TILED_P(VS, P, real) template int launch_step_tiled_p<VS, P, real>(const StepLaunch<real>&);
 
 }  // namespace sllbm

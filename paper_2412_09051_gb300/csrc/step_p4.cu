@@ -7,4 +7,8 @@ SLLBM_INSTANTIATE_STEP(0, 4, float)
 SLLBM_INSTANTIATE_STEP(1, 4, float)
 SLLBM_INSTANTIATE_STEP(2, 4, float)
 SLLBM_INSTANTIATE_STEP_COMPACT(3, 4, float)
+SLLBM_INSTANTIATE_TILED_P(0, 4, float)
+SLLBM_INSTANTIATE_TILED_P(1, 4, float)
+SLLBM_INSTANTIATE_TILED_P(2, 4, float)
+SLLBM_INSTANTIATE_TILED_P(3, 4, float)
 }  // namespace sllbm

@@ -5,4 +5,8 @@ SLLBM_INSTANTIATE_STEP(0, 4, double)
 SLLBM_INSTANTIATE_STEP(1, 4, double)
 SLLBM_INSTANTIATE_STEP(2, 4, double)
 SLLBM_INSTANTIATE_STEP_COMPACT(3, 4, double)
+SLLBM_INSTANTIATE_TILED_P(0, 4, double)
+SLLBM_INSTANTIATE_TILED_P(1, 4, double)
+SLLBM_INSTANTIATE_TILED_P(2, 4, double)
+SLLBM_INSTANTIATE_TILED_P(3, 4, double)
 }  // namespace sllbm

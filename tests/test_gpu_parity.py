@@ -195,6 +195,33 @@ def test_streaming_modes_agree(built_lib, modes):
     assert _scale_err(fa, fb, w) < 1e-5 and _scale_err(ga, gb, w) < 1e-5
 
 
+@pytest.mark.parametrize("name,cells", [("channel", (4, 3, 3)), ("mixing", (4, 4, 3))])
+def test_tiled_order4_matches_oracle_and_class_kernel(built_lib, name, cells):
+    """Order p = 4 (the paper's): the warp-tiled kernel (16 x-nodes, so it is
+    eligible) against the oracle over 3 steps and against the one-thread-per-
+    node class kernel over 5 (3 z cells: with 8 z nodes the +-4 offsets
+    would be ambiguous on the periodic axis and the kernel is not eligible)."""
+    cfg = get_config(name, cells=cells, p=4)
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    a, b = _sim(cfg, "fp32", 2), _sim(cfg, "fp32", 3)
+    assert a.info.stream_mode == 2 and b.info.stream_mode == 3
+    rho, u, T = initial_fields(cfg, mesh.X)
+    f, g = ost.init_equilibrium(rho, u, T, xi, w, par.cv)
+    Tw = ost.isothermal_nodes(rec, par)
+    for s in (a, b):
+        s.init_state(rho, u, T)
+    for k in range(3):
+        f, g = ost.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
+        a.step(1)
+        fa, ga = a.get_state()
+        assert _scale_err(fa, f, w) < 1e-5 and _scale_err(ga, g, w) < 1e-5, k
+    a.step(2)
+    b.step(5)
+    fa, ga = a.get_state()
+    fb, gb = b.get_state()
+    assert _scale_err(fa, fb, w) < 1e-5 and _scale_err(ga, gb, w) < 1e-5
+
+
 def test_checkpoint_resume_bitwise(built_lib):
     cfg = get_config("mixing", cells=(3, 8, 2))
     s = _sim(cfg, "fp32")
