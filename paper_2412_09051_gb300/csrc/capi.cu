@@ -974,7 +974,7 @@ int step_once(sllbm_ctx* ctx, float* feat) {
             } else if (ctx->mlp_tensor) {
                 L.mlp_tc = ctx->mlp_tc;
                 L.status = ctx->d_status;
-                rc = launch_step_tiled<1, float, 3>(L);
+                rc = launch_step_tiled_smem_tc<1, float>(L);
             } else {
                 rc = launch_step_tiled<1, float, 1>(L);
             }

@@ -290,9 +290,12 @@ namespace sllbm {
 // deviations of the thread's node sit at Sf[i * stride], Sg[i * stride]; the
 // post-collision pair of velocity i is written to out[i * NN] (out == nullptr:
 // no store).
-template <class VSET, typename real, typename V2, int stride>
+// KEEP: the post-collision pair stays in Sf / Sg (quasi-equilibrium and
+// forcing applied in place) and f^neq of the streamed state goes to Sn; out is
+// not used (the learned correction is added before the store).
+template <class VSET, typename real, typename V2, int stride, bool KEEP = false>
 __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* Sf, real* Sg, real Tw,
-                                             V2* out, int NN) {
+                                             V2* out, int NN, real* Sn = nullptr) {
     constexpr int Q = VSET::Q;
     constexpr int D = VSET::D;
     // blocked compensation: plain sums over groups of 5 velocities, the
@@ -365,7 +368,7 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
     real q0 = 0, q1 = 0, q2 = 0;
     // BGK relaxation of velocity i; accumulates the heat flux of the
     // quasi-equilibrium term
-    auto relax = [&](int i, real& fo, real& go) {
+    auto relax = [&](int i, real& fo, real& go, real& fno) {
         real cd;
         const real P1 = p1(i, t, cd);
         const real fe = C.w[i] * (rho * P1 + rho_d);
@@ -378,26 +381,62 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
         if (D == 3) q2 += (C.xi[i][2] - u2) * h;
         fo = f - om * fn;
         go = g - om * gn;
+        fno = fn;
     };
     // one loop per destination, chosen once: a per-velocity test in the
     // unrolled loop costs instruction fetch on every node
-    if (C.quasi || C.forced) {
+    if (KEEP) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            real fo, go;
-            relax(i, fo, go);
+            real fo, go, fn;
+            relax(i, fo, go, fn);
+            Sf[i * stride] = fo;
+            Sg[i * stride] = go;
+            Sn[i * stride] = fn;
+        }
+    } else if (C.quasi || C.forced) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            real fo, go, fn;
+            relax(i, fo, go, fn);
             Sf[i * stride] = fo;
             Sg[i * stride] = go;
         }
     } else if (out) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            real fo, go;
-            relax(i, fo, go);
+            real fo, go, fn;
+            relax(i, fo, go, fn);
             out[i * NN] = Vec2<real>::make(fo, go);
         }
     }
-    if (C.quasi || C.forced) {
+    if (KEEP && (C.quasi || C.forced)) {
+        const real a = om - om_pr;
+        q0 *= C.quasi ? a : real(0);
+        q1 *= C.quasi ? a : real(0);
+        q2 *= C.quasi ? a : real(0);
+        const real v0 = u0 + C.force_dt[0] * inv_rho, v1 = u1 + C.force_dt[1] * inv_rho;
+        const real v2 = D == 3 ? u2 + C.force_dt[2] * inv_rho : real(0);
+        const real V = v0 * v0 + v1 * v1 + v2 * v2;
+#pragma unroll 1
+        for (int i = 0; i < Q; ++i) {
+            real dq = C.xi[i][0] * q0 + C.xi[i][1] * q1;
+            if (D == 3) dq += C.xi[i][2] * q2;
+            Sg[i * stride] += C.w[i] * dq;
+            if (C.forced) {   // Kupershtokh exact-difference forcing (Sec. 4.3)
+                real cd;
+                const real pa = p1(i, t, cd);
+                real c = C.xi[i][0] * v0 + C.xi[i][1] * v1;
+                if (D == 3) c += C.xi[i][2] * v2;
+                const real k2 = real(0.5) - real(0.25) * V + real(0.25) * t * C.sCv[i];
+                const real k1 = real(1.0) - real(0.5) * V + real(0.5) * t * C.sBv[i];
+                const real k0 = -real(0.5) * V + real(0.125) * V * V + real(0.5) * t * C.sAv[i] -
+                                real(0.25) * t * V * C.sBv[i] + real(0.125) * t * t * C.sEv[i];
+                Sf[i * stride] += C.w[i] * rho * (eq_poly1(c, k0, k1, k2) - pa);
+            }
+        }
+    }
+    if (!KEEP && (C.quasi || C.forced)) {
         const real a = om - om_pr;
         q0 *= C.quasi ? a : real(0);
         q1 *= C.quasi ? a : real(0);

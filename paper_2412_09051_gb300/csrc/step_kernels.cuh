@@ -355,35 +355,29 @@ __global__ void __launch_bounds__(128) k_step_gather(const typename Vec2<real>::
 // shuffles from the neighbouring lanes (offsets within [-H, H], checked at
 // setup).  Only lanes H .. H+W-1 store.
 // MLPM: 0 plain collision, 1 learned correction on CUDA cores, 2 export of
-// the MLP features, 3 learned correction on the tensor cores (mlp_tc.cuh:
-// every thread of the block takes part, idle warps included).
+// the MLP features (the tensor-core correction runs in k_step_tiled_smem_tc).
 template <int VS, int H, typename real, int MLPM>
 __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T* __restrict__ fg,
                                                     typename Vec2<real>::T* __restrict__ fgo,
                                                     const TileRec<real>* __restrict__ tab,
                                                     const real* __restrict__ twt, const StepGeom G,
                                                     const CollideConst<real> C, const float* __restrict__ mlp_img,
-                                                    float* __restrict__ feat, const uint16_t* __restrict__ mlp_tc,
-                                                    int* __restrict__ status) {
+                                                    float* __restrict__ feat) {
     using VSET = VelSet<VS>;
     using V2 = typename Vec2<real>::T;
     constexpr int Q = VSET::Q;
     constexpr int D = VSET::D;
     constexpr int W = 32 - 2 * H;
     constexpr int NR = D == 3 ? 9 : 3;
-    constexpr bool TC = MLPM == 3;
-    extern __shared__ __align__(16) unsigned char dyn_smem[];   // 16 B: enough for the no-swizzle operand tiles
-    float* mlp_s = reinterpret_cast<float*>(dyn_smem + (TC ? MlpTc<Q, D>::OFF_TAIL : 0));
-    if (MLPM == 1 || MLPM == 2) mlp_load<Q, D>(mlp_img, mlp_s);   // whole block, before any early exit
-    uint32_t tbase = 0;
-    if (TC) tbase = mlp_tc_setup<Q, D>(mlp_img, mlp_tc, dyn_smem);
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    float* mlp_s = reinterpret_cast<float*>(dyn_smem);
+    if (MLPM) mlp_load<Q, D>(mlp_img, mlp_s);        // whole block, before any early exit
     const int lane = threadIdx.x & 31;
     const int gw = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
     const int Nx = G.N[0], N1 = G.N[1];
     const int tiles = (Nx + W - 1) / W;
     const int rows = D == 3 ? N1 * G.N[2] : N1;
-    const bool live = gw < tiles * rows;         // whole warps
-    if (!TC && !live) return;
+    if (gw >= tiles * rows) return;              // whole warps only
     const int row = gw / tiles;
     const int x0 = (gw - row * tiles) * W;
     const int ky = row % N1;
@@ -400,10 +394,7 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
     const bool seam = (py && (ky < 3 || ky >= N1 - 3)) || (D == 3 && (kz < 3 || kz >= G.N[2] - 3));
     const V2* base = fg + n;
     real fs[Q], gs[Q];
-    if (TC && !live) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) fs[i] = gs[i] = real(0);
-    } else Unroll<0, Q>::run([&](auto ic) {
+    Unroll<0, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         const TileRec<real>* r = tab + i * G.n_classes + cls;
         const int4 h0 = __ldg(reinterpret_cast<const int4*>(r));
@@ -455,20 +446,7 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
         fs[i] = of;
         gs[i] = og;
     });
-    if (TC) {
-        float z[Q];
-        const MlpView<Q, D> M(mlp_s, typename MlpView<Q, D>::TailOnly{});
-        if (live) {
-            real fneq[Q];
-            collide_node<VSET, real>(C, fs, gs, twt[cls], fneq);
-            mlp_moments<Q, D, real>(M, fneq, z);
-        } else {
-#pragma unroll
-            for (int k = 0; k < Q; ++k) z[k] = 0.f;
-        }
-        mlp_correct_tc<Q, D, real>(M, C, dyn_smem, tbase, z, fs, status);   // whole block; frees TMEM
-        if (!live) return;
-    } else if (MLPM) {
+    if (MLPM) {
         real fneq[Q];
         collide_node<VSET, real>(C, fs, gs, twt[cls], fneq);
         const MlpView<Q, D> M(mlp_s);
@@ -633,12 +611,180 @@ int launch_step_tiled(const StepLaunch<real>& L) {
     const int64_t rows = D == 3 ? int64_t(L.G.N[1]) * L.G.N[2] : L.G.N[1];
     const int64_t threads = int64_t(tiles) * rows * 32;
     const int bs = 128;   // = TC_M: the tensor-core MLP takes one node per TMEM lane
-    const size_t smem = MLPM == 3 ? size_t(MlpTc<Q, D>::SMEM) : MLPM ? sizeof(float) * mlp_image_floats(Q, D) : 0;
-    if (MLPM == 3 && (!L.mlp_tc || !L.status)) return SLLBM_ERR_ARG;
+    const size_t smem = MLPM ? sizeof(float) * mlp_image_floats(Q, D) : 0;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_step_tiled<VS, H, real, MLPM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     k_step_tiled<VS, H, real, MLPM><<<unsigned((threads + bs - 1) / bs), bs, smem, L.stream>>>(
-        L.fg, L.fgo, L.tile, L.tw, L.G, *L.C, L.mlp_img, L.feat, L.mlp_tc, L.status);
+        L.fg, L.fgo, L.tile, L.tw, L.G, *L.C, L.mlp_img, L.feat);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
+// ------------------------------------------------------------ warp-tiled smem state + learned correction on tcgen05
+// k_step_tiled_smem's streaming and shared-memory collision, then the learned
+// correction on the tensor cores (mlp_tc.cuh).  The node state (f, g and
+// f^neq, 3 Q x 128 values) lives in the shared-memory region of the MMA
+// activation operands, which the network needs only after the collision, so a
+// block takes 51 KB of shared memory and fits 4 per SM next to 4 x 128 TMEM
+// columns.  Every thread of the block takes part (idle warps carry zeros).
+template <int VS, typename real>
+__global__ void __launch_bounds__(128, 4) k_step_tiled_smem_tc(const typename Vec2<real>::T* __restrict__ fg,
+                                                            typename Vec2<real>::T* __restrict__ fgo,
+                                                            const TileRec<real>* __restrict__ tab,
+                                                            const real* __restrict__ twt, const StepGeom G,
+                                                            const CollideConst<real> C,
+                                                            const float* __restrict__ mlp_img,
+                                                            const uint16_t* __restrict__ mlp_tc,
+                                                            int* __restrict__ status) {
+    using VSET = VelSet<VS>;
+    using V2 = typename Vec2<real>::T;
+    using L = MlpTc<VSET::Q, VSET::D>;
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    constexpr int H = 3, W = 32 - 2 * H;
+    constexpr int NR = D == 3 ? 9 : 3;
+    constexpr int stride = 128;                  // the launch block size
+    static_assert(3 * Q * stride * sizeof(real) <= 2 * L::A_BYTES, "node state fits the operand buffers");
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const uint32_t tbase = mlp_tc_setup<Q, D>(mlp_img, mlp_tc, dyn_smem);   // whole block
+    real* S = reinterpret_cast<real*>(dyn_smem + L::OFF_AHI);
+    const int lane = threadIdx.x & 31;
+    const int gw = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    const int Nx = G.N[0], N1 = G.N[1];
+    const int tiles = (Nx + W - 1) / W;
+    const int rows = D == 3 ? N1 * G.N[2] : N1;
+    const bool live = gw < tiles * rows;         // whole warps
+    const int row = live ? gw / tiles : 0;
+    const int x0 = (gw - row * tiles) * W;
+    const int ky = row % N1;
+    const int kz = D == 3 ? row / N1 : 0;
+    int kx = (x0 - H + lane) % Nx;
+    if (kx < 0) kx += Nx;
+    const bool store = live && lane >= H && lane < H + W && (x0 + lane - H) < Nx;
+    const int NN = int(G.n_nodes);
+    const int plane = Nx * N1;
+    const int n = kx + Nx * ky + plane * kz;
+    const bool py = G.periodic[1] != 0;
+    const int cls = (kx & 1) + G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));
+    const bool seam = (py && (ky < 3 || ky >= N1 - 3)) || (D == 3 && (kz < 3 || kz >= G.N[2] - 3));
+    real* Sf = S + threadIdx.x;
+    real* Sg = S + Q * stride + threadIdx.x;
+    real* Sn = S + 2 * Q * stride + threadIdx.x;
+    if (live) {
+        const V2* base = fg + n;
+        // velocities in groups of GV: all record loads of a group, then all source
+        // loads (unconditional: equilibrium records read a valid dummy address), then
+        // the arithmetic, so GV velocities' memory latencies overlap
+        constexpr int GV = 3;
+    #pragma unroll 1
+        for (int i0 = 0; i0 < Q; i0 += GV) {
+            TileRec<real> r[GV];
+    #pragma unroll
+            for (int u = 0; u < GV; ++u) {
+                const int i = min(i0 + u, Q - 1);
+                const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes + cls);
+                int4* dst = reinterpret_cast<int4*>(&r[u]);
+    #pragma unroll
+                for (int k = 0; k < int(sizeof(TileRec<real>) / 16); ++k) dst[k] = __ldg(src + k);
+            }
+            V2 v[GV][NR];
+    #pragma unroll
+            for (int u = 0; u < GV; ++u) {
+                // equilibrium records carry zero offsets and their own velocity as
+                // source, so their (unused) loads read a valid row
+                const bool eq = (r[u].meta & 15) == REC_EQ;
+                int rel[NR];
+    #pragma unroll
+                for (int k = 0; k < NR; ++k) rel[k] = r[u].rel[k];
+                if (seam && !eq) {
+    #pragma unroll
+                    for (int k = 0; k < NR; ++k) {
+                        const int dy = ((r[u].dyzp >> (4 * (k % 3))) & 15) - 8;
+                        const int dz = D == 3 ? ((r[u].dyzp >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+                        int ty = ky + dy, tz = kz + dz;
+                        if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
+                        if (D == 3) { tz += tz < 0 ? G.N[2] : 0; tz -= tz >= G.N[2] ? G.N[2] : 0; }
+                        rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
+                    }
+                }
+                const V2* p = base + (r[u].meta >> 8) * NN;
+    #pragma unroll
+                for (int k = 0; k < NR; ++k) v[u][k] = __ldg(p + rel[k]);
+            }
+    #pragma unroll
+            for (int u = 0; u < GV; ++u) {
+                const int i = i0 + u;
+                if (i >= Q) break;
+                const int kind = r[u].meta & 15;
+                const int bid = (r[u].meta >> 4) & 15;
+                real of, og;
+                if (kind == REC_EQ) {
+                    of = C.eqf[bid][i];
+                    og = C.eqg[bid][i];
+                } else {
+                    real sf = 0, sg = 0;
+    #pragma unroll
+                    for (int k = 0; k < NR; ++k) {
+                        sf += r[u].rw[k] * v[u][k].x;
+                        sg += r[u].rw[k] * v[u][k].y;
+                    }
+                    of = 0;
+                    og = 0;
+    #pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        // source lane; halo lanes may point outside the warp (the
+                        // shuffle wraps) but their results are never stored
+                        const int dl = lane + ((r[u].dxp >> (4 * a)) & 15) - 8;
+                        of += r[u].wx[a] * __shfl_sync(0xffffffffu, sf, dl);
+                        og += r[u].wx[a] * __shfl_sync(0xffffffffu, sg, dl);
+                    }
+                    if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+                }
+                Sf[i * stride] = of;
+                Sg[i * stride] = og;
+            }
+        }
+        collide_smem<VSET, real, V2, 128, true>(C, Sf, Sg, twt[cls], static_cast<V2*>(nullptr), NN, Sn);
+    }
+    const MlpView<Q, D> M(reinterpret_cast<const float*>(dyn_smem + L::OFF_TAIL), typename MlpView<Q, D>::TailOnly{});
+    float z[Q];
+    real f[Q], g[Q];
+    if (live) {
+        real fneq[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            f[i] = Sf[i * stride];
+            g[i] = Sg[i * stride];
+            fneq[i] = Sn[i * stride];
+        }
+        mlp_moments<Q, D, real>(M, fneq, z);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            f[i] = g[i] = real(0);
+            z[i] = 0.f;
+        }
+    }
+    __syncthreads();                             // node state read: the operand buffers are free
+    mlp_correct_tc<Q, D, real>(M, C, dyn_smem, tbase, z, f, status);   // whole block; frees TMEM
+    if (store) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fgo[int64_t(i) * NN + n] = Vec2<real>::make(f[i], g[i]);
+    }
+}
+
+template <int VS, typename real>
+int launch_step_tiled_smem_tc(const StepLaunch<real>& L) {
+    constexpr int H = 3, W = 32 - 2 * H;
+    constexpr int Q = VelSet<VS>::Q, D = VelSet<VS>::D;
+    if (!L.mlp_tc || !L.status || !L.mlp_img) return SLLBM_ERR_ARG;
+    const int tiles = (L.G.N[0] + W - 1) / W;
+    const int64_t rows = D == 3 ? int64_t(L.G.N[1]) * L.G.N[2] : L.G.N[1];
+    const int64_t threads = int64_t(tiles) * rows * 32;
+    const int bs = 128;   // = TC_M: one node per TMEM lane
+    const size_t smem = size_t(MlpTc<Q, D>::SMEM);
+    cudaFuncSetAttribute(k_step_tiled_smem_tc<VS, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_step_tiled_smem_tc<VS, real><<<unsigned((threads + bs - 1) / bs), bs, smem, L.stream>>>(
+        L.fg, L.fgo, L.tile, L.tw, L.G, *L.C, L.mlp_img, L.mlp_tc, L.status);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
@@ -998,11 +1144,11 @@ int launch_step_gather(const StepLaunch<real>& L) {
 #define SLLBM_EXTERN_TILED_MLP(VS, real)                                          \
     extern template int launch_step_tiled<VS, real, 1>(const StepLaunch<real>&);  \
     extern template int launch_step_tiled<VS, real, 2>(const StepLaunch<real>&);  \
-    extern template int launch_step_tiled<VS, real, 3>(const StepLaunch<real>&);
+    extern template int launch_step_tiled_smem_tc<VS, real>(const StepLaunch<real>&);
 #define SLLBM_INSTANTIATE_TILED_MLP(VS, real)                              \
     template int launch_step_tiled<VS, real, 1>(const StepLaunch<real>&);  \
     template int launch_step_tiled<VS, real, 2>(const StepLaunch<real>&);  \
-    template int launch_step_tiled<VS, real, 3>(const StepLaunch<real>&);
+    template int launch_step_tiled_smem_tc<VS, real>(const StepLaunch<real>&);
 
 #define SLLBM_INSTANTIATE_STEP(VS, P, real)                                              \
     template int launch_step_structured<VS, P, real>(const StepLaunch<real>&);           \
