@@ -236,7 +236,7 @@ __device__ __forceinline__ void mlp_correct_tc(const MlpView<Q, D>& M, const Col
     }
     bool ok = tc_layer<L::K1, MLP_H>(ahi, alo, bw1, tbase, bar, 0);
     if (ok) {
-#pragma unroll
+#pragma unroll 1   // runtime chunk loops keep the tanh code small (instruction fetch)
         for (int c = 0; c < MLP_H / 16; ++c) {
             float v[16];
             tc_ld16(trow + 16 * c, v);
@@ -248,7 +248,7 @@ __device__ __forceinline__ void mlp_correct_tc(const MlpView<Q, D>& M, const Col
         ok = tc_layer<MLP_H, MLP_H>(ahi, alo, bw2, tbase + MLP_H, bar, 1);
     }
     if (ok) {
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < MLP_H / 16; ++c) {
             float v[16];
             tc_ld16(trow + MLP_H + 16 * c, v);

@@ -749,14 +749,21 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem_tc(const typename Ve
     float z[Q];
     real f[Q], g[Q];
     if (live) {
-        real fneq[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             f[i] = Sf[i * stride];
             g[i] = Sg[i * stride];
-            fneq[i] = Sn[i * stride];
         }
-        mlp_moments<Q, D, real>(M, fneq, z);
+        // z_k = sum_i Phi_ki f^neq_i, summed in i order as mlp_moments does,
+        // with a runtime velocity loop (a small body for the instruction cache)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) z[k] = 0.f;
+#pragma unroll 1
+        for (int i = 0; i < Q; ++i) {
+            const float fn = float(Sn[i * stride]);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) z[k] += M.phi[k * Q + i] * fn;
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
