@@ -305,6 +305,20 @@ int sllbm_conservation_static(sllbm_ctx* ctx, double* out);
 int sllbm_plane_profiles(sllbm_ctx* ctx, double* y, double* rho_bar, double* u_bar, double* u_favre, double* T_bar,
                          double* p_bar, double* R);
 
+/* Averages over time as well as over x and z (the statistics of a developed
+ * channel or mixing layer): sllbm_stats_accumulate adds the current state's
+ * plane means (the sums behind sllbm_plane_profiles) to running sums on the
+ * device (enqueued on the context's stream, no host synchronisation);
+ * sllbm_stats_reset clears them; sllbm_plane_profiles_mean derives the same
+ * profiles as sllbm_plane_profiles from the time averages of those means,
+ * i.e. Favre averages and Reynolds stresses over x, z and the accumulated
+ * states (*samples: how many; SLLBM_ERR_STATE if none).  Axis-aligned meshes
+ * only. */
+int sllbm_stats_accumulate(sllbm_ctx* ctx);
+int sllbm_stats_reset(sllbm_ctx* ctx);
+int sllbm_plane_profiles_mean(sllbm_ctx* ctx, double* y, double* rho_bar, double* u_bar, double* u_favre,
+                              double* T_bar, double* p_bar, double* R, int64_t* samples);
+
 /* Temporal mixing layer thicknesses (Sec. 4.4) of the current state:
  *   delta_theta = 1 / (rho0 du^2) * integral over y of
  *                 rho_bar (du/2 - u1~)(du/2 + u1~) dy

@@ -33,11 +33,18 @@ def _planes(mesh, a):
 def plane_profiles(mesh, rho, u, T):
     """Per y-node plane: y, rho_bar, u_bar [N1, D], u_favre [N1, D], T_bar,
     p_bar (p = rho T), R [N1, D, D] (Favre Reynolds stresses)."""
+    return plane_profiles_over_states(mesh, [(rho, u, T)])
+
+
+def plane_profiles_over_states(mesh, states):
+    """plane_profiles with the averages taken over x, z and a list of states
+    [(rho, u, T), ...] (Reynolds averages over the homogeneous directions and
+    time): every state contributes its nodes of each plane as samples."""
     if mesh.kind == KIND_NACA:
         raise ValueError("plane statistics need an axis-aligned mesh")
-    r = _planes(mesh, rho)
-    U = _planes(mesh, u)
-    t = _planes(mesh, T)
+    r = np.concatenate([_planes(mesh, s[0]) for s in states], axis=1)
+    U = np.concatenate([_planes(mesh, s[1]) for s in states], axis=1)
+    t = np.concatenate([_planes(mesh, s[2]) for s in states], axis=1)
     rb = r.mean(axis=1)
     ub = U.mean(axis=1)
     uf = (r[:, :, None] * U).mean(axis=1) / rb[:, None]

@@ -82,6 +82,9 @@ _SIGS = {
     "sllbm_mlp_path": (C.c_int, [_P, C.c_int32]),
     "sllbm_plane_profiles": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "sllbm_mixing_thickness": (C.c_int, [_P, C.c_double, C.c_double, _P, _P]),
+    "sllbm_stats_accumulate": (C.c_int, [_P]),
+    "sllbm_stats_reset": (C.c_int, [_P]),
+    "sllbm_plane_profiles_mean": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "sllbm_plane_cp": (C.c_int, [_P, C.c_int32, C.c_double, C.c_double, _P, _P, _P]),
     "sllbm_device_status": (C.c_int, [_P, _P]),
     "sllbm_moment_basis": (C.c_int, [_P, _P, _P]),

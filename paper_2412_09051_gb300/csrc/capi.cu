@@ -76,7 +76,7 @@ int launch_moments_f32(int vs, const float2* fg, int64_t N, const CollideConst<f
                        double* u, double* T, cudaStream_t s);
 int plane_stat_count(int D);
 int launch_plane_sums(const double* rho, const double* u, const double* T, int D, int N0, int N1, int N2,
-                      double* out, cudaStream_t s);
+                      double* out, int accumulate, cudaStream_t s);
 int launch_plane_cp(const double* rho, const double* T, int N0, int N1, int N2, int j, double p0, double denom,
                     double* out, cudaStream_t s);
 void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
@@ -513,7 +513,7 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->d_red, ctx->d_flag,
                     ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status,
-                    ctx->d_plane, ctx->d_cp};
+                    ctx->d_plane, ctx->d_cp, ctx->d_plane_acc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -1346,7 +1346,7 @@ int plane_means(sllbm_ctx* ctx, std::vector<double>& S) {
     rc = moments_on_device(ctx, r, u, T);
     if (rc) return rc;
     if (!ctx->d_plane) CK(cudaMalloc(&ctx->d_plane, sizeof(double) * m.N[1] * K));
-    rc = launch_plane_sums(r, u, T, m.D, m.N[0], m.N[1], m.D == 3 ? m.N[2] : 1, ctx->d_plane, ctx->stream);
+    rc = launch_plane_sums(r, u, T, m.D, m.N[0], m.N[1], m.D == 3 ? m.N[2] : 1, ctx->d_plane, 0, ctx->stream);
     if (rc) return fail(ctx, rc, "plane statistics launch failed");
     S.assign(size_t(m.N[1]) * K, 0.0);
     CK(cudaMemcpyAsync(S.data(), ctx->d_plane, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1371,12 +1371,10 @@ std::vector<double> lagrange_coeffs(const std::vector<double>& xh, int a) {
 }
 }  // namespace
 
-int sllbm_plane_profiles(sllbm_ctx* ctx, double* y, double* rho_bar, double* u_bar, double* u_favre, double* T_bar,
-                         double* p_bar, double* R) {
-    if (!ctx) return SLLBM_ERR_ARG;
-    std::vector<double> S;
-    int rc = plane_means(ctx, S);
-    if (rc) return rc;
+namespace {
+// profiles from plane means S [N1][K] (instantaneous or averaged over time)
+void derive_profiles(const sllbm_ctx* ctx, const std::vector<double>& S, double* y, double* rho_bar, double* u_bar,
+                     double* u_favre, double* T_bar, double* p_bar, double* R) {
     const HostMesh& m = ctx->mesh;
     const int D = m.D, K = plane_stat_count(D);
     for (int j = 0; j < m.N[1]; ++j) {
@@ -1402,6 +1400,64 @@ int sllbm_plane_profiles(sllbm_ctx* ctx, double* y, double* rho_bar, double* u_b
                 }
         }
     }
+}
+}  // namespace
+
+int sllbm_plane_profiles(sllbm_ctx* ctx, double* y, double* rho_bar, double* u_bar, double* u_favre, double* T_bar,
+                         double* p_bar, double* R) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    std::vector<double> S;
+    int rc = plane_means(ctx, S);
+    if (rc) return rc;
+    derive_profiles(ctx, S, y, rho_bar, u_bar, u_favre, T_bar, p_bar, R);
+    return SLLBM_OK;
+}
+
+int sllbm_stats_accumulate(sllbm_ctx* ctx) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    int rc = plane_checks(ctx);
+    if (rc) return rc;
+    cudaSetDevice(ctx->device);
+    const HostMesh& m = ctx->mesh;
+    const int K = plane_stat_count(m.D);
+    if (!ctx->d_plane_acc) {
+        CK(cudaMalloc(&ctx->d_plane_acc, sizeof(double) * m.N[1] * K));
+        CK(cudaMemsetAsync(ctx->d_plane_acc, 0, sizeof(double) * m.N[1] * K, ctx->stream));
+        ctx->stats_samples = 0;
+    }
+    double *r, *u, *T;
+    rc = moments_on_device(ctx, r, u, T);
+    if (rc) return rc;
+    rc = launch_plane_sums(r, u, T, m.D, m.N[0], m.N[1], m.D == 3 ? m.N[2] : 1, ctx->d_plane_acc, 1, ctx->stream);
+    if (rc) return fail(ctx, rc, "plane statistics launch failed");
+    ++ctx->stats_samples;
+    return SLLBM_OK;
+}
+
+int sllbm_stats_reset(sllbm_ctx* ctx) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    ctx->stats_samples = 0;
+    if (ctx->d_plane_acc) {
+        cudaSetDevice(ctx->device);
+        CK(cudaMemsetAsync(ctx->d_plane_acc, 0, sizeof(double) * ctx->mesh.N[1] * plane_stat_count(ctx->mesh.D),
+                           ctx->stream));
+    }
+    return SLLBM_OK;
+}
+
+int sllbm_plane_profiles_mean(sllbm_ctx* ctx, double* y, double* rho_bar, double* u_bar, double* u_favre,
+                              double* T_bar, double* p_bar, double* R, int64_t* samples) {
+    if (!ctx) return SLLBM_ERR_ARG;
+    if (samples) *samples = ctx->stats_samples;
+    if (ctx->stats_samples == 0) return fail(ctx, SLLBM_ERR_STATE, "no state accumulated (sllbm_stats_accumulate)");
+    cudaSetDevice(ctx->device);
+    const HostMesh& m = ctx->mesh;
+    const int K = plane_stat_count(m.D);
+    std::vector<double> S(size_t(m.N[1]) * K);
+    CK(cudaMemcpyAsync(S.data(), ctx->d_plane_acc, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (double& v : S) v /= double(ctx->stats_samples);
+    derive_profiles(ctx, S, y, rho_bar, u_bar, u_favre, T_bar, p_bar, R);
     return SLLBM_OK;
 }
 

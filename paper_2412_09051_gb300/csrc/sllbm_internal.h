@@ -148,6 +148,8 @@ struct sllbm_ctx {
     uint16_t* mlp_tc = nullptr;          // BF16 weight tiles, canonical K-major layout (device)
     int* d_status = nullptr;             // device status word (tensor-core MLP)
     double* d_plane = nullptr;           // plane statistics [N1][K]
+    double* d_plane_acc = nullptr;       // running sums over time of the plane statistics
+    int64_t stats_samples = 0;           // states accumulated into d_plane_acc
     double* d_cp = nullptr;              // pressure coefficient of one node plane
     double force[3] = {0.0, 0.0, 0.0};   // body force density (Kupershtokh forcing)
     double ctl_integral = 0.0;           // PI controller state

@@ -11,7 +11,7 @@ namespace sllbm {
 template <int D>
 __global__ void __launch_bounds__(128) k_plane_sums(const double* __restrict__ rho, const double* __restrict__ u,
                                                     const double* __restrict__ T, int N0, int N1, int N2,
-                                                    double* __restrict__ out) {
+                                                    double* __restrict__ out, int accumulate) {
     constexpr int K = 3 + 2 * D + D * (D + 1) / 2;
     __shared__ double sh[K][128];
     const int j = blockIdx.x;
@@ -48,7 +48,11 @@ __global__ void __launch_bounds__(128) k_plane_sums(const double* __restrict__ r
             for (int k = 0; k < K; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x < K) out[int64_t(j) * K + threadIdx.x] = sh[threadIdx.x][0] / double(M);
+    if (threadIdx.x < K) {
+        const double v = sh[threadIdx.x][0] / double(M);
+        double& o = out[int64_t(j) * K + threadIdx.x];
+        o = accumulate ? o + v : v;   // accumulate: running sums over time of the plane means
+    }
 }
 
 // C_P = (rho T - p0) / denom at the nodes of plane j, x fastest then z
@@ -64,12 +68,12 @@ __global__ void k_plane_cp(const double* __restrict__ rho, const double* __restr
 int plane_stat_count(int D) { return 3 + 2 * D + D * (D + 1) / 2; }
 
 int launch_plane_sums(const double* rho, const double* u, const double* T, int D, int N0, int N1, int N2,
-                      double* out, cudaStream_t s) {
+                      double* out, int accumulate, cudaStream_t s) {
     if (N1 <= 0) return SLLBM_ERR_ARG;
     if (D == 2)
-        k_plane_sums<2><<<N1, 128, 0, s>>>(rho, u, T, N0, N1, N2, out);
+        k_plane_sums<2><<<N1, 128, 0, s>>>(rho, u, T, N0, N1, N2, out, accumulate);
     else if (D == 3)
-        k_plane_sums<3><<<N1, 128, 0, s>>>(rho, u, T, N0, N1, N2, out);
+        k_plane_sums<3><<<N1, 128, 0, s>>>(rho, u, T, N0, N1, N2, out, accumulate);
     else
         return SLLBM_ERR_ARG;
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;

@@ -174,6 +174,25 @@ class Sim:
         self._call("sllbm_plane_profiles", *[_ptr(out[k])[0] for k in ("y", "rho", "u", "u_favre", "T", "p", "R")])
         return out
 
+    def stats_accumulate(self):
+        """Adds the current state's plane means to the running sums (device, async)."""
+        self._call("sllbm_stats_accumulate")
+
+    def stats_reset(self):
+        self._call("sllbm_stats_reset")
+
+    def plane_profiles_mean(self):
+        """Profiles of sllbm_plane_profiles from the time-averaged plane means;
+        also returns the number of accumulated states under 'samples'."""
+        N1, D = self.info.nodes[1], self.D
+        out = dict(y=np.zeros(N1), rho=np.zeros(N1), u=np.zeros((N1, D)), u_favre=np.zeros((N1, D)),
+                   T=np.zeros(N1), p=np.zeros(N1), R=np.zeros((N1, D, D)))
+        n = C.c_int64()
+        self._call("sllbm_plane_profiles_mean", *[_ptr(out[k])[0] for k in ("y", "rho", "u", "u_favre", "T", "p", "R")],
+                   C.byref(n))
+        out["samples"] = n.value
+        return out
+
     def mixing_thickness(self, du, rho0=1.0):
         """(delta_theta, delta_omega) of the current state (sllbm_mixing_thickness)."""
         th, om = C.c_double(), C.c_double()

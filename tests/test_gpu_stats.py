@@ -59,6 +59,32 @@ def test_plane_profiles_match_oracle(built_lib, name, cells):
     s.close()
 
 
+def test_time_averaged_profiles_match_oracle(built_lib):
+    """Running sums over three states of the channel (every second step):
+    the time-and-plane averages against the oracle over the same states."""
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = get_config("channel", cells=(4, 6, 3))
+    mesh = _mesh(cfg)
+    s = Sim(cfg)
+    s.init_state(*initial_fields(cfg, s.node_coords()))
+    s.stats_reset()
+    states = []
+    for k in range(3):
+        s.stats_accumulate()
+        states.append(s.moments())
+        s.step(2)
+    g = s.plane_profiles_mean()
+    assert g["samples"] == 3
+    ref = stats.plane_profiles_over_states(mesh, states)
+    for k in ("y", "rho", "u", "u_favre", "T", "p", "R"):
+        assert _close(g[k], ref[k], 1e-12), k
+    s.stats_reset()
+    from paper_2412_09051_gb300.capi import SllbmError
+    with pytest.raises(SllbmError):
+        s.plane_profiles_mean()
+    s.close()
+
+
 @pytest.mark.parametrize("side", [0, 1])
 def test_pressure_coefficient_matches_oracle(built_lib, side):
     from paper_2412_09051_gb300.sim import Sim

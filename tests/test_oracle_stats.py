@@ -96,3 +96,25 @@ def test_plane_nodes_are_the_boundary_planes():
         n = stats.plane_nodes(mesh, side)
         assert len(n) == mesh.N[0] * mesh.N[2] and len(set(n)) == len(n)
         assert np.allclose(mesh.X[n, 1], y)
+
+
+def test_averages_over_states():
+    """Time averages: one state repeated gives the instantaneous profiles; the
+    Reynolds means of two states are the averages of their means; R over two
+    states includes the fluctuation between them (u1 = +-A in the two states
+    of a uniform field: R_11 = A^2)."""
+    mesh = Mesh(0, 2, (6, 3), (2.0, 1.0))
+    rho, u, T = _fields_cos(mesh, 0.1, 0.2, 0.1, 0.5, 1.0, 0.02)
+    one = stats.plane_profiles(mesh, rho, u, T)
+    rep = stats.plane_profiles_over_states(mesh, [(rho, u, T)] * 3)
+    for k in ("rho", "u", "u_favre", "T", "p", "R"):
+        assert np.abs(one[k] - rep[k]).max() < 1e-15
+    u2 = u * 1.3
+    two = stats.plane_profiles_over_states(mesh, [(rho, u, T), (rho, u2, T)])
+    assert np.abs(two["u"] - 0.5 * (one["u"] + stats.plane_profiles(mesh, rho, u2, T)["u"])).max() < 1e-15
+    A = 0.3
+    ones = np.ones(mesh.n_nodes)
+    ua, ub = np.zeros((mesh.n_nodes, 2)), np.zeros((mesh.n_nodes, 2))
+    ua[:, 0], ub[:, 0] = A, -A
+    pr = stats.plane_profiles_over_states(mesh, [(ones, ua, ones), (ones, ub, ones)])
+    assert np.allclose(pr["u_favre"][:, 0], 0.0, atol=1e-16) and np.allclose(pr["R"][:, 0, 0], A * A, rtol=1e-15)
