@@ -12,10 +12,12 @@ from workloads import get_config, initial_fields
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("name", ["channel", "mixing", "naca", "tgv2d"])
-def test_fullsize_sampled_step(built_lib, name):
+@pytest.mark.parametrize("name,over", [("channel", {}), ("mixing", {}), ("naca", {}), ("tgv2d", {}),
+                                       # the paper's order p = 4 at the channel's node count (tiled order-4 kernel)
+                                       ("channel", {"cells": (32, 24, 24), "p": 4})])
+def test_fullsize_sampled_step(built_lib, name, over):
     from paper_2412_09051_gb300.sim import Sim
-    cfg = get_config(name)
+    cfg = get_config(name, **over)
     m = cfg["mesh"]
     mesh = Mesh(m["kind"], m["p"], m["cells"], m["length"], m.get("stretch", 1.0), m.get("central", 0),
                 m.get("thickness", 0.12))
@@ -29,6 +31,8 @@ def test_fullsize_sampled_step(built_lib, name):
     rec = trace(mesh, xi, opp, cfg["dt"], cfg["bcs"], nodes=nodes)
     f1, g1 = ost.step_sample_from_fields(mesh, rec, rho, u, T, xi, w, par)
     sim = Sim(cfg)
+    if over.get("p") == 4:
+        assert sim.info.stream_mode == 2              # the warp-tiled order-4 kernel, as bench.py runs it
     assert np.abs(sim.node_coords() - mesh.X).max() < 1e-12 * np.abs(mesh.X).max()
     sim.init_state(rho, u, T)
     sim.step(1)
