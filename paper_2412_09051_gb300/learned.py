@@ -228,3 +228,72 @@ def evaluate(model, case, fine_cells=128, steps=20, spinup=4):
         s.close()
     ref.close()
     return out
+
+
+def _resample(a, n_to):
+    """Periodic Fourier resampling of node fields [..., n, n] (uniform nodes,
+    x fastest) onto an n_to x n_to grid over the same box (evaluation only)."""
+    n = a.shape[-1]
+    F = np.fft.fft2(a, axes=(-2, -1))
+    k = min(n, n_to) // 2
+    G = np.zeros(a.shape[:-2] + (n_to, n_to), dtype=complex)
+    for sy in (slice(0, k), slice(-k, None)):
+        for sx in (slice(0, k), slice(-k, None)):
+            G[..., sy, sx] = F[..., sy, sx]
+    return np.fft.ifft2(G, axes=(-2, -1)).real * (n_to * n_to) / (n * n)
+
+
+def evaluate_equal_cost(model, case, fine_cells=128, steps=10, spinup=4, mid_cells=80):
+    """The learned coarse run against a plain run of about the same GPU cost:
+    plain and learned at fine_cells/2 cells (`steps` steps), and plain at
+    mid_cells cells whose step count reaches the same time (cost about
+    (mid/coarse)^3 the plain coarse run in 2D).  Errors of rho, u, T against
+    the FP64 fine reference at each run's own nodes (the reference resampled
+    by Fourier interpolation, the box being periodic), and GPU seconds per run."""
+    import torch
+    from workloads import initial_fields
+    kind, mach, seed = case
+    cf = case_cfg(None, fine_cells, kind, mach, seed)
+    cc = case_cfg(None, fine_cells // 2, kind, mach, seed)
+    cm = case_cfg(None, mid_cells, kind, mach, seed)
+    t_end = steps * cc["dt"]
+    m_steps = int(round(t_end / cm["dt"]))
+    cm["dt"] = t_end / m_steps
+    ref = Sim(cf, precision="fp64")
+    nf = ref.info.nodes[0]
+    ref.init_state(*initial_fields(cf, ref.node_coords()))
+    ref.step(spinup)
+    f0, g0 = ref.get_state()
+    ref.step(int(round(t_end / cf["dt"])))
+    rr, ur, Tr = ref.moments()
+    out = {}
+    runs = (("plain_coarse", cc, False, steps), ("learned_coarse", cc, True, steps),
+            ("plain_mid", cm, False, m_steps))
+    for name, cfg, learned, n_steps in runs:
+        s = Sim(cfg, precision="fp32")
+        n = s.info.nodes[0]
+        Q = f0.shape[0]
+        if learned:
+            set_mlp(s, model["w"], model["b"], model["s_in"], model["sigma"])
+        fi = _resample(f0.reshape(Q, nf, nf), n).reshape(Q, -1)
+        gi = _resample(g0.reshape(Q, nf, nf), n).reshape(Q, -1)
+        s.set_state(fi, gi)
+        s.step(1)                                    # warm-up launch outside the timing
+        s.set_state(fi, gi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(n_steps)
+        s.sync()
+        dt = time.perf_counter() - t0
+        rho_s, u_s, T_s = s.moments()
+        rho_r = _resample(rr.reshape(nf, nf), n).ravel()
+        T_r = _resample(Tr.reshape(nf, nf), n).ravel()
+        u_r = np.stack([_resample(ur[:, d].reshape(nf, nf), n).ravel() for d in range(2)], axis=1)
+        out[name] = dict(cells=cfg["mesh"]["cells"][0], steps=n_steps,
+                         err_rho=float(np.sqrt(np.mean((rho_s - rho_r) ** 2))),
+                         err_u=float(np.sqrt(np.mean((u_s - u_r) ** 2))),
+                         err_T=float(np.sqrt(np.mean((T_s - T_r) ** 2))),
+                         gpu_s=dt)
+        s.close()
+    ref.close()
+    return out
