@@ -141,6 +141,9 @@ def test_setup_matches_oracle(built_lib, name):
     inner &= ~clamped | (np.abs(rec["xi"]).max(axis=2) < 1 - 1e-6)
     assert (r["cell"][inner] == rec["cell"][inner]).all()
     assert np.abs(r["xi"][inner] - rec["xi"][inner]).max() < 1e-10
+    print(f"PARITY setup {name}: source points {np.abs(d).max() / max(1.0, scale):.2e} (relative), "
+          f"reference coordinates {np.abs(r['xi'][inner] - rec['xi'][inner]).max():.2e}, "
+          f"clamped records {int(clamped.sum())}")
     sim.close()
 
 
@@ -162,16 +165,20 @@ def test_steps_match_oracle(built_lib, name, mode):
     fg, gg = sim.get_state()
     assert _scale_err(fg, f, w) < (1e-14 if prec == "fp64" else 1e-7)
     Tw = ost.isothermal_nodes(rec, par)
+    worst = 0.0
     for k in range(3):
         f, g = ost.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
         sim.step(1)
         fg, gg = sim.get_state()
         ef, eg = _scale_err(fg, f, w), _scale_err(gg, g, w)
         assert ef < tol and eg < tol, (k, ef, eg)
+        worst = max(worst, ef, eg)
     r0, u0, T0 = ost.moments(f, g, xi, par.cv)
     r1, u1, T1 = sim.moments()
     assert np.abs(r1 - r0).max() < tol and np.abs(T1 - T0).max() < tol
     assert np.abs(u1 - u0).max() < tol * max(1.0, np.abs(u0).max())
+    em = max(np.abs(r1 - r0).max(), np.abs(T1 - T0).max(), np.abs(u1 - u0).max() / max(1.0, np.abs(u0).max()))
+    print(f"PARITY step {name} mode {sim.info.stream_mode}: populations {worst:.2e} moments {em:.2e}")
     sim.close()
 
 
