@@ -336,10 +336,13 @@ __device__ __forceinline__ void collide_smem(const CollideConst<real>& C, real* 
         real c = C.xi[i][0] * u0 + C.xi[i][1] * u1;
         if (D == 3) c += C.xi[i][2] * u2;
         cd = c;
-        const real k2 = real(0.5) - real(0.25) * U + real(0.25) * tt * C.sCv[i];
-        const real k1 = real(1.0) - real(0.5) * U + real(0.5) * tt * C.sBv[i];
-        const real k0 = -real(0.5) * U + real(0.125) * U * U + real(0.5) * tt * C.sAv[i] -
-                        real(0.25) * tt * U * C.sBv[i] + real(0.125) * tt * tt * C.sEv[i];
+        // per-shell coefficients: in the unrolled loops the shell is a
+        // compile-time index, so velocities of one shell share k0, k1, k2
+        const int sh = VSET::shell(i);
+        const real k2 = real(0.5) - real(0.25) * U + real(0.25) * tt * C.sC[sh];
+        const real k1 = real(1.0) - real(0.5) * U + real(0.5) * tt * C.sB[sh];
+        const real k0 = -real(0.5) * U + real(0.125) * U * U + real(0.5) * tt * C.sA[sh] -
+                        real(0.25) * tt * U * C.sB[sh] + real(0.125) * tt * tt * C.sE[sh];
         return eq_poly1(c, k0, k1, k2);
     };
     if (!(Tw != Tw)) {   // isothermal wall correction (Eq. thermalBC)
