@@ -1342,7 +1342,7 @@ int plane_means(sllbm_ctx* ctx, std::vector<double>& S) {
     cudaSetDevice(ctx->device);
     const HostMesh& m = ctx->mesh;
     const int K = plane_stat_count(m.D);
-    double *r, *u, *T;
+    double *r = nullptr, *u = nullptr, *T = nullptr;
     rc = moments_on_device(ctx, r, u, T);
     if (rc) return rc;
     if (!ctx->d_plane) CK(cudaMalloc(&ctx->d_plane, sizeof(double) * m.N[1] * K));
@@ -1425,7 +1425,7 @@ int sllbm_stats_accumulate(sllbm_ctx* ctx) {
         CK(cudaMemsetAsync(ctx->d_plane_acc, 0, sizeof(double) * m.N[1] * K, ctx->stream));
         ctx->stats_samples = 0;
     }
-    double *r, *u, *T;
+    double *r = nullptr, *u = nullptr, *T = nullptr;
     rc = moments_on_device(ctx, r, u, T);
     if (rc) return rc;
     rc = launch_plane_sums(r, u, T, m.D, m.N[0], m.N[1], m.D == 3 ? m.N[2] : 1, ctx->d_plane_acc, 1, ctx->stream);
@@ -1513,7 +1513,7 @@ int sllbm_plane_cp(sllbm_ctx* ctx, int32_t side, double p0, double mach, double*
             for (int d = 0; d < m.D; ++d) x[q * m.D + d] = m.X[size_t(n) * m.D + d];
         }
     if (cp) {
-        double *r, *u, *T;
+        double *r = nullptr, *u = nullptr, *T = nullptr;
         int rc = moments_on_device(ctx, r, u, T);
         if (rc) return rc;
         if (!ctx->d_cp) CK(cudaMalloc(&ctx->d_cp, sizeof(double) * M));
