@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "sllbm_internal.h"
@@ -55,6 +56,8 @@ SLLBM_EXTERN_STEP(0, 4, double)
 SLLBM_EXTERN_STEP(1, 4, double)
 SLLBM_EXTERN_STEP(2, 4, double)
 SLLBM_EXTERN_STEP_COMPACT(3, 4, double)
+SLLBM_EXTERN_ROW(1, float)
+SLLBM_EXTERN_ROW(3, float)
 SLLBM_EXTERN_TILED_P(0, 4, float)
 SLLBM_EXTERN_TILED_P(1, 4, float)
 SLLBM_EXTERN_TILED_P(2, 4, float)
@@ -312,6 +315,27 @@ template <typename real>
 int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const int vs = ctx->velset, p = ctx->mesh.p;
     const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_SMEM;
+    if constexpr (std::is_same<real, float>::value) {
+        // a periodic row that fits one block exactly: one block per row, where
+        // the block's shared memory still lets 16 warps reside per SM (D3Q45
+        // rows of 192 nodes take 78 KB per block: 12 warps, slower than the
+        // warp tiles)
+        const int nx = ctx->mesh.N[0];
+        if (st && ctx->tiled && ctx->mode == SLLBM_STREAM_STRUCTURED && (vs == 1 || vs == 3) &&
+            (nx == 32 || nx == 64 || nx == 128 || (nx == 192 && vs == 1) || nx == 256)) {
+#define ROWCASE(VS)                                                   \
+    if (vs == VS) {                                                   \
+        if (nx == 32) return launch_step_row_smem<VS, real, 32>(L);   \
+        if (nx == 64) return launch_step_row_smem<VS, real, 64>(L);   \
+        if (nx == 128) return launch_step_row_smem<VS, real, 128>(L); \
+        if (nx == 192) return launch_step_row_smem<VS, real, 192>(L); \
+        return launch_step_row_smem<VS, real, 256>(L);                \
+    }
+            ROWCASE(1)
+            ROWCASE(3)
+#undef ROWCASE
+        }
+    }
     if (st && ctx->tiled) {
         const bool reg = ctx->mode == SLLBM_STREAM_TILED_REG;
         switch (vs) {

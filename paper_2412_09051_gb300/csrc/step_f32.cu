@@ -9,4 +9,5 @@ SLLBM_INSTANTIATE_TILED(0, float)
 SLLBM_INSTANTIATE_TILED(1, float)
 SLLBM_INSTANTIATE_TILED(2, float)
 SLLBM_INSTANTIATE_TILED_MLP(1, float)
+SLLBM_INSTANTIATE_ROW(1, float)
 }  // namespace sllbm

@@ -3,4 +3,5 @@
 namespace sllbm {
 SLLBM_INSTANTIATE_STEP(3, 2, float)
 SLLBM_INSTANTIATE_TILED(3, float)
+SLLBM_INSTANTIATE_ROW(3, float)
 }  // namespace sllbm

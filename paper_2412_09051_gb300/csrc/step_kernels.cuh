@@ -619,6 +619,126 @@ int launch_step_tiled(const StepLaunch<real>& L) {
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
+// ------------------------------------------------------------ one block per periodic row
+// The streaming and collision of k_step_tiled_smem with one block of NXB = Nx
+// threads per (y, z) row of a periodic x axis: every lane is an output node
+// (the warp tiles spend 6 of 32 lanes on halos), and the x factor reads the
+// neighbouring nodes' row sums from a shared row buffer, double-buffered per
+// group of velocities with one block barrier per group.
+template <int VS, typename real, int NXB>
+__global__ void __launch_bounds__(256, 2) k_step_row_smem(const typename Vec2<real>::T* __restrict__ fg,
+                                                       typename Vec2<real>::T* __restrict__ fgo,
+                                                       const TileRec<real>* __restrict__ tab,
+                                                       const real* __restrict__ twt, const StepGeom G,
+                                                       const CollideConst<real> C) {
+    using VSET = VelSet<VS>;
+    using V2 = typename Vec2<real>::T;
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    constexpr int NR = D == 3 ? 9 : 3;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    real* S = reinterpret_cast<real*>(dyn_smem);
+    real* XB = S + 2 * Q * NXB;
+    const int Nx = NXB, N1 = G.N[1];
+    const int row = blockIdx.x;
+    const int ky = row % N1;
+    const int kz = D == 3 ? row / N1 : 0;
+    const int kx = threadIdx.x;
+    const int NN = int(G.n_nodes);
+    const int plane = Nx * N1;
+    const int n = kx + Nx * ky + plane * kz;
+    const bool py = G.periodic[1] != 0;
+    const int cls = (kx & 1) + G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));
+    const bool seam = (py && (ky < 3 || ky >= N1 - 3)) || (D == 3 && (kz < 3 || kz >= G.N[2] - 3));
+    constexpr int stride = NXB;
+    real* Sf = S + threadIdx.x;
+    real* Sg = S + Q * stride + threadIdx.x;
+    const V2* base = fg + n;
+    constexpr int GV = 3;
+    int grp = 0;
+#pragma unroll 1
+    for (int i0 = 0; i0 < Q; i0 += GV, ++grp) {
+        TileRec<real> r[GV];
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const int i = min(i0 + u, Q - 1);
+            const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes + cls);
+            int4* dst = reinterpret_cast<int4*>(&r[u]);
+#pragma unroll
+            for (int k = 0; k < int(sizeof(TileRec<real>) / 16); ++k) dst[k] = __ldg(src + k);
+        }
+        V2 v[GV][NR];
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const bool eq = (r[u].meta & 15) == REC_EQ;
+            int rel[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) rel[k] = r[u].rel[k];
+            if (seam && !eq) {
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const int dy = ((r[u].dyzp >> (4 * (k % 3))) & 15) - 8;
+                    const int dz = D == 3 ? ((r[u].dyzp >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+                    int ty = ky + dy, tz = kz + dz;
+                    if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
+                    if (D == 3) { tz += tz < 0 ? G.N[2] : 0; tz -= tz >= G.N[2] ? G.N[2] : 0; }
+                    rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
+                }
+            }
+            const V2* p = base + (r[u].meta >> 8) * NN;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) v[u][k] = __ldg(p + rel[k]);
+        }
+        real* xb = XB + (grp & 1) * (GV * 2 * NXB);
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            real sf = 0, sg = 0;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                sf += r[u].rw[k] * v[u][k].x;
+                sg += r[u].rw[k] * v[u][k].y;
+            }
+            xb[(2 * u) * NXB + threadIdx.x] = sf;
+            xb[(2 * u + 1) * NXB + threadIdx.x] = sg;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const int i = i0 + u;
+            if (i >= Q) break;
+            const int kind = r[u].meta & 15;
+            const int bid = (r[u].meta >> 4) & 15;
+            real of = 0, og = 0;
+            if (kind == REC_EQ) {
+                of = C.eqf[bid][i];
+                og = C.eqg[bid][i];
+            } else {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int j = int(threadIdx.x) + ((r[u].dxp >> (4 * a)) & 15) - 8;
+                    j += j < 0 ? NXB : (j >= NXB ? -NXB : 0);
+                    of += r[u].wx[a] * xb[(2 * u) * NXB + j];
+                    og += r[u].wx[a] * xb[(2 * u + 1) * NXB + j];
+                }
+                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+            }
+            Sf[i * stride] = of;
+            Sg[i * stride] = og;
+        }
+    }
+    collide_smem<VSET, real, V2, NXB>(C, Sf, Sg, twt[cls], fgo + n, NN);
+}
+
+template <int VS, typename real, int NXB>
+int launch_step_row_smem(const StepLaunch<real>& L) {
+    constexpr int Q = VelSet<VS>::Q, D = VelSet<VS>::D;
+    const int rows = D == 3 ? L.G.N[1] * L.G.N[2] : L.G.N[1];
+    const size_t smem = sizeof(real) * (2 * Q * NXB + 2 * 3 * 2 * NXB);
+    cudaFuncSetAttribute(k_step_row_smem<VS, real, NXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_step_row_smem<VS, real, NXB><<<rows, NXB, smem, L.stream>>>(L.fg, L.fgo, L.tile, L.tw, L.G, *L.C);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
 // ------------------------------------------------------------ warp-tiled smem state + learned correction on tcgen05
 // k_step_tiled_smem's streaming and shared-memory collision, then the learned
 // correction on the tensor cores (mlp_tc.cuh).  The node state (f, g and
@@ -1169,6 +1289,11 @@ int launch_step_gather(const StepLaunch<real>& L) {
 #define SLLBM_INSTANTIATE_STEP_COMPACT(VS, P, real)                                    \
     template int launch_step_structured_smem<VS, P, real>(const StepLaunch<real>&);    \
     template int launch_step_gather_smem<VS, P, real>(const StepLaunch<real>&);
+#define SLLBM_ROW_WIDTHS(X, VS, real) X(VS, real, 32) X(VS, real, 64) X(VS, real, 128) X(VS, real, 192) X(VS, real, 256)
+#define SLLBM_EXTERN_ROW1(VS, real, W) extern template int launch_step_row_smem<VS, real, W>(const StepLaunch<real>&);
+#define SLLBM_INSTANTIATE_ROW1(VS, real, W) template int launch_step_row_smem<VS, real, W>(const StepLaunch<real>&);
+#define SLLBM_EXTERN_ROW(VS, real) SLLBM_ROW_WIDTHS(SLLBM_EXTERN_ROW1, VS, real)
+#define SLLBM_INSTANTIATE_ROW(VS, real) SLLBM_ROW_WIDTHS(SLLBM_INSTANTIATE_ROW1, VS, real)
 #define SLLBM_EXTERN_TILED_P(VS, P, real) extern template int launch_step_tiled_p<VS, P, real>(const StepLaunch<real>&);
 #define SLLBM_INSTANTIATE_TILED_P(VS, P, real) template int launch_step_tiled_p<VS, P, real>(const StepLaunch<real>&);
 
