@@ -260,6 +260,7 @@ def run_gpu(args, ws, rank, local):
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     ms_total = ev[0].elapsed_time(ev[-1])
     cons, rc = sim.conservation(check=False)
+    kernel_name = sim.step_kernel()
     dev_status = sim.device_status() if args.learned != "none" else 0
 
     # end to end through the C ABI: every step, the H2D copy of the step's
@@ -341,11 +342,9 @@ def run_gpu(args, ws, rank, local):
                          "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                          "peak_source": f"{psrc} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "kernel": ({2: "k_step_tiled_smem", 4: "k_step_tiled", 3: "k_step_structured",
-                                     1: "k_step_gather", 5: "k_step_gather_smem"}.get(
-                             sim.info.stream_mode, "k_step") if args.learned == "none"
-                             else f"k_step_tiled (learned, MLP on {'tensor' if args.learned == 'tensor' else 'CUDA'}"
-                                  " cores)") + f"<{cfg['velset']}>"},
+                         "kernel": kernel_name + f"<{cfg['velset']}>" +
+                                   ("" if args.learned == "none" else
+                                    f" (learned, MLP on {'tensor' if args.learned == 'tensor' else 'CUDA'} cores)")},
             "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d * ws,
                     "d2h_bytes_per_step": d2h * ws},
             "gpu_launches": args.steps,

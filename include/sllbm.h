@@ -161,6 +161,8 @@ typedef struct {
     int64_t n_records;     /* number of departure records                          */
     int64_t n_boundary_records;  /* records whose trajectory left the domain       */
     int64_t n_isothermal_nodes;  /* nodes with an isothermal-wall trajectory       */
+    char     step_kernel[32];     /* name of the kernel the last step launched
+                                     ("" before the first step)                   */
 } sllbm_info_t;
 
 typedef struct sllbm_ctx sllbm_ctx;

@@ -50,7 +50,7 @@ class Info(C.Structure):
                 ("nodes", C.c_int32 * 3), ("cells", C.c_int32 * 3), ("precision", C.c_int32),
                 ("stream_mode", C.c_int32), ("state_bytes", C.c_int64), ("table_bytes", C.c_int64),
                 ("n_records", C.c_int64), ("n_boundary_records", C.c_int64),
-                ("n_isothermal_nodes", C.c_int64)]
+                ("n_isothermal_nodes", C.c_int64), ("step_kernel", C.c_char * 32)]
 
 
 _P = C.c_void_p

@@ -323,6 +323,7 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
         const int nx = ctx->mesh.N[0];
         if (st && ctx->tiled && ctx->mode == SLLBM_STREAM_STRUCTURED && (vs == 1 || vs == 3) &&
             (nx == 32 || nx == 64 || nx == 128 || (nx == 192 && vs == 1) || nx == 256)) {
+            ctx->step_kernel = "k_step_row_smem";
 #define ROWCASE(VS)                                                   \
     if (vs == VS) {                                                   \
         if (nx == 32) return launch_step_row_smem<VS, real, 32>(L);   \
@@ -338,6 +339,7 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     }
     if (st && ctx->tiled) {
         const bool reg = ctx->mode == SLLBM_STREAM_TILED_REG;
+        ctx->step_kernel = reg ? "k_step_tiled" : "k_step_tiled_smem";
         switch (vs) {
             case 0: return reg ? launch_step_tiled<0, real>(L) : launch_step_tiled_smem<0, real>(L);
             case 1: return reg ? launch_step_tiled<1, real>(L) : launch_step_tiled_smem<1, real>(L);
@@ -348,6 +350,7 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     if (st && ctx->tiled_p == 4) {
         StepLaunch<real> Lp = L;
         Lp.tilep = ctx->tile_tab;
+        ctx->step_kernel = "k_step_tiled_p";
         switch (vs) {
             case 0: return launch_step_tiled_p<0, 4, real>(Lp);
             case 1: return launch_step_tiled_p<1, 4, real>(Lp);
@@ -356,6 +359,7 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
         }
     }
     const bool gsm = ctx->mode == SLLBM_STREAM_GATHER_SMEM;
+    ctx->step_kernel = st ? "k_step_structured" : (gsm ? "k_step_gather_smem" : "k_step_gather");
 #define CASE(VS, P)                                                                                    \
     if (vs == VS && p == P)                                                                            \
         return st ? launch_step_structured<VS, P, real>(L)                                             \
@@ -369,8 +373,10 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     CASE(1, 4)
     CASE(2, 4)
 #undef CASE
-    if (vs == 3 && p == 4)
+    if (vs == 3 && p == 4) {
+        ctx->step_kernel = st ? "k_step_structured_smem" : "k_step_gather_smem";
         return st ? launch_step_structured_smem<3, 4, real>(L) : launch_step_gather_smem<3, 4, real>(L);
+    }
     return fail(ctx, SLLBM_ERR_UNSUPPORTED,
                 "velocity set / order combination not built (p must be 2 or 4, or 3 for D2Q19)");
 }
@@ -843,6 +849,8 @@ int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
     o->n_records = int64_t(ctx->mesh.n_nodes) * ctx->vs.Q;
     o->n_boundary_records = ctx->n_boundary_records;
     o->n_isothermal_nodes = ctx->n_isothermal_nodes;
+    std::strncpy(o->step_kernel, ctx->step_kernel, sizeof(o->step_kernel) - 1);
+    o->step_kernel[sizeof(o->step_kernel) - 1] = 0;
     return SLLBM_OK;
 }
 
@@ -993,6 +1001,7 @@ int step_once(sllbm_ctx* ctx, float* feat) {
             if (!(ctx->tiled && ctx->velset == SLLBM_D2Q19))
                 return fail(ctx, SLLBM_ERR_UNSUPPORTED,
                             "learned collision is built for D2Q19 with the warp-tiled structured kernel");
+            ctx->step_kernel = mlpm == 1 && ctx->mlp_tensor ? "k_step_tiled_smem_tc" : "k_step_tiled";
             if (mlpm == 2) {
                 rc = launch_step_tiled<1, float, 2>(L);
             } else if (ctx->mlp_tensor) {

@@ -118,6 +118,7 @@ struct sllbm_ctx {
     int mode = SLLBM_STREAM_GATHER;      // resolved
     bool tiled = false;                  // structured mode runs the warp-tiled kernel
     int tiled_p = 0;                     // order of the warp-tiled order-P table (4), 0: none
+    const char* step_kernel = "";        // kernel of the last step launched (sllbm_info)
     int precision = SLLBM_FP32;
     // device geometry
     double* dV[3] = {nullptr, nullptr, nullptr};

@@ -164,6 +164,12 @@ class Sim:
     def sync(self):
         self._call("sllbm_sync")
 
+    def step_kernel(self):
+        """Name of the kernel the last step launched (sllbm_info)."""
+        info = capi.Info()
+        self._call("sllbm_info", C.byref(info))
+        return info.step_kernel.decode()
+
     # ---------------------------------------------------------------- statistics
     def plane_profiles(self):
         """Reynolds / Favre plane averages (sllbm_plane_profiles): dict of

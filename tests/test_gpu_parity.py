@@ -181,7 +181,10 @@ def test_steps_match_oracle(built_lib, name, mode):
     assert np.abs(r1 - r0).max() < tol and np.abs(T1 - T0).max() < tol
     assert np.abs(u1 - u0).max() < tol * max(1.0, np.abs(u0).max())
     em = max(np.abs(r1 - r0).max(), np.abs(T1 - T0).max(), np.abs(u1 - u0).max() / max(1.0, np.abs(u0).max()))
-    print(f"PARITY step {name} mode {sim.info.stream_mode}: populations {worst:.2e} moments {em:.2e}")
+    kern = sim.step_kernel()
+    if "row32" in name and mode == 0:
+        assert kern == "k_step_row_smem"                 # one block per 32-node row
+    print(f"PARITY step {name} mode {sim.info.stream_mode} ({kern}): populations {worst:.2e} moments {em:.2e}")
     sim.close()
 
 
@@ -215,6 +218,7 @@ def test_tiled_order4_matches_oracle_and_class_kernel(built_lib, name, cells):
     mesh, xi, w, opp, par, rec = oracle_case(cfg)
     a, b = _sim(cfg, "fp32", 2), _sim(cfg, "fp32", 3)
     assert a.info.stream_mode == 2 and b.info.stream_mode == 3
+    assert a.step_kernel() == ""                  # no step launched yet
     rho, u, T = initial_fields(cfg, mesh.X)
     f, g = ost.init_equilibrium(rho, u, T, xi, w, par.cv)
     Tw = ost.isothermal_nodes(rec, par)
@@ -223,6 +227,7 @@ def test_tiled_order4_matches_oracle_and_class_kernel(built_lib, name, cells):
     for k in range(3):
         f, g = ost.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
         a.step(1)
+        assert a.step_kernel() == "k_step_tiled_p"
         fa, ga = a.get_state()
         assert _scale_err(fa, f, w) < 1e-5 and _scale_err(ga, g, w) < 1e-5, k
     a.step(2)
