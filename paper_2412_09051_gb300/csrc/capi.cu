@@ -56,6 +56,8 @@ SLLBM_EXTERN_STEP(0, 4, double)
 SLLBM_EXTERN_STEP(1, 4, double)
 SLLBM_EXTERN_STEP(2, 4, double)
 SLLBM_EXTERN_STEP_COMPACT(3, 4, double)
+SLLBM_EXTERN_ROWP(1, float)
+SLLBM_EXTERN_ROWP(3, float)
 SLLBM_EXTERN_ROW(1, float)
 SLLBM_EXTERN_ROW(3, float)
 SLLBM_EXTERN_TILED_P(0, 4, float)
@@ -350,6 +352,23 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     if (st && ctx->tiled_p == 4) {
         StepLaunch<real> Lp = L;
         Lp.tilep = ctx->tile_tab;
+        if constexpr (std::is_same<real, float>::value) {
+            // order 4, a periodic row that fits one block: one block per row
+            const int nx = ctx->mesh.N[0];
+            if ((vs == 1 || vs == 3) && (nx == 32 || nx == 64 || nx == 128 || nx == 256)) {
+                ctx->step_kernel = "k_step_row_p";
+#define ROWPCASE(VS)                                                     \
+    if (vs == VS) {                                                      \
+        if (nx == 32) return launch_step_row_p<VS, 4, real, 32>(Lp);     \
+        if (nx == 64) return launch_step_row_p<VS, 4, real, 64>(Lp);     \
+        if (nx == 128) return launch_step_row_p<VS, 4, real, 128>(Lp);   \
+        return launch_step_row_p<VS, 4, real, 256>(Lp);                  \
+    }
+                ROWPCASE(1)
+                ROWPCASE(3)
+#undef ROWPCASE
+            }
+        }
         ctx->step_kernel = "k_step_tiled_p";
         switch (vs) {
             case 0: return launch_step_tiled_p<0, 4, real>(Lp);

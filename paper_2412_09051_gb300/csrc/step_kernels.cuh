@@ -739,6 +739,112 @@ int launch_step_row_smem(const StepLaunch<real>& L) {
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
+// ------------------------------------------------------------ one block per periodic row, order P
+// k_step_tiled_p's order-P streaming with one block of NXB = Nx threads per
+// (y, z) row (no halo lanes: the warp tiles spend 2P of 32 lanes on halos);
+// the x factor reads the neighbouring nodes' row sums from a shared row
+// buffer, double-buffered per velocity with one block barrier per velocity.
+template <int VS, int P, typename real, int NXB>
+__global__ void __launch_bounds__(256, 2) k_step_row_p(const typename Vec2<real>::T* __restrict__ fg,
+                                                    typename Vec2<real>::T* __restrict__ fgo,
+                                                    const TileRecP<real, P>* __restrict__ tab,
+                                                    const real* __restrict__ twt, const StepGeom G,
+                                                    const CollideConst<real> C) {
+    using VSET = VelSet<VS>;
+    using V2 = typename Vec2<real>::T;
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    constexpr int NZ = D == 3 ? P + 1 : 1;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    real* S = reinterpret_cast<real*>(dyn_smem);
+    real* XB = S + 2 * Q * NXB;                  // [2 buffers][f, g][NXB]
+    const int Nx = NXB, N1 = G.N[1], N2 = D == 3 ? G.N[2] : 1;
+    const int row = blockIdx.x;
+    const int ky = row % N1;
+    const int kz = row / N1;
+    const int kx = threadIdx.x;
+    const int NN = int(G.n_nodes);
+    const int plane = Nx * N1;
+    const int n = kx + Nx * ky + plane * kz;
+    const bool py = G.periodic[1] != 0;
+    const int cls = (kx % P) + G.ncls[0] * ((py ? (ky % P) : ky) + G.ncls[1] * (D == 3 ? (kz % P) : 0));
+    constexpr int stride = NXB;
+    real* Sf = S + threadIdx.x;
+    real* Sg = S + Q * stride + threadIdx.x;
+    const V2* base = fg + n;
+    // row-buffer index: counts the velocities that exchange (equilibrium
+    // records skip the exchange and its barrier), so two uses of one buffer
+    // always have the other buffer's barrier between them
+    int nx_used = 0;
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) {
+        const TileRecP<real, P> r = tab[i * G.n_classes + cls];
+        const int kind = r.meta & 15;            // uniform over the row (checked at setup)
+        const int bid = (r.meta >> 4) & 15;
+        real of = 0, og = 0;
+        if (kind == REC_EQ) {
+            of = C.eqf[bid][i];
+            og = C.eqg[bid][i];
+        } else {
+            int oy[P + 1], oz[NZ];
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                int ty = ky + ((r.dyp >> (4 * b)) & 15) - 8;
+                if (py) ty += ty < 0 ? N1 : (ty >= N1 ? -N1 : 0);
+                oy[b] = (ty - ky) * Nx;
+            }
+#pragma unroll
+            for (int c = 0; c < NZ; ++c) {
+                int tz = kz + ((r.dzp >> (4 * c)) & 15) - 8;
+                tz += tz < 0 ? N2 : (tz >= N2 ? -N2 : 0);
+                oz[c] = D == 3 ? (tz - kz) * plane : 0;
+            }
+            const V2* p = base + (r.meta >> 8) * NN;
+            real sf = 0, sg = 0;
+#pragma unroll
+            for (int c = 0; c < NZ; ++c) {
+                real tf = 0, tg = 0;
+#pragma unroll
+                for (int b = 0; b <= P; ++b) {
+                    const V2 v = __ldg(p + oy[b] + oz[c]);
+                    tf += r.wy[b] * v.x;
+                    tg += r.wy[b] * v.y;
+                }
+                const real wz = D == 3 ? r.wz[c] : real(1);
+                sf += wz * tf;
+                sg += wz * tg;
+            }
+            real* xb = XB + (nx_used++ & 1) * (2 * NXB);
+            xb[threadIdx.x] = sf;
+            xb[NXB + threadIdx.x] = sg;
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a <= P; ++a) {
+                int j = int(threadIdx.x) + ((r.dxp >> (4 * a)) & 15) - 8;
+                j += j < 0 ? NXB : (j >= NXB ? -NXB : 0);
+                of += r.wx[a] * xb[j];
+                og += r.wx[a] * xb[NXB + j];
+            }
+            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+        }
+        Sf[i * stride] = of;
+        Sg[i * stride] = og;
+    }
+    collide_smem<VSET, real, V2, NXB>(C, Sf, Sg, twt[cls], fgo + n, NN);
+}
+
+template <int VS, int P, typename real, int NXB>
+int launch_step_row_p(const StepLaunch<real>& L) {
+    constexpr int Q = VelSet<VS>::Q, D = VelSet<VS>::D;
+    if (!L.tilep) return SLLBM_ERR_ARG;
+    const int rows = D == 3 ? L.G.N[1] * L.G.N[2] : L.G.N[1];
+    const size_t smem = sizeof(real) * (2 * Q * NXB + 2 * 2 * NXB);
+    cudaFuncSetAttribute(k_step_row_p<VS, P, real, NXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_step_row_p<VS, P, real, NXB><<<rows, NXB, smem, L.stream>>>(
+        L.fg, L.fgo, static_cast<const TileRecP<real, P>*>(L.tilep), L.tw, L.G, *L.C);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
 // ------------------------------------------------------------ warp-tiled smem state + learned correction on tcgen05
 // k_step_tiled_smem's streaming and shared-memory collision, then the learned
 // correction on the tensor cores (mlp_tc.cuh).  The node state (f, g and
@@ -1294,6 +1400,11 @@ int launch_step_gather(const StepLaunch<real>& L) {
 #define SLLBM_INSTANTIATE_ROW1(VS, real, W) template int launch_step_row_smem<VS, real, W>(const StepLaunch<real>&);
 #define SLLBM_EXTERN_ROW(VS, real) SLLBM_ROW_WIDTHS(SLLBM_EXTERN_ROW1, VS, real)
 #define SLLBM_INSTANTIATE_ROW(VS, real) SLLBM_ROW_WIDTHS(SLLBM_INSTANTIATE_ROW1, VS, real)
+#define SLLBM_ROWP_WIDTHS(X, VS, real) X(VS, real, 32) X(VS, real, 64) X(VS, real, 128) X(VS, real, 256)
+#define SLLBM_EXTERN_ROWP1(VS, real, W) extern template int launch_step_row_p<VS, 4, real, W>(const StepLaunch<real>&);
+#define SLLBM_INSTANTIATE_ROWP1(VS, real, W) template int launch_step_row_p<VS, 4, real, W>(const StepLaunch<real>&);
+#define SLLBM_EXTERN_ROWP(VS, real) SLLBM_ROWP_WIDTHS(SLLBM_EXTERN_ROWP1, VS, real)
+#define SLLBM_INSTANTIATE_ROWP(VS, real) SLLBM_ROWP_WIDTHS(SLLBM_INSTANTIATE_ROWP1, VS, real)
 #define SLLBM_EXTERN_TILED_P(VS, P, real) extern template int launch_step_tiled_p<VS, P, real>(const StepLaunch<real>&);
 #define SLLBM_INSTANTIATE_TILED_P(VS, P, real) template int launch_step_tiled_p<VS, P, real>(const StepLaunch<real>&);
 

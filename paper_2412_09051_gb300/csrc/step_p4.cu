@@ -11,4 +11,6 @@ SLLBM_INSTANTIATE_TILED_P(0, 4, float)
 SLLBM_INSTANTIATE_TILED_P(1, 4, float)
 SLLBM_INSTANTIATE_TILED_P(2, 4, float)
 SLLBM_INSTANTIATE_TILED_P(3, 4, float)
+SLLBM_INSTANTIATE_ROWP(1, float)
+SLLBM_INSTANTIATE_ROWP(3, float)
 }  // namespace sllbm

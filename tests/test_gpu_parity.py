@@ -208,10 +208,13 @@ def test_streaming_modes_agree(built_lib, modes):
     assert _scale_err(fa, fb, w) < 1e-5 and _scale_err(ga, gb, w) < 1e-5
 
 
-@pytest.mark.parametrize("name,cells", [("channel", (4, 3, 3)), ("mixing", (4, 4, 3))])
-def test_tiled_order4_matches_oracle_and_class_kernel(built_lib, name, cells):
+@pytest.mark.parametrize("name,cells,kernel", [("channel", (4, 3, 3), "k_step_tiled_p"),
+                                              ("mixing", (4, 4, 3), "k_step_tiled_p"),
+                                              ("channel", (8, 3, 3), "k_step_row_p")])   # 32-node rows
+def test_tiled_order4_matches_oracle_and_class_kernel(built_lib, name, cells, kernel):
     """Order p = 4 (the paper's): the warp-tiled kernel (16 x-nodes, so it is
-    eligible) against the oracle over 3 steps and against the one-thread-per-
+    eligible; 32 x-nodes: one block per row) against the oracle over 3 steps
+    and against the one-thread-per-
     node class kernel over 5 (3 z cells: with 8 z nodes the +-4 offsets
     would be ambiguous on the periodic axis and the kernel is not eligible)."""
     cfg = get_config(name, cells=cells, p=4)
@@ -227,7 +230,7 @@ def test_tiled_order4_matches_oracle_and_class_kernel(built_lib, name, cells):
     for k in range(3):
         f, g = ost.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
         a.step(1)
-        assert a.step_kernel() == "k_step_tiled_p"
+        assert a.step_kernel() == kernel
         fa, ga = a.get_state()
         assert _scale_err(fa, f, w) < 1e-5 and _scale_err(ga, g, w) < 1e-5, k
     a.step(2)
