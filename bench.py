@@ -244,6 +244,7 @@ def run_gpu(args, ws, rank, local):
     # warm-up
     sim.step(args.warmup)
     sim.sync()
+    cons0, _ = sim.conservation(check=False)     # FP64 sums before the timed steps (untimed)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     if dist:
         dist.barrier()
@@ -350,6 +351,11 @@ def run_gpu(args, ws, rank, local):
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "conservation_rc": rc,
+            # relative change over the timed steps of the FP64 sums of rho and of
+            # 2 rho E: bounce-back walls with periodic other axes (the channel)
+            # conserve mass, isothermal walls exchange energy, open boundaries both
+            "conservation_drift": {"mass": float((cons[0] - cons0[0]) / cons0[0]),
+                                   "energy": float((cons[-1] - cons0[-1]) / cons0[-1]), "steps": args.steps},
             **({"learned": {"mlp": args.learned, "device_status": dev_status,
                             "mlp_tflops": round(mlp_flops_per_node(Q) * N / (avg_launch_ms / 1e3) / 1e12, 2)}}
                if args.learned != "none" else {}),
