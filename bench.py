@@ -352,8 +352,9 @@ def run_gpu(args, ws, rank, local):
             "clocks": clk.summary(),
             "conservation_rc": rc,
             # relative change over the timed steps of the FP64 sums of rho and of
-            # 2 rho E: bounce-back walls with periodic other axes (the channel)
-            # conserve mass, isothermal walls exchange energy, open boundaries both
+            # 2 rho E: interpolation on a non-uniform mesh and at the walls'
+            # reflected departure points is not conservative, isothermal walls
+            # exchange energy, open boundaries both
             "conservation_drift": {"mass": float((cons[0] - cons0[0]) / cons0[0]),
                                    "energy": float((cons[-1] - cons0[-1]) / cons0[-1]), "steps": args.steps},
             **({"learned": {"mlp": args.learned, "device_status": dev_status,

@@ -392,10 +392,33 @@ int sllbm_mlp_set(sllbm_ctx* ctx, const uint16_t* w_bf16, const float* biases, c
 int sllbm_mlp_path(sllbm_ctx* ctx, int32_t path);
 
 /* Device status word of the context: synchronises the context's stream,
- * writes the word to *code (0: nothing recorded, SLLBM_DEV_TC_TIMEOUT: a
- * tensor-core wait ran out) and clears it.  Host pointer. */
+ * writes the word to *code and clears it.  Host pointer.  The word is an OR
+ * of bits: 0 nothing recorded; SLLBM_DEV_TC_TIMEOUT a tensor-core wait ran
+ * out.  The SLLBM_DEV_BAD_* bits come only from the bounds-checked debug build
+ * (sllbm_build_flags() & SLLBM_BUILD_CHECKED), whose step kernels test every
+ * index they take from a record table or derive from one, replace an index
+ * outside its range by 0 (so no access leaves its buffer; the result is then
+ * wrong) and record:
+ *   SLLBM_DEV_BAD_NODE  a source node outside the mesh (per axis, or relative
+ *                       to the arriving node outside [0, n_nodes));
+ *   SLLBM_DEV_BAD_POP   a source population outside [0, Q);
+ *   SLLBM_DEV_BAD_REC   a record slot outside its table (class, tile record),
+ *                       a boundary-state id outside [0, 2), or a gather-code
+ *                       cell outside [0, cells);
+ *   SLLBM_DEV_BAD_SMEM  a row-buffer slot outside the block's row.
+ * The paper has no counterpart: it is the substitute for a memory checker. */
 #define SLLBM_DEV_TC_TIMEOUT 1
+#define SLLBM_DEV_BAD_NODE   2
+#define SLLBM_DEV_BAD_POP    4
+#define SLLBM_DEV_BAD_REC    8
+#define SLLBM_DEV_BAD_SMEM   16
 int sllbm_device_status(sllbm_ctx* ctx, int32_t* code);
+
+/* How the loaded library was compiled: an OR of SLLBM_BUILD_* bits
+ * (SLLBM_BUILD_CHECKED: the bounds-checked debug build, compiled with
+ * -DSLLBM_CHECKED).  Needs no context and no GPU; never fails. */
+#define SLLBM_BUILD_CHECKED 1
+int sllbm_build_flags(void);
 
 /* One plain step (no correction) that also writes the non-equilibrium
  * moments z [N][Q] (FP32) of the step's streamed state. */

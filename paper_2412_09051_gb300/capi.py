@@ -9,6 +9,7 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsllbm.so")
+CHECKED_LIB_PATH = os.path.join(HERE, "libsllbm_checked.so")     # bounds-checked debug build
 
 OK = 0
 ERRORS = {-1: "SLLBM_ERR_ARG", -2: "SLLBM_ERR_CUDA", -3: "SLLBM_ERR_ARCH", -4: "SLLBM_ERR_NOMEM",
@@ -17,7 +18,8 @@ ERRORS = {-1: "SLLBM_ERR_ARG", -2: "SLLBM_ERR_CUDA", -3: "SLLBM_ERR_ARCH", -4: "
 MESH = dict(box=0, channel=1, mixing=2, naca=3)
 VELSET = dict(D2Q9=0, D2Q19=1, D2Q25=2, D3Q45=3)
 MLP_TENSOR, MLP_SIMT = 0, 1
-DEV_TC_TIMEOUT = 1
+DEV_TC_TIMEOUT, DEV_BAD_NODE, DEV_BAD_POP, DEV_BAD_REC, DEV_BAD_SMEM = 1, 2, 4, 8, 16
+BUILD_CHECKED = 1
 FP64, FP32 = 0, 1
 STREAM_AUTO, STREAM_GATHER, STREAM_STRUCTURED, STREAM_STRUCTURED_NODE, STREAM_TILED_REG, STREAM_GATHER_SMEM = \
     0, 1, 2, 3, 4, 5
@@ -87,6 +89,7 @@ _SIGS = {
     "sllbm_plane_profiles_mean": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "sllbm_plane_cp": (C.c_int, [_P, C.c_int32, C.c_double, C.c_double, _P, _P, _P]),
     "sllbm_device_status": (C.c_int, [_P, _P]),
+    "sllbm_build_flags": (C.c_int, []),
     "sllbm_moment_basis": (C.c_int, [_P, _P, _P]),
     "sllbm_train_create": (C.c_int, [_P, _P, C.POINTER(_P)]),
     "sllbm_train_destroy": (C.c_int, [_P]),
@@ -105,7 +108,8 @@ _lib = None
 
 
 def lib(path=None):
-    """Load libsllbm.so (raises OSError when it has not been built)."""
+    """Load libsllbm.so, or the library at path (the first call decides; raises
+    OSError when it has not been built)."""
     global _lib
     if _lib is None:
         p = path or LIB_PATH

@@ -713,6 +713,11 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
             G.ncls[d] = d < D ? (m.periodic[d] ? m.p : m.N[d]) : 1;
             G.n_classes *= G.ncls[d];
         }
+        CK(cudaMalloc(&ctx->d_status, sizeof(int)));
+        CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+#ifdef SLLBM_CHECKED
+        G.status = ctx->d_status;
+#endif
         const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_SMEM;
         ctx->n_rec_units = st ? G.n_classes : N;
         const int64_t U = ctx->n_rec_units;
@@ -1145,6 +1150,14 @@ int sllbm_device_status(sllbm_ctx* ctx, int32_t* code) {
     CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
     *code = v;
     return SLLBM_OK;
+}
+
+int sllbm_build_flags(void) {
+#ifdef SLLBM_CHECKED
+    return SLLBM_BUILD_CHECKED;
+#else
+    return 0;
+#endif
 }
 
 int sllbm_moment_basis(const sllbm_ctx* ctx, double* Phi, double* P) {

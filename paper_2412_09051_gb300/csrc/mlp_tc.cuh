@@ -271,7 +271,7 @@ __device__ __forceinline__ void mlp_correct_tc(const MlpView<Q, D>& M, const Col
         }
         mlp_project_add<Q, D, real>(M, C, o, f);
     } else if (r == 0) {
-        atomicExch(status, SLLBM_DEV_TC_TIMEOUT);
+        atomicOr(status, SLLBM_DEV_TC_TIMEOUT);
     }
     tc_fence_before();
     __syncthreads();

@@ -101,6 +101,10 @@ struct StepGeom {             // structured / gather kernel geometry
     int ncls[3];              // classes per dimension (p if periodic, else N)
     int64_t n_nodes;
     int n_classes;
+#ifdef SLLBM_CHECKED
+    int* status;              // device status word of the context (bounds checks of the debug build;
+                              // the release layout is kept: a longer struct changes register allocation)
+#endif
 };
 
 }  // namespace sllbm

@@ -4,6 +4,7 @@
 // thread per arrival node, all 2Q streamed values held in registers.
 #pragma once
 #include "mlp.cuh"
+#include "checked.cuh"
 #include "mlp_tc.cuh"
 #include "sllbm_internal.h"
 
@@ -92,16 +93,16 @@ __global__ void __launch_bounds__(128) k_step_structured(const typename Vec2<rea
     real fs[Q], gs[Q];
     Unroll<0, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        const ClassRec<real>& r = tab[i * G.n_classes + cls];
+        const ClassRec<real>& r = tab[i * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC)];
         const int meta = __ldg(&r.meta);
         const int kind = meta & 15;
         const int bid = (meta >> 4) & 15;
         if (kind == REC_EQ) {
-            fs[i] = C.eqf[bid][i];
-            gs[i] = C.eqg[bid][i];
+            fs[i] = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            gs[i] = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             return;
         }
-        const int src = meta >> 8;
+        const int src = SLLBM_CHK(meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP);
         int64_t off[3][P + 1];
         real wt[3][P + 1];
 #pragma unroll
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(128) k_step_structured(const typename Vec2<rea
             for (int a = 0; a <= P; ++a) {
                 int kk = c * P + a;
                 if (G.periodic[d]) kk = wrapi(kk, G.N[d]);
-                off[d][a] = kk * stride;
+                off[d][a] = SLLBM_CHK(kk, G.N[d], G.status, SLLBM_DEV_BAD_NODE) * stride;
                 wt[d][a] = __ldg(&r.wt[d][a]);
             }
         }
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(128) k_step_structured(const typename Vec2<rea
                 sg += wt[2][c3] * ug;
             }
         }
-        if (kind == REC_BB || kind == REC_BB_ISO) sf += C.mw[bid][i];
+        if (kind == REC_BB || kind == REC_BB_ISO) sf += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
         fs[i] = sf;
         gs[i] = sg;
     });
@@ -204,14 +205,14 @@ __global__ void __launch_bounds__(128, 4) k_step_structured_smem(const typename 
     real* Sg = S + Q * stride + threadIdx.x;
 #pragma unroll 1
     for (int i = 0; i < Q; ++i) {
-        const ClassRec<real>& r = tab[i * G.n_classes + cls];
+        const ClassRec<real>& r = tab[i * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC)];
         const int meta = __ldg(&r.meta);
         const int kind = meta & 15;
         const int bid = (meta >> 4) & 15;
         real of, og;
         if (kind == REC_EQ) {
-            of = C.eqf[bid][i];
-            og = C.eqg[bid][i];
+            of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
         } else {
             int64_t off[3][P + 1];
             real wt[3][P + 1];
@@ -228,12 +229,12 @@ __global__ void __launch_bounds__(128, 4) k_step_structured_smem(const typename 
                 for (int a = 0; a <= P; ++a) {
                     int kk = c * P + a;
                     if (d < D && G.periodic[d]) kk = wrapi(kk, G.N[d]);
-                    off[d][a] = d < D ? kk * st : 0;
+                    off[d][a] = d < D ? SLLBM_CHK(kk, G.N[d], G.status, SLLBM_DEV_BAD_NODE) * st : 0;
                     wt[d][a] = d < D ? __ldg(&r.wt[d][a]) : real(0);
                 }
             }
-            interp_direct<D, P, real, V2>(fg + int64_t(meta >> 8) * NN, off, wt, of, og);
-            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+            interp_direct<D, P, real, V2>(fg + int64_t(SLLBM_CHK(meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP)) * NN, off, wt, of, og);
+            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
         }
         Sf[i * stride] = of;
         Sg[i * stride] = og;
@@ -275,11 +276,11 @@ __global__ void __launch_bounds__(128) k_step_gather(const typename Vec2<real>::
         const int kind = (cw >> 24) & 15;
         const int bid = (cw >> 28) & 15;
         if (kind == REC_EQ) {
-            fs[i] = C.eqf[bid][i];
-            gs[i] = C.eqg[bid][i];
+            fs[i] = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            gs[i] = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             return;
         }
-        const int cell = cw & 0xFFFFFF;
+        const int cell = SLLBM_CHK(cw & 0xFFFFFF, C0 * C1 * (D == 3 ? G.cells[2] : 1), G.status, SLLBM_DEV_BAD_REC);
         int cc[3];
         cc[0] = cell % C0;
         cc[1] = (cell / C0) % C1;
@@ -295,10 +296,10 @@ __global__ void __launch_bounds__(128) k_step_gather(const typename Vec2<real>::
             for (int a = 0; a <= P; ++a) {
                 int kk = cc[d] * P + a;
                 if (G.periodic[d]) kk = wrapi(kk, G.N[d]);
-                off[d][a] = kk * stride;
+                off[d][a] = SLLBM_CHK(kk, G.N[d], G.status, SLLBM_DEV_BAD_NODE) * stride;
             }
         }
-        const int src = (kind == REC_BB || kind == REC_BB_ISO) ? C.opp[i] : i;
+        const int src = SLLBM_CHK((kind == REC_BB || kind == REC_BB_ISO) ? C.opp[i] : i, Q, G.status, SLLBM_DEV_BAD_POP);
         const typename Vec2<real>::T* p = fg + int64_t(src) * NN;
         real sf = 0, sg = 0;
         if (D == 2) {
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(128) k_step_gather(const typename Vec2<real>::
                 sg += wt[2][c3] * ug;
             }
         }
-        if (kind == REC_BB || kind == REC_BB_ISO) sf += C.mw[bid][i];
+        if (kind == REC_BB || kind == REC_BB_ISO) sf += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
         fs[i] = sf;
         gs[i] = sg;
     });
@@ -396,13 +397,13 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
     real fs[Q], gs[Q];
     Unroll<0, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        const TileRec<real>* r = tab + i * G.n_classes + cls;
+        const TileRec<real>* r = tab + i * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC);
         const int4 h0 = __ldg(reinterpret_cast<const int4*>(r));
         const int kind = h0.x & 15;
         const int bid = (h0.x >> 4) & 15;
         if (kind == REC_EQ) {
-            fs[i] = C.eqf[bid][i];
-            gs[i] = C.eqg[bid][i];
+            fs[i] = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            gs[i] = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             return;
         }
         int rel[12];
@@ -425,11 +426,11 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
                 rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
             }
         }
-        const V2* p = base + (h0.x >> 8) * NN;
+        const V2* p = base + SLLBM_CHK(h0.x >> 8, Q, G.status, SLLBM_DEV_BAD_POP) * NN;
         real sf = 0, sg = 0;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            const V2 v = __ldg(p + rel[k]);
+            const V2 v = __ldg(p + SLLBM_CHK_REL(n, rel[k], NN, G.status));
             const real wk = __ldg(&r->rw[k]);
             sf += wk * v.x;
             sg += wk * v.y;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(128) k_step_tiled(const typename Vec2<real>::T
             of += wx * __shfl_sync(0xffffffffu, sf, dl);
             og += wx * __shfl_sync(0xffffffffu, sg, dl);
         }
-        if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+        if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
         fs[i] = of;
         gs[i] = og;
     });
@@ -522,7 +523,7 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem(const typename Vec2<
 #pragma unroll
         for (int u = 0; u < GV; ++u) {
             const int i = min(i0 + u, Q - 1);
-            const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes + cls);
+            const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC));
             int4* dst = reinterpret_cast<int4*>(&r[u]);
 #pragma unroll
             for (int k = 0; k < int(sizeof(TileRec<real>) / 16); ++k) dst[k] = __ldg(src + k);
@@ -547,9 +548,9 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem(const typename Vec2<
                     rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
                 }
             }
-            const V2* p = base + (r[u].meta >> 8) * NN;
+            const V2* p = base + SLLBM_CHK(r[u].meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP) * NN;
 #pragma unroll
-            for (int k = 0; k < NR; ++k) v[u][k] = __ldg(p + rel[k]);
+            for (int k = 0; k < NR; ++k) v[u][k] = __ldg(p + SLLBM_CHK_REL(n, rel[k], NN, G.status));
         }
 #pragma unroll
         for (int u = 0; u < GV; ++u) {
@@ -559,8 +560,8 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem(const typename Vec2<
             const int bid = (r[u].meta >> 4) & 15;
             real of, og;
             if (kind == REC_EQ) {
-                of = C.eqf[bid][i];
-                og = C.eqg[bid][i];
+                of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+                og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             } else {
                 real sf = 0, sg = 0;
 #pragma unroll
@@ -578,7 +579,7 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem(const typename Vec2<
                     of += r[u].wx[a] * __shfl_sync(0xffffffffu, sf, dl);
                     og += r[u].wx[a] * __shfl_sync(0xffffffffu, sg, dl);
                 }
-                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             }
             Sf[i * stride] = of;
             Sg[i * stride] = og;
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(256, 2) k_step_row_smem(const typename Vec2<re
 #pragma unroll
         for (int u = 0; u < GV; ++u) {
             const int i = min(i0 + u, Q - 1);
-            const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes + cls);
+            const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC));
             int4* dst = reinterpret_cast<int4*>(&r[u]);
 #pragma unroll
             for (int k = 0; k < int(sizeof(TileRec<real>) / 16); ++k) dst[k] = __ldg(src + k);
@@ -685,9 +686,9 @@ __global__ void __launch_bounds__(256, 2) k_step_row_smem(const typename Vec2<re
                     rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
                 }
             }
-            const V2* p = base + (r[u].meta >> 8) * NN;
+            const V2* p = base + SLLBM_CHK(r[u].meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP) * NN;
 #pragma unroll
-            for (int k = 0; k < NR; ++k) v[u][k] = __ldg(p + rel[k]);
+            for (int k = 0; k < NR; ++k) v[u][k] = __ldg(p + SLLBM_CHK_REL(n, rel[k], NN, G.status));
         }
         real* xb = XB + (grp & 1) * (GV * 2 * NXB);
 #pragma unroll
@@ -710,17 +711,18 @@ __global__ void __launch_bounds__(256, 2) k_step_row_smem(const typename Vec2<re
             const int bid = (r[u].meta >> 4) & 15;
             real of = 0, og = 0;
             if (kind == REC_EQ) {
-                of = C.eqf[bid][i];
-                og = C.eqg[bid][i];
+                of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+                og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             } else {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     int j = int(threadIdx.x) + ((r[u].dxp >> (4 * a)) & 15) - 8;
                     j += j < 0 ? NXB : (j >= NXB ? -NXB : 0);
+                    j = SLLBM_CHK(j, NXB, G.status, SLLBM_DEV_BAD_SMEM);
                     of += r[u].wx[a] * xb[(2 * u) * NXB + j];
                     og += r[u].wx[a] * xb[(2 * u + 1) * NXB + j];
                 }
-                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             }
             Sf[i * stride] = of;
             Sg[i * stride] = og;
@@ -778,13 +780,13 @@ __global__ void __launch_bounds__(256, 2) k_step_row_p(const typename Vec2<real>
     int nx_used = 0;
 #pragma unroll 1
     for (int i = 0; i < Q; ++i) {
-        const TileRecP<real, P> r = tab[i * G.n_classes + cls];
+        const TileRecP<real, P> r = tab[i * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC)];
         const int kind = r.meta & 15;            // uniform over the row (checked at setup)
         const int bid = (r.meta >> 4) & 15;
         real of = 0, og = 0;
         if (kind == REC_EQ) {
-            of = C.eqf[bid][i];
-            og = C.eqg[bid][i];
+            of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
         } else {
             int oy[P + 1], oz[NZ];
 #pragma unroll
@@ -799,14 +801,14 @@ __global__ void __launch_bounds__(256, 2) k_step_row_p(const typename Vec2<real>
                 tz += tz < 0 ? N2 : (tz >= N2 ? -N2 : 0);
                 oz[c] = D == 3 ? (tz - kz) * plane : 0;
             }
-            const V2* p = base + (r.meta >> 8) * NN;
+            const V2* p = base + SLLBM_CHK(r.meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP) * NN;
             real sf = 0, sg = 0;
 #pragma unroll
             for (int c = 0; c < NZ; ++c) {
                 real tf = 0, tg = 0;
 #pragma unroll
                 for (int b = 0; b <= P; ++b) {
-                    const V2 v = __ldg(p + oy[b] + oz[c]);
+                    const V2 v = __ldg(p + SLLBM_CHK_REL(n, oy[b] + oz[c], NN, G.status));
                     tf += r.wy[b] * v.x;
                     tg += r.wy[b] * v.y;
                 }
@@ -822,10 +824,11 @@ __global__ void __launch_bounds__(256, 2) k_step_row_p(const typename Vec2<real>
             for (int a = 0; a <= P; ++a) {
                 int j = int(threadIdx.x) + ((r.dxp >> (4 * a)) & 15) - 8;
                 j += j < 0 ? NXB : (j >= NXB ? -NXB : 0);
+                j = SLLBM_CHK(j, NXB, G.status, SLLBM_DEV_BAD_SMEM);
                 of += r.wx[a] * xb[j];
                 og += r.wx[a] * xb[NXB + j];
             }
-            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
         }
         Sf[i * stride] = of;
         Sg[i * stride] = og;
@@ -907,7 +910,7 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem_tc(const typename Ve
     #pragma unroll
             for (int u = 0; u < GV; ++u) {
                 const int i = min(i0 + u, Q - 1);
-                const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes + cls);
+                const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC));
                 int4* dst = reinterpret_cast<int4*>(&r[u]);
     #pragma unroll
                 for (int k = 0; k < int(sizeof(TileRec<real>) / 16); ++k) dst[k] = __ldg(src + k);
@@ -932,9 +935,9 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem_tc(const typename Ve
                         rel[k] = (ty - ky) * Nx + (tz - kz) * plane;
                     }
                 }
-                const V2* p = base + (r[u].meta >> 8) * NN;
+                const V2* p = base + SLLBM_CHK(r[u].meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP) * NN;
     #pragma unroll
-                for (int k = 0; k < NR; ++k) v[u][k] = __ldg(p + rel[k]);
+                for (int k = 0; k < NR; ++k) v[u][k] = __ldg(p + SLLBM_CHK_REL(n, rel[k], NN, G.status));
             }
     #pragma unroll
             for (int u = 0; u < GV; ++u) {
@@ -944,8 +947,8 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem_tc(const typename Ve
                 const int bid = (r[u].meta >> 4) & 15;
                 real of, og;
                 if (kind == REC_EQ) {
-                    of = C.eqf[bid][i];
-                    og = C.eqg[bid][i];
+                    of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+                    og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
                 } else {
                     real sf = 0, sg = 0;
     #pragma unroll
@@ -963,7 +966,7 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_smem_tc(const typename Ve
                         of += r[u].wx[a] * __shfl_sync(0xffffffffu, sf, dl);
                         og += r[u].wx[a] * __shfl_sync(0xffffffffu, sg, dl);
                     }
-                    if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+                    if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
                 }
                 Sf[i * stride] = of;
                 Sg[i * stride] = og;
@@ -1068,13 +1071,13 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_p(const typename Vec2<rea
     const V2* base = fg + n;
 #pragma unroll 1
     for (int i = 0; i < Q; ++i) {
-        const TileRecP<real, P> r = tab[i * G.n_classes + cls];
+        const TileRecP<real, P> r = tab[i * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC)];
         const int kind = r.meta & 15;
         const int bid = (r.meta >> 4) & 15;
         real of = 0, og = 0;
         if (kind == REC_EQ) {
-            of = C.eqf[bid][i];
-            og = C.eqg[bid][i];
+            of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
         } else {
             int oy[P + 1], oz[NZ];
 #pragma unroll
@@ -1089,14 +1092,14 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_p(const typename Vec2<rea
                 tz += tz < 0 ? N2 : (tz >= N2 ? -N2 : 0);
                 oz[c] = D == 3 ? (tz - kz) * plane : 0;
             }
-            const V2* p = base + (r.meta >> 8) * NN;
+            const V2* p = base + SLLBM_CHK(r.meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP) * NN;
             real sf = 0, sg = 0;
 #pragma unroll
             for (int c = 0; c < NZ; ++c) {
                 real tf = 0, tg = 0;
 #pragma unroll
                 for (int b = 0; b <= P; ++b) {
-                    const V2 v = __ldg(p + oy[b] + oz[c]);
+                    const V2 v = __ldg(p + SLLBM_CHK_REL(n, oy[b] + oz[c], NN, G.status));
                     tf += r.wy[b] * v.x;
                     tg += r.wy[b] * v.y;
                 }
@@ -1112,7 +1115,7 @@ __global__ void __launch_bounds__(128, 4) k_step_tiled_p(const typename Vec2<rea
                 of += r.wx[a] * __shfl_sync(0xffffffffu, sf, dl);
                 og += r.wx[a] * __shfl_sync(0xffffffffu, sg, dl);
             }
-            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
         }
         Sf[i * stride] = of;
         Sg[i * stride] = og;
@@ -1183,10 +1186,10 @@ __global__ void __launch_bounds__(128, 4) k_step_gather_smem(const typename Vec2
             const int bid = (cw >> 28) & 15;
             real of, og;
             if (kind == REC_EQ) {
-                of = C.eqf[bid][i];
-                og = C.eqg[bid][i];
+                of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+                og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             } else {
-                const int cell = cw & 0xFFFFFF;
+                const int cell = SLLBM_CHK(cw & 0xFFFFFF, C0 * C1 * (D == 3 ? G.cells[2] : 1), G.status, SLLBM_DEV_BAD_REC);
                 int cc[3];
                 cc[0] = cell % C0;
                 cc[1] = (cell / C0) % C1;
@@ -1206,12 +1209,12 @@ __global__ void __launch_bounds__(128, 4) k_step_gather_smem(const typename Vec2
                     for (int a = 0; a <= P; ++a) {
                         int kk = cc[d] * P + a;
                         if (d < D && G.periodic[d]) kk = wrapi(kk, G.N[d]);
-                        off[d][a] = d < D ? kk * st : 0;
+                        off[d][a] = d < D ? SLLBM_CHK(kk, G.N[d], G.status, SLLBM_DEV_BAD_NODE) * st : 0;
                     }
                 }
-                const int src = (kind == REC_BB || kind == REC_BB_ISO) ? C.opp[i] : i;
+                const int src = SLLBM_CHK((kind == REC_BB || kind == REC_BB_ISO) ? C.opp[i] : i, Q, G.status, SLLBM_DEV_BAD_POP);
                 interp_direct<D, P, real, V2>(fg + int64_t(src) * NN, off, wt, of, og);
-                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             }
             Sf[i * stride] = of;
             Sg[i * stride] = og;
@@ -1235,7 +1238,7 @@ __global__ void __launch_bounds__(128, 4) k_step_gather_smem(const typename Vec2
             const int i = min(i0 + u, Q - 1);
             const int kind = (cw[u] >> 24) & 15;
             const bool eq = kind == REC_EQ;
-            const int cell = eq ? 0 : (cw[u] & 0xFFFFFF);
+            const int cell = SLLBM_CHK(eq ? 0 : (cw[u] & 0xFFFFFF), C0 * C1 * (D == 3 ? G.cells[2] : 1), G.status, SLLBM_DEV_BAD_REC);
             int cc[3];
             cc[0] = cell % C0;
             cc[1] = (cell / C0) % C1;
@@ -1249,10 +1252,10 @@ __global__ void __launch_bounds__(128, 4) k_step_gather_smem(const typename Vec2
                 for (int a = 0; a <= P; ++a) {
                     int kk = cc[d] * P + a;
                     if (G.periodic[d]) kk = wrapi(kk, G.N[d]);
-                    off[d][a] = kk * st;
+                    off[d][a] = SLLBM_CHK(kk, G.N[d], G.status, SLLBM_DEV_BAD_NODE) * st;
                 }
             }
-            const int src = eq ? 0 : ((kind == REC_BB || kind == REC_BB_ISO) ? C.opp[i] : i);
+            const int src = SLLBM_CHK(eq ? 0 : ((kind == REC_BB || kind == REC_BB_ISO) ? C.opp[i] : i), Q, G.status, SLLBM_DEV_BAD_POP);
             const V2* p = fg + int64_t(src) * NN;
             if (D == 2) {
 #pragma unroll
@@ -1277,8 +1280,8 @@ __global__ void __launch_bounds__(128, 4) k_step_gather_smem(const typename Vec2
             const int bid = (cw[u] >> 28) & 15;
             real of = 0, og = 0;
             if (kind == REC_EQ) {
-                of = C.eqf[bid][i];
-                og = C.eqg[bid][i];
+                of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+                og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             } else {
                 if (D == 2) {
 #pragma unroll
@@ -1311,7 +1314,7 @@ __global__ void __launch_bounds__(128, 4) k_step_gather_smem(const typename Vec2
                         og += wt[u][2][c3] * ug;
                     }
                 }
-                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[bid][i];
+                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
             }
             Sf[i * stride] = of;
             Sg[i * stride] = og;
