@@ -315,6 +315,9 @@ def run_gpu(args, ws, rank, local):
     peaks, psrc = _peaks()
     alg_bytes = algorithmic_bytes_per_node(Q, real_bytes) * N
     achieved = alg_bytes / (avg_launch_ms / 1e3) / 1e9
+    # curved meshes stream a per-(node, velocity) departure table (cell code
+    # + D reference coordinates) besides the populations: second roofline
+    table_bytes = sim.info.table_bytes if "gather" in kernel_name else 0
     line = None
     if rank == 0:
         traffic = None
@@ -343,6 +346,10 @@ def run_gpu(args, ws, rank, local):
                          "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                          "peak_source": f"{psrc} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": alg_bytes,
+                         **({"with_table": {"algorithmic_bytes_per_launch": alg_bytes + table_bytes,
+                                            "achieved": round((alg_bytes + table_bytes) / (avg_launch_ms / 1e3) / 1e9, 1),
+                                            "frac": round((alg_bytes + table_bytes) / (avg_launch_ms / 1e3) / 1e9
+                                                          / peaks["hbm_gbs"], 4)}} if table_bytes else {}),
                          "kernel": kernel_name + f"<{cfg['velset']}>" +
                                    ("" if args.learned == "none" else
                                     f" (learned, MLP on {'tensor' if args.learned == 'tensor' else 'CUDA'} cores)")},
@@ -372,7 +379,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--config", default="channel")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
