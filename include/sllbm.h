@@ -113,6 +113,12 @@ extern "C" {
                                        kernel that carries the learned collision); p = 2 only,
                                        p = 4 runs the order-4 shared-memory warp-tiled kernel    */
 #define SLLBM_STREAM_GATHER_SMEM 5  /* per-record gather with the node state in shared memory    */
+#define SLLBM_STREAM_ROW_COPY    6  /* as SLLBM_STREAM_STRUCTURED, but where one block takes a
+                                       periodic row (FP32, p = 2, D2Q19 rows of 32..256 nodes,
+                                       D3Q45 rows of 32..128) the source rows of each velocity are
+                                       staged in shared memory by the bulk-copy (TMA) engine, six
+                                       velocities ahead, instead of loaded by every thread; other
+                                       meshes run the SLLBM_STREAM_STRUCTURED kernels             */
 
 /* ------------------------------------------------------------------ descriptors */
 typedef struct {
@@ -394,7 +400,7 @@ int sllbm_mlp_path(sllbm_ctx* ctx, int32_t path);
 /* Device status word of the context: synchronises the context's stream,
  * writes the word to *code and clears it.  Host pointer.  The word is an OR
  * of bits: 0 nothing recorded; SLLBM_DEV_TC_TIMEOUT a tensor-core wait ran
- * out.  The SLLBM_DEV_BAD_* bits come only from the bounds-checked debug build
+ * out; SLLBM_DEV_COPY_TIMEOUT a bulk-copy wait ran out.  The SLLBM_DEV_BAD_* bits come only from the bounds-checked debug build
  * (sllbm_build_flags() & SLLBM_BUILD_CHECKED), whose step kernels test every
  * index they take from a record table or derive from one, replace an index
  * outside its range by 0 (so no access leaves its buffer; the result is then
@@ -412,6 +418,8 @@ int sllbm_mlp_path(sllbm_ctx* ctx, int32_t path);
 #define SLLBM_DEV_BAD_POP    4
 #define SLLBM_DEV_BAD_REC    8
 #define SLLBM_DEV_BAD_SMEM   16
+#define SLLBM_DEV_COPY_TIMEOUT 32  /* a bulk-copy wait of SLLBM_STREAM_ROW_COPY ran out: that
+                                      block stored nothing                                       */
 int sllbm_device_status(sllbm_ctx* ctx, int32_t* code);
 
 /* How the loaded library was compiled: an OR of SLLBM_BUILD_* bits

@@ -18,11 +18,12 @@ ERRORS = {-1: "SLLBM_ERR_ARG", -2: "SLLBM_ERR_CUDA", -3: "SLLBM_ERR_ARCH", -4: "
 MESH = dict(box=0, channel=1, mixing=2, naca=3)
 VELSET = dict(D2Q9=0, D2Q19=1, D2Q25=2, D3Q45=3)
 MLP_TENSOR, MLP_SIMT = 0, 1
-DEV_TC_TIMEOUT, DEV_BAD_NODE, DEV_BAD_POP, DEV_BAD_REC, DEV_BAD_SMEM = 1, 2, 4, 8, 16
+DEV_TC_TIMEOUT, DEV_BAD_NODE, DEV_BAD_POP, DEV_BAD_REC, DEV_BAD_SMEM, DEV_COPY_TIMEOUT = 1, 2, 4, 8, 16, 32
 BUILD_CHECKED = 1
 FP64, FP32 = 0, 1
 STREAM_AUTO, STREAM_GATHER, STREAM_STRUCTURED, STREAM_STRUCTURED_NODE, STREAM_TILED_REG, STREAM_GATHER_SMEM = \
     0, 1, 2, 3, 4, 5
+STREAM_ROW_COPY = 6
 
 
 class Bc(C.Structure):

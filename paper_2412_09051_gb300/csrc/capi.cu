@@ -60,6 +60,8 @@ SLLBM_EXTERN_ROWP(1, float)
 SLLBM_EXTERN_ROWP(3, float)
 SLLBM_EXTERN_ROW(1, float)
 SLLBM_EXTERN_ROW(3, float)
+SLLBM_EXTERN_ROWC(1, float)
+SLLBM_EXTERN_ROWC(3, float)
 SLLBM_EXTERN_TILED_P(0, 4, float)
 SLLBM_EXTERN_TILED_P(1, 4, float)
 SLLBM_EXTERN_TILED_P(2, 4, float)
@@ -313,6 +315,24 @@ void build_tile_table(const sllbm_ctx* c, const std::vector<Rec64>& rec, std::ve
         }
 }
 
+// True when, for every velocity and every (y, z) class, the records of the two
+// x parities share kind, source population, y/z offsets and y/z weights: the
+// source rows of a velocity are then the same for a whole periodic x row.
+template <typename real>
+bool row_uniform_table(const sllbm_ctx* c, const std::vector<TileRec<real>>& t) {
+    const StepGeom& G = c->geom;
+    if (G.ncls[0] != 2) return false;
+    for (int i = 0; i < c->vs.Q; ++i)
+        for (int cl = 0; cl < G.n_classes; cl += 2) {
+            const TileRec<real>& a = t[size_t(i) * G.n_classes + cl];
+            const TileRec<real>& b = t[size_t(i) * G.n_classes + cl + 1];
+            if (a.meta != b.meta || a.dyzp != b.dyzp) return false;
+            for (int k = 0; k < 9; ++k)
+                if (a.rw[k] != b.rw[k]) return false;
+        }
+    return true;
+}
+
 template <typename real>
 int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const int vs = ctx->velset, p = ctx->mesh.p;
@@ -323,6 +343,22 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
         // rows of 192 nodes take 78 KB per block: 12 warps, slower than the
         // warp tiles)
         const int nx = ctx->mesh.N[0];
+        if (st && ctx->tiled && ctx->row_copy && ctx->row_uniform && ctx->mode == SLLBM_STREAM_STRUCTURED &&
+            (vs == 1 || vs == 3) && (nx == 32 || nx == 64 || nx == 128 || (nx == 256 && vs == 1))) {
+            ctx->step_kernel = "k_step_row_copy";
+            StepLaunch<real> Lc = L;
+            Lc.status = ctx->d_status;
+#define ROWCCASE(VS)                                                        \
+    if (vs == VS) {                                                         \
+        if (nx == 32) return launch_step_row_copy<VS, real, 32, 6>(Lc);     \
+        if (nx == 64) return launch_step_row_copy<VS, real, 64, 6>(Lc);     \
+        if (nx == 128) return launch_step_row_copy<VS, real, 128, 6>(Lc);   \
+    }
+            ROWCCASE(1)
+            ROWCCASE(3)
+#undef ROWCCASE
+            return launch_step_row_copy<1, real, 256, 6>(Lc);
+        }
         if (st && ctx->tiled && ctx->mode == SLLBM_STREAM_STRUCTURED && (vs == 1 || vs == 3) &&
             (nx == 32 || nx == 64 || nx == 128 || (nx == 192 && vs == 1) || nx == 256)) {
             ctx->step_kernel = "k_step_row_smem";
@@ -627,6 +663,10 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
     const bool axis = ctx->mesh.kind != SLLBM_MESH_NACA;
     int mode = params->stream_mode;
     if (mode == SLLBM_STREAM_AUTO) mode = axis ? SLLBM_STREAM_STRUCTURED : SLLBM_STREAM_GATHER;
+    if (mode == SLLBM_STREAM_ROW_COPY) {
+        ctx->row_copy = true;
+        mode = SLLBM_STREAM_STRUCTURED;
+    }
     if ((mode == SLLBM_STREAM_STRUCTURED || mode == SLLBM_STREAM_STRUCTURED_NODE || mode == SLLBM_STREAM_TILED_REG) &&
         !axis) {
         ctx->last_error = "structured streaming needs axis-aligned cells";
@@ -808,6 +848,7 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
                 } else {
                     std::vector<TileRec<float>> t;
                     build_tile_table(ctx, rec, t);
+                    ctx->row_uniform = row_uniform_table(ctx, t);
                     CK(cudaMalloc(&ctx->tile_tab, sizeof(TileRec<float>) * t.size()));
                     CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(TileRec<float>) * t.size(),
                                        cudaMemcpyHostToDevice, s));
@@ -867,7 +908,7 @@ int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
     o->stream_mode = ((ctx->mode == SLLBM_STREAM_STRUCTURED || ctx->mode == SLLBM_STREAM_TILED_REG) && !ctx->tiled &&
                       !ctx->tiled_p)
                          ? SLLBM_STREAM_STRUCTURED_NODE
-                         : ctx->mode;
+                         : (ctx->row_copy ? SLLBM_STREAM_ROW_COPY : ctx->mode);
     o->state_bytes = int64_t(2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q);
     o->table_bytes = ctx->table_bytes;
     o->n_records = int64_t(ctx->mesh.n_nodes) * ctx->vs.Q;

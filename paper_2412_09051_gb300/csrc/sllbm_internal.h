@@ -121,6 +121,8 @@ struct sllbm_ctx {
     sllbm::HostMesh mesh;
     int mode = SLLBM_STREAM_GATHER;      // resolved
     bool tiled = false;                  // structured mode runs the warp-tiled kernel
+    bool row_copy = false;               // SLLBM_STREAM_ROW_COPY requested
+    bool row_uniform = false;            // both x parities share each velocity's y/z stencil
     int tiled_p = 0;                     // order of the warp-tiled order-P table (4), 0: none
     const char* step_kernel = "";        // kernel of the last step launched (sllbm_info)
     int precision = SLLBM_FP32;

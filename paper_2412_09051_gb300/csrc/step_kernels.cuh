@@ -4,6 +4,7 @@
 // thread per arrival node, all 2Q streamed values held in registers.
 #pragma once
 #include "mlp.cuh"
+#include "bulk.cuh"
 #include "checked.cuh"
 #include "mlp_tc.cuh"
 #include "sllbm_internal.h"
@@ -741,6 +742,174 @@ int launch_step_row_smem(const StepLaunch<real>& L) {
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
+// ------------------------------------------------------------ one block per periodic row, source rows copied by the bulk-copy engine
+// k_step_row_smem with the source rows staged in shared memory by the TMA
+// bulk-copy engine instead of loaded by every thread.  On a periodic x axis
+// the (p+1)^(D-1) source rows of a velocity, (ky + dy_b, kz + dz_c), are
+// whole x rows of NXB nodes of one population (contiguous, NXB float2), and
+// the y/z stencil is the same for both x parities (checked at setup), so one
+// thread issues NR row copies per velocity into one of NST stages, NST
+// velocities ahead, completing on the stage's mbarrier; every thread then
+// contracts its own column from shared memory (no per-thread addressing or
+// gathers).  A stage is refilled after the block barrier that follows its
+// use (velocities in groups of GV, one barrier per group as in
+// k_step_row_smem).  Every wait is bounded: on a timeout the block records
+// SLLBM_DEV_COPY_TIMEOUT, stops issuing and computing, waits (bounded) for
+// the copies it issued and returns without storing.
+template <int VS, typename real, int NXB, int NST>
+__global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
+    k_step_row_copy(const typename Vec2<real>::T* __restrict__ fg, typename Vec2<real>::T* __restrict__ fgo,
+                    const TileRec<real>* __restrict__ tab, const real* __restrict__ twt, const StepGeom G,
+                    const CollideConst<real> C, int* __restrict__ status) {
+    using VSET = VelSet<VS>;
+    using V2 = typename Vec2<real>::T;
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    constexpr int NR = D == 3 ? 9 : 3;
+    constexpr int GV = 3;
+    static_assert(NST % GV == 0 && NST >= GV, "stages hold whole velocity groups");
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    V2* RB = reinterpret_cast<V2*>(dyn_smem);                          // [NST][NR][NXB] staged rows
+    real* S = reinterpret_cast<real*>(RB + NST * NR * NXB);            // [f, g][Q][NXB] streamed state
+    real* XB = S + 2 * Q * NXB;                                        // [2][GV][f, g][NXB] row sums
+    uint64_t* bars = reinterpret_cast<uint64_t*>(XB + 2 * GV * 2 * NXB);   // [NST]
+    __shared__ int abort_flag;
+    const int N1 = G.N[1], N2 = D == 3 ? G.N[2] : 1;
+    const int row = blockIdx.x;
+    const int ky = row % N1;
+    const int kz = D == 3 ? row / N1 : 0;
+    const int NN = int(G.n_nodes);
+    const int plane = NXB * N1;
+    const int n = int(threadIdx.x) + NXB * ky + plane * kz;
+    const bool py = G.periodic[1] != 0;
+    const int cls0 = G.ncls[0] * ((py ? (ky & 1) : ky) + G.ncls[1] * (D == 3 ? (kz & 1) : 0));   // x parity 0
+    const int cls = int(threadIdx.x & 1) + cls0;
+    const uint32_t bar0 = smem_u32(bars);
+    const uint32_t rb0 = smem_u32(RB);
+    // producer (thread 0): the NR row copies of velocity i into stage i % NST
+    auto issue = [&](int i) {
+        const TileRec<real>* r = tab + i * G.n_classes + SLLBM_CHK(cls0, G.n_classes, G.status, SLLBM_DEV_BAD_REC);
+        const int meta = __ldg(&r->meta);
+        const uint32_t bar = bar0 + 8u * uint32_t(i % NST);
+        if ((meta & 15) == REC_EQ) {           // equilibrium record: no source rows
+            mbar_arrive(bar);
+            return;
+        }
+        const int dyzp = __ldg(&r->dyzp);
+        const V2* src = fg + int64_t(SLLBM_CHK(meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP)) * NN;
+        mbar_arrive_expect_tx(bar, uint32_t(NR * NXB * sizeof(V2)));
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            int ty = ky + ((dyzp >> (4 * (k % 3))) & 15) - 8;
+            int tz = D == 3 ? kz + ((dyzp >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+            if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
+            if (D == 3) { tz += tz < 0 ? N2 : 0; tz -= tz >= N2 ? N2 : 0; }
+            ty = SLLBM_CHK(ty, N1, G.status, SLLBM_DEV_BAD_NODE);
+            tz = SLLBM_CHK(tz, N2, G.status, SLLBM_DEV_BAD_NODE);
+            bulk_g2s(rb0 + uint32_t(((i % NST) * NR + k) * NXB * sizeof(V2)), src + (int64_t(tz) * N1 + ty) * NXB,
+                     uint32_t(NXB * sizeof(V2)), bar);
+        }
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(bar0 + 8u * uint32_t(s), 1);
+        abort_flag = 0;
+    }
+    __syncthreads();
+    int issued = 0;                             // velocities whose copies were issued (thread 0)
+    if (threadIdx.x == 0)
+        for (; issued < NST && issued < Q; ++issued) issue(issued);
+    real* Sf = S + threadIdx.x;
+    real* Sg = S + Q * NXB + threadIdx.x;
+    int grp = 0, waited = 0;
+#pragma unroll 1
+    for (int i0 = 0; i0 < Q; i0 += GV, ++grp) {
+        TileRec<real> r[GV];                    // meta / dxp / dyzp and the weights (no node offsets)
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const int i = min(i0 + u, Q - 1);
+            const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes +
+                                                            SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC));
+            int4* dst = reinterpret_cast<int4*>(&r[u]);
+            dst[0] = __ldg(src);
+#pragma unroll
+            for (int k = 4; k < 7; ++k) dst[k] = __ldg(src + k);
+        }
+        bool ok = true;
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const int i = i0 + u;
+            if (i < Q) ok = mbar_wait(bar0 + 8u * uint32_t(i % NST), uint32_t((i / NST) & 1)) && ok;
+        }
+        waited = min(i0 + GV, Q);
+        if (!ok) abort_flag = 1;
+        real* xb = XB + (grp & 1) * (GV * 2 * NXB);
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const V2* rb = RB + ((i0 + u) % NST) * NR * NXB + threadIdx.x;
+            real sf = 0, sg = 0;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                const V2 v = rb[k * NXB];
+                sf += r[u].rw[k] * v.x;
+                sg += r[u].rw[k] * v.y;
+            }
+            xb[(2 * u) * NXB + threadIdx.x] = sf;
+            xb[(2 * u + 1) * NXB + threadIdx.x] = sg;
+        }
+        __syncthreads();
+        if (abort_flag) break;                  // block-uniform after the barrier
+        // the group's stages are free: refill them GV * (NST / GV) velocities ahead
+        if (threadIdx.x == 0)
+            for (; issued < i0 + GV + NST && issued < Q; ++issued) issue(issued);
+#pragma unroll
+        for (int u = 0; u < GV; ++u) {
+            const int i = i0 + u;
+            if (i >= Q) break;
+            const int kind = r[u].meta & 15;
+            const int bid = (r[u].meta >> 4) & 15;
+            real of = 0, og = 0;
+            if (kind == REC_EQ) {
+                of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+                og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            } else {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int j = int(threadIdx.x) + ((r[u].dxp >> (4 * a)) & 15) - 8;
+                    j += j < 0 ? NXB : (j >= NXB ? -NXB : 0);
+                    j = SLLBM_CHK(j, NXB, G.status, SLLBM_DEV_BAD_SMEM);
+                    of += r[u].wx[a] * xb[(2 * u) * NXB + j];
+                    og += r[u].wx[a] * xb[(2 * u + 1) * NXB + j];
+                }
+                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            }
+            Sf[i * NXB] = of;
+            Sg[i * NXB] = og;
+        }
+    }
+    if (abort_flag) {
+        if (threadIdx.x == 0) {
+            atomicOr(status, SLLBM_DEV_COPY_TIMEOUT);
+            // wait (bounded) for the copies issued but not yet waited for
+            for (int i = waited; i < issued; ++i) mbar_wait(bar0 + 8u * uint32_t(i % NST), uint32_t((i / NST) & 1));
+        }
+        return;
+    }
+    collide_smem<VSET, real, V2, NXB>(C, Sf, Sg, twt[cls], fgo + n, NN);
+}
+
+template <int VS, typename real, int NXB, int NST>
+int launch_step_row_copy(const StepLaunch<real>& L) {
+    constexpr int Q = VelSet<VS>::Q, D = VelSet<VS>::D;
+    constexpr int NR = D == 3 ? 9 : 3;
+    if (!L.status) return SLLBM_ERR_ARG;
+    const int rows = D == 3 ? L.G.N[1] * L.G.N[2] : L.G.N[1];
+    const size_t smem = sizeof(typename Vec2<real>::T) * NST * NR * NXB + sizeof(real) * (2 * Q * NXB + 2 * 3 * 2 * NXB) +
+                        sizeof(uint64_t) * NST;
+    cudaFuncSetAttribute(k_step_row_copy<VS, real, NXB, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_step_row_copy<VS, real, NXB, NST><<<rows, NXB, smem, L.stream>>>(L.fg, L.fgo, L.tile, L.tw, L.G, *L.C, L.status);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
 // ------------------------------------------------------------ one block per periodic row, order P
 // k_step_tiled_p's order-P streaming with one block of NXB = Nx threads per
 // (y, z) row (no halo lanes: the warp tiles spend 2P of 32 lanes on halos);
@@ -1403,6 +1572,14 @@ int launch_step_gather(const StepLaunch<real>& L) {
 #define SLLBM_INSTANTIATE_ROW1(VS, real, W) template int launch_step_row_smem<VS, real, W>(const StepLaunch<real>&);
 #define SLLBM_EXTERN_ROW(VS, real) SLLBM_ROW_WIDTHS(SLLBM_EXTERN_ROW1, VS, real)
 #define SLLBM_INSTANTIATE_ROW(VS, real) SLLBM_ROW_WIDTHS(SLLBM_INSTANTIATE_ROW1, VS, real)
+// bulk-copy row kernel: widths whose six stages fit next to the state (D3Q45 up to 128 nodes)
+#define SLLBM_ROWC_WIDTHS(X, VS, real) X(VS, real, 32) X(VS, real, 64) X(VS, real, 128) SLLBM_ROWC_W256_##VS(X, real)
+#define SLLBM_ROWC_W256_1(X, real) X(1, real, 256)
+#define SLLBM_ROWC_W256_3(X, real)
+#define SLLBM_EXTERN_ROWC1(VS, real, W) extern template int launch_step_row_copy<VS, real, W, 6>(const StepLaunch<real>&);
+#define SLLBM_INSTANTIATE_ROWC1(VS, real, W) template int launch_step_row_copy<VS, real, W, 6>(const StepLaunch<real>&);
+#define SLLBM_EXTERN_ROWC(VS, real) SLLBM_ROWC_WIDTHS(SLLBM_EXTERN_ROWC1, VS, real)
+#define SLLBM_INSTANTIATE_ROWC(VS, real) SLLBM_ROWC_WIDTHS(SLLBM_INSTANTIATE_ROWC1, VS, real)
 #define SLLBM_ROWP_WIDTHS(X, VS, real) X(VS, real, 32) X(VS, real, 64) X(VS, real, 128) X(VS, real, 256)
 #define SLLBM_EXTERN_ROWP1(VS, real, W) extern template int launch_step_row_p<VS, 4, real, W>(const StepLaunch<real>&);
 #define SLLBM_INSTANTIATE_ROWP1(VS, real, W) template int launch_step_row_p<VS, 4, real, W>(const StepLaunch<real>&);

@@ -24,7 +24,7 @@ def cases():
     out = []
     for name in CASES:
         cfg, prec = _cfg(name)
-        for mode in (0, 1, 3, 4, 5):
+        for mode in (0, 1, 3, 4, 5, 6):
             if mode not in (0, 5) and cfg["mesh"]["kind"] == 3:
                 continue
             out.append((f"{name}_m{mode}", cfg, prec, mode, None))

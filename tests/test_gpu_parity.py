@@ -151,12 +151,13 @@ def test_setup_matches_oracle(built_lib, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5, 6])
 def test_steps_match_oracle(built_lib, name, mode):
     """Every streaming mode (0 auto: warp-tiled with shared-memory state where
     eligible, 1 gather with register state, 3 one thread per node with
     class records, 4 warp-tiled with register state, 5 gather with
-    shared-memory state) against the oracle."""
+    shared-memory state, 6 rows staged by the bulk-copy engine where a
+    periodic row fits one block) against the oracle."""
     cfg, prec, mesh, xi, w, opp, par, rec = _oracle(name)
     if mode not in (0, 5) and mesh.kind == 3:
         pytest.skip("curved mesh runs the gather modes (0 = 1)")
@@ -184,6 +185,8 @@ def test_steps_match_oracle(built_lib, name, mode):
     kern = sim.step_kernel()
     if "row32" in name and mode == 0:
         assert kern == "k_step_row_smem"                 # one block per 32-node row
+    if "row32" in name and mode == 6:
+        assert kern == "k_step_row_copy"                 # the same rows staged by bulk copies
     print(f"PARITY step {name} mode {sim.info.stream_mode} ({kern}): populations {worst:.2e} moments {em:.2e}")
     sim.close()
 
