@@ -747,9 +747,10 @@ int launch_step_row_smem(const StepLaunch<real>& L) {
 // bulk-copy engine instead of loaded by every thread.  On a periodic x axis
 // the (p+1)^(D-1) source rows of a velocity, (ky + dy_b, kz + dz_c), are
 // whole x rows of NXB nodes of one population (contiguous, NXB float2), and
-// the y/z stencil is the same for both x parities (checked at setup), so one
-// thread issues NR row copies per velocity into one of NST stages, NST
-// velocities ahead, completing on the stage's mbarrier; every thread then
+// the y/z stencil is the same for both x parities (checked at setup), so the
+// first warp issues NR row copies per velocity (one per lane and round) into
+// one of NST stages, NST velocities ahead, completing on the stage's
+// mbarrier; every thread then
 // contracts its own column from shared memory (no per-thread addressing or
 // gathers).  A stage is refilled after the block barrier that follows its
 // use (velocities in groups of GV, one barrier per group as in
@@ -786,28 +787,41 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
     const int cls = int(threadIdx.x & 1) + cls0;
     const uint32_t bar0 = smem_u32(bars);
     const uint32_t rb0 = smem_u32(RB);
-    // producer (thread 0): the NR row copies of velocity i into stage i % NST
-    auto issue = [&](int i) {
-        const TileRec<real>* r = tab + i * G.n_classes + SLLBM_CHK(cls0, G.n_classes, G.status, SLLBM_DEV_BAD_REC);
-        const int meta = __ldg(&r->meta);
-        const uint32_t bar = bar0 + 8u * uint32_t(i % NST);
-        if ((meta & 15) == REC_EQ) {           // equilibrium record: no source rows
-            mbar_arrive(bar);
-            return;
+    // producer (warp 0, all lanes): the copies of velocities [ib, ie), at most
+    // NST of them; lane u < ie - ib arms the barrier of velocity ib + u, then
+    // every lane issues one row copy per round
+    auto issue = [&](int ib, int ie) {
+        const int lane = int(threadIdx.x & 31);
+        int meta = REC_EQ, dyzp = 0;
+        if (lane < ie - ib) {
+            const int i = ib + lane;
+            const TileRec<real>* r = tab + i * G.n_classes + SLLBM_CHK(cls0, G.n_classes, G.status, SLLBM_DEV_BAD_REC);
+            meta = __ldg(&r->meta);
+            dyzp = __ldg(&r->dyzp);
+            const uint32_t bar = bar0 + 8u * uint32_t(i % NST);
+            if ((meta & 15) == REC_EQ) mbar_arrive(bar);            // equilibrium record: no source rows
+            else mbar_arrive_expect_tx(bar, uint32_t(NR * NXB * sizeof(V2)));
         }
-        const int dyzp = __ldg(&r->dyzp);
-        const V2* src = fg + int64_t(SLLBM_CHK(meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP)) * NN;
-        mbar_arrive_expect_tx(bar, uint32_t(NR * NXB * sizeof(V2)));
+        __syncwarp();
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            int ty = ky + ((dyzp >> (4 * (k % 3))) & 15) - 8;
-            int tz = D == 3 ? kz + ((dyzp >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
-            if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
-            if (D == 3) { tz += tz < 0 ? N2 : 0; tz -= tz >= N2 ? N2 : 0; }
-            ty = SLLBM_CHK(ty, N1, G.status, SLLBM_DEV_BAD_NODE);
-            tz = SLLBM_CHK(tz, N2, G.status, SLLBM_DEV_BAD_NODE);
-            bulk_g2s(rb0 + uint32_t(((i % NST) * NR + k) * NXB * sizeof(V2)), src + (int64_t(tz) * N1 + ty) * NXB,
-                     uint32_t(NXB * sizeof(V2)), bar);
+        for (int round = 0; round < (NST * NR + 31) / 32; ++round) {
+            const int c = round * 32 + lane;
+            const int u = min(c / NR, 31), k = c - (c / NR) * NR;
+            const int m = __shfl_sync(0xffffffffu, meta, u);
+            const int d = __shfl_sync(0xffffffffu, dyzp, u);
+            if (c < (ie - ib) * NR && (m & 15) != REC_EQ) {
+                const int i = ib + u;
+                int ty = ky + ((d >> (4 * (k % 3))) & 15) - 8;
+                int tz = D == 3 ? kz + ((d >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+                if (py) { ty += ty < 0 ? N1 : 0; ty -= ty >= N1 ? N1 : 0; }
+                if (D == 3) { tz += tz < 0 ? N2 : 0; tz -= tz >= N2 ? N2 : 0; }
+                ty = SLLBM_CHK(ty, N1, G.status, SLLBM_DEV_BAD_NODE);
+                tz = SLLBM_CHK(tz, N2, G.status, SLLBM_DEV_BAD_NODE);
+                const V2* src = fg + int64_t(SLLBM_CHK(m >> 8, Q, G.status, SLLBM_DEV_BAD_POP)) * NN +
+                                (int64_t(tz) * N1 + ty) * NXB;
+                bulk_g2s(rb0 + uint32_t(((i % NST) * NR + k) * NXB * sizeof(V2)), src, uint32_t(NXB * sizeof(V2)),
+                         bar0 + 8u * uint32_t(i % NST));
+            }
         }
     };
     if (threadIdx.x == 0) {
@@ -815,9 +829,8 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
         abort_flag = 0;
     }
     __syncthreads();
-    int issued = 0;                             // velocities whose copies were issued (thread 0)
-    if (threadIdx.x == 0)
-        for (; issued < NST && issued < Q; ++issued) issue(issued);
+    int issued = min(NST, Q);                   // velocities whose copies were issued (warp 0)
+    if (threadIdx.x < 32) issue(0, issued);
     real* Sf = S + threadIdx.x;
     real* Sg = S + Q * NXB + threadIdx.x;
     int grp = 0, waited = 0;
@@ -840,8 +853,8 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
             const int i = i0 + u;
             if (i < Q) ok = mbar_wait(bar0 + 8u * uint32_t(i % NST), uint32_t((i / NST) & 1)) && ok;
         }
-        waited = min(i0 + GV, Q);
-        if (!ok) abort_flag = 1;
+        if (ok) waited = min(i0 + GV, Q);
+        else abort_flag = 1;
         real* xb = XB + (grp & 1) * (GV * 2 * NXB);
 #pragma unroll
         for (int u = 0; u < GV; ++u) {
@@ -858,9 +871,12 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
         }
         __syncthreads();
         if (abort_flag) break;                  // block-uniform after the barrier
-        // the group's stages are free: refill them GV * (NST / GV) velocities ahead
-        if (threadIdx.x == 0)
-            for (; issued < i0 + GV + NST && issued < Q; ++issued) issue(issued);
+        // the group's stages are free: refill them NST velocities ahead
+        if (threadIdx.x < 32 && issued < Q) {
+            const int ie = min(i0 + GV + NST, Q);
+            issue(issued, ie);
+            issued = ie;
+        }
 #pragma unroll
         for (int u = 0; u < GV; ++u) {
             const int i = i0 + u;
