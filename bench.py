@@ -324,7 +324,8 @@ def run_gpu(args, ws, rank, local):
         tf = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tf):
             try:
-                traffic = json.load(open(tf)).get(cfg["name"])
+                # DRAM bytes per launch from one ncu capture, keyed by workload and kernel
+                traffic = json.load(open(tf)).get(f"{cfg['name']}|{kernel_name}")
             except Exception:
                 traffic = None
         line = {
