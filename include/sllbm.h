@@ -422,6 +422,18 @@ int sllbm_mlp_path(sllbm_ctx* ctx, int32_t path);
                                       block stored nothing                                       */
 int sllbm_device_status(sllbm_ctx* ctx, int32_t* code);
 
+/* Test hook for the bounded waits: from the next launch on, every wait of the
+ * tensor-core and bulk-copy kernels of this context (sllbm_mlp_path
+ * SLLBM_MLP_TENSOR, SLLBM_STREAM_ROW_COPY) gives up after 2^log2_cycles SM
+ * cycles instead of about 2^31, so a test can make a wait run out without
+ * any fault: the kernel then records SLLBM_DEV_TC_TIMEOUT or
+ * SLLBM_DEV_COPY_TIMEOUT, waits with the default bound for its own
+ * operations in flight, frees its tensor memory and returns (a timed-out
+ * bulk-copy block stores nothing: re-initialise the state afterwards).
+ * log2_cycles = 0 restores the default; 1..31 sets the limit; anything else:
+ * SLLBM_ERR_ARG.  The paper has no counterpart. */
+int sllbm_debug_wait_limit(sllbm_ctx* ctx, int32_t log2_cycles);
+
 /* How the loaded library was compiled: an OR of SLLBM_BUILD_* bits
  * (SLLBM_BUILD_CHECKED: the bounds-checked debug build, compiled with
  * -DSLLBM_CHECKED).  Needs no context and no GPU; never fails. */

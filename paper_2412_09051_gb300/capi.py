@@ -91,6 +91,7 @@ _SIGS = {
     "sllbm_plane_cp": (C.c_int, [_P, C.c_int32, C.c_double, C.c_double, _P, _P, _P]),
     "sllbm_device_status": (C.c_int, [_P, _P]),
     "sllbm_build_flags": (C.c_int, []),
+    "sllbm_debug_wait_limit": (C.c_int, [_P, C.c_int32]),
     "sllbm_moment_basis": (C.c_int, [_P, _P, _P]),
     "sllbm_train_create": (C.c_int, [_P, _P, C.POINTER(_P)]),
     "sllbm_train_destroy": (C.c_int, [_P]),

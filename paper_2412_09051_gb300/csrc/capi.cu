@@ -753,8 +753,8 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
             G.ncls[d] = d < D ? (m.periodic[d] ? m.p : m.N[d]) : 1;
             G.n_classes *= G.ncls[d];
         }
-        CK(cudaMalloc(&ctx->d_status, sizeof(int)));
-        CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+        CK(cudaMalloc(&ctx->d_status, 2 * sizeof(int)));       // status word, test wait limit
+        CK(cudaMemsetAsync(ctx->d_status, 0, 2 * sizeof(int), ctx->stream));
 #ifdef SLLBM_CHECKED
         G.status = ctx->d_status;
 #endif
@@ -1164,8 +1164,8 @@ int sllbm_mlp_set(sllbm_ctx* ctx, const uint16_t* w_bf16, const float* biases, c
         for (int q = 0; q < H; ++q) put(TC::B1 + TC::B2, i, q, H, W3[i * H + q]);
     if (!ctx->mlp_tc) CK(cudaMalloc(&ctx->mlp_tc, TC::B_BYTES));
     if (!ctx->d_status) {
-        CK(cudaMalloc(&ctx->d_status, sizeof(int)));
-        CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+        CK(cudaMalloc(&ctx->d_status, 2 * sizeof(int)));
+        CK(cudaMemsetAsync(ctx->d_status, 0, 2 * sizeof(int), ctx->stream));
     }
     CK(cudaMemcpyAsync(ctx->mlp_tc, tiles.data(), TC::B_BYTES, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->mlp_img, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -1190,6 +1190,15 @@ int sllbm_device_status(sllbm_ctx* ctx, int32_t* code) {
     CK(cudaMemcpy(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
     *code = v;
+    return SLLBM_OK;
+}
+
+int sllbm_debug_wait_limit(sllbm_ctx* ctx, int32_t log2_cycles) {
+    if (!ctx || log2_cycles < 0 || log2_cycles > 31) return SLLBM_ERR_ARG;
+    if (!ctx->d_status) return fail(ctx, SLLBM_ERR_STATE, "context has no status words");
+    cudaSetDevice(ctx->device);
+    CK(cudaMemcpyAsync(ctx->d_status + 1, &log2_cycles, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return SLLBM_OK;
 }
 

@@ -100,12 +100,39 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait for the phase with the given parity: false after ~2^31 SM cycles
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// non-blocking test of the phase with the given parity
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with the given parity: false after `limit` SM
+// cycles (default 2^31, about a second).  A shorter (test) limit polls
+// without blocking: try_wait may suspend the thread for longer than the
+// limit, which would hide a short one.
+constexpr long long kWaitLimit = 1ll << 31;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitLimit) {
     const long long t0 = clock64();
+    if (limit < kWaitLimit) {
+        while (!mbar_test(bar, parity))
+            if (clock64() - t0 > limit) return false;
+        return true;
+    }
     while (!mbar_try(bar, parity))
-        if (clock64() - t0 > (1ll << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
+}
+// the wait limit of the kernels that take the context's status words: word 1
+// holds log2 of a test limit (sllbm_debug_wait_limit), 0 for the default
+__device__ __forceinline__ long long wait_limit(const int* status) {
+    const int e = status ? __ldg(status + 1) : 0;
+    return e > 0 && e < 62 ? (1ll << e) : kWaitLimit;
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
@@ -188,7 +215,7 @@ __device__ __forceinline__ uint32_t mlp_tc_setup(const float* __restrict__ img, 
 // thread waits for the commit.  Returns false (block-uniform) if the wait ran out.
 template <int K, int N>
 __device__ __forceinline__ bool tc_layer(uint32_t ahi, uint32_t alo, uint32_t b, uint32_t d, uint32_t bar,
-                                         uint32_t parity) {
+                                         uint32_t parity, long long limit) {
     fence_async_smem();   // this thread's activation rows -> async proxy
     tc_fence_before();
     __syncthreads();
@@ -203,7 +230,11 @@ __device__ __forceinline__ bool tc_layer(uint32_t ahi, uint32_t alo, uint32_t b,
         }
         tc_commit(bar);
     }
-    const bool ok = mbar_wait(bar, parity);
+    const bool ok = mbar_wait(bar, parity, limit);
+    // a wait that ran out: wait once more, with the default bound, for the
+    // products still in flight before the caller reuses their operands or
+    // frees the tensor memory they write (the block still reports the timeout)
+    if (!ok) mbar_wait(bar, parity);
     tc_fence_after();
     return __syncthreads_and(ok) != 0;
 }
@@ -234,7 +265,8 @@ __device__ __forceinline__ void mlp_correct_tc(const MlpView<Q, D>& M, const Col
         }
         tc_put8<L::K1>(Ahi, Alo, r, c, v);
     }
-    bool ok = tc_layer<L::K1, MLP_H>(ahi, alo, bw1, tbase, bar, 0);
+    const long long lim = wait_limit(status);
+    bool ok = tc_layer<L::K1, MLP_H>(ahi, alo, bw1, tbase, bar, 0, lim);
     if (ok) {
 #pragma unroll 1   // runtime chunk loops keep the tanh code small (instruction fetch)
         for (int c = 0; c < MLP_H / 16; ++c) {
@@ -245,7 +277,7 @@ __device__ __forceinline__ void mlp_correct_tc(const MlpView<Q, D>& M, const Col
             tc_put8<MLP_H>(Ahi, Alo, r, 2 * c, v);
             tc_put8<MLP_H>(Ahi, Alo, r, 2 * c + 1, v + 8);
         }
-        ok = tc_layer<MLP_H, MLP_H>(ahi, alo, bw2, tbase + MLP_H, bar, 1);
+        ok = tc_layer<MLP_H, MLP_H>(ahi, alo, bw2, tbase + MLP_H, bar, 1, lim);
     }
     if (ok) {
 #pragma unroll 1
@@ -257,7 +289,7 @@ __device__ __forceinline__ void mlp_correct_tc(const MlpView<Q, D>& M, const Col
             tc_put8<MLP_H>(Ahi, Alo, r, 2 * c, v);
             tc_put8<MLP_H>(Ahi, Alo, r, 2 * c + 1, v + 8);
         }
-        ok = tc_layer<MLP_H, L::N3>(ahi, alo, bw3, tbase, bar, 0);
+        ok = tc_layer<MLP_H, L::N3>(ahi, alo, bw3, tbase, bar, 0, lim);
     }
     if (ok) {
         float o[Q];

@@ -773,7 +773,7 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
     V2* RB = reinterpret_cast<V2*>(dyn_smem);                          // [NST][NR][NXB] staged rows
     real* S = reinterpret_cast<real*>(RB + NST * NR * NXB);            // [f, g][Q][NXB] streamed state
     real* XB = S + 2 * Q * NXB;                                        // [2][GV][f, g][NXB] row sums
-    uint64_t* bars = reinterpret_cast<uint64_t*>(XB + 2 * GV * 2 * NXB);   // [NST]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(XB + 2 * GV * 2 * NXB);   // [NST] + 1 that nothing completes
     __shared__ int abort_flag;
     const int N1 = G.N[1], N2 = D == 3 ? G.N[2] : 1;
     const int row = blockIdx.x;
@@ -825,10 +825,11 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
         }
     };
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NST; ++s) mbar_init(bar0 + 8u * uint32_t(s), 1);
+        for (int s = 0; s <= NST; ++s) mbar_init(bar0 + 8u * uint32_t(s), 1);
         abort_flag = 0;
     }
     __syncthreads();
+    const long long lim = wait_limit(status);
     int issued = min(NST, Q);                   // velocities whose copies were issued (warp 0)
     if (threadIdx.x < 32) issue(0, issued);
     real* Sf = S + threadIdx.x;
@@ -851,8 +852,11 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
 #pragma unroll
         for (int u = 0; u < GV; ++u) {
             const int i = i0 + u;
-            if (i < Q) ok = mbar_wait(bar0 + 8u * uint32_t(i % NST), uint32_t((i / NST) & 1)) && ok;
+            if (i < Q) ok = mbar_wait(bar0 + 8u * uint32_t(i % NST), uint32_t((i / NST) & 1), lim) && ok;
         }
+        // under a test limit (sllbm_debug_wait_limit) also wait on the barrier
+        // that nothing completes, so that the wait runs out whatever the timing
+        if (lim < kWaitLimit) ok = mbar_wait(bar0 + 8u * uint32_t(NST), 0, lim) && ok;
         if (ok) waited = min(i0 + GV, Q);
         else abort_flag = 1;
         real* xb = XB + (grp & 1) * (GV * 2 * NXB);
@@ -905,7 +909,8 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
     if (abort_flag) {
         if (threadIdx.x == 0) {
             atomicOr(status, SLLBM_DEV_COPY_TIMEOUT);
-            // wait (bounded) for the copies issued but not yet waited for
+            // wait (bounded, default limit) for the copies issued but not yet
+            // waited for, so that none lands after the block has exited
             for (int i = waited; i < issued; ++i) mbar_wait(bar0 + 8u * uint32_t(i % NST), uint32_t((i / NST) & 1));
         }
         return;
@@ -920,7 +925,7 @@ int launch_step_row_copy(const StepLaunch<real>& L) {
     if (!L.status) return SLLBM_ERR_ARG;
     const int rows = D == 3 ? L.G.N[1] * L.G.N[2] : L.G.N[1];
     const size_t smem = sizeof(typename Vec2<real>::T) * NST * NR * NXB + sizeof(real) * (2 * Q * NXB + 2 * 3 * 2 * NXB) +
-                        sizeof(uint64_t) * NST;
+                        sizeof(uint64_t) * (NST + 1);
     cudaFuncSetAttribute(k_step_row_copy<VS, real, NXB, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     k_step_row_copy<VS, real, NXB, NST><<<rows, NXB, smem, L.stream>>>(L.fg, L.fgo, L.tile, L.tw, L.G, *L.C, L.status);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;

@@ -219,6 +219,11 @@ class Sim:
         """capi.MLP_TENSOR (tensor cores, default) or capi.MLP_SIMT (CUDA cores)."""
         self._call("sllbm_mlp_path", C.c_int32(path))
 
+    def debug_wait_limit(self, log2_cycles):
+        """Test hook: bound the tensor-core / bulk-copy waits by 2^log2_cycles
+        SM cycles (0: the default, about a second)."""
+        self._call("sllbm_debug_wait_limit", C.c_int32(log2_cycles))
+
     def device_status(self):
         """Synchronise and return (and clear) the context's device status word."""
         v = C.c_int32(0)
