@@ -25,6 +25,8 @@ CASES = {
     # rows of 32 nodes: one block per periodic row in the structured mode
     "channel_row32_fp32": (lambda: get_config("channel", cells=(16, 4, 3)), "fp32"),
     "box_row32_d2q19_fp32": (lambda: get_config("learned", cells=16), "fp32"),
+    # 32-node rows between equilibrium boundaries: the row kernels' equilibrium records
+    "mixing_row32_fp32": (lambda: get_config("mixing", cells=(16, 8, 3)), "fp32"),
     # order p = 4, the order of every case in Sec. 4
     "tgv2d_p4_fp64": (lambda: dict(get_config("tgv2d", cells=4), mesh=dict(kind=0, p=4, cells=(4, 3),
                                                                            length=(6.2831853, 5.0))), "fp64"),
