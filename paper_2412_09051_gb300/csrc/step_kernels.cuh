@@ -935,7 +935,8 @@ int launch_step_row_copy(const StepLaunch<real>& L) {
 // k_step_tiled_p's order-P streaming with one block of NXB = Nx threads per
 // (y, z) row (no halo lanes: the warp tiles spend 2P of 32 lanes on halos);
 // the x factor reads the neighbouring nodes' row sums from a shared row
-// buffer, double-buffered per velocity with one block barrier per velocity.
+// buffer, double-buffered per pair of velocities with one block barrier per
+// pair.
 template <int VS, int P, typename real, int NXB>
 __global__ void __launch_bounds__(256, 2) k_step_row_p(const typename Vec2<real>::T* __restrict__ fg,
                                                     typename Vec2<real>::T* __restrict__ fgo,
@@ -949,7 +950,7 @@ __global__ void __launch_bounds__(256, 2) k_step_row_p(const typename Vec2<real>
     constexpr int NZ = D == 3 ? P + 1 : 1;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     real* S = reinterpret_cast<real*>(dyn_smem);
-    real* XB = S + 2 * Q * NXB;                  // [2 buffers][f, g][NXB]
+    real* XB = S + 2 * Q * NXB;                  // [2 buffers][2 velocities][f, g][NXB]
     const int Nx = NXB, N1 = G.N[1], N2 = D == 3 ? G.N[2] : 1;
     const int row = blockIdx.x;
     const int ky = row % N1;
@@ -964,64 +965,77 @@ __global__ void __launch_bounds__(256, 2) k_step_row_p(const typename Vec2<real>
     real* Sf = S + threadIdx.x;
     real* Sg = S + Q * stride + threadIdx.x;
     const V2* base = fg + n;
-    // row-buffer index: counts the velocities that exchange (equilibrium
-    // records skip the exchange and its barrier), so two uses of one buffer
-    // always have the other buffer's barrier between them
-    int nx_used = 0;
+    // velocities in pairs: both pairs' row sums go through one buffer of the
+    // double-buffered row buffer with one block barrier per pair (equilibrium
+    // records write zeros), so two uses of one buffer always have the other
+    // buffer's barrier between them
 #pragma unroll 1
-    for (int i = 0; i < Q; ++i) {
-        const TileRecP<real, P> r = tab[i * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC)];
-        const int kind = r.meta & 15;            // uniform over the row (checked at setup)
-        const int bid = (r.meta >> 4) & 15;
-        real of = 0, og = 0;
-        if (kind == REC_EQ) {
-            of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
-            og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
-        } else {
-            int oy[P + 1], oz[NZ];
+    for (int i0 = 0, pr = 0; i0 < Q; i0 += 2, ++pr) {
+        TileRecP<real, P> r[2];
 #pragma unroll
-            for (int b = 0; b <= P; ++b) {
-                int ty = ky + ((r.dyp >> (4 * b)) & 15) - 8;
-                if (py) ty += ty < 0 ? N1 : (ty >= N1 ? -N1 : 0);
-                oy[b] = (ty - ky) * Nx;
-            }
+        for (int u = 0; u < 2; ++u)
+            r[u] = tab[min(i0 + u, Q - 1) * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC)];
+        real* xb = XB + (pr & 1) * (2 * 2 * NXB);   // [u][f, g][NXB]
 #pragma unroll
-            for (int c = 0; c < NZ; ++c) {
-                int tz = kz + ((r.dzp >> (4 * c)) & 15) - 8;
-                tz += tz < 0 ? N2 : (tz >= N2 ? -N2 : 0);
-                oz[c] = D == 3 ? (tz - kz) * plane : 0;
-            }
-            const V2* p = base + SLLBM_CHK(r.meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP) * NN;
+        for (int u = 0; u < 2; ++u) {
             real sf = 0, sg = 0;
-#pragma unroll
-            for (int c = 0; c < NZ; ++c) {
-                real tf = 0, tg = 0;
+            if ((r[u].meta & 15) != REC_EQ && i0 + u < Q) {   // kind uniform over the row (checked at setup)
+                int oy[P + 1], oz[NZ];
 #pragma unroll
                 for (int b = 0; b <= P; ++b) {
-                    const V2 v = __ldg(p + SLLBM_CHK_REL(n, oy[b] + oz[c], NN, G.status));
-                    tf += r.wy[b] * v.x;
-                    tg += r.wy[b] * v.y;
+                    int ty = ky + ((r[u].dyp >> (4 * b)) & 15) - 8;
+                    if (py) ty += ty < 0 ? N1 : (ty >= N1 ? -N1 : 0);
+                    oy[b] = (ty - ky) * Nx;
                 }
-                const real wz = D == 3 ? r.wz[c] : real(1);
-                sf += wz * tf;
-                sg += wz * tg;
-            }
-            real* xb = XB + (nx_used++ & 1) * (2 * NXB);
-            xb[threadIdx.x] = sf;
-            xb[NXB + threadIdx.x] = sg;
-            __syncthreads();
 #pragma unroll
-            for (int a = 0; a <= P; ++a) {
-                int j = int(threadIdx.x) + ((r.dxp >> (4 * a)) & 15) - 8;
-                j += j < 0 ? NXB : (j >= NXB ? -NXB : 0);
-                j = SLLBM_CHK(j, NXB, G.status, SLLBM_DEV_BAD_SMEM);
-                of += r.wx[a] * xb[j];
-                og += r.wx[a] * xb[NXB + j];
+                for (int c = 0; c < NZ; ++c) {
+                    int tz = kz + ((r[u].dzp >> (4 * c)) & 15) - 8;
+                    tz += tz < 0 ? N2 : (tz >= N2 ? -N2 : 0);
+                    oz[c] = D == 3 ? (tz - kz) * plane : 0;
+                }
+                const V2* p = base + SLLBM_CHK(r[u].meta >> 8, Q, G.status, SLLBM_DEV_BAD_POP) * NN;
+#pragma unroll
+                for (int c = 0; c < NZ; ++c) {
+                    real tf = 0, tg = 0;
+#pragma unroll
+                    for (int b = 0; b <= P; ++b) {
+                        const V2 v = __ldg(p + SLLBM_CHK_REL(n, oy[b] + oz[c], NN, G.status));
+                        tf += r[u].wy[b] * v.x;
+                        tg += r[u].wy[b] * v.y;
+                    }
+                    const real wz = D == 3 ? r[u].wz[c] : real(1);
+                    sf += wz * tf;
+                    sg += wz * tg;
+                }
             }
-            if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            xb[(2 * u) * NXB + threadIdx.x] = sf;
+            xb[(2 * u + 1) * NXB + threadIdx.x] = sg;
         }
-        Sf[i * stride] = of;
-        Sg[i * stride] = og;
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = i0 + u;
+            if (i >= Q) break;
+            const int kind = r[u].meta & 15;
+            const int bid = (r[u].meta >> 4) & 15;
+            real of = 0, og = 0;
+            if (kind == REC_EQ) {
+                of = C.eqf[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+                og = C.eqg[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            } else {
+#pragma unroll
+                for (int a = 0; a <= P; ++a) {
+                    int j = int(threadIdx.x) + ((r[u].dxp >> (4 * a)) & 15) - 8;
+                    j += j < 0 ? NXB : (j >= NXB ? -NXB : 0);
+                    j = SLLBM_CHK(j, NXB, G.status, SLLBM_DEV_BAD_SMEM);
+                    of += r[u].wx[a] * xb[(2 * u) * NXB + j];
+                    og += r[u].wx[a] * xb[(2 * u + 1) * NXB + j];
+                }
+                if (kind == REC_BB || kind == REC_BB_ISO) of += C.mw[SLLBM_CHK(bid, 2, G.status, SLLBM_DEV_BAD_REC)][i];
+            }
+            Sf[i * stride] = of;
+            Sg[i * stride] = og;
+        }
     }
     collide_smem<VSET, real, V2, NXB>(C, Sf, Sg, twt[cls], fgo + n, NN);
 }
@@ -1031,7 +1045,7 @@ int launch_step_row_p(const StepLaunch<real>& L) {
     constexpr int Q = VelSet<VS>::Q, D = VelSet<VS>::D;
     if (!L.tilep) return SLLBM_ERR_ARG;
     const int rows = D == 3 ? L.G.N[1] * L.G.N[2] : L.G.N[1];
-    const size_t smem = sizeof(real) * (2 * Q * NXB + 2 * 2 * NXB);
+    const size_t smem = sizeof(real) * (2 * Q * NXB + 2 * 2 * 2 * NXB);
     cudaFuncSetAttribute(k_step_row_p<VS, P, real, NXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     k_step_row_p<VS, P, real, NXB><<<rows, NXB, smem, L.stream>>>(
         L.fg, L.fgo, static_cast<const TileRecP<real, P>*>(L.tilep), L.tw, L.G, *L.C);
