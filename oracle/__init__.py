@@ -21,7 +21,11 @@ collision, thermal correction, forcing and mass rescaling are pinned by
 closed forms, invariants and special cases (tests/test_oracle_*.py); the
 quasi-equilibrium term (Pr != 1) by its relaxation-rate invariants, the
 Prandtl scaling of the compressible Couette temperature rise and the
-thermal part of the sound attenuation.  The curved-wall bounce-back and the
-outlet scheme are pinned only geometrically (source points, populations
-read): "parity partly unpinned" for those two boundary schemes.
+thermal part of the sound attenuation.  The outlet scheme and the
+equilibrium boundary are pinned by the far-field fixed point of a uniform
+free stream (the population read, the boundary state) and geometrically
+(mirrored source point); the bounce-back by its geometry (reflected source
+point, opposite population) and, on flat walls, by the Couette profile.
+The curved-wall bounce-back has no value pin beyond its geometry: "parity
+partly unpinned" for that scheme.
 """

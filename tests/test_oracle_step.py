@@ -159,6 +159,37 @@ def test_outlet_mirror_point():
         assert rec["src"][i, n] == i
 
 
+def test_far_field_keeps_the_free_stream():
+    """Sec. 3.3.1 / 3.3.3: a uniform free stream at the far-field state is a
+    fixed point of a step wherever no trajectory meets the airfoil: the
+    equilibrium records reproduce it and the outlet records read population i
+    of a uniform field.  Every node off the wall ring (its outlet and
+    equilibrium records included) keeps it to round-off; an outlet that read
+    the opposite population instead breaks it at O(1)."""
+    cfg = get_config("naca", cells=(16, 4))
+    cfg["mesh"]["stretch"] = 1.6
+    cfg["dt"] = 0.05
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    bc = cfg["bcs"][1]
+    N = mesh.n_nodes
+    u = np.tile(np.asarray(bc["u"][:2], dtype=float), (N, 1))
+    f, g = st.init_equilibrium(np.full(N, bc["rho"]), u, np.full(N, bc["T"]), xi, w, par.cv)
+    Tw = st.isothermal_nodes(rec, par)
+    N0 = mesh.N[0]
+    off_wall = np.arange(N0, N)                      # radial index >= 1
+    ring = np.arange(N - N0, N)                      # far-field ring
+    assert (rec["kind"][:, ring] == REC_OUTLET).sum() > 0 and (rec["kind"][:, ring] == REC_EQ).sum() > 0
+    f1, g1 = st.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
+    scale = np.abs(f).max()
+    assert np.abs(f1 - f)[:, off_wall].max() < 1e-13 * scale
+    assert np.abs(g1 - g)[:, off_wall].max() < 1e-13 * np.abs(g).max()
+    bad = {k: v.copy() for k, v in rec.items()}
+    m = bad["kind"] == REC_OUTLET
+    bad["src"][m] = np.asarray(opp)[np.nonzero(m)[0]]
+    f2, _ = st.step(mesh, bad, f, g, xi, w, par, Tw=Tw)
+    assert np.abs(f2 - f)[:, ring].max() > 0.1 * scale
+
+
 def _shear_decay_rate(cells, dt, mu, steps):
     cfg = box_cfg(cells=(cells, 1), p=2, L=(2 * math.pi, 2 * math.pi / cells), dt=dt, mu=mu)
     mesh, xi, w, opp, par, rec = oracle_case(cfg)
