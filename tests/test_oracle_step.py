@@ -190,6 +190,26 @@ def test_far_field_keeps_the_free_stream():
     assert np.abs(f2 - f)[:, ring].max() > 0.1 * scale
 
 
+def test_curved_wall_keeps_a_resting_fluid():
+    """Sec. 3.3.2 on the curved NACA wall: a fluid at rest at the far-field
+    state is a fixed point of the step at every node, the bounce-back records
+    included (the interpolated reflected point of a uniform field, an opposite
+    population of equal weight, no momentum from a wall at rest); an
+    interpolation at the reflected point whose weights do not sum to one, or
+    a spurious wall-momentum term, breaks it."""
+    cfg = get_config("naca", cells=(16, 4))
+    cfg["mesh"]["stretch"] = 1.6
+    cfg["dt"] = 0.05
+    cfg["bcs"] = [dict(cfg["bcs"][0]), dict(cfg["bcs"][1], u=(0.0, 0.0, 0.0))]
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    assert ((rec["kind"] == REC_BB) | (rec["kind"] == REC_BB_ISO)).sum() > 0
+    N = mesh.n_nodes
+    f, g = st.init_equilibrium(np.full(N, 1.0), np.zeros((N, 2)), np.full(N, 1.0), xi, w, par.cv)
+    f1, g1 = st.step(mesh, rec, f, g, xi, w, par, Tw=st.isothermal_nodes(rec, par))
+    assert np.abs(f1 - f).max() < 1e-13 * np.abs(f).max()
+    assert np.abs(g1 - g).max() < 1e-13 * np.abs(g).max()
+
+
 def _shear_decay_rate(cells, dt, mu, steps):
     cfg = box_cfg(cells=(cells, 1), p=2, L=(2 * math.pi, 2 * math.pi / cells), dt=dt, mu=mu)
     mesh, xi, w, opp, par, rec = oracle_case(cfg)
