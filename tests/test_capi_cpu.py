@@ -43,3 +43,14 @@ def test_create_without_gpu_reports_arch(built_lib):
     with pytest.raises(SllbmError) as e:
         Sim(get_config("tgv2d", cells=4))
     assert e.value.code == -3
+
+
+def test_release_build_flags_and_null_context_arguments(built_lib):
+    """sllbm_build_flags needs no context or GPU: 0 for the release build.
+    Calls that take a context reject NULL with SLLBM_ERR_ARG before touching
+    a device."""
+    assert built_lib.sllbm_build_flags() == 0
+    assert built_lib.sllbm_debug_wait_limit(None, 0) == -1
+    code = ctypes.c_int32(7)
+    assert built_lib.sllbm_device_status(None, ctypes.byref(code)) == -1
+    assert built_lib.sllbm_mlp_path(None, 0) == -1
