@@ -362,13 +362,15 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
         if (st && ctx->tiled && ctx->mode == SLLBM_STREAM_STRUCTURED && (vs == 1 || vs == 3) &&
             (nx == 32 || nx == 64 || nx == 128 || (nx == 192 && vs == 1) || nx == 256)) {
             ctx->step_kernel = "k_step_row_smem";
+            StepLaunch<real> Lr = L;
+            Lr.row = static_cast<const RowRec*>(ctx->row_tab);
 #define ROWCASE(VS)                                                   \
     if (vs == VS) {                                                   \
-        if (nx == 32) return launch_step_row_smem<VS, real, 32>(L);   \
-        if (nx == 64) return launch_step_row_smem<VS, real, 64>(L);   \
-        if (nx == 128) return launch_step_row_smem<VS, real, 128>(L); \
-        if (nx == 192) return launch_step_row_smem<VS, real, 192>(L); \
-        return launch_step_row_smem<VS, real, 256>(L);                \
+        if (nx == 32) return launch_step_row_smem<VS, real, 32>(Lr);   \
+        if (nx == 64) return launch_step_row_smem<VS, real, 64>(Lr);   \
+        if (nx == 128) return launch_step_row_smem<VS, real, 128>(Lr); \
+        if (nx == 192) return launch_step_row_smem<VS, real, 192>(Lr); \
+        return launch_step_row_smem<VS, real, 256>(Lr);                \
     }
             ROWCASE(1)
             ROWCASE(3)
@@ -596,7 +598,7 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
-                    ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->d_red, ctx->d_flag,
+                    ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->row_tab, ctx->d_red, ctx->d_flag,
                     ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status,
                     ctx->d_plane, ctx->d_cp, ctx->d_plane_acc};
     for (void* p : ptrs)
@@ -849,6 +851,21 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
                     std::vector<TileRec<float>> t;
                     build_tile_table(ctx, rec, t);
                     ctx->row_uniform = row_uniform_table(ctx, t);
+                    std::vector<RowRec> rr(t.size());
+                    for (size_t k = 0; k < t.size(); ++k) {
+                        RowRec& o = rr[k];
+                        o.meta = t[k].meta;
+                        o.dxp = t[k].dxp;
+                        o.dyzp = t[k].dyzp;
+                        for (int q = 0; q < 9; ++q) {
+                            o.rel[q] = t[k].rel[q];
+                            o.rw[q] = t[k].rw[q];
+                        }
+                        for (int q = 0; q < 3; ++q) o.wx[q] = t[k].wx[q];
+                    }
+                    CK(cudaMalloc(&ctx->row_tab, sizeof(RowRec) * rr.size()));
+                    CK(cudaMemcpyAsync(ctx->row_tab, rr.data(), sizeof(RowRec) * rr.size(), cudaMemcpyHostToDevice, s));
+                    CK(cudaStreamSynchronize(s));
                     CK(cudaMalloc(&ctx->tile_tab, sizeof(TileRec<float>) * t.size()));
                     CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(TileRec<float>) * t.size(),
                                        cudaMemcpyHostToDevice, s));

@@ -87,6 +87,16 @@ struct TileRec {              // warp-tiled record (per velocity and class), 16-
     real wx[3];               // x weights
 };
 
+struct RowRec {               // TileRec<float> without padding, for the one-block-per-row kernel (96 B)
+    int32_t meta;             // kind | bid << 4 | src << 8
+    int32_t dxp;              // offsets of the 3 x taps, (dx + 8) in 4-bit fields
+    int32_t dyzp;             // dy[3] (bits 0..11) and dz[3] (bits 12..23), (d + 8) in 4-bit fields
+    int32_t rel[9];           // node offsets of the (y, z) source rows, no periodic wrap
+    float rw[9];              // y x z weight products
+    float wx[3];              // x weights
+};
+static_assert(sizeof(RowRec) == 96, "six 16-byte loads per record");
+
 template <typename real, int P>
 struct alignas(16) TileRecP {  // warp-tiled record of order P (per velocity and class), factorised
     int32_t meta;             // kind | bid << 4 | src << 8
@@ -135,6 +145,7 @@ struct sllbm_ctx {
     // step tables
     void* cls_tab = nullptr;             // ClassRec<real>[Q][n_classes]
     void* tile_tab = nullptr;            // TileRec<real>[Q][n_classes] (warp-tiled kernel)
+    void* row_tab = nullptr;             // RowRec[Q][n_classes] (one-block-per-row kernel, FP32)
     int32_t* g_code = nullptr;           // gather: [Q][N] cell | kind<<24 | bid<<28
     void* g_xi = nullptr;                // gather: real [Q][D][N]
     void* tw_tab = nullptr;              // real: per class (structured) or node (gather); NaN none

@@ -28,6 +28,7 @@ struct StepLaunch {
     const void* tilep = nullptr;        // warp-tiled records of order P (TileRecP), P > 2
     const uint16_t* mlp_tc = nullptr;   // BF16 weight tiles of the tensor-core MLP (mlp_tc.cuh)
     int* status = nullptr;              // device status word (tensor-core MLP)
+    const RowRec* row = nullptr;        // one-block-per-row records (FP32)
 };
 
 __device__ __forceinline__ int wrapi(int k, int N) { return k >= N ? k - N : k; }
@@ -630,7 +631,7 @@ int launch_step_tiled(const StepLaunch<real>& L) {
 template <int VS, typename real, int NXB>
 __global__ void __launch_bounds__(256, 2) k_step_row_smem(const typename Vec2<real>::T* __restrict__ fg,
                                                        typename Vec2<real>::T* __restrict__ fgo,
-                                                       const TileRec<real>* __restrict__ tab,
+                                                       const RowRec* __restrict__ tab,
                                                        const real* __restrict__ twt, const StepGeom G,
                                                        const CollideConst<real> C) {
     using VSET = VelSet<VS>;
@@ -660,14 +661,14 @@ __global__ void __launch_bounds__(256, 2) k_step_row_smem(const typename Vec2<re
     int grp = 0;
 #pragma unroll 1
     for (int i0 = 0; i0 < Q; i0 += GV, ++grp) {
-        TileRec<real> r[GV];
+        RowRec r[GV];
 #pragma unroll
         for (int u = 0; u < GV; ++u) {
             const int i = min(i0 + u, Q - 1);
             const int4* src = reinterpret_cast<const int4*>(tab + i * G.n_classes + SLLBM_CHK(cls, G.n_classes, G.status, SLLBM_DEV_BAD_REC));
             int4* dst = reinterpret_cast<int4*>(&r[u]);
 #pragma unroll
-            for (int k = 0; k < int(sizeof(TileRec<real>) / 16); ++k) dst[k] = __ldg(src + k);
+            for (int k = 0; k < int(sizeof(RowRec) / 16); ++k) dst[k] = __ldg(src + k);
         }
         V2 v[GV][NR];
 #pragma unroll
@@ -738,7 +739,9 @@ int launch_step_row_smem(const StepLaunch<real>& L) {
     const int rows = D == 3 ? L.G.N[1] * L.G.N[2] : L.G.N[1];
     const size_t smem = sizeof(real) * (2 * Q * NXB + 2 * 3 * 2 * NXB);
     cudaFuncSetAttribute(k_step_row_smem<VS, real, NXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    k_step_row_smem<VS, real, NXB><<<rows, NXB, smem, L.stream>>>(L.fg, L.fgo, L.tile, L.tw, L.G, *L.C);
+    static_assert(std::is_same<real, float>::value, "row records are FP32");
+    if (!L.row) return SLLBM_ERR_ARG;
+    k_step_row_smem<VS, real, NXB><<<rows, NXB, smem, L.stream>>>(L.fg, L.fgo, L.row, L.tw, L.G, *L.C);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 
