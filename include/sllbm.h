@@ -181,7 +181,7 @@ typedef struct sllbm_ctx sllbm_ctx;
  * trajectories that leave the domain) and allocates two population buffers.
  * Errors: SLLBM_ERR_ARG (bad descriptor), SLLBM_ERR_ARCH (not sm_103),
  * SLLBM_ERR_NOMEM, SLLBM_ERR_DP_NOT_FOUND (setup caps exceeded), SLLBM_ERR_CUDA.
- * On error *out is NULL and the message is available from sllbm_error_text(). */
+ * On error *out is NULL and the message is available from sllbm_last_error(NULL). */
 int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params* params,
                  sllbm_ctx** out);
 
@@ -285,9 +285,12 @@ int sllbm_conservation(sllbm_ctx* ctx, double* out);
  *   - Limit: one partial per 256 nodes, at most 26,211 blocks in 3D
  *     (6,710,016 nodes) and 32,764 blocks in 2D (8,387,584 nodes); larger
  *     meshes get SLLBM_ERR_ARG with the limit in sllbm_last_error().
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress)
+ *     with the context's device current, so a device reset between calls is
+ *     harmless.
+ *   - The call waits for the context's stream (it copies the sums and the
+ *     positivity flag to the host and synchronises), so it cannot be issued
+ *     while that stream is being captured into a CUDA graph.
  *   - Every call on a device shares the one array and leaves the last
  *     call's sums in it; the positivity flag is cleared at the start of each
  *     call.  Calls that overlap on the GPU (different streams or contexts of

@@ -777,7 +777,6 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
     real* S = reinterpret_cast<real*>(RB + NST * NR * NXB);            // [f, g][Q][NXB] streamed state
     real* XB = S + 2 * Q * NXB;                                        // [2][GV][f, g][NXB] row sums
     uint64_t* bars = reinterpret_cast<uint64_t*>(XB + 2 * GV * 2 * NXB);   // [NST] + 1 that nothing completes
-    __shared__ int abort_flag;
     const int N1 = G.N[1], N2 = D == 3 ? G.N[2] : 1;
     const int row = blockIdx.x;
     const int ky = row % N1;
@@ -829,7 +828,6 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
     };
     if (threadIdx.x == 0) {
         for (int s = 0; s <= NST; ++s) mbar_init(bar0 + 8u * uint32_t(s), 1);
-        abort_flag = 0;
     }
     __syncthreads();
     const long long lim = wait_limit(status);
@@ -838,6 +836,7 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
     real* Sf = S + threadIdx.x;
     real* Sg = S + Q * NXB + threadIdx.x;
     int grp = 0, waited = 0;
+    bool aborted = false;
 #pragma unroll 1
     for (int i0 = 0; i0 < Q; i0 += GV, ++grp) {
         TileRec<real> r[GV];                    // meta / dxp / dyzp and the weights (no node offsets)
@@ -861,7 +860,6 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
         // that nothing completes, so that the wait runs out whatever the timing
         if (lim < kWaitLimit) ok = mbar_wait(bar0 + 8u * uint32_t(NST), 0, lim) && ok;
         if (ok) waited = min(i0 + GV, Q);
-        else abort_flag = 1;
         real* xb = XB + (grp & 1) * (GV * 2 * NXB);
 #pragma unroll
         for (int u = 0; u < GV; ++u) {
@@ -876,8 +874,14 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
             xb[(2 * u) * NXB + threadIdx.x] = sf;
             xb[(2 * u + 1) * NXB + threadIdx.x] = sg;
         }
-        __syncthreads();
-        if (abort_flag) break;                  // block-uniform after the barrier
+        // block barrier and vote in one: every thread sees the same answer,
+        // so the break is block-uniform (a shared flag written before the
+        // barrier could be overwritten by a thread that is already a group
+        // ahead before a slower thread has read it)
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
         // the group's stages are free: refill them NST velocities ahead
         if (threadIdx.x < 32 && issued < Q) {
             const int ie = min(i0 + GV + NST, Q);
@@ -909,7 +913,7 @@ __global__ void __launch_bounds__(NXB, (VelSet<VS>::D == 3 ? 256 : 512) / NXB)
             Sg[i * NXB] = og;
         }
     }
-    if (abort_flag) {
+    if (aborted) {
         if (threadIdx.x == 0) {
             atomicOr(status, SLLBM_DEV_COPY_TIMEOUT);
             // wait (bounded, default limit) for the copies issued but not yet

@@ -1,5 +1,4 @@
 // Initialisation, state conversion, moment readout and FP64 conservation sums.
-#include <mutex>
 #include <string>
 
 #include "sllbm_internal.h"
@@ -329,8 +328,6 @@ __global__ void k_conserve_blocks(const typename Vec2<real>::T* __restrict__ fg,
 }
 
 namespace {
-std::mutex g_static_mu;
-void* g_static_ptr[64] = {};   // device address of g_static_scratch, per device ordinal
 
 template <typename real>
 int launch_conserve_blocks(int vs, const typename Vec2<real>::T* fg, int64_t N, const CollideConst<double>& C,
@@ -355,10 +352,6 @@ extern "C" int sllbm_conservation_static(sllbm_ctx* ctx, double* out) {
         return SLLBM_ERR_STATE;
     }
     const int dev = ctx->device;
-    if (dev < 0 || dev >= 64) {
-        ctx->last_error = "device ordinal out of range for the static scratch table";
-        return SLLBM_ERR_ARG;
-    }
     if (cudaSetDevice(dev) != cudaSuccess) {
         ctx->last_error = "cudaSetDevice failed";
         return SLLBM_ERR_CUDA;
@@ -372,20 +365,18 @@ extern "C" int sllbm_conservation_static(sllbm_ctx* ctx, double* out) {
                           " nodes for D = " + std::to_string(D) + " (this mesh has " + std::to_string(N) + ")";
         return SLLBM_ERR_ARG;
     }
-    // first call on this device: look up the device address of the array
+    // the device address of the array, looked up on every call with the
+    // context's device current: a cached address would go stale if the
+    // caller reset the device (the module, and the array, are then reloaded)
     double* base = nullptr;
     {
-        std::lock_guard<std::mutex> lk(g_static_mu);
-        if (!g_static_ptr[dev]) {
-            void* p = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-            if (e != cudaSuccess || !p) {
-                ctx->last_error = std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
-                return SLLBM_ERR_CUDA;
-            }
-            g_static_ptr[dev] = p;
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            ctx->last_error = std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+            return SLLBM_ERR_CUDA;
         }
-        base = static_cast<double*>(g_static_ptr[dev]);
+        base = static_cast<double*>(p);
     }
     int* flag = reinterpret_cast<int*>(base);
     double* sums = base + 8;

@@ -1,7 +1,8 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
 
 Tolerances: FP64 setup quantities (node coordinates, departure points, the
-velocity set) 1e-12; FP64 populations 1e-12 relative to each velocity's
+velocity set, the reference coordinates of every departure point that is
+neither on a cell face nor a clamped boundary point) 1e-12; FP64 populations 1e-12 relative to each velocity's
 scale; FP32-offset populations 1e-5 relative (same scale), moments 1e-5.
 """
 import numpy as np
@@ -145,7 +146,8 @@ def test_setup_matches_oracle(built_lib, name):
     inner = (kind != REC_EQ) & (np.abs(rec["xi"]).max(axis=2) < 1 - 1e-9)
     inner &= ~clamped | (np.abs(rec["xi"]).max(axis=2) < 1 - 1e-6)
     assert (r["cell"][inner] == rec["cell"][inner]).all()
-    assert np.abs(r["xi"][inner] - rec["xi"][inner]).max() < 1e-10
+    # FP64 Newton inversion: reference coordinates to 1e-12 (they are O(1))
+    assert np.abs(r["xi"][inner] - rec["xi"][inner]).max() < 1e-12
     print(f"PARITY setup {name}: source points {np.abs(d).max() / max(1.0, scale):.2e} (relative), "
           f"reference coordinates {np.abs(r['xi'][inner] - rec['xi'][inner]).max():.2e}, "
           f"clamped records {int(clamped.sum())}")
