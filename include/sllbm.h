@@ -119,6 +119,13 @@ extern "C" {
                                        staged in shared memory by the bulk-copy (TMA) engine, six
                                        velocities ahead, instead of loaded by every thread; other
                                        meshes run the SLLBM_STREAM_STRUCTURED kernels             */
+#define SLLBM_STREAM_ROWS_TMEM   7  /* as SLLBM_STREAM_STRUCTURED, but where the mesh allows it
+                                       (FP32, p = 2, D3Q45 rows of 32, 64 or 128 nodes or D2Q19
+                                       rows of 32..256, periodic x and z, x taps within two
+                                       nodes) a persistent kernel takes tiles of 512 nodes (whole
+                                       x rows), keeps each node's 2Q streamed values in tensor
+                                       memory and stages every source row a tile reads once in
+                                       shared memory with the bulk-copy (TMA) engine            */
 
 /* ------------------------------------------------------------------ descriptors */
 typedef struct {

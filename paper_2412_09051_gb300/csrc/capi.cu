@@ -88,6 +88,11 @@ int launch_plane_cp(const double* rho, const double* T, int N0, int N1, int N2, 
                     double* out, cudaStream_t s);
 void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
                         std::vector<double>& P);
+bool rows_tmem_shape(int D, int nx, int& ty, int& tz);
+size_t rows_tmem_smem_bytes(int D, int nx, const TmGeom& T);
+int launch_rows_tmem(int vs, int nx, const float2* fg, float2* fgo, const int32_t* head, const TmRec* recs,
+                     const uint64_t* xmask, const float* tw, const StepGeom& G, const CollideConst<float>& C,
+                     const TmGeom& T, int* status, cudaStream_t s, int grid);
 void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
                         std::vector<double>& P, std::vector<int>* degree);
 }  // namespace sllbm
@@ -333,11 +338,163 @@ bool row_uniform_table(const sllbm_ctx* c, const std::vector<TileRec<real>>& t) 
     return true;
 }
 
+// Tables of the tensor-memory row-tile kernel (step_tmem.cuh) from the warp
+// tile records: tiles of TY x TZ whole x rows.  Per (velocity, tile class):
+// the source rows that the (y, z) taps of the tile's rows read -- taps of
+// zero weight dropped (a velocity with no motion along an axis interpolates
+// at a node: one tap there) -- as runs of consecutive y rows per (population,
+// z), each run one contiguous block of memory (one bulk copy; rows between
+// two needed ones are copied too); per (row, x parity) the record with the
+// taps' row slots in the stage; per tile class the velocities whose x factor
+// is not the identity.  Returns false (tables not built) where the kernel
+// does not apply.
+bool build_rows_tmem(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::vector<int32_t>& head,
+                     std::vector<TmRec>& recs, std::vector<uint64_t>& xmask) {
+    const HostMesh& m = c->mesh;
+    const StepGeom& G = c->geom;
+    const int Q = c->vs.Q, D = m.D, NX = m.N[0], N1 = m.N[1], N2 = D == 3 ? m.N[2] : 1;
+    int TY = 0, TZ = 0;
+    if (c->precision != SLLBM_FP32 || m.p != 2 || !c->tiled || !c->row_uniform) return false;
+    if (!((c->velset == SLLBM_D3Q45 && D == 3) || (c->velset == SLLBM_D2Q19 && D == 2))) return false;
+    if (!rows_tmem_shape(D, NX, TY, TZ) || G.ncls[0] != 2 || !m.periodic[0]) return false;
+    const bool py = m.periodic[1] != 0;
+    if (py && N1 % TY) return false;
+    if (D == 3 && (!m.periodic[2] || N2 % TZ)) return false;
+    if (int64_t(Q) * m.n_nodes >= (int64_t(1) << 31)) return false;
+    const int NR = TY * TZ;
+    TmGeom T{};
+    T.ntile_y = (N1 + TY - 1) / TY;
+    T.ntile_z = D == 3 ? N2 / TZ : 1;
+    T.ntiles = T.ntile_y * T.ntile_z;
+    T.n_tc = py ? 1 : T.ntile_y;
+    head.assign(size_t(Q) * T.n_tc * TM_HEAD, 0);
+    recs.assign(size_t(Q) * T.n_tc * NR * 2, TmRec{});
+    xmask.assign(size_t(T.n_tc), 0);
+    const int NRT = D == 3 ? 9 : 3;
+    int max_rows = 1;
+    struct Tap {
+        int src, dy, dz;
+        float w;
+    };
+    for (int i = 0; i < Q; ++i)
+        for (int tc = 0; tc < T.n_tc; ++tc) {
+            const int y0 = py ? 0 : tc * TY;
+            int32_t* h = &head[(size_t(i) * T.n_tc + tc) * TM_HEAD];
+            std::vector<std::vector<Tap>> taps(NR);     // per row of the tile
+            std::vector<int> cls0(NR, -1);
+            for (int r = 0; r < NR; ++r) {
+                const int ry = r % TY, rz = r / TY;
+                const int y = y0 + ry, z = rz;
+                if (y >= N1) continue;                   // beyond a ragged last tile: an idle row
+                cls0[r] = G.ncls[0] * ((py ? (y & 1) : y) + G.ncls[1] * (D == 3 ? (z & 1) : 0));
+                const TileRec<float>& a = t[size_t(i) * G.n_classes + cls0[r]];
+                if ((a.meta & 15) == REC_EQ) continue;
+                for (int k = 0; k < NRT; ++k) {
+                    const float wk = a.rw[k];
+                    if (std::fabs(wk) < 1e-12f) continue;
+                    const int dy = ((a.dyzp >> (4 * (k % 3))) & 15) - 8;
+                    const int dz = D == 3 ? ((a.dyzp >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+                    taps[r].push_back({a.meta >> 8, ry + dy, rz + dz, wk});
+                }
+            }
+            // runs: per (population, z) the y range from the lowest to the highest row read
+            struct Run {
+                int src, dz, ylo, yhi, slot;
+            };
+            std::vector<Run> runs;
+            for (int r = 0; r < NR; ++r)
+                for (const Tap& tp : taps[r]) {
+                    bool found = false;
+                    for (Run& u : runs)
+                        if (u.src == tp.src && u.dz == tp.dz) {
+                            u.ylo = std::min(u.ylo, tp.dy);
+                            u.yhi = std::max(u.yhi, tp.dy);
+                            found = true;
+                        }
+                    if (!found) runs.push_back({tp.src, tp.dz, tp.dy, tp.dy, 0});
+                }
+            if (int(runs.size()) > TM_MAX_RUNS) return false;
+            int nrows = 0;
+            for (size_t q = 0; q < runs.size(); ++q) {
+                Run& u = runs[q];
+                if (u.ylo + 128 < 0 || u.yhi + 128 > 255 || u.dz + 128 < 0 || u.dz + 128 > 255 ||
+                    u.yhi - u.ylo + 1 > 63)
+                    return false;
+                u.slot = nrows;
+                nrows += u.yhi - u.ylo + 1;
+                h[2 + q] = tm_pack_run(u.src, u.ylo, u.dz, u.yhi - u.ylo + 1);
+                h[2 + TM_MAX_RUNS + q] = u.slot;
+            }
+            if (nrows > TM_MAX_ROWS) return false;
+            h[0] = int(runs.size());
+            h[1] = nrows;
+            max_rows = std::max(max_rows, nrows);
+            bool xchg = false;
+            for (int r = 0; r < NR; ++r) {
+                TmRec* o = &recs[((size_t(i) * T.n_tc + tc) * NR + r) * 2];
+                if (cls0[r] < 0) {
+                    for (int xp = 0; xp < 2; ++xp) o[xp].meta = REC_EQ;
+                    continue;
+                }
+                const TileRec<float>& a = t[size_t(i) * G.n_classes + cls0[r]];
+                const int kind = a.meta & 15;
+                for (int xp = 0; xp < 2; ++xp) {
+                    const TileRec<float>& b = t[size_t(i) * G.n_classes + cls0[r] + xp];
+                    if (b.meta != a.meta) return false;
+                    TmRec& ro = o[xp];
+                    ro.meta = b.meta;
+                    ro.ntap = int(taps[r].size());
+                    if (kind == REC_EQ) continue;
+                    const int dx0 = (b.dxp & 15) - 8;
+                    for (int q = 0; q < 3; ++q)
+                        if (((b.dxp >> (4 * q)) & 15) - 8 != dx0 + q) return false;
+                    if (dx0 < -2 || dx0 > 0) return false;
+                    ro.dx0 = dx0;
+                    for (int q = 0; q < 3; ++q) ro.wx[q] = b.wx[q];
+                    for (size_t q = 0; q < taps[r].size(); ++q) {
+                        const Tap& tp = taps[r][q];
+                        int sl = -1;
+                        for (const Run& u : runs)
+                            if (u.src == tp.src && u.dz == tp.dz) sl = u.slot + tp.dy - u.ylo;
+                        ro.off[q] = sl * NX * 8;
+                        ro.w[q] = tp.w;
+                    }
+                    // the identity x factor: weight one at the node itself
+                    bool ident = true;
+                    for (int q = 0; q < 3; ++q) {
+                        const double target = (dx0 + q == 0) ? 1.0 : 0.0;
+                        if (std::fabs(double(b.wx[q]) - target) > 1e-12) ident = false;
+                    }
+                    if (!ident) xchg = true;
+                }
+            }
+            if (xchg) xmask[tc] |= uint64_t(1) << i;
+        }
+    T.rows_bytes = max_rows * NX * 8;
+    T.stage_bytes = T.rows_bytes + NR * 2 * int(sizeof(TmRec));
+    const size_t fixed = sizeof(float2) * 2 * NR * (NX + 4) + 16;
+    const size_t budget = 227 * 1024;
+    int nst = int((budget - fixed) / (size_t(T.stage_bytes) + 16));
+    nst = std::min(nst, 16) & ~1;         // a multiple of the two producer warps
+    if (nst < 2) return false;
+    T.nst = nst;
+    c->tm = T;
+    c->tm_ty = TY;
+    c->tm_tz = TZ;
+    return true;
+}
+
 template <typename real>
 int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const int vs = ctx->velset, p = ctx->mesh.p;
     const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_SMEM;
     if constexpr (std::is_same<real, float>::value) {
+        if (st && ctx->rows_tmem && ctx->want_tmem) {
+            ctx->step_kernel = "k_step_rows_tmem";
+            return launch_rows_tmem(vs, ctx->mesh.N[0], L.fg, L.fgo, ctx->tm_head,
+                                    static_cast<const TmRec*>(ctx->tm_recs), ctx->tm_xmask, L.tw, L.G, *L.C,
+                                    ctx->tm, ctx->d_status, L.stream, ctx->tm_grid);
+        }
         // a periodic row that fits one block exactly: one block per row, where
         // the block's shared memory still lets 16 warps reside per SM (D3Q45
         // rows of 192 nodes take 78 KB per block: 12 warps, slower than the
@@ -600,7 +757,7 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->row_tab, ctx->d_red, ctx->d_flag,
                     ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status,
-                    ctx->d_plane, ctx->d_cp, ctx->d_plane_acc};
+                    ctx->d_plane, ctx->d_cp, ctx->d_plane_acc, ctx->tm_head, ctx->tm_recs, ctx->tm_xmask};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -667,6 +824,10 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
     if (mode == SLLBM_STREAM_AUTO) mode = axis ? SLLBM_STREAM_STRUCTURED : SLLBM_STREAM_GATHER;
     if (mode == SLLBM_STREAM_ROW_COPY) {
         ctx->row_copy = true;
+        mode = SLLBM_STREAM_STRUCTURED;
+    }
+    if (mode == SLLBM_STREAM_ROWS_TMEM) {
+        ctx->want_tmem = true;
         mode = SLLBM_STREAM_STRUCTURED;
     }
     if ((mode == SLLBM_STREAM_STRUCTURED || mode == SLLBM_STREAM_STRUCTURED_NODE || mode == SLLBM_STREAM_TILED_REG) &&
@@ -866,6 +1027,25 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
                     CK(cudaMalloc(&ctx->row_tab, sizeof(RowRec) * rr.size()));
                     CK(cudaMemcpyAsync(ctx->row_tab, rr.data(), sizeof(RowRec) * rr.size(), cudaMemcpyHostToDevice, s));
                     CK(cudaStreamSynchronize(s));
+                    std::vector<int32_t> th;
+                    std::vector<TmRec> tr;
+                    std::vector<uint64_t> tx;
+                    if (ctx->want_tmem && build_rows_tmem(ctx, t, th, tr, tx)) {
+                        CK(cudaMalloc(&ctx->tm_head, sizeof(int32_t) * th.size()));
+                        CK(cudaMalloc(&ctx->tm_recs, sizeof(TmRec) * tr.size()));
+                        CK(cudaMalloc(&ctx->tm_xmask, sizeof(uint64_t) * tx.size()));
+                        CK(cudaMemcpyAsync(ctx->tm_head, th.data(), sizeof(int32_t) * th.size(),
+                                           cudaMemcpyHostToDevice, s));
+                        CK(cudaMemcpyAsync(ctx->tm_recs, tr.data(), sizeof(TmRec) * tr.size(),
+                                           cudaMemcpyHostToDevice, s));
+                        CK(cudaMemcpyAsync(ctx->tm_xmask, tx.data(), sizeof(uint64_t) * tx.size(),
+                                           cudaMemcpyHostToDevice, s));
+                        CK(cudaStreamSynchronize(s));
+                        int sms = 0;
+                        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+                        ctx->tm_grid = std::min(ctx->tm.ntiles, sms);
+                        ctx->rows_tmem = true;
+                    }
                     CK(cudaMalloc(&ctx->tile_tab, sizeof(TileRec<float>) * t.size()));
                     CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(TileRec<float>) * t.size(),
                                        cudaMemcpyHostToDevice, s));
@@ -925,7 +1105,8 @@ int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
     o->stream_mode = ((ctx->mode == SLLBM_STREAM_STRUCTURED || ctx->mode == SLLBM_STREAM_TILED_REG) && !ctx->tiled &&
                       !ctx->tiled_p)
                          ? SLLBM_STREAM_STRUCTURED_NODE
-                         : (ctx->row_copy ? SLLBM_STREAM_ROW_COPY : ctx->mode);
+                         : (ctx->row_copy ? SLLBM_STREAM_ROW_COPY
+                                          : (ctx->want_tmem && ctx->rows_tmem ? SLLBM_STREAM_ROWS_TMEM : ctx->mode));
     o->state_bytes = int64_t(2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q);
     o->table_bytes = ctx->table_bytes;
     o->n_records = int64_t(ctx->mesh.n_nodes) * ctx->vs.Q;

@@ -106,6 +106,39 @@ struct alignas(16) TileRecP {  // warp-tiled record of order P (per velocity and
     real wx[P + 1], wy[P + 1], wz[P + 1];   // 1D Lagrange weights
 };
 
+// per (velocity, tile class, row of the tile, x parity): the streaming record
+// of the rows' arrival nodes (96 bytes, staged with the source rows)
+struct alignas(16) TmRec {
+    int32_t meta;       // kind | bid << 4 | src << 8
+    int32_t ntap;       // number of (y, z) taps (0 for equilibrium records)
+    int32_t dx0;        // offset of the first of the three consecutive x taps (-2 .. 0)
+    float wx[3];        // x weights
+    int32_t off[9];     // byte offsets of the taps' source rows within the stage
+    float w[9];         // (y, z) weight products
+};
+static_assert(sizeof(TmRec) == 96, "six 16-byte loads per record");
+
+constexpr int TM_HEAD = 66;          // ints per (velocity, tile class) copy list: runs, rows, 32 runs, their first slots
+constexpr int TM_MAX_RUNS = 32;
+constexpr int TM_MAX_ROWS = 64;      // rows per stage
+constexpr int TM_COLS = 96;          // tensor-memory columns per warp (2 Q <= 96)
+constexpr int TM_ALLOC = 512;        // columns allocated per CTA (one CTA per SM)
+
+struct TmGeom {
+    int ntile_y, ntile_z, ntiles;    // tiles along y, along z, total
+    int n_tc;                        // tile classes (y tiles on a non-periodic y axis, else 1)
+    int nst;                         // pipeline stages
+    int rows_bytes;                  // bytes of source rows per stage (max rows x NX x 8)
+    int stage_bytes;                 // rows_bytes + the tile's records
+};
+
+// one entry of a copy list: a run of `len` consecutive y rows (contiguous in
+// memory) of one source population at one z, starting at y and z relative to
+// the tile origin
+inline constexpr int32_t tm_pack_run(int src, int dy, int dz, int len) {
+    return src | ((dy + 128) << 6) | ((dz + 128) << 14) | (len << 22);
+}
+
 struct StepGeom {             // structured / gather kernel geometry
     int N[3], cells[3], periodic[3];
     int ncls[3];              // classes per dimension (p if periodic, else N)
@@ -134,6 +167,13 @@ struct sllbm_ctx {
     bool row_copy = false;               // SLLBM_STREAM_ROW_COPY requested
     bool row_uniform = false;            // both x parities share each velocity's y/z stencil
     int tiled_p = 0;                     // order of the warp-tiled order-P table (4), 0: none
+    bool want_tmem = false;              // SLLBM_STREAM_ROWS_TMEM requested
+    bool rows_tmem = false;              // tables of the tensor-memory row-tile kernel built
+    int tm_ty = 0, tm_tz = 0, tm_grid = 0;   // its tile shape (rows along y, z) and grid
+    sllbm::TmGeom tm{};
+    int32_t* tm_head = nullptr;          // copy lists [Q][n_tc][TM_HEAD]
+    void* tm_recs = nullptr;             // TmRec [Q][n_tc][TY TZ][2]
+    uint64_t* tm_xmask = nullptr;        // [n_tc]: velocities whose x factor needs the row exchange
     const char* step_kernel = "";        // kernel of the last step launched (sllbm_info)
     int precision = SLLBM_FP32;
     // device geometry
