@@ -125,7 +125,12 @@ extern "C" {
                                        nodes) a persistent kernel takes tiles of 512 nodes (whole
                                        x rows), keeps each node's 2Q streamed values in tensor
                                        memory and stages every source row a tile reads once in
-                                       shared memory with the bulk-copy (TMA) engine            */
+                                       shared memory with the bulk-copy (TMA) engine.  With
+                                       D3Q45, SLLBM_STREAM_AUTO and SLLBM_STREAM_STRUCTURED use
+                                       this kernel wherever it applies                           */
+#define SLLBM_STREAM_ROW_SMEM    8  /* as SLLBM_STREAM_STRUCTURED without the tensor-memory
+                                       row-tile kernel (the one-block-per-row and warp-tiled
+                                       kernels): for comparisons                                 */
 
 /* ------------------------------------------------------------------ descriptors */
 typedef struct {

@@ -489,7 +489,7 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const int vs = ctx->velset, p = ctx->mesh.p;
     const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_SMEM;
     if constexpr (std::is_same<real, float>::value) {
-        if (st && ctx->rows_tmem && ctx->want_tmem) {
+        if (st && ctx->rows_tmem && !ctx->row_copy) {
             ctx->step_kernel = "k_step_rows_tmem";
             return launch_rows_tmem(vs, ctx->mesh.N[0], L.fg, L.fgo, ctx->tm_head,
                                     static_cast<const TmRec*>(ctx->tm_recs), ctx->tm_xmask, L.tw, L.G, *L.C,
@@ -826,10 +826,13 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
         ctx->row_copy = true;
         mode = SLLBM_STREAM_STRUCTURED;
     }
-    if (mode == SLLBM_STREAM_ROWS_TMEM) {
+    // the row-tile kernel with the node state in tensor memory: requested
+    // explicitly, or by default for the 45-velocity set on structured meshes
+    // (faster there; the one-block-per-row kernel stays the default in 2D)
+    if (mode == SLLBM_STREAM_ROWS_TMEM ||
+        ((mode == SLLBM_STREAM_AUTO || mode == SLLBM_STREAM_STRUCTURED) && velset == SLLBM_D3Q45))
         ctx->want_tmem = true;
-        mode = SLLBM_STREAM_STRUCTURED;
-    }
+    if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_ROW_SMEM) mode = SLLBM_STREAM_STRUCTURED;
     if ((mode == SLLBM_STREAM_STRUCTURED || mode == SLLBM_STREAM_STRUCTURED_NODE || mode == SLLBM_STREAM_TILED_REG) &&
         !axis) {
         ctx->last_error = "structured streaming needs axis-aligned cells";
@@ -1106,7 +1109,7 @@ int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
                       !ctx->tiled_p)
                          ? SLLBM_STREAM_STRUCTURED_NODE
                          : (ctx->row_copy ? SLLBM_STREAM_ROW_COPY
-                                          : (ctx->want_tmem && ctx->rows_tmem ? SLLBM_STREAM_ROWS_TMEM : ctx->mode));
+                                          : (ctx->rows_tmem ? SLLBM_STREAM_ROWS_TMEM : ctx->mode));
     o->state_bytes = int64_t(2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q);
     o->table_bytes = ctx->table_bytes;
     o->n_records = int64_t(ctx->mesh.n_nodes) * ctx->vs.Q;

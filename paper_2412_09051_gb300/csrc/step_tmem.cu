@@ -23,7 +23,7 @@ size_t rows_tmem_smem_bytes(int D, int nx, const TmGeom& T) {
     int ty = 0, tz = 0;
     if (!rows_tmem_shape(D, nx, ty, tz)) return 0;
     const size_t b = size_t(T.nst) * T.stage_bytes + sizeof(float2) * 2 * ty * tz * (nx + 4) +
-                     sizeof(uint64_t) * 2 * T.nst + 16;
+                     sizeof(uint64_t) * (2 * T.nst + 1) + 16;
     return b < 120 * 1024 ? 120 * 1024 : b;
 }
 

@@ -275,8 +275,10 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     unsigned char* stages = dyn_smem;                                         // [nst][rows | records]
     float2* XB = reinterpret_cast<float2*>(stages + size_t(T.nst) * T.stage_bytes);   // [2][NR][XBW]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(XB + 2 * NR * XBW);          // full[nst], empty[nst]
-    uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * T.nst);           // TMEM base, abort flag
+    uint64_t* bars = reinterpret_cast<uint64_t*>(XB + 2 * NR * XBW);
+    // full[nst], empty[nst], and one barrier that nothing completes (waited
+    // on only under a test wait limit, so that the timeout path runs)
+    uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * T.nst + 1);       // TMEM base, abort flag
     volatile int* abort_flag = reinterpret_cast<volatile int*>(slot + 1);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -291,6 +293,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             mbar_init(full0 + 8u * uint32_t(s), 1);
             mbar_init(empty0 + 8u * uint32_t(s), NW);
         }
+        mbar_init(full0 + 16u * uint32_t(T.nst), 1);
         *abort_flag = 0;
     }
     if (warp == 0) {
@@ -433,7 +436,12 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
 #pragma unroll 1
             for (int i = 0; i < Q; ++i) {
                 const uint32_t fb = full0 + 8u * uint32_t(s);
-                if (!*abort_flag && !mbar_wait(fb, uint32_t(ph), lim)) {
+                // under a test wait limit the first velocity also waits on the
+                // barrier that nothing completes, so that the wait runs out
+                // whatever the timing (sllbm_debug_wait_limit)
+                if (!*abort_flag && (!mbar_wait(fb, uint32_t(ph), lim) ||
+                                     (lim < kWaitLimit && i == 0 &&
+                                      !mbar_wait(full0 + 16u * uint32_t(T.nst), 0, lim)))) {
                     atomicOr(status, SLLBM_DEV_COPY_TIMEOUT);
                     *abort_flag = 1;
                 }

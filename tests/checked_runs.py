@@ -35,6 +35,10 @@ def cases():
         cfg = box_cfg(cells=cells, p=2, L=(1.0,) * len(cells), dt=0.01, velset=velset)
         for prec in ("fp32", "fp64"):
             out.append((f"box_{velset}_{'x'.join(map(str, cells))}_{prec}", cfg, prec, 0, None))
+    # the tensor-memory row-tile kernel on each tile shape
+    from tests.test_gpu_rows_tmem import CASES as TM_CASES
+    for name, mk in TM_CASES.items():
+        out.append((f"rows_tmem_{name}_m7", mk(), "fp32", 7, None))
     learned = get_config("learned", cells=8)
     learned["init"] = dict(kind="isentropic_vortex", mach=0.6, seed=3)
     for path in ("tensor", "simt"):

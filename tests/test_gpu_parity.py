@@ -155,13 +155,14 @@ def test_setup_matches_oracle(built_lib, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5, 6])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5, 6, 7])
 def test_steps_match_oracle(built_lib, name, mode):
     """Every streaming mode (0 auto: warp-tiled with shared-memory state where
     eligible, 1 gather with register state, 3 one thread per node with
     class records, 4 warp-tiled with register state, 5 gather with
     shared-memory state, 6 rows staged by the bulk-copy engine where a
-    periodic row fits one block) against the oracle."""
+    periodic row fits one block, 7 tiles of rows with the node state in
+    tensor memory where eligible) against the oracle."""
     cfg, prec, mesh, xi, w, opp, par, rec = _oracle(name)
     if mode not in (0, 5) and mesh.kind == 3:
         pytest.skip("curved mesh runs the gather modes (0 = 1)")
@@ -191,6 +192,8 @@ def test_steps_match_oracle(built_lib, name, mode):
         assert kern == "k_step_row_smem"                 # one block per 32-node row
     if "row32" in name and mode == 6:
         assert kern == "k_step_row_copy"                 # the same rows staged by bulk copies
+    if name == "box_row32_d2q19_fp32" and mode == 7:
+        assert kern == "k_step_rows_tmem"                # 16 rows of 32 nodes per tile
     print(f"PARITY step {name} mode {sim.info.stream_mode} ({kern}): populations {worst:.2e} moments {em:.2e}")
     sim.close()
 

@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 MODE = 7
 
 CASES = {
-    "channel_nx128": lambda: get_config("channel", cells=(64, 3, 1)),      # 128 x 7 x 2 nodes, ragged y tile
+    "channel_nx128": lambda: get_config("channel", cells=(64, 3, 3)),      # 128 x 7 x 6 nodes, ragged y tile
     "channel_nx64": lambda: get_config("channel", cells=(32, 3, 2)),       # 64 x 7 x 4
     "channel_nx32": lambda: get_config("channel", cells=(16, 4, 4)),       # 32 x 9 x 8, tiles of 4 x 4 rows
     "mixing_nx64": lambda: get_config("mixing", cells=(32, 4, 2)),         # equilibrium boundaries in y
@@ -69,7 +69,7 @@ def test_rows_tmem_agrees_with_row_kernel(built_lib):
     kernel: the same step up to FP32 summation order."""
     from paper_2412_09051_gb300.sim import Sim
     cfg = get_config("channel", cells=(64, 6, 4))
-    a, b = Sim(cfg, stream_mode=MODE), Sim(cfg, stream_mode=2)
+    a, b = Sim(cfg, stream_mode=MODE), Sim(cfg, stream_mode=8)
     X = a.node_coords()
     rho, u, T = initial_fields(cfg, X)
     for s in (a, b):
@@ -84,6 +84,20 @@ def test_rows_tmem_agrees_with_row_kernel(built_lib):
     print(f"PARITY rows_tmem vs row_smem, 5 channel steps: {max(ef, eg):.2e}")
     a.close()
     b.close()
+
+
+def test_rows_tmem_is_the_default_for_d3q45(built_lib):
+    """With the 45-velocity set, the automatic and the structured modes take
+    the row-tile kernel where it applies; SLLBM_STREAM_ROW_SMEM does not."""
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = get_config("channel", cells=(32, 3, 3))
+    for mode, kernel in ((0, "k_step_rows_tmem"), (2, "k_step_rows_tmem"), (8, "k_step_row_smem")):
+        s = Sim(cfg, stream_mode=mode)
+        s.init_state(*initial_fields(cfg, s.node_coords()))
+        s.step(1)
+        assert s.step_kernel() == kernel, (mode, s.step_kernel())
+        assert s.info.stream_mode == (MODE if kernel == "k_step_rows_tmem" else 2)
+        s.close()
 
 
 def test_rows_tmem_fullsize_channel_sampled(built_lib):
