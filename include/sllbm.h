@@ -131,6 +131,16 @@ extern "C" {
 #define SLLBM_STREAM_ROW_SMEM    8  /* as SLLBM_STREAM_STRUCTURED without the tensor-memory
                                        row-tile kernel (the one-block-per-row and warp-tiled
                                        kernels): for comparisons                                 */
+#define SLLBM_STREAM_TENSOR      9  /* the SLLBM_STREAM_ROWS_TMEM kernel with the (y, z) part of
+                                       the streaming on the tensor cores: per velocity and tile
+                                       the product of the staged source rows (128 x-nodes x the
+                                       velocity's rows, f and g separately) with the tile's
+                                       interpolation weights (its rows x 4 tile rows), tcgen05
+                                       kind::tf32 with both operands split into TF32 hi and lo
+                                       parts (hi hi + hi lo + lo hi: FP32 accuracy), FP32
+                                       accumulators in tensor memory; D3Q45 rows of 128 nodes only
+                                       (elsewhere as SLLBM_STREAM_ROWS_TMEM), opt-in: slower than
+                                       the CUDA-core contraction                                 */
 
 /* ------------------------------------------------------------------ descriptors */
 typedef struct {

@@ -90,9 +90,9 @@ void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vec
                         std::vector<double>& P);
 bool rows_tmem_shape(int D, int nx, int& ty, int& tz);
 size_t rows_tmem_smem_bytes(int D, int nx, const TmGeom& T);
-int launch_rows_tmem(int vs, int nx, const float2* fg, float2* fgo, const int32_t* head, const TmRec* recs,
-                     const uint64_t* xmask, const float* tw, const StepGeom& G, const CollideConst<float>& C,
-                     const TmGeom& T, int* status, cudaStream_t s, int grid);
+int launch_rows_tmem(int vs, int nx, const float2* fg, float2* fgo, const float* bop, const int32_t* head,
+                     const TmRec* recs, const uint64_t* xmask, const float* tw, const StepGeom& G,
+                     const CollideConst<float>& C, const TmGeom& T, int* status, cudaStream_t s, int grid);
 void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
                         std::vector<double>& P, std::vector<int>* degree);
 }  // namespace sllbm
@@ -348,8 +348,26 @@ bool row_uniform_table(const sllbm_ctx* c, const std::vector<TileRec<real>>& t) 
 // taps' row slots in the stage; per tile class the velocities whose x factor
 // is not the identity.  Returns false (tables not built) where the kernel
 // does not apply.
+// FP32 rounded to TF32 (10 mantissa bits, nearest, ties away from zero: the
+// device's cvt.rna.tf32.f32)
+float tf32_rna(float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    float o;
+    std::memcpy(&o, &u, 4);
+    return o;
+}
+
+// byte offset of element (r, k) of an R x K FP32/TF32 operand in the
+// canonical K-major layout without swizzle: 8 x 16-byte core matrices, 128 B
+// apart along K and K * 32 B apart along R (K a multiple of 4)
+inline int tf32_canon_offset(int r, int k, int K) {
+    return (r >> 3) * (K * 32) + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
 bool build_rows_tmem(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::vector<int32_t>& head,
-                     std::vector<TmRec>& recs, std::vector<uint64_t>& xmask) {
+                     std::vector<TmRec>& recs, std::vector<uint64_t>& xmask, std::vector<float>& bop) {
     const HostMesh& m = c->mesh;
     const StepGeom& G = c->geom;
     const int Q = c->vs.Q, D = m.D, NX = m.N[0], N1 = m.N[1], N2 = D == 3 ? m.N[2] : 1;
@@ -472,7 +490,36 @@ bool build_rows_tmem(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::ve
         }
     T.rows_bytes = max_rows * NX * 8;
     T.stage_bytes = T.rows_bytes + NR * 2 * int(sizeof(TmRec));
-    const size_t fixed = sizeof(float2) * 2 * NR * (NX + 4) + 16;
+    size_t fixed = sizeof(float2) * 2 * NR * (NX + 4) + 16;
+    if (c->want_tc) {
+        // tensor-core variant (128-node rows, tiles of 4 rows): per (velocity,
+        // tile class) the weights of the (y, z) contraction as the product's
+        // B operand, N = 16 (rows of the tile, zero padded) x K = kp (the
+        // velocity's source rows, zero padded), split into TF32 hi and lo
+        // parts, in the canonical K-major layout
+        if (NX != 128 || NR > 16) return false;
+        const int kp = (max_rows + 7) / 8 * 8;
+        T.kp = kp;
+        bop.assign(size_t(Q) * T.n_tc * 2 * 16 * kp, 0.f);
+        for (int i = 0; i < Q; ++i)
+            for (int tc = 0; tc < T.n_tc; ++tc) {
+                float* hi = &bop[(size_t(i) * T.n_tc + tc) * 2 * 16 * kp];
+                float* lo = hi + 16 * kp;
+                for (int r = 0; r < NR; ++r)
+                    for (int xp = 0; xp < 1; ++xp) {
+                        const TmRec& ro = recs[((size_t(i) * T.n_tc + tc) * NR + r) * 2 + xp];
+                        if ((ro.meta & 15) == REC_EQ) continue;
+                        for (int q = 0; q < ro.ntap; ++q) {
+                            const int k = ro.off[q] / (NX * 8);
+                            const float h = tf32_rna(ro.w[q]);
+                            hi[tf32_canon_offset(r, k, kp) / 4] = h;
+                            lo[tf32_canon_offset(r, k, kp) / 4] = tf32_rna(ro.w[q] - h);
+                        }
+                    }
+            }
+        T.stage_bytes += 2 * 16 * kp * 4;
+        fixed += 4 * size_t(NX) * kp * 4 + 1024 + 8;       // the A operands (f, g x hi, lo), alignment, barrier
+    }
     const size_t budget = 227 * 1024;
     int nst = int((budget - fixed) / (size_t(T.stage_bytes) + 16));
     nst = std::min(nst, 16) & ~1;         // a multiple of the two producer warps
@@ -490,8 +537,8 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_SMEM;
     if constexpr (std::is_same<real, float>::value) {
         if (st && ctx->rows_tmem && !ctx->row_copy) {
-            ctx->step_kernel = "k_step_rows_tmem";
-            return launch_rows_tmem(vs, ctx->mesh.N[0], L.fg, L.fgo, ctx->tm_head,
+            ctx->step_kernel = ctx->tm.kp ? "k_step_rows_tmem_tc" : "k_step_rows_tmem";
+            return launch_rows_tmem(vs, ctx->mesh.N[0], L.fg, L.fgo, ctx->tm_bop, ctx->tm_head,
                                     static_cast<const TmRec*>(ctx->tm_recs), ctx->tm_xmask, L.tw, L.G, *L.C,
                                     ctx->tm, ctx->d_status, L.stream, ctx->tm_grid);
         }
@@ -757,7 +804,8 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->row_tab, ctx->d_red, ctx->d_flag,
                     ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status,
-                    ctx->d_plane, ctx->d_cp, ctx->d_plane_acc, ctx->tm_head, ctx->tm_recs, ctx->tm_xmask};
+                    ctx->d_plane, ctx->d_cp, ctx->d_plane_acc, ctx->tm_head, ctx->tm_recs, ctx->tm_xmask,
+                    ctx->tm_bop};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -829,10 +877,12 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
     // the row-tile kernel with the node state in tensor memory: requested
     // explicitly, or by default for the 45-velocity set on structured meshes
     // (faster there; the one-block-per-row kernel stays the default in 2D)
-    if (mode == SLLBM_STREAM_ROWS_TMEM ||
+    if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_TENSOR ||
         ((mode == SLLBM_STREAM_AUTO || mode == SLLBM_STREAM_STRUCTURED) && velset == SLLBM_D3Q45))
         ctx->want_tmem = true;
-    if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_ROW_SMEM) mode = SLLBM_STREAM_STRUCTURED;
+    ctx->want_tc = mode == SLLBM_STREAM_TENSOR;
+    if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_ROW_SMEM || mode == SLLBM_STREAM_TENSOR)
+        mode = SLLBM_STREAM_STRUCTURED;
     if ((mode == SLLBM_STREAM_STRUCTURED || mode == SLLBM_STREAM_STRUCTURED_NODE || mode == SLLBM_STREAM_TILED_REG) &&
         !axis) {
         ctx->last_error = "structured streaming needs axis-aligned cells";
@@ -1033,7 +1083,13 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
                     std::vector<int32_t> th;
                     std::vector<TmRec> tr;
                     std::vector<uint64_t> tx;
-                    if (ctx->want_tmem && build_rows_tmem(ctx, t, th, tr, tx)) {
+                    std::vector<float> tb;
+                    if (ctx->want_tmem && build_rows_tmem(ctx, t, th, tr, tx, tb)) {
+                        if (!tb.empty()) {
+                            CK(cudaMalloc(&ctx->tm_bop, sizeof(float) * tb.size()));
+                            CK(cudaMemcpyAsync(ctx->tm_bop, tb.data(), sizeof(float) * tb.size(),
+                                               cudaMemcpyHostToDevice, s));
+                        }
                         CK(cudaMalloc(&ctx->tm_head, sizeof(int32_t) * th.size()));
                         CK(cudaMalloc(&ctx->tm_recs, sizeof(TmRec) * tr.size()));
                         CK(cudaMalloc(&ctx->tm_xmask, sizeof(uint64_t) * tx.size()));
@@ -1109,7 +1165,8 @@ int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
                       !ctx->tiled_p)
                          ? SLLBM_STREAM_STRUCTURED_NODE
                          : (ctx->row_copy ? SLLBM_STREAM_ROW_COPY
-                                          : (ctx->rows_tmem ? SLLBM_STREAM_ROWS_TMEM : ctx->mode));
+                                          : (ctx->rows_tmem ? (ctx->tm.kp ? SLLBM_STREAM_TENSOR : SLLBM_STREAM_ROWS_TMEM)
+                                                            : ctx->mode));
     o->state_bytes = int64_t(2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q);
     o->table_bytes = ctx->table_bytes;
     o->n_records = int64_t(ctx->mesh.n_nodes) * ctx->vs.Q;

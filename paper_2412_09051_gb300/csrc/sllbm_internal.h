@@ -129,7 +129,8 @@ struct TmGeom {
     int n_tc;                        // tile classes (y tiles on a non-periodic y axis, else 1)
     int nst;                         // pipeline stages
     int rows_bytes;                  // bytes of source rows per stage (max rows x NX x 8)
-    int stage_bytes;                 // rows_bytes + the tile's records
+    int stage_bytes;                 // rows_bytes + the tile's records (+ the weight operands: tensor-core variant)
+    int kp;                          // tensor-core variant: the product's K, max rows padded to 8 (else 0)
 };
 
 // one entry of a copy list: a run of `len` consecutive y rows (contiguous in
@@ -168,6 +169,8 @@ struct sllbm_ctx {
     bool row_uniform = false;            // both x parities share each velocity's y/z stencil
     int tiled_p = 0;                     // order of the warp-tiled order-P table (4), 0: none
     bool want_tmem = false;              // SLLBM_STREAM_ROWS_TMEM requested
+    bool want_tc = false;                // SLLBM_STREAM_TENSOR requested: (y, z) contraction on tcgen05
+    float* tm_bop = nullptr;             // its weight operands [Q][n_tc][hi, lo][16 x kp] (canonical layout)
     bool rows_tmem = false;              // tables of the tensor-memory row-tile kernel built
     int tm_ty = 0, tm_tz = 0, tm_grid = 0;   // its tile shape (rows along y, z) and grid
     sllbm::TmGeom tm{};

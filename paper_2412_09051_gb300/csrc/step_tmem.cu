@@ -22,17 +22,24 @@ bool rows_tmem_shape(int D, int nx, int& ty, int& tz) {
 size_t rows_tmem_smem_bytes(int D, int nx, const TmGeom& T) {
     int ty = 0, tz = 0;
     if (!rows_tmem_shape(D, nx, ty, tz)) return 0;
-    const size_t b = size_t(T.nst) * T.stage_bytes + sizeof(float2) * 2 * ty * tz * (nx + 4) +
-                     sizeof(uint64_t) * (2 * T.nst + 1) + 16;
+    size_t b = size_t(T.nst) * T.stage_bytes + sizeof(float2) * 2 * ty * tz * (nx + 4) +
+               sizeof(uint64_t) * (2 * T.nst + 1) + 16;
+    if (T.kp) b = (b + 1023) / 1024 * 1024 + 4 * size_t(nx) * T.kp * 4 + 8;   // A operands, MMA barrier
     return b < 120 * 1024 ? 120 * 1024 : b;
 }
 
-int launch_rows_tmem(int vs, int nx, const float2* fg, float2* fgo, const int32_t* head, const TmRec* recs,
-                     const uint64_t* xmask, const float* tw, const StepGeom& G, const CollideConst<float>& C,
-                     const TmGeom& T, int* status, cudaStream_t s, int grid) {
+int launch_rows_tmem(int vs, int nx, const float2* fg, float2* fgo, const float* bop, const int32_t* head,
+                     const TmRec* recs, const uint64_t* xmask, const float* tw, const StepGeom& G,
+                     const CollideConst<float>& C, const TmGeom& T, int* status, cudaStream_t s, int grid) {
 #define TMCASE(VS, NX, TY, TZ) \
     if (vs == VS && nx == NX)  \
-        return launch_step_rows_tmem<VS, NX, TY, TZ>(fg, fgo, head, recs, xmask, tw, G, C, T, status, s, grid);
+        return launch_step_rows_tmem<VS, NX, TY, TZ, false>(fg, fgo, bop, head, recs, xmask, tw, G, C, T, status, s, grid);
+    if (T.kp) {
+        if (vs == 3 && nx == 128)
+            return launch_step_rows_tmem<3, 128, 2, 2, true>(fg, fgo, bop, head, recs, xmask, tw, G, C, T, status, s,
+                                                             grid);
+        return SLLBM_ERR_UNSUPPORTED;
+    }
     TMCASE(3, 128, 2, 2)
     TMCASE(3, 64, 4, 2)
     TMCASE(3, 32, 4, 4)

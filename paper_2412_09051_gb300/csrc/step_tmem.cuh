@@ -58,6 +58,49 @@ __device__ __forceinline__ void tm_st16(uint32_t taddr, const float (&v)[16]) {
 }
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// one FP32 column of this thread's TMEM lane (warp-collective; waits)
+__device__ __forceinline__ float tm_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n\ttcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r)
+                 : "r"(taddr)
+                 : "memory");
+    return __uint_as_float(r);
+}
+// FP32 rounded to TF32 (cvt.rna: nearest, ties away from zero), in an FP32 container
+__device__ __forceinline__ float to_tf32(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ void sts1(uint32_t a, float v) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ float2 lds2_tm(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+// tcgen05.mma of kind::tf32: D (TMEM) += A (smem) . B (smem)^T
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+// byte offset of element (r, k) of an R x K TF32 operand in the canonical
+// K-major layout without swizzle (8 x 16-byte core matrices, 128 B apart
+// along K, K * 32 B apart along R)
+__device__ __forceinline__ uint32_t tf32_canon(int r, int k, int K) {
+    return uint32_t((r >> 3) * (K * 32) + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
 // barrier over the `count` threads of one x row (ids 1 .. TY TZ; 0 is
 // __syncthreads); rows of one warp synchronise with __syncwarp instead
 __device__ __forceinline__ void row_bar(int id, int count) {
@@ -254,9 +297,16 @@ __device__ __forceinline__ void collide_tmem(const CollideConst<float>& C, uint3
 
 // ------------------------------------------------------------ the kernel
 // NX x TY x TZ consumer threads (one arrival node each) and two producer warps.
-template <int VS, int NX, int TY, int TZ>
+// TC: the (y, z) contraction of each velocity as tensor-core products
+// (128-node rows): D_f, D_g [128 x-nodes x 16] = A_f, A_g [x-nodes x kp
+// source rows] . W [kp x 16 tile rows, zero padded], A split by the
+// consumers and W by the host into TF32 hi and lo parts, three products
+// (hi hi, hi lo, lo hi) into FP32 accumulators in tensor-memory columns
+// 384 .. 415 (the node state uses 0 .. 383).
+template <int VS, int NX, int TY, int TZ, bool TC>
 __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
-    k_step_rows_tmem(const float2* __restrict__ fg, float2* __restrict__ fgo, const int32_t* __restrict__ head,
+    k_step_rows_tmem(const float2* __restrict__ fg, float2* __restrict__ fgo, const float* __restrict__ bop,
+                     const int32_t* __restrict__ head,
                      const TmRec* __restrict__ recs, const uint64_t* __restrict__ xmask,
                      const float* __restrict__ twt, const StepGeom G,
                      const CollideConst<float> C, const TmGeom T, int* __restrict__ status) {
@@ -271,7 +321,9 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
     constexpr int REC_BYTES = NR * 2 * int(sizeof(TmRec));
     static_assert(NT % 128 == 0 && NW <= 16 && 2 * Q <= TM_COLS, "tile shape");
     static_assert(NX % 32 == 0 && NX >= 32, "whole warps per row");
-    static_assert(NX == 32 || NR <= 15, "named barriers 1 .. NR, one per row of more than one warp");
+    static_assert(NX == 32 || NR <= 14, "named barriers 1 .. NR (one per row of more than one warp), 15");
+    static_assert(!TC || (NX == 128 && NR <= 16 && NW * TM_COLS / 4 + 32 <= TM_ALLOC), "tensor-core variant");
+    constexpr int B_FLOATS = 2 * 16;              // per K column of the weight operands (hi, lo) x 16 rows
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     unsigned char* stages = dyn_smem;                                         // [nst][rows | records]
     float2* XB = reinterpret_cast<float2*>(stages + size_t(T.nst) * T.stage_bytes);   // [2][NR][XBW]
@@ -280,6 +332,12 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
     // on only under a test wait limit, so that the timeout path runs)
     uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * T.nst + 1);       // TMEM base, abort flag
     volatile int* abort_flag = reinterpret_cast<volatile int*>(slot + 1);
+    // tensor-core variant: the A operands (f hi, f lo, g hi, g lo; 1024-byte
+    // aligned) and the products' barrier
+    const size_t a_off = ((reinterpret_cast<unsigned char*>(slot) + 16 - dyn_smem) + 1023) / 1024 * 1024;
+    const uint32_t aop = smem_u32(dyn_smem + a_off);
+    const uint32_t AOPB = uint32_t(NX * T.kp * 4);                            // bytes of one A operand
+    const uint32_t mma_bar = aop + 4 * AOPB;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * uint32_t(T.nst);
@@ -294,6 +352,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             mbar_init(empty0 + 8u * uint32_t(s), NW);
         }
         mbar_init(full0 + 16u * uint32_t(T.nst), 1);
+        if (TC) mbar_init(mma_bar, 1);
         *abort_flag = 0;
     }
     if (warp == 0) {
@@ -364,7 +423,8 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             }
             const uint32_t fb = full0 + 8u * uint32_t(s);
             const uint32_t sb = st0 + uint32_t(s) * uint32_t(T.stage_bytes);
-            if (lane == 0) mbar_arrive_expect_tx(fb, uint32_t(ha.rows * NX * 8 + REC_BYTES));
+            const uint32_t b_bytes = TC ? uint32_t(B_FLOATS * T.kp * 4) : 0u;
+            if (lane == 0) mbar_arrive_expect_tx(fb, uint32_t(ha.rows * NX * 8 + REC_BYTES) + b_bytes);
             __syncwarp();
             if (lane < ha.n) {
                 // this lane's run: population, first y and z (relative to the tile), rows
@@ -398,6 +458,9 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             if (lane == 31)
                 bulk_g2s(sb + uint32_t(T.rows_bytes), recs + (size_t(i) * T.n_tc + tc) * (NR * 2),
                          uint32_t(REC_BYTES), fb);
+            if (TC && lane == 30)
+                bulk_g2s(sb + uint32_t(T.rows_bytes + REC_BYTES), bop + (size_t(i) * T.n_tc + tc) * B_FLOATS * T.kp,
+                         b_bytes, fb);
             ++seq;
             s += NPW;
             if (s >= T.nst) {
@@ -423,7 +486,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
         const int x = tid % NX, r = tid / NX;
         const int ry = r % TY, rz = r / TY;
         const uint32_t tl = tbase + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(TM_COLS * (warp >> 2));
-        int s = 0, ph = 0, xb = 0;
+        int s = 0, ph = 0, xb = 0, mph = 0;
         for (int tile = blockIdx.x; tile < T.ntiles; tile += gridDim.x) {
             const int ty = tile % T.ntile_y, tz = tile / T.ntile_y;
             const int y = ty * TY + ry, z = D == 3 ? tz * TZ + rz : 0;
@@ -457,7 +520,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                 const float wx0 = __int_as_float(q0.w), wx1 = __int_as_float(q1.x), wx2 = __int_as_float(q1.y);
                 const unsigned char* bx = st + 8 * x;
                 float2 sum = make_float2(0.f, 0.f);
-                if (ntap > 0) {
+                if (!TC && ntap > 0) {
                     const int4 q2 = reinterpret_cast<const int4*>(rp)[2];
                     const int4 q3 = reinterpret_cast<const int4*>(rp)[3];
                     const int4 q4 = reinterpret_cast<const int4*>(rp)[4];
@@ -482,6 +545,63 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                         for (int k = 0; k < 9; ++k)
                             if (k < ntap) tap(k);
                     }
+                }
+                if constexpr (TC) {
+                    // split the staged rows into TF32 hi and lo parts, K-major
+                    // (thread (x, r) takes the source rows k = r, r + NR, ..);
+                    // rows beyond the velocity's own are zero
+                    const int kp = T.kp;
+                    const int rows = live ? __ldg(head + (size_t(i) * T.n_tc + (py ? 0 : ty)) * TM_HEAD + 1) : 0;
+                    const uint32_t sa = smem_u32(st);
+                    for (int k = r; k < kp; k += NR) {
+                        float2 v = make_float2(0.f, 0.f);
+                        if (k < rows) v = lds2_tm(sa + uint32_t(k * NX * 8 + 8 * x));
+                        const float fh = to_tf32(v.x), gh = to_tf32(v.y);
+                        const uint32_t o = aop + tf32_canon(x, k, kp);
+                        sts1(o, fh);
+                        sts1(o + AOPB, to_tf32(v.x - fh));
+                        sts1(o + 2 * AOPB, gh);
+                        sts1(o + 3 * AOPB, to_tf32(v.y - gh));
+                    }
+                    fence_async_smem();       // generic-proxy writes -> the tensor cores
+                    tc_fence_before();
+                    row_bar(15, NT);          // every consumer has written its part
+                    if (tid == 0) {
+                        tc_fence_after();
+                        constexpr uint32_t id = tc_idesc_tf32(128, 16);
+                        const uint32_t bb = sa + uint32_t(T.rows_bytes + REC_BYTES);   // W hi | W lo
+                        const uint32_t sbo = uint32_t(kp * 32);
+#pragma unroll 1
+                        for (int h = 0; h < 2; ++h) {
+                            const uint32_t d = tbase + 384u + 16u * uint32_t(h);
+                            const uint32_t ahi = aop + 2u * uint32_t(h) * AOPB, alo = ahi + AOPB;
+#pragma unroll 1
+                            for (int kk = 0; kk < kp / 8; ++kk) {
+                                const uint64_t bh = tc_sdesc(bb + 256u * kk, 128, sbo);
+                                const uint64_t bl = tc_sdesc(bb + uint32_t(16 * kp * 4) + 256u * kk, 128, sbo);
+                                const uint64_t ah = tc_sdesc(ahi + 256u * kk, 128, sbo);
+                                const uint64_t al = tc_sdesc(alo + 256u * kk, 128, sbo);
+                                tc_mma_tf32(d, ah, bh, id, kk > 0 ? 1u : 0u);
+                                tc_mma_tf32(d, ah, bl, id, 1u);
+                                tc_mma_tf32(d, al, bh, id, 1u);
+                            }
+                        }
+                        tc_commit(mma_bar);
+                    }
+                    // the products are complete (a wait that runs out waits
+                    // once more with the default bound, so that no product
+                    // is in flight when its operands or accumulators are reused)
+                    if (!mbar_wait(mma_bar, uint32_t(mph), lim)) {
+                        mbar_wait(mma_bar, uint32_t(mph));
+                        atomicOr(status, SLLBM_DEV_TC_TIMEOUT);
+                        *abort_flag = 1;
+                    }
+                    mph ^= 1;
+                    tc_fence_after();
+                    const uint32_t td = tbase + (uint32_t(32 * (warp & 3)) << 16) + 384u + uint32_t(r);
+                    sum.x = tm_ld1(td);
+                    sum.y = tm_ld1(td + 16u);
+                    tc_fence_before();
                 }
                 // this warp has read the stage: release it to the producer
                 __syncwarp();
@@ -532,16 +652,16 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
 
 size_t rows_tmem_smem_bytes(int D, int nx, const TmGeom& T);
 
-template <int VS, int NX, int TY, int TZ>
-int launch_step_rows_tmem(const float2* fg, float2* fgo, const int32_t* head, const TmRec* recs,
+template <int VS, int NX, int TY, int TZ, bool TC>
+int launch_step_rows_tmem(const float2* fg, float2* fgo, const float* bop, const int32_t* head, const TmRec* recs,
                           const uint64_t* xmask, const float* tw, const StepGeom& G, const CollideConst<float>& C,
                           const TmGeom& T, int* status, cudaStream_t stream, int grid) {
     constexpr int NR = TY * TZ;
     const size_t smem = rows_tmem_smem_bytes(VelSet<VS>::D, NX, T);
-    if (cudaFuncSetAttribute(k_step_rows_tmem<VS, NX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_step_rows_tmem<VS, NX, TY, TZ, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(smem)) != cudaSuccess)
         return SLLBM_ERR_CUDA;
-    k_step_rows_tmem<VS, NX, TY, TZ><<<grid, NX * NR + 64, smem, stream>>>(fg, fgo, head, recs, xmask, tw, G, C, T,
+    k_step_rows_tmem<VS, NX, TY, TZ, TC><<<grid, NX * NR + 64, smem, stream>>>(fg, fgo, bop, head, recs, xmask, tw, G, C, T,
                                                                                status);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }

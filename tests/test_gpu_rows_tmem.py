@@ -129,3 +129,67 @@ def test_rows_tmem_fullsize_channel_sampled(built_lib):
     assert worst < 1e-5
     print(f"PARITY rows_tmem fullsize channel: {len(nodes)} sampled nodes, populations {worst:.2e}")
     sim.close()
+
+
+TC_CASES = {
+    "channel_nx128": lambda: get_config("channel", cells=(64, 3, 3)),      # isothermal walls, ragged y tile
+    "mixing_nx128": lambda: get_config("mixing", cells=(64, 4, 3)),        # equilibrium boundaries
+}
+
+
+@pytest.mark.parametrize("name", list(TC_CASES))
+def test_tensor_core_streaming_matches_oracle(built_lib, name):
+    """SLLBM_STREAM_TENSOR: the (y, z) contraction of every velocity on the
+    tensor cores (tcgen05 kind::tf32, operands split into TF32 hi and lo
+    parts), the rest of the step as in the row-tile kernel; 3 steps against
+    the oracle at the FP32 tolerance."""
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = TC_CASES[name]()
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    sim = Sim(cfg, precision="fp32", stream_mode=9)
+    assert sim.info.stream_mode == 9, "the tensor-core streaming must be eligible for this mesh"
+    rho, u, T = initial_fields(cfg, mesh.X)
+    sim.init_state(rho, u, T)
+    f, g = ost.init_equilibrium(rho, u, T, xi, w, par.cv)
+    Tw = ost.isothermal_nodes(rec, par)
+    worst = 0.0
+    for k in range(3):
+        f, g = ost.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
+        sim.step(1)
+        assert sim.step_kernel() == "k_step_rows_tmem_tc"
+        fg, gg = sim.get_state()
+        ef, eg = _scale_err(fg, f, w), _scale_err(gg, g, w)
+        assert ef < 1e-5 and eg < 1e-5, (k, ef, eg)
+        worst = max(worst, ef, eg)
+    assert sim.device_status() == 0
+    print(f"PARITY tensor-core streaming {name} {mesh.N}: populations {worst:.2e}")
+    sim.close()
+
+
+def test_tensor_core_streaming_fullsize_channel_sampled(built_lib):
+    """The benchmark's channel with the tensor-core streaming: one step,
+    sampled nodes computed by the oracle."""
+    from oracle.departure import trace
+    from oracle.mesh import Mesh
+    from oracle.velocity_sets import velocity_set
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = get_config("channel")
+    m = cfg["mesh"]
+    mesh = Mesh(m["kind"], m["p"], m["cells"], m["length"], m.get("stretch", 1.0), m.get("central", 0))
+    xi, w, opp = velocity_set(cfg["velset"])
+    par = ost.Params(cfg["dt"], cfg["gamma"], cfg["Pr"], cfg["mu_ref"], cfg["T_ref"], cfg["mu_exp"], cfg["bcs"])
+    rho, u, T = initial_fields(cfg, mesh.X)
+    rng = np.random.default_rng(13)
+    nodes = np.unique(np.concatenate([rng.integers(0, mesh.n_nodes, 60), np.arange(40),
+                                      mesh.n_nodes - 1 - np.arange(40)]))
+    rec = trace(mesh, xi, opp, cfg["dt"], cfg["bcs"], nodes=nodes)
+    f1, g1 = ost.step_sample_from_fields(mesh, rec, rho, u, T, xi, w, par)
+    sim = Sim(cfg, stream_mode=9)
+    sim.init_state(rho, u, T)
+    sim.step(1)
+    assert sim.step_kernel() == "k_step_rows_tmem_tc"
+    fg, gg = sim.get_state()
+    worst = max(_scale_err(fg[:, nodes], f1, w), _scale_err(gg[:, nodes], g1, w))
+    assert worst < 1e-5
+    print(f"PARITY tensor-core streaming fullsize channel: {len(nodes)} sampled nodes, populations {worst:.2e}")
+    sim.close()
