@@ -52,7 +52,8 @@ class ClockSampler:
         cmd = ["nvidia-smi", "-i", str(self.index),
                "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
                "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-               "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"]
+               "clocks_event_reasons.sw_power_cap,clocks.mem,clocks.max.mem,power.draw",
+               "--format=csv,noheader,nounits", "-lms", "100"]
         try:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
@@ -78,12 +79,22 @@ class ClockSampler:
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+
+        def col(k):
+            out = []
+            for r in self.rows:
+                if len(r) > k:
+                    try:
+                        out.append(float(r[k]))
+                    except ValueError:
+                        pass
+            return out
+        sm, mx, mem, mmx, pw = col(0), col(1), col(6), col(7), col(8)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in self.rows for k in range(4) if r[2 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "mem_mhz": statistics.median(mem) if mem else None, "mem_max_mhz": max(mmx) if mmx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(self.rows)}
 
 
 def aggregate(ms_total, nodes, steps, e2e_s, dist=None, device="cpu"):
@@ -245,21 +256,27 @@ def run_gpu(args, ws, rank, local):
     sim.step(args.warmup)
     sim.sync()
     cons0, _ = sim.conservation(check=False)     # FP64 sums before the timed steps (untimed)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+    # `repeats` timing windows of K steps each, every window bracketed by a
+    # barrier and a device synchronisation; the reported window is the median
+    # one (best and all windows are reported beside it)
+    windows, per = [], []
     with ClockSampler(local) as clk:
-        with torch.cuda.stream(stream):
-            ev[0].record(stream)
-            for k in range(args.steps):
-                sim.step(1)
-                ev[k + 1].record(stream)
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    ms_total = ev[0].elapsed_time(ev[-1])
+        for rep in range(args.repeats):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                ev[0].record(stream)
+                for k in range(args.steps):
+                    sim.step(1)
+                    ev[k + 1].record(stream)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            per += [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+            windows.append(ev[0].elapsed_time(ev[-1]))
+    ms_total = statistics.median(windows)
     cons, rc = sim.conservation(check=False)
     kernel_name = sim.step_kernel()
     dev_status = sim.device_status() if args.learned != "none" else 0
@@ -356,7 +373,12 @@ def run_gpu(args, ws, rank, local):
                                     f" (learned, MLP on {'tensor' if args.learned == 'tensor' else 'CUDA'} cores)")},
             "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d * ws,
                     "d2h_bytes_per_step": d2h * ws},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * args.repeats,
+            "repeats": {"n": args.repeats, "steps_each": args.steps,
+                        "median_mlups": round(N * args.steps / (statistics.median(windows) / 1e3) / 1e6, 2),
+                        "best_mlups": round(N * args.steps / (min(windows) / 1e3) / 1e6, 2),
+                        "window_ms": [round(w, 4) for w in windows],
+                        "note": "value is the median window; gpu_launches counts every window"},
             "clocks": clk.summary(),
             "conservation_rc": rc,
             # relative change over the timed steps of the FP64 sums of rho and of
@@ -381,6 +403,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--repeats", type=int, default=3, help="timed windows of --steps steps; value is the median")
     ap.add_argument("--config", default="channel")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -242,6 +242,22 @@ int sllbm_set_state(sllbm_ctx* ctx, const double* f, const double* g, int32_t on
 int sllbm_get_state_raw(sllbm_ctx* ctx, void* fg, int32_t on_device);
 int sllbm_set_state_raw(sllbm_ctx* ctx, const void* fg, int32_t on_device);
 
+/* Node layers of constant x index x0 .. x0 + nx - 1 (every (y, z) row, every
+ * population) of the current state, copied to / from the caller's buffer in
+ * the raw format of sllbm_get_state_raw restricted to those x: element
+ * [i][row][k][0] = f_i - w_i and [i][row][k][1] = g_i - w_i (2 c_v - D) at
+ * x = x0 + k, row = y + N_y z; 2 Q N_y N_z nx values of the context's
+ * precision.  This is the halo exchange of a domain decomposition along x
+ * (the paper's runs are multi-node, Sec. 4; it does not describe the
+ * decomposition): each part steps its slab plus halo layers as a periodic
+ * domain and refreshes the halo layers from its neighbours after each step.
+ * on_device = 0: host buffer (staged through context-owned device scratch,
+ * synchronises the stream); 1: device buffer (asynchronous on the context
+ * stream).  Errors: SLLBM_ERR_ARG (NULL buffer, x range outside [0, N_x)),
+ * SLLBM_ERR_STATE (no state). */
+int sllbm_get_x_layers(sllbm_ctx* ctx, int32_t x0, int32_t nx, void* buf, int32_t on_device);
+int sllbm_set_x_layers(sllbm_ctx* ctx, int32_t x0, int32_t nx, const void* buf, int32_t on_device);
+
 /* ------------------------------------------------------------------ stepping */
 
 /* Advance n time steps (Eq. 1 with the boundary schemes of Sec. 3.3): one

@@ -70,6 +70,8 @@ _SIGS = {
     "sllbm_set_state": (C.c_int, [_P, _P, _P, C.c_int32]),
     "sllbm_get_state_raw": (C.c_int, [_P, _P, C.c_int32]),
     "sllbm_set_state_raw": (C.c_int, [_P, _P, C.c_int32]),
+    "sllbm_get_x_layers": (C.c_int, [_P, C.c_int32, C.c_int32, _P, C.c_int32]),
+    "sllbm_set_x_layers": (C.c_int, [_P, C.c_int32, C.c_int32, _P, C.c_int32]),
     "sllbm_step": (C.c_int, [_P, C.c_int64]),
     "sllbm_step_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "sllbm_read_moments": (C.c_int, [_P, _P, _P, _P, C.c_int32]),

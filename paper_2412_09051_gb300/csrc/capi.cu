@@ -35,6 +35,8 @@ template <typename real>
 int launch_conserve(int vs, int D, const typename Vec2<real>::T* fg, int64_t N, const CollideConst<double>& C,
                     double* part, int* flag, double* out, cudaStream_t s);
 int conserve_blocks();
+template <typename V2>
+int launch_x_layers(V2* fg, V2* buf, int64_t NN, int Nx, int rows, int x0, int nx, int Q, int dir, cudaStream_t s);
 template <typename real>
 int launch_scale_state(typename Vec2<real>::T* fg, int64_t N, int Q, const double* w, const double* wg, double s,
                        cudaStream_t st);
@@ -805,7 +807,7 @@ int sllbm_destroy(sllbm_ctx* ctx) {
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->row_tab, ctx->d_red, ctx->d_flag,
                     ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status,
                     ctx->d_plane, ctx->d_cp, ctx->d_plane_acc, ctx->tm_head, ctx->tm_recs, ctx->tm_xmask,
-                    ctx->tm_bop};
+                    ctx->tm_bop, ctx->d_layers};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -1600,6 +1602,49 @@ int sllbm_departure_records(sllbm_ctx* ctx, int32_t* kind, int32_t* src, int32_t
             }
         }
     return SLLBM_OK;
+}
+
+namespace {
+// pack (dir 0) or unpack (dir 1) node layers x0 .. x0 + nx - 1 of the current state
+int x_layers(sllbm_ctx* ctx, int32_t x0, int32_t nx, void* buf, int32_t on_device, int dir) {
+    if (!ctx || !buf || nx <= 0 || x0 < 0 || x0 + nx > ctx->mesh.N[0]) return SLLBM_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, SLLBM_ERR_STATE, "state not initialised");
+    cudaSetDevice(ctx->device);
+    const HostMesh& m = ctx->mesh;
+    const int rows = m.N[1] * (m.D == 3 ? m.N[2] : 1);
+    const size_t bytes = 2 * real_size(ctx) * size_t(ctx->vs.Q) * rows * nx;
+    void* dbuf = buf;
+    if (!on_device) {
+        if (ctx->layer_bytes < bytes) {
+            if (ctx->d_layers) cudaFree(ctx->d_layers);
+            ctx->d_layers = nullptr;
+            ctx->layer_bytes = 0;
+            CK(cudaMalloc(&ctx->d_layers, bytes));
+            ctx->layer_bytes = bytes;
+        }
+        dbuf = ctx->d_layers;
+        if (dir == 1) CK(cudaMemcpyAsync(dbuf, buf, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    const int rc = ctx->precision == SLLBM_FP64
+                       ? launch_x_layers<double2>((double2*)ctx->fg[ctx->cur], (double2*)dbuf, m.n_nodes, m.N[0],
+                                                  rows, x0, nx, ctx->vs.Q, dir, ctx->stream)
+                       : launch_x_layers<float2>((float2*)ctx->fg[ctx->cur], (float2*)dbuf, m.n_nodes, m.N[0], rows,
+                                                 x0, nx, ctx->vs.Q, dir, ctx->stream);
+    if (rc) return fail(ctx, rc, "layer copy launch failed");
+    if (!on_device) {
+        if (dir == 0) CK(cudaMemcpyAsync(buf, dbuf, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return SLLBM_OK;
+}
+}  // namespace
+
+int sllbm_get_x_layers(sllbm_ctx* ctx, int32_t x0, int32_t nx, void* buf, int32_t on_device) {
+    return x_layers(ctx, x0, nx, buf, on_device, 0);
+}
+
+int sllbm_set_x_layers(sllbm_ctx* ctx, int32_t x0, int32_t nx, const void* buf, int32_t on_device) {
+    return x_layers(ctx, x0, nx, const_cast<void*>(buf), on_device, 1);
 }
 
 int sllbm_sync(sllbm_ctx* ctx) {

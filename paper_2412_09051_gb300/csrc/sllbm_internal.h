@@ -216,6 +216,8 @@ struct sllbm_ctx {
     double ctl_integral = 0.0;           // PI controller state
     double* d_wref = nullptr;            // reference weights w_i, w_i (2 c_v - D) for rescaling
     float* d_feat = nullptr;             // scratch for host feature reads
+    void* d_layers = nullptr;            // staging of node layers read from / written to host memory
+    size_t layer_bytes = 0;
     int* d_flag = nullptr;
     sllbm::StepGeom geom{};
     sllbm::CollideConst<float> cc32{};

@@ -1,4 +1,5 @@
 // Initialisation, state conversion, moment readout and FP64 conservation sums.
+#include <algorithm>
 #include <string>
 
 #include "sllbm_internal.h"
@@ -271,6 +272,36 @@ int launch_scale_state(typename Vec2<real>::T* fg, int64_t N, int Q, const doubl
 }
 template int launch_scale_state<float>(float2*, int64_t, int, const double*, const double*, double, cudaStream_t);
 template int launch_scale_state<double>(double2*, int64_t, int, const double*, const double*, double, cudaStream_t);
+
+// node layers x0 .. x0 + nx - 1 of the state (all populations, all (y, z)
+// rows) to / from a packed buffer [Q][rows][nx] of (f, g) pairs (dir 0: pack,
+// 1: unpack); x0 + nx <= Nx
+template <typename V2>
+__global__ void k_x_layers(V2* __restrict__ fg, V2* __restrict__ buf, int64_t NN, int Nx, int rows, int x0, int nx,
+                           int Q, int dir) {
+    const int64_t tot = int64_t(Q) * rows * nx;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < tot; k += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = k / (int64_t(rows) * nx);
+        const int64_t rem = k - i * rows * nx;
+        const int64_t row = rem / nx;
+        const int dx = int(rem - row * nx);
+        const int64_t n = int64_t(x0 + dx) + int64_t(Nx) * row;
+        if (dir == 0) buf[k] = fg[i * NN + n];
+        else fg[i * NN + n] = buf[k];
+    }
+}
+
+template <typename V2>
+int launch_x_layers(V2* fg, V2* buf, int64_t NN, int Nx, int rows, int x0, int nx, int Q, int dir, cudaStream_t s) {
+    const int64_t tot = int64_t(Q) * rows * nx;
+    const int bs = 256;
+    const int64_t blocks = std::min<int64_t>((tot + bs - 1) / bs, 152 * 16);
+    if (tot == 0) return SLLBM_OK;
+    k_x_layers<V2><<<unsigned(blocks), bs, 0, s>>>(fg, buf, NN, Nx, rows, x0, nx, Q, dir);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+template int launch_x_layers<float2>(float2*, float2*, int64_t, int, int, int, int, int, int, cudaStream_t);
+template int launch_x_layers<double2>(double2*, double2*, int64_t, int, int, int, int, int, int, cudaStream_t);
 
 }  // namespace sllbm
 

@@ -143,6 +143,20 @@ class Sim:
         p, dev = _ptr(fg)
         self._call("sllbm_set_state_raw", p, dev)
 
+    def get_x_layers(self, x0, nx, out=None):
+        """Node layers x0 .. x0 + nx - 1, raw format [Q, rows, nx, 2] (numpy, or a
+        torch CUDA tensor for a device copy)."""
+        if out is None:
+            rows = self.info.nodes[1] * (self.info.nodes[2] if self.D == 3 else 1)
+            out = np.zeros((self.Q, rows, nx, 2), dtype=np.float64 if self.fp64 else np.float32)
+        p, dev = _ptr(out)
+        self._call("sllbm_get_x_layers", int(x0), int(nx), p, dev)
+        return out
+
+    def set_x_layers(self, x0, nx, buf):
+        p, dev = _ptr(buf)
+        self._call("sllbm_set_x_layers", int(x0), int(nx), p, dev)
+
     def step(self, n=1):
         self._call("sllbm_step", C.c_int64(n))
 
