@@ -297,3 +297,64 @@ def evaluate_equal_cost(model, case, fine_cells=128, steps=10, spinup=4, mid_cel
         s.close()
     ref.close()
     return out
+
+
+def frontier(model, case, coarse_cells=64, plain_factors=(1.0, 1.25, 1.5), steps=10, spinup=4, repeats=3):
+    """Cost-error frontier of the plain method against the learned point:
+    plain runs at coarse_cells times each factor (time step scaled with the
+    cell size, step counts reaching the same time) and the learned run at
+    coarse_cells, each started from the FP64 reference at twice the coarse
+    resolution after `spinup` steps (Fourier resampled) and compared with it
+    at the end (rho, u, T errors at each run's own nodes); GPU time of each
+    run, the best of `repeats` timed repetitions after a warm-up launch."""
+    import torch
+    from workloads import initial_fields
+    kind, mach, seed = case
+    fine_cells = 2 * coarse_cells
+    cf = case_cfg(None, fine_cells, kind, mach, seed)
+    cc = case_cfg(None, coarse_cells, kind, mach, seed)
+    t_end = steps * cc["dt"]
+    ref = Sim(cf, precision="fp64")
+    nf = ref.info.nodes[0]
+    ref.init_state(*initial_fields(cf, ref.node_coords()))
+    ref.step(spinup)
+    f0, g0 = ref.get_state()
+    ref.step(int(round(t_end / cf["dt"])))
+    rr, ur, Tr = ref.moments()
+    ref.close()
+    runs = [(f"plain_x{fac:g}", int(round(coarse_cells * fac)), False) for fac in plain_factors]
+    runs.append(("learned_x1", coarse_cells, True))
+    out = {}
+    for name, cells, learned in runs:
+        cfg = case_cfg(None, cells, kind, mach, seed)
+        n_steps = int(round(t_end / cfg["dt"]))
+        cfg["dt"] = t_end / n_steps
+        s = Sim(cfg, precision="fp32")
+        n = s.info.nodes[0]
+        Q = f0.shape[0]
+        if learned:
+            set_mlp(s, model["w"], model["b"], model["s_in"], model["sigma"])
+        fi = _resample(f0.reshape(Q, nf, nf), n).reshape(Q, -1)
+        gi = _resample(g0.reshape(Q, nf, nf), n).reshape(Q, -1)
+        best = None
+        for _ in range(repeats):
+            s.set_state(fi, gi)
+            s.step(1)                                # warm-up launch outside the timing
+            s.set_state(fi, gi)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step(n_steps)
+            s.sync()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        rho_s, u_s, T_s = s.moments()
+        rho_r = _resample(rr.reshape(nf, nf), n).ravel()
+        T_r = _resample(Tr.reshape(nf, nf), n).ravel()
+        u_r = np.stack([_resample(ur[:, d].reshape(nf, nf), n).ravel() for d in range(2)], axis=1)
+        out[name] = dict(cells=cells, steps=n_steps, nodes=int(s.N), kernel=s.step_kernel(),
+                         err_rho=float(np.sqrt(np.mean((rho_s - rho_r) ** 2))),
+                         err_u=float(np.sqrt(np.mean((u_s - u_r) ** 2))),
+                         err_T=float(np.sqrt(np.mean((T_s - T_r) ** 2))),
+                         gpu_s=best)
+        s.close()
+    return out

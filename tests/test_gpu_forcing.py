@@ -92,3 +92,31 @@ def test_pi_controller_spins_up_to_target(built_lib):
     assert abs(cc[1] / N - target) < 0.1 * target
     assert np.isfinite(F).all()
     assert abs(cc[0] - c0[0]) < 1e-4 * c0[0]
+
+
+def test_pi_controller_force_sequence_matches_host_law(built_lib):
+    """The PI control law of Sec. 4.3 as read here, restated on the host in
+    FP64 and replayed on the library's own FP64 momentum sums: every
+    control_every steps e = target - mean(rho u_x), I += e control_every dt,
+    F_x = F0 + kp e + ki I.  Stepping one control period per call, the force
+    the library sets must equal the host's to 1e-12 at every update."""
+    cfg = get_config("channel", cells=(4, 12, 3))
+    sim = _sim(cfg, "fp32")
+    N = sim.N
+    Tw = cfg["bcs"][0]["T"]
+    sim.init_state(np.ones(N), np.zeros((N, 3)), np.full(N, Tw))
+    target, F0, kp, ki, every = 0.05, 1e-3, 20.0, 100.0, 5
+    integral = 0.0
+    forces = []
+    for period in range(12):
+        F = sim.step_controlled(every, target, F0, kp=kp, ki=ki, control_every=every, rescale_every=0,
+                                target_mass=0.0)
+        c, rc = sim.conservation(check=False)
+        e = target - c[1] / N
+        integral += e * every * cfg["dt"]
+        Fh = F0 + kp * e + ki * integral
+        assert abs(F[0] - Fh) <= 1e-12 * max(1.0, abs(Fh)), (period, F[0], Fh)
+        assert F[1] == 0.0 and F[2] == 0.0
+        forces.append(F[0])
+    assert np.ptp(forces) > 1e-3                   # the force did change over the periods
+    sim.close()

@@ -251,3 +251,31 @@ def test_learned_against_plain_at_equal_cost(built_lib):
             assert np.isfinite([v["err_rho"], v["err_u"], v["err_T"]]).all()
         ratio = res["plain_mid"]["gpu_s"] / res["learned_coarse"]["gpu_s"]
         assert 0.3 < ratio < 3.0
+
+
+@pytest.mark.parametrize("coarse", [64, 256])
+def test_learned_frontier_two_sizes(built_lib, coarse):
+    """Measurement (printed as FRONTIER lines and recorded in the design
+    notes): the plain method's cost-error frontier (1, 1.25 and 1.5 times
+    the coarse resolution) against the learned run at the coarse resolution,
+    at a launch-bound size (64 coarse cells) and a size where the step time
+    scales with the nodes (256 coarse cells, 262k nodes), each with a network
+    trained on 2x coarse-grained pairs of its own size.  Asserted: finite
+    errors, a plain frontier whose error falls with resolution, and learned
+    and plain runs at the coarse size taking the corrected and the plain kernels."""
+    from paper_2412_09051_gb300 import learned as L
+    from paper_2412_09051_gb300.sim import Sim
+    train_cases = [("isentropic_vortex", m, s) for m in (0.3, 0.6, 0.9, 1.2) for s in (0, 1)] + \
+                  [("shear_layer", m, s) for m in (0.3, 0.6, 0.9, 1.2) for s in (0,)]
+    snaps = 6 if coarse == 64 else 2
+    Z, R = L.generate_pairs(train_cases, fine_cells=2 * coarse, snapshots=snaps, stride=6)
+    model = L.train(Sim(get_config("learned", cells=coarse)), Z, R, epochs=40)
+    for case in (("isentropic_vortex", 1.0, 21), ("shear_layer", 0.8, 5)):
+        res = L.frontier(model, case, coarse_cells=coarse)
+        for name, v in res.items():
+            print(f"FRONTIER coarse={coarse} {case[0]} {name}: cells {v['cells']} steps {v['steps']} "
+                  f"gpu {v['gpu_s'] * 1e3:.3f} ms err rho {v['err_rho']:.3e} u {v['err_u']:.3e} "
+                  f"T {v['err_T']:.3e} ({v['kernel']})")
+            assert np.isfinite([v["err_rho"], v["err_u"], v["err_T"]]).all()
+        assert res["plain_x1.5"]["err_u"] < res["plain_x1"]["err_u"]
+        assert res["learned_x1"]["kernel"] == "k_step_tiled_smem_tc"
