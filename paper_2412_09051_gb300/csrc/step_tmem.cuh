@@ -502,15 +502,15 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                 // under a test wait limit the first velocity also waits on the
                 // barrier that nothing completes, so that the wait runs out
                 // whatever the timing (sllbm_debug_wait_limit)
-                if (!*abort_flag && (!mbar_wait(fb, uint32_t(ph), lim) ||
-                                     (lim < kWaitLimit && i == 0 &&
-                                      !mbar_wait(full0 + 16u * uint32_t(T.nst), 0, lim)))) {
+                bool live = !*abort_flag;
+                if (live && (!mbar_wait(fb, uint32_t(ph), lim) ||
+                             (lim < kWaitLimit && i == 0 && !mbar_wait(full0 + 16u * uint32_t(T.nst), 0, lim)))) {
                     atomicOr(status, SLLBM_DEV_COPY_TIMEOUT);
                     *abort_flag = 1;
+                    live = false;
                 }
                 // after an abort the stage may never have been written: read
                 // no offsets from it (an empty equilibrium record instead)
-                const bool live = !*abort_flag;
                 const unsigned char* st = stages + size_t(s) * T.stage_bytes;
                 const TmRec* rp = reinterpret_cast<const TmRec*>(st + T.rows_bytes) + (r * 2 + (x & 1));
                 const int4 q0 = reinterpret_cast<const int4*>(rp)[0];
@@ -529,10 +529,13 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                     const float w[9] = {__int_as_float(q3.w), __int_as_float(q4.x), __int_as_float(q4.y),
                                         __int_as_float(q4.z), __int_as_float(q4.w), __int_as_float(q5.x),
                                         __int_as_float(q5.y), __int_as_float(q5.z), __int_as_float(q5.w)};
+                    // two accumulators (even and odd taps): half the dependent chain
+                    float2 sum1 = make_float2(0.f, 0.f);
                     auto tap = [&](int k) {
                         const float2 v = *reinterpret_cast<const float2*>(
                             bx + SLLBM_CHK(off[k], T.rows_bytes, G.status, SLLBM_DEV_BAD_SMEM));
-                        sum = __ffma2_rn(make_float2(w[k], w[k]), v, sum);
+                        if (k & 1) sum1 = __ffma2_rn(make_float2(w[k], w[k]), v, sum1);
+                        else sum = __ffma2_rn(make_float2(w[k], w[k]), v, sum);
                     };
                     if (ntap == 9) {
 #pragma unroll
@@ -545,6 +548,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                         for (int k = 0; k < 9; ++k)
                             if (k < ntap) tap(k);
                     }
+                    sum = __fadd2_rn(sum, sum1);
                 }
                 if constexpr (TC) {
                     // split the staged rows into TF32 hi and lo parts, K-major
