@@ -19,6 +19,9 @@ Modules and the passage each follows:
 Parity status: the velocity sets, equilibrium, interpolation, inverse maps,
 collision, thermal correction, forcing and mass rescaling are pinned by
 closed forms, invariants and special cases (tests/test_oracle_*.py); the
+temperature-dependent viscosity law of Sec. 4.3 by the shear-wave decay in
+gas at T != T_ref (and per-node relaxation factors); the learned network's
+forward pass and correction by a hand-evaluated one-path network; the
 quasi-equilibrium term (Pr != 1) by its relaxation-rate invariants, the
 Prandtl scaling of the compressible Couette temperature rise and the
 thermal part of the sound attenuation.  The outlet scheme and the
