@@ -141,6 +141,11 @@ extern "C" {
                                        accumulators in tensor memory; D3Q45 rows of 128 nodes only
                                        (elsewhere as SLLBM_STREAM_ROWS_TMEM), opt-in: slower than
                                        the CUDA-core contraction                                 */
+#define SLLBM_STREAM_ROWS_PAIRS 10  /* the SLLBM_STREAM_ROWS_TMEM design with two arrival nodes
+                                       (x even, x + 1) per consumer thread and one TMA tensor copy
+                                       per (source population, velocity, tile): D3Q45 rows of 64
+                                       or 128 nodes, D2Q19 rows of 64 or 128, periodic x and z
+                                       (elsewhere as SLLBM_STREAM_ROWS_TMEM)                     */
 
 /* ------------------------------------------------------------------ descriptors */
 typedef struct {

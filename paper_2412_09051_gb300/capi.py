@@ -24,7 +24,7 @@ FP64, FP32 = 0, 1
 STREAM_AUTO, STREAM_GATHER, STREAM_STRUCTURED, STREAM_STRUCTURED_NODE, STREAM_TILED_REG, STREAM_GATHER_SMEM = \
     0, 1, 2, 3, 4, 5
 STREAM_ROW_COPY = 6
-STREAM_ROWS_TMEM, STREAM_ROW_SMEM, STREAM_TENSOR = 7, 8, 9
+STREAM_ROWS_TMEM, STREAM_ROW_SMEM, STREAM_TENSOR, STREAM_ROWS_PAIRS = 7, 8, 9, 10
 
 
 class Bc(C.Structure):

@@ -11,6 +11,9 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "sllbm_internal.h"
 #include "mlp.cuh"
 #include "step_kernels.cuh"
@@ -91,6 +94,11 @@ int launch_plane_cp(const double* rho, const double* T, int N0, int N1, int N2, 
 void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
                         std::vector<double>& P);
 bool rows_tmem_shape(int D, int nx, int& ty, int& tz);
+bool rows_pairs_shape(int D, int nx, int& ty, int& tz);
+size_t rows_pairs_smem(int D, int nx, const TmGeom2& T);
+int launch_rows_pairs(int vs, int nx, const float2* fg, float2* fgo, const void* maps, const int32_t* head,
+                      const TmRec2* recs, const uint64_t* xmask, const float* tw, const StepGeom& G,
+                      const CollideConst<float>& C, const TmGeom2& T, int* status, cudaStream_t s, int grid);
 size_t rows_tmem_smem_bytes(int D, int nx, const TmGeom& T);
 int launch_rows_tmem(int vs, int nx, const float2* fg, float2* fgo, const float* bop, const int32_t* head,
                      const TmRec* recs, const uint64_t* xmask, const float* tw, const StepGeom& G,
@@ -533,11 +541,209 @@ bool build_rows_tmem(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::ve
     return true;
 }
 
+// Tables of the row-tile kernel with two nodes per thread (step_tmem2.cuh):
+// tiles of TY x TZ whole x rows.  Per (velocity, tile class): one box of
+// source rows per population (the y range times the z range of the (y, z)
+// taps of the tile's rows with non-zero weight: each row's taps are a product
+// of y and z offsets, so the union is that box), copied by one TMA tensor
+// copy; per tile row one record with the taps' slots and weights and the x
+// weights of its even and odd nodes over six row sums; per tile class the
+// velocities whose x factor is not the identity.  False where it does not apply.
+bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::vector<int32_t>& head,
+                      std::vector<TmRec2>& recs, std::vector<uint64_t>& xmask) {
+    const HostMesh& m = c->mesh;
+    const StepGeom& G = c->geom;
+    const int Q = c->vs.Q, D = m.D, NX = m.N[0], N1 = m.N[1], N2 = D == 3 ? m.N[2] : 1;
+    int TY = 0, TZ = 0;
+    if (c->precision != SLLBM_FP32 || m.p != 2 || !c->tiled || !c->row_uniform) return false;
+    if (!((c->velset == SLLBM_D3Q45 && D == 3) || (c->velset == SLLBM_D2Q19 && D == 2))) return false;
+    if (!rows_pairs_shape(D, NX, TY, TZ) || G.ncls[0] != 2 || !m.periodic[0]) return false;
+    const bool py = m.periodic[1] != 0;
+    if (py && N1 % TY) return false;
+    if (D == 3 && (!m.periodic[2] || N2 % TZ)) return false;
+    if (int64_t(Q) * m.n_nodes >= (int64_t(1) << 31)) return false;
+    const int NR = TY * TZ;
+    TmGeom2 T{};
+    T.ntile_y = (N1 + TY - 1) / TY;
+    T.ntile_z = D == 3 ? N2 / TZ : 1;
+    T.ntiles = T.ntile_y * T.ntile_z;
+    T.n_tc = py ? 1 : T.ntile_y;
+    head.assign(size_t(Q) * T.n_tc * TM2_HEAD, 0);
+    recs.assign(size_t(Q) * T.n_tc * NR, TmRec2{});
+    xmask.assign(size_t(T.n_tc), 0);
+    const int NRT = D == 3 ? 9 : 3;
+    int max_rows = 1;
+    std::vector<int> shapes;
+    struct Tap {
+        int src, dy, dz;
+        float w;
+    };
+    struct Box {
+        int src, ylo, yhi, zlo, zhi, slot;
+    };
+    for (int i = 0; i < Q; ++i)
+        for (int tc = 0; tc < T.n_tc; ++tc) {
+            const int y0 = py ? 0 : tc * TY;
+            int32_t* h = &head[(size_t(i) * T.n_tc + tc) * TM2_HEAD];
+            std::vector<std::vector<Tap>> taps(NR);
+            std::vector<int> cls0(NR, -1);
+            for (int r = 0; r < NR; ++r) {
+                const int ry = r % TY, rz = r / TY;
+                const int y = y0 + ry, z = rz;
+                if (y >= N1) continue;                   // beyond a ragged last tile: an idle row
+                cls0[r] = G.ncls[0] * ((py ? (y & 1) : y) + G.ncls[1] * (D == 3 ? (z & 1) : 0));
+                const TileRec<float>& a = t[size_t(i) * G.n_classes + cls0[r]];
+                if ((a.meta & 15) == REC_EQ) continue;
+                for (int k = 0; k < NRT; ++k) {
+                    const float wk = a.rw[k];
+                    if (std::fabs(wk) < 1e-12f) continue;
+                    const int dy = ((a.dyzp >> (4 * (k % 3))) & 15) - 8;
+                    const int dz = D == 3 ? ((a.dyzp >> (12 + 4 * (k / 3))) & 15) - 8 : 0;
+                    taps[r].push_back({a.meta >> 8, ry + dy, rz + dz, wk});
+                }
+            }
+            std::vector<Box> boxes;
+            for (int r = 0; r < NR; ++r)
+                for (const Tap& tp : taps[r]) {
+                    bool found = false;
+                    for (Box& b : boxes)
+                        if (b.src == tp.src) {
+                            b.ylo = std::min(b.ylo, tp.dy);
+                            b.yhi = std::max(b.yhi, tp.dy);
+                            b.zlo = std::min(b.zlo, tp.dz);
+                            b.zhi = std::max(b.zhi, tp.dz);
+                            found = true;
+                        }
+                    if (!found) boxes.push_back({tp.src, tp.dy, tp.dy, tp.dz, tp.dz, 0});
+                }
+            if (int(boxes.size()) > TM2_MAX_BOXES) return false;
+            int nrows = 0;
+            for (size_t q = 0; q < boxes.size(); ++q) {
+                Box& b = boxes[q];
+                const int ny = b.yhi - b.ylo + 1, nz = b.zhi - b.zlo + 1;
+                if (b.ylo + 128 < 0 || b.yhi + 128 > 255 || b.zlo + 128 < 0 || b.zhi + 128 > 255 || ny > 64 ||
+                    nz > 64 || ny > N1 || nz > N2)
+                    return false;
+                int map = -1;
+                for (size_t k = 0; k < shapes.size(); ++k)
+                    if (shapes[k] == (ny | (nz << 8))) map = int(k);
+                if (map < 0) {
+                    if (int(shapes.size()) == TM2_MAX_MAPS) return false;
+                    map = int(shapes.size());
+                    shapes.push_back(ny | (nz << 8));
+                }
+                b.slot = nrows;
+                nrows += ny * nz;
+                h[2 + q] = tm2_pack_box(b.src, b.ylo, b.zlo, map);
+                h[2 + TM2_MAX_BOXES + q] = b.slot;
+                h[2 + 2 * TM2_MAX_BOXES + q] = ny | (nz << 8);
+            }
+            if (nrows > TM2_MAX_ROWS) return false;
+            h[0] = int(boxes.size());
+            h[1] = nrows;
+            max_rows = std::max(max_rows, nrows);
+            bool xchg = false;
+            for (int r = 0; r < NR; ++r) {
+                TmRec2& ro = recs[(size_t(i) * T.n_tc + tc) * NR + r];
+                ro.meta = REC_EQ;
+                if (cls0[r] < 0) continue;              // an idle row
+                const TileRec<float>& a = t[size_t(i) * G.n_classes + cls0[r]];
+                ro.meta = a.meta;
+                ro.ntap = int(taps[r].size());
+                if ((a.meta & 15) == REC_EQ) continue;
+                for (size_t q = 0; q < taps[r].size(); ++q) {
+                    const Tap& tp = taps[r][q];
+                    int sl = -1;
+                    for (const Box& bx : boxes)
+                        if (bx.src == tp.src) sl = bx.slot + (tp.dz - bx.zlo) * (bx.yhi - bx.ylo + 1) + (tp.dy - bx.ylo);
+                    ro.off[q] = sl * NX * 8;
+                    ro.w[q] = tp.w;
+                }
+                // x weights over the window of row sums: the even node x reads
+                // x - 2 .. x + 2 (slots 0 .. 4), the odd node x + 1 reads
+                // x - 1 .. x + 3 (its slots 0 .. 4); a tap at offset d from the
+                // node sits in slot d + 2 of its window
+                for (int xp = 0; xp < 2; ++xp) {
+                    const TileRec<float>& b = t[size_t(i) * G.n_classes + cls0[r] + xp];
+                    if (b.meta != a.meta) return false;
+                    float* wx = xp ? ro.wxo : ro.wxe;
+                    for (int q = 0; q < 3; ++q) {
+                        const int d = ((b.dxp >> (4 * q)) & 15) - 8;
+                        if (d < -2 || d > 2) return false;
+                        wx[d + 2] += b.wx[q];
+                    }
+                    for (int q = 0; q < 5; ++q)
+                        if (std::fabs(double(wx[q]) - (q == 2 ? 1.0 : 0.0)) > 1e-12) xchg = true;
+                }
+            }
+            if (xchg) xmask[tc] |= uint64_t(1) << i;
+        }
+    T.rows_bytes = max_rows * NX * 8;
+    T.stage_bytes = T.rows_bytes + NR * int(sizeof(TmRec2));
+    const size_t fixed = sizeof(float2) * 4 * NR * (NX + 4) + 8 + 16;     // two halo rows per group
+    const size_t budget = 227 * 1024;
+    int nst = int((budget - fixed) / (size_t(T.stage_bytes) + 16));
+    nst = std::min(nst, 16) & ~1;          // two rings (one per consumer group) of nst / 2 stages
+    if (nst < 4) return false;
+    T.nst = nst;
+    c->tm2 = T;
+    c->tm2_box = shapes;
+    return true;
+}
+
+// TMA tensor maps of the two-nodes-per-thread row-tile kernel: state buffer b
+// viewed as the 4D FP32 tensor [Q][Nz][Ny][2 NX] (innermost last), one map
+// per box shape {2 NX, rows along y, rows along z, 1}; maps[b * shapes + k].
+// The encoder comes from the driver through the runtime's entry-point query.
+int encode_tm2_maps(sllbm_ctx* c) {
+    const HostMesh& m = c->mesh;
+    const int NX = m.N[0], N1 = m.N[1], N2 = m.D == 3 ? m.N[2] : 1, Q = c->vs.Q;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return fail(c, SLLBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const int nm = int(c->tm2_box.size());
+    std::vector<CUtensorMap> maps(size_t(2) * nm);
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < nm; ++k) {
+            const cuuint64_t dims[4] = {cuuint64_t(2 * NX), cuuint64_t(N1), cuuint64_t(N2), cuuint64_t(Q)};
+            const cuuint64_t strides[3] = {cuuint64_t(2 * NX) * 4, cuuint64_t(2 * NX) * N1 * 4,
+                                           cuuint64_t(2 * NX) * N1 * N2 * 4};
+            const cuuint32_t box[4] = {cuuint32_t(2 * NX), cuuint32_t(c->tm2_box[k] & 255),
+                                       cuuint32_t(c->tm2_box[k] >> 8), 1};
+            const cuuint32_t es[4] = {1, 1, 1, 1};
+            const CUresult r = enc(&maps[size_t(b) * nm + k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->fg[b], dims,
+                                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return fail(c, SLLBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string(int(r)) + ")");
+        }
+    cudaError_t e = cudaMalloc(&c->tm2_maps, sizeof(CUtensorMap) * maps.size());
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+    e = cudaMemcpyAsync(c->tm2_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                        c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy of the tensor maps");
+    return SLLBM_OK;
+}
+
 template <typename real>
 int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const int vs = ctx->velset, p = ctx->mesh.p;
     const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_SMEM;
     if constexpr (std::is_same<real, float>::value) {
+        if (st && ctx->rows_tm2 && !ctx->row_copy) {
+            ctx->step_kernel = "k_step_rows_pairs";
+            const int b = static_cast<const void*>(L.fg) == ctx->fg[0] ? 0 : 1;
+            const char* maps = static_cast<const char*>(ctx->tm2_maps) +
+                               size_t(b) * ctx->tm2_box.size() * sizeof(CUtensorMap);
+            return launch_rows_pairs(vs, ctx->mesh.N[0], L.fg, L.fgo, maps, ctx->tm2_head,
+                                     static_cast<const TmRec2*>(ctx->tm2_recs), ctx->tm_xmask, L.tw, L.G, *L.C,
+                                     ctx->tm2, ctx->d_status, L.stream, ctx->tm_grid);
+        }
         if (st && ctx->rows_tmem && !ctx->row_copy) {
             ctx->step_kernel = ctx->tm.kp ? "k_step_rows_tmem_tc" : "k_step_rows_tmem";
             return launch_rows_tmem(vs, ctx->mesh.N[0], L.fg, L.fgo, ctx->tm_bop, ctx->tm_head,
@@ -807,7 +1013,7 @@ int sllbm_destroy(sllbm_ctx* ctx) {
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->row_tab, ctx->d_red, ctx->d_flag,
                     ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status,
                     ctx->d_plane, ctx->d_cp, ctx->d_plane_acc, ctx->tm_head, ctx->tm_recs, ctx->tm_xmask,
-                    ctx->tm_bop, ctx->d_layers};
+                    ctx->tm_bop, ctx->d_layers, ctx->tm2_head, ctx->tm2_recs, ctx->tm2_maps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -879,11 +1085,13 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
     // the row-tile kernel with the node state in tensor memory: requested
     // explicitly, or by default for the 45-velocity set on structured meshes
     // (faster there; the one-block-per-row kernel stays the default in 2D)
-    if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_TENSOR ||
+    if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_TENSOR || mode == SLLBM_STREAM_ROWS_PAIRS ||
         ((mode == SLLBM_STREAM_AUTO || mode == SLLBM_STREAM_STRUCTURED) && velset == SLLBM_D3Q45))
         ctx->want_tmem = true;
     ctx->want_tc = mode == SLLBM_STREAM_TENSOR;
-    if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_ROW_SMEM || mode == SLLBM_STREAM_TENSOR)
+    ctx->want_tm2 = mode == SLLBM_STREAM_ROWS_PAIRS;
+    if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_ROW_SMEM || mode == SLLBM_STREAM_TENSOR ||
+        mode == SLLBM_STREAM_ROWS_PAIRS)
         mode = SLLBM_STREAM_STRUCTURED;
     if ((mode == SLLBM_STREAM_STRUCTURED || mode == SLLBM_STREAM_STRUCTURED_NODE || mode == SLLBM_STREAM_TILED_REG) &&
         !axis) {
@@ -1086,7 +1294,26 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
                     std::vector<TmRec> tr;
                     std::vector<uint64_t> tx;
                     std::vector<float> tb;
-                    if (ctx->want_tmem && build_rows_tmem(ctx, t, th, tr, tx, tb)) {
+                    std::vector<TmRec2> tr2;
+                    if (ctx->want_tm2 && build_rows_pairs(ctx, t, th, tr2, tx)) {
+                        CK(cudaMalloc(&ctx->tm2_head, sizeof(int32_t) * th.size()));
+                        CK(cudaMalloc(&ctx->tm2_recs, sizeof(TmRec2) * tr2.size()));
+                        CK(cudaMalloc(&ctx->tm_xmask, sizeof(uint64_t) * tx.size()));
+                        CK(cudaMemcpyAsync(ctx->tm2_head, th.data(), sizeof(int32_t) * th.size(),
+                                           cudaMemcpyHostToDevice, s));
+                        CK(cudaMemcpyAsync(ctx->tm2_recs, tr2.data(), sizeof(TmRec2) * tr2.size(),
+                                           cudaMemcpyHostToDevice, s));
+                        CK(cudaMemcpyAsync(ctx->tm_xmask, tx.data(), sizeof(uint64_t) * tx.size(),
+                                           cudaMemcpyHostToDevice, s));
+                        CK(cudaStreamSynchronize(s));
+                        int sms = 0;
+                        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+                        ctx->tm_grid = std::min(ctx->tm2.ntiles, sms);
+                        ctx->rows_tm2 = true;
+                        th.clear();
+                        tx.clear();
+                    }
+                    if (!ctx->rows_tm2 && ctx->want_tmem && build_rows_tmem(ctx, t, th, tr, tx, tb)) {
                         if (!tb.empty()) {
                             CK(cudaMalloc(&ctx->tm_bop, sizeof(float) * tb.size()));
                             CK(cudaMemcpyAsync(ctx->tm_bop, tb.data(), sizeof(float) * tb.size(),
@@ -1142,6 +1369,10 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
         for (int b = 0; b < 2; ++b) {
             CK(cudaMalloc(&ctx->fg[b], 2 * rs * N * Q));
         }
+        if (ctx->rows_tm2) {
+            const int r3 = encode_tm2_maps(ctx);          // the maps name the state buffers
+            if (r3 != SLLBM_OK) return r3;
+        }
         CK(cudaMalloc(&ctx->d_red, sizeof(double) * (conserve_blocks() * 5 + 8)));
         CK(cudaStreamSynchronize(s));
         return SLLBM_OK;
@@ -1167,8 +1398,10 @@ int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
                       !ctx->tiled_p)
                          ? SLLBM_STREAM_STRUCTURED_NODE
                          : (ctx->row_copy ? SLLBM_STREAM_ROW_COPY
-                                          : (ctx->rows_tmem ? (ctx->tm.kp ? SLLBM_STREAM_TENSOR : SLLBM_STREAM_ROWS_TMEM)
-                                                            : ctx->mode));
+                                          : (ctx->rows_tm2 ? SLLBM_STREAM_ROWS_PAIRS
+                                             : (ctx->rows_tmem ? (ctx->tm.kp ? SLLBM_STREAM_TENSOR
+                                                                             : SLLBM_STREAM_ROWS_TMEM)
+                                                               : ctx->mode)));
     o->state_bytes = int64_t(2 * real_size(ctx) * ctx->mesh.n_nodes * ctx->vs.Q);
     o->table_bytes = ctx->table_bytes;
     o->n_records = int64_t(ctx->mesh.n_nodes) * ctx->vs.Q;

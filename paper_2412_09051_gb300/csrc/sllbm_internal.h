@@ -140,6 +140,41 @@ inline constexpr int32_t tm_pack_run(int src, int dy, int dz, int len) {
     return src | ((dy + 128) << 6) | ((dz + 128) << 14) | (len << 22);
 }
 
+// Row-tile kernel with two arrival nodes per thread (step_tmem2.cuh): per
+// (velocity, tile class, tile row) the record of the row's even and odd x
+// nodes (128 bytes), the (y, z) taps shared by both, the x weights of each
+// over a window of six row sums (x - 2 .. x + 3 of the even node x)
+struct alignas(16) TmRec2 {
+    int32_t meta;       // kind | bid << 4 | src << 8
+    int32_t ntap;       // (y, z) taps
+    int32_t off[9];     // byte offsets of the taps' source rows within the stage
+    float w[9];         // (y, z) weight products
+    float wxe[5];       // even node x: weights of the row sums at x - 2 .. x + 2
+    float wxo[5];       // odd node x + 1: weights of the row sums at x - 1 .. x + 3
+    int32_t pad[2];
+};
+static_assert(sizeof(TmRec2) == 128, "eight 16-byte loads per record");
+
+constexpr int TM2_MAX_BOXES = 4;     // boxes (one per source population) per (velocity, tile class)
+constexpr int TM2_HEAD = 16;         // ints per copy list: boxes, rows, per box: entry, first slot,
+                                     // rows along y | along z << 8 (2 + 3 * 4 = 14, padded)
+constexpr int TM2_MAX_ROWS = 64;     // rows of one velocity's boxes
+constexpr int TM2_MAX_MAPS = 32;     // box shapes (tensor maps)
+
+struct TmGeom2 {
+    int ntile_y, ntile_z, ntiles;    // tiles along y, along z, total
+    int n_tc;                        // tile classes (y tiles on a non-periodic y axis, else 1)
+    int nst;                         // pipeline stages, a multiple of the 2 producer warps
+    int rows_bytes;                  // bytes of source rows per stage (max rows x NX x 8)
+    int stage_bytes;                 // rows_bytes + the tile's records
+};
+
+// one box of a copy list: population, first y and z relative to the tile
+// origin, shape index (its tensor map)
+inline constexpr int32_t tm2_pack_box(int src, int dy, int dz, int map) {
+    return src | ((dy + 128) << 6) | ((dz + 128) << 14) | (map << 22);
+}
+
 struct StepGeom {             // structured / gather kernel geometry
     int N[3], cells[3], periodic[3];
     int ncls[3];              // classes per dimension (p if periodic, else N)
@@ -176,6 +211,13 @@ struct sllbm_ctx {
     sllbm::TmGeom tm{};
     int32_t* tm_head = nullptr;          // copy lists [Q][n_tc][TM_HEAD]
     void* tm_recs = nullptr;             // TmRec [Q][n_tc][TY TZ][2]
+    bool want_tm2 = false;               // SLLBM_STREAM_ROWS_PAIRS requested
+    bool rows_tm2 = false;               // tables of the two-nodes-per-thread row-tile kernel built
+    sllbm::TmGeom2 tm2{};
+    int32_t* tm2_head = nullptr;         // box lists [Q][n_tc][TM2_HEAD]
+    void* tm2_recs = nullptr;            // TmRec2 [Q][n_tc][TY TZ]
+    void* tm2_maps = nullptr;            // TMA tensor maps [2 state buffers][box shapes]
+    std::vector<int> tm2_box;            // box shapes: rows along y | rows along z << 8
     uint64_t* tm_xmask = nullptr;        // [n_tc]: velocities whose x factor needs the row exchange
     const char* step_kernel = "";        // kernel of the last step launched (sllbm_info)
     int precision = SLLBM_FP32;

@@ -1,0 +1,415 @@
+// Fused SLLBM step, row tiles with two arrival nodes per thread: the design of
+// step_tmem.cuh (persistent CTAs owning tiles of TY x TZ whole periodic x
+// rows, the 2Q streamed values of every node in tensor memory, the source
+// rows of each velocity staged once per tile in shared memory) with
+//   * one consumer thread per pair of x nodes (x even, x + 1): one stage wait,
+//     one row record (the (y, z) taps are the same for both x parities) and
+//     16-byte tap loads serve two nodes, and the x factor of both comes from
+//     a window of six row sums read as three 16-byte loads;
+//   * one TMA tensor copy per source population and velocity: the union of a
+//     tile's (y, z) taps of one population is a box of rows (y range x z
+//     range: each row's taps are a product of y and z offsets), copied with
+//     cp.async.bulk.tensor over the state viewed as [Q][Nz][Ny][2 NX] FP32
+//     (row by row with bulk copies where a box crosses a periodic seam).
+// Collision: collide_tmem (step_tmem.cuh) once per node of the pair.  Every
+// wait is bounded, with the abort protocol of step_tmem.cuh.
+#pragma once
+#include "step_tmem.cuh"
+
+namespace sllbm {
+
+// TMA tensor copy of one box of a 4D tensor (tiled mode) from global to
+// shared memory: `tmap` is the generic address of a CUtensorMap in global
+// memory, (c0, c1, c2, c3) the box's first element (c0 times the element
+// size a multiple of 16 bytes); the bytes count against bar's transaction count
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ float4 lds4f(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ int4 lds4(uint32_t a) {
+    int4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts4f(uint32_t a, float4 v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Two consumer groups of NX / 2 x TY x TZ threads and one producer warp per
+// group.  Group h streams the velocities i = h, h + 2, ... for every pair of
+// the tile (thread (row, pair) writes both nodes' values into its tensor-memory
+// lane); its producer warp fills the group's own ring of nst / 2 stages, so
+// that every stage has one producer and one group of consumers.  After the
+// tile's velocities a barrier of all consumers; then thread (h, pair) collides
+// node h of its pair (one node per thread).
+template <int VS, int NX, int TY, int TZ>
+__global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
+    k_step_rows_pairs(const float2* __restrict__ fg, float2* __restrict__ fgo, const void* __restrict__ maps,
+                      const int32_t* __restrict__ head, const TmRec2* __restrict__ recs,
+                      const uint64_t* __restrict__ xmask, const float* __restrict__ twt, const StepGeom G,
+                      const CollideConst<float> C, const TmGeom2 T, int* __restrict__ status) {
+    using VSET = VelSet<VS>;
+    constexpr int Q = VSET::Q;
+    constexpr int D = VSET::D;
+    constexpr int NR = TY * TZ;                   // rows per tile
+    constexpr int NP = NX / 2;                    // node pairs per row
+    constexpr int NG = NP * NR;                   // threads of one consumer group (one per pair)
+    constexpr int NT = 2 * NG;                    // consumer threads
+    constexpr int NW = NT / 32;                   // consumer warps
+    constexpr int NWG = NW / 2;                   // consumer warps per group
+    constexpr int XBW = NX + 4;                   // halo row of the x exchange
+    constexpr int REC_BYTES = NR * int(sizeof(TmRec2));
+    static_assert(NG == 256 && NW == 16, "two groups of 256 pairs: 512 nodes per tile");
+    static_assert(NP % 32 == 0 && (NP == 32 || 2 * NR <= 14), "whole warps per row; named barriers 1 .. 2 NR");
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    unsigned char* stages = dyn_smem;                                         // [nst][rows | records]
+    float2* XB = reinterpret_cast<float2*>(stages + size_t(T.nst) * T.stage_bytes);   // [group][2][NR][XBW]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(XB + 4 * NR * XBW);
+    // full[nst], empty[nst], and one barrier that nothing completes (waited
+    // on only under a test wait limit, so that the timeout path runs)
+    uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * T.nst + 1);       // TMEM base, abort flag
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(slot + 1);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nsh = T.nst / 2;                                                // stages per ring
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * uint32_t(T.nst);
+    const uint32_t st0 = smem_u32(stages);
+    const int NN = int(G.n_nodes);
+    const int N1 = G.N[1], N2 = D == 3 ? G.N[2] : 1;
+    const bool py = G.periodic[1] != 0;
+    const long long lim = wait_limit(status);
+    if (tid == 0) {
+        for (int s = 0; s < T.nst; ++s) {
+            mbar_init(full0 + 8u * uint32_t(s), 1);
+            mbar_init(empty0 + 8u * uint32_t(s), NWG);
+        }
+        mbar_init(full0 + 16u * uint32_t(T.nst), 1);
+        *abort_flag = 0;
+    }
+    if (warp == 0) {
+        tc_alloc(smem_u32(slot), TM_ALLOC);
+        tc_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(slot);
+    const int my_tiles = int(blockIdx.x) < T.ntiles ? (T.ntiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+
+    if (warp >= NW) {
+        // ------------------------------------------------ producer warps
+        // Producer h issues the velocities of group h, as the sequence
+        // k = (tile, j) with velocity i = h + 2 j, into stages
+        // h nst / 2 + (k mod nst / 2).  The box list of its next velocity is
+        // loaded while the current one is issued.
+        const int h = warp - NW;
+        const int nv = (Q - h + 1) / 2;                       // velocities of this group
+        const int total = my_tiles * nv;
+        int s = 0, ph = 0;
+        long long seq = 0;
+        int cur_tile = -1, y0 = 0, z0 = 0, tc = 0;
+        struct Hd {
+            int n, rows, e, sl, bd;      // boxes, rows; this lane's box, its first slot, its shape
+        };
+        auto fetch = [&](int k) {
+            Hd hd{0, 0, 0, 0, 0};
+            if (k < total) {
+                const int tile = int(blockIdx.x) + (k / nv) * int(gridDim.x), i = h + 2 * (k % nv);
+                const int tcl = py ? 0 : tile % T.ntile_y;
+                const int32_t* hp = head + (size_t(i) * T.n_tc + tcl) * TM2_HEAD;
+                hd.n = __ldg(hp);
+                hd.rows = __ldg(hp + 1);
+                if (lane < TM2_MAX_BOXES) {
+                    hd.e = __ldg(hp + 2 + lane);
+                    hd.sl = __ldg(hp + 2 + TM2_MAX_BOXES + lane);
+                    hd.bd = __ldg(hp + 2 + 2 * TM2_MAX_BOXES + lane);
+                }
+            }
+            return hd;
+        };
+        Hd ha = fetch(0);
+#pragma unroll 1
+        for (int k = 0; k < total; ++k) {
+            const Hd hb = fetch(k + 1);
+            const int kt = k / nv, i = h + 2 * (k - kt * nv);
+            if (kt != cur_tile) {
+                cur_tile = kt;
+                const int tile = int(blockIdx.x) + kt * int(gridDim.x);
+                const int ty = tile % T.ntile_y, tz = tile / T.ntile_y;
+                y0 = ty * TY;
+                z0 = tz * TZ;
+                tc = py ? 0 : ty;
+            }
+            const int sg = h * nsh + s;                        // the stage
+            if (seq >= nsh) {
+                // the stage's previous contents have been read by every warp of the group
+                bool ok = !*abort_flag && mbar_wait(empty0 + 8u * uint32_t(sg), uint32_t(ph ^ 1), lim);
+                // a consumer that gave up still arrives (after setting the
+                // flag): re-read the flag, so that no copy is issued into a
+                // stage whose previous copies may still be in flight
+                ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+                if (!ok) {
+                    if (lane == 0) {
+                        atomicOr(status, SLLBM_DEV_COPY_TIMEOUT);
+                        *abort_flag = 1;
+                    }
+                    break;
+                }
+            }
+            const uint32_t fb = full0 + 8u * uint32_t(sg);
+            const uint32_t sb = st0 + uint32_t(sg) * uint32_t(T.stage_bytes);
+            if (lane == 0) mbar_arrive_expect_tx(fb, uint32_t(ha.rows * NX * 8 + REC_BYTES));
+            __syncwarp();
+            if (lane < ha.n) {
+                // this lane's box: population, first y and z (relative to the
+                // tile), shape (tensor map); rows [slot, slot + by bz) of the stage
+                const int e = ha.e;
+                const int src = min(e & 63, Q - 1), map = (e >> 22) & 63;
+                const int by = ha.bd & 255, bz = ha.bd >> 8;
+                const int ys = y0 + ((e >> 6) & 255) - 128;
+                const int zs = D == 3 ? z0 + ((e >> 14) & 255) - 128 : 0;
+                const uint32_t dst = sb + uint32_t(ha.sl * NX * 8);
+                if (ys >= 0 && ys + by <= N1 && zs >= 0 && zs + bz <= N2) {
+                    tma_load_4d(dst, static_cast<const char*>(maps) + size_t(map) * 128, 0, ys, zs, src, fb);
+                } else {
+                    // a box across a periodic seam: its rows one z at a time,
+                    // each y run in one or two pieces (bulk copies)
+                    for (int dz = 0; dz < bz; ++dz) {
+                        int z = zs + dz;
+                        if (D == 3) {
+                            z += z < 0 ? N2 : 0;
+                            z -= z >= N2 ? N2 : 0;
+                        }
+                        z = min(max(z, 0), N2 - 1);      // every copy stays inside the mesh
+                        const float2* pop = fg + size_t(src) * NN + size_t(z) * N1 * NX;
+                        const uint32_t d = dst + uint32_t(dz * by * NX * 8);
+                        int y = ys;
+                        if (py) {
+                            y += y < 0 ? N1 : 0;
+                            y -= y >= N1 ? N1 : 0;
+                            y = min(max(y, 0), N1 - 1);
+                            const int l1 = min(by, N1 - y);
+                            bulk_g2s(d, pop + size_t(y) * NX, uint32_t(l1 * NX * 8), fb);
+                            if (by > l1) bulk_g2s(d + uint32_t(l1 * NX * 8), pop, uint32_t((by - l1) * NX * 8), fb);
+                        } else {
+                            y = min(max(y, 0), N1 - by);
+                            bulk_g2s(d, pop + size_t(y) * NX, uint32_t(by * NX * 8), fb);
+                        }
+                    }
+                }
+            }
+            if (lane == 31)
+                bulk_g2s(sb + uint32_t(T.rows_bytes), recs + (size_t(i) * T.n_tc + tc) * NR, uint32_t(REC_BYTES),
+                         fb);
+            ++seq;
+            if (++s == nsh) {
+                s = 0;
+                ph ^= 1;
+            }
+            ha = hb;
+        }
+        // on an abort: wait (bounded, default limit) for every copy issued,
+        // so that none lands in shared memory after the CTA has exited
+        if (*abort_flag && lane == 0) {
+            const long long first = seq > nsh ? seq - nsh : 0;
+            for (long long q = first; q < seq; ++q)
+                mbar_wait(full0 + 8u * uint32_t(h * nsh + int(q % nsh)), uint32_t((q / nsh) & 1));
+        }
+    } else {
+        // ------------------------------------------------ consumers
+        // thread (group h, row r, pair xp): nodes x = 2 xp (even) and x + 1
+        // (odd); their 2Q values in columns [0, 96) and [96, 192) of a
+        // 192-column block of the thread's tensor-memory lane, the same lane
+        // and block for both groups (warps w and w + 8)
+        const int h = tid / NG, pt = tid % NG;
+        const int r = pt / NP, xp = pt % NP, x = 2 * xp;
+        const int ry = r % TY, rz = r / TY;
+        const int nv = (Q - h + 1) / 2;
+        const uint32_t tl = tbase + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(2 * TM_COLS * ((warp & 7) >> 2));
+        const uint32_t xb0 = smem_u32(XB) + uint32_t((2 * h * NR + r) * XBW * 8);   // this row's halo row, buffer 0
+        constexpr uint32_t XBB = uint32_t(NR * XBW * 8);                           // bytes of one buffer
+        int s = 0, ph = 0, xb = 0;
+        for (int tile = blockIdx.x; tile < T.ntiles; tile += gridDim.x) {
+            const int ty = tile % T.ntile_y, tz = tile / T.ntile_y;
+            const int y = ty * TY + ry, z = D == 3 ? tz * TZ + rz : 0;
+            const bool real = y < N1;
+            // velocities whose x factor needs the row exchange, for this tile
+            // class: read from global memory, so that every thread of a row
+            // takes the same barriers whatever the stage holds
+            const uint64_t xm = __ldg(xmask + (py ? 0 : ty));
+#pragma unroll 1
+            for (int j = 0; j < nv; ++j) {
+                const int i = h + 2 * j;
+                const int sg = h * nsh + s;
+                const uint32_t fb = full0 + 8u * uint32_t(sg);
+                bool live = !*abort_flag;
+                // under a test wait limit the first velocity also waits on the
+                // barrier that nothing completes (sllbm_debug_wait_limit)
+                if (live && (!mbar_wait(fb, uint32_t(ph), lim) ||
+                             (lim < kWaitLimit && j == 0 && !mbar_wait(full0 + 16u * uint32_t(T.nst), 0, lim)))) {
+                    atomicOr(status, SLLBM_DEV_COPY_TIMEOUT);
+                    *abort_flag = 1;
+                    live = false;
+                }
+                const uint32_t sa = st0 + uint32_t(sg) * uint32_t(T.stage_bytes);
+                const uint32_t ra = sa + uint32_t(T.rows_bytes) + uint32_t(r * int(sizeof(TmRec2)));
+                const bool xc = (xm >> i) & 1;
+                // after an abort the stage may never have been written: nothing
+                // is read from it (an empty equilibrium record instead)
+                int meta = REC_EQ;
+                float2 sa2 = make_float2(0.f, 0.f), sb2 = make_float2(0.f, 0.f), sa2b = sa2, sb2b = sb2;
+                float wxe[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, wxo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                if (live) {
+                    const int4 q0 = lds4(ra), q1 = lds4(ra + 16), q2 = lds4(ra + 32);
+                    meta = q0.x;
+                    const int ntap = q0.y;
+                    if (xc) {
+                        const float4 q5 = lds4f(ra + 80), q6 = lds4f(ra + 96), q7 = lds4f(ra + 112);
+                        wxe[0] = q5.x; wxe[1] = q5.y; wxe[2] = q5.z; wxe[3] = q5.w; wxe[4] = q6.x;
+                        wxo[0] = q6.y; wxo[1] = q6.z; wxo[2] = q6.w; wxo[3] = q7.x; wxo[4] = q7.y;
+                    }
+                    if (ntap > 0) {
+                        const int4 q3 = lds4(ra + 48), q4 = lds4(ra + 64);
+                        const int off[9] = {q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z};
+                        const float w[9] = {__int_as_float(q2.w), __int_as_float(q3.x), __int_as_float(q3.y),
+                                            __int_as_float(q3.z), __int_as_float(q3.w), __int_as_float(q4.x),
+                                            __int_as_float(q4.y), __int_as_float(q4.z), __int_as_float(q4.w)};
+                        const uint32_t bx = sa + uint32_t(16 * xp);
+                        // both nodes' (f, g) per tap in one 16-byte load; two
+                        // accumulators per node (even and odd taps)
+                        auto tap = [&](int k) {
+                            const float4 v = lds4f(bx + uint32_t(SLLBM_CHK(off[k], T.rows_bytes, G.status,
+                                                                             SLLBM_DEV_BAD_SMEM)));
+                            const float2 wk = make_float2(w[k], w[k]);
+                            if (k & 1) {
+                                sa2b = __ffma2_rn(wk, make_float2(v.x, v.y), sa2b);
+                                sb2b = __ffma2_rn(wk, make_float2(v.z, v.w), sb2b);
+                            } else {
+                                sa2 = __ffma2_rn(wk, make_float2(v.x, v.y), sa2);
+                                sb2 = __ffma2_rn(wk, make_float2(v.z, v.w), sb2);
+                            }
+                        };
+                        if (ntap == 9) {
+#pragma unroll
+                            for (int k = 0; k < 9; ++k) tap(k);
+                        } else if (ntap == 3) {
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) tap(k);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 9; ++k)
+                                if (k < ntap) tap(k);
+                        }
+                        sa2 = __fadd2_rn(sa2, sa2b);
+                        sb2 = __fadd2_rn(sb2, sb2b);
+                    }
+                }
+                // this warp has read the stage: release it to the producer
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty0 + 8u * uint32_t(sg));
+                float2 oa = sa2, ob = sb2;
+                if (xc) {
+                    // x factor: each node's three x taps among the six row
+                    // sums x - 2 .. x + 3 (halo row: slot k holds x = k - 2,
+                    // with the periodic images of the first and last two)
+                    const uint32_t xr = xb0 + (xb ? XBB : 0u);
+                    const float4 pr = make_float4(sa2.x, sa2.y, sb2.x, sb2.y);
+                    sts4f(xr + uint32_t(8 * (x + 2)), pr);
+                    if (xp == 0) sts4f(xr + uint32_t(8 * (NX + 2)), pr);
+                    if (xp == NP - 1) sts4f(xr, pr);
+                    if (NP == 32)
+                        __syncwarp();
+                    else
+                        row_bar(1 + r + h * NR, NP);
+                    const float4 w0 = lds4f(xr + uint32_t(8 * x));           // x - 2, x - 1
+                    const float4 w1 = lds4f(xr + uint32_t(8 * (x + 2)));     // x, x + 1
+                    const float4 w2 = lds4f(xr + uint32_t(8 * (x + 4)));     // x + 2, x + 3
+                    const float2 win[6] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w),
+                                           make_float2(w1.x, w1.y), make_float2(w1.z, w1.w),
+                                           make_float2(w2.x, w2.y), make_float2(w2.z, w2.w)};
+                    oa = __fmul2_rn(make_float2(wxe[0], wxe[0]), win[0]);
+                    ob = __fmul2_rn(make_float2(wxo[0], wxo[0]), win[1]);
+#pragma unroll
+                    for (int m = 1; m < 5; ++m) {
+                        oa = __ffma2_rn(make_float2(wxe[m], wxe[m]), win[m], oa);
+                        ob = __ffma2_rn(make_float2(wxo[m], wxo[m]), win[m + 1], ob);
+                    }
+                    xb ^= 1;
+                }
+                const int kind = meta & 15;
+                if (kind != REC_INTERIOR) {
+                    const int bid = SLLBM_CHK((meta >> 4) & 15, 2, G.status, SLLBM_DEV_BAD_REC) & 1;
+                    if (kind == REC_EQ) {
+                        oa = ob = make_float2(C.eqf[bid][i], C.eqg[bid][i]);
+                    } else if (kind == REC_BB || kind == REC_BB_ISO) {
+                        oa.x += C.mw[bid][i];
+                        ob.x += C.mw[bid][i];
+                    }
+                }
+                tm_st2(tl + 2 * i, oa.x, oa.y);
+                tm_st2(tl + TM_COLS + 2 * i, ob.x, ob.y);
+                if (++s == nsh) {
+                    s = 0;
+                    ph ^= 1;
+                }
+            }
+            // both groups' values of the tile are in tensor memory
+            tm_wait_st();
+            tc_fence_before();
+            row_bar(15, NT);
+            tc_fence_after();
+            // thread (h, pair) collides node x + h
+            const int n = x + h + NX * (y + N1 * z);
+            const int cls = G.ncls[0] * ((py ? (y & 1) : (real ? y : 0)) + G.ncls[1] * (D == 3 ? (z & 1) : 0)) + h;
+            const float qnan = __int_as_float(0x7fc00000);
+            collide_tmem<VSET>(C, tl + uint32_t(h * TM_COLS), real ? __ldg(twt + cls) : qnan, fgo + n, NN,
+                               real && !*abort_flag);
+            // every collision has read its node before the next tile's stores
+            tc_fence_before();
+            row_bar(15, NT);
+            tc_fence_after();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tc_dealloc(tbase, TM_ALLOC);
+    }
+}
+
+// shared memory of one CTA: the stages, the x-exchange halo rows, the
+// barriers, the tensor-memory slot; at least 120 KB, so that one CTA resides
+// per SM (each allocates all of the SM's tensor-memory columns)
+inline size_t rows_pairs_smem_bytes(const TmGeom2& T, int nx, int nr) {
+    const size_t b = size_t(T.nst) * T.stage_bytes + sizeof(float2) * 4 * nr * (nx + 4) +
+                     sizeof(uint64_t) * (2 * T.nst + 1) + 16;
+    return b < 120 * 1024 ? 120 * 1024 : b;
+}
+
+template <int VS, int NX, int TY, int TZ>
+int launch_step_rows_pairs(const float2* fg, float2* fgo, const void* maps, const int32_t* head, const TmRec2* recs,
+                           const uint64_t* xmask, const float* tw, const StepGeom& G, const CollideConst<float>& C,
+                           const TmGeom2& T, int* status, cudaStream_t stream, int grid) {
+    const size_t smem = rows_pairs_smem_bytes(T, NX, TY * TZ);
+    if (cudaFuncSetAttribute(k_step_rows_pairs<VS, NX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem)) != cudaSuccess)
+        return SLLBM_ERR_CUDA;
+    k_step_rows_pairs<VS, NX, TY, TZ><<<grid, NX * TY * TZ + 64, smem, stream>>>(fg, fgo, maps, head, recs, xmask, tw,
+                                                                                 G, C, T, status);
+    return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+}
+
+}  // namespace sllbm

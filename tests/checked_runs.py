@@ -39,6 +39,9 @@ def cases():
     from tests.test_gpu_rows_tmem import CASES as TM_CASES
     for name, mk in TM_CASES.items():
         out.append((f"rows_tmem_{name}_m7", mk(), "fp32", 7, None))
+    from tests.test_gpu_rows_tmem import PAIR_CASES
+    for name, mk in PAIR_CASES.items():
+        out.append((f"rows_pairs_{name}_m10", mk(), "fp32", 10, None))
     learned = get_config("learned", cells=8)
     learned["init"] = dict(kind="isentropic_vortex", mach=0.6, seed=3)
     for path in ("tensor", "simt"):

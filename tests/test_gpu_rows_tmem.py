@@ -193,3 +193,96 @@ def test_tensor_core_streaming_fullsize_channel_sampled(built_lib):
     assert worst < 1e-5
     print(f"PARITY tensor-core streaming fullsize channel: {len(nodes)} sampled nodes, populations {worst:.2e}")
     sim.close()
+
+
+PAIR_CASES = {
+    "channel_nx128": lambda: get_config("channel", cells=(64, 3, 3)),      # 2 x 2 rows of 128, ragged y tile
+    "channel_nx64": lambda: get_config("channel", cells=(32, 3, 2)),       # 4 x 2 rows of 64
+    "mixing_nx64": lambda: get_config("mixing", cells=(32, 4, 2)),         # equilibrium boundaries in y
+    "mixing_nx128": lambda: get_config("mixing", cells=(64, 4, 3)),
+    "box_d2q19_nx64": lambda: get_config("learned", cells=32),             # 2D, 8 rows per tile, periodic y
+    "box_d2q19_nx128": lambda: get_config("learned", cells=64),            # 2D, 4 rows per tile
+}
+
+
+@pytest.mark.parametrize("name", list(PAIR_CASES))
+def test_rows_pairs_matches_oracle(built_lib, name):
+    """SLLBM_STREAM_ROWS_PAIRS: two arrival nodes per consumer thread, one
+    TMA tensor copy per source population and velocity (bulk copies row by
+    row across a periodic seam); 3 steps against the oracle at the FP32
+    tolerance."""
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = PAIR_CASES[name]()
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    sim = Sim(cfg, precision="fp32", stream_mode=10)
+    assert sim.info.stream_mode == 10, "the two-nodes-per-thread kernel must be eligible for this mesh"
+    rho, u, T = initial_fields(cfg, mesh.X)
+    sim.init_state(rho, u, T)
+    f, g = ost.init_equilibrium(rho, u, T, xi, w, par.cv)
+    Tw = ost.isothermal_nodes(rec, par)
+    worst = 0.0
+    for k in range(3):
+        f, g = ost.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
+        sim.step(1)
+        assert sim.step_kernel() == "k_step_rows_pairs"
+        fg, gg = sim.get_state()
+        ef, eg = _scale_err(fg, f, w), _scale_err(gg, g, w)
+        assert ef < 1e-5 and eg < 1e-5, (k, ef, eg)
+        worst = max(worst, ef, eg)
+    assert sim.device_status() == 0
+    print(f"PARITY rows_pairs {name} {mesh.N}: populations {worst:.2e}")
+    sim.close()
+
+
+def test_rows_pairs_agrees_with_rows_tmem(built_lib):
+    """5 channel steps against the one-node-per-thread row-tile kernel: the
+    same step up to FP32 summation order."""
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = get_config("channel", cells=(64, 6, 4))
+    a, b = Sim(cfg, stream_mode=10), Sim(cfg, stream_mode=MODE)
+    X = a.node_coords()
+    rho, u, T = initial_fields(cfg, X)
+    for s in (a, b):
+        s.init_state(rho, u, T)
+        s.step(5)
+    assert a.step_kernel() == "k_step_rows_pairs" and b.step_kernel() == "k_step_rows_tmem"
+    fa, ga = a.get_state()
+    fb, gb = b.get_state()
+    _, w, _ = a.velocity_set()
+    ef, eg = _scale_err(fa, fb, w), _scale_err(ga, gb, w)
+    assert ef < 1e-5 and eg < 1e-5, (ef, eg)
+    assert a.device_status() == 0
+    print(f"PARITY rows_pairs vs rows_tmem, 5 channel steps: {max(ef, eg):.2e}")
+    a.close()
+    b.close()
+
+
+def test_rows_pairs_fullsize_channel_sampled(built_lib):
+    """The benchmark's channel (128 x 97 x 96 nodes) with two nodes per
+    thread: one step from the seeded state, sampled nodes (random, both
+    walls) computed by the oracle."""
+    from oracle.departure import trace
+    from oracle.mesh import Mesh
+    from oracle.velocity_sets import velocity_set
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = get_config("channel")
+    m = cfg["mesh"]
+    mesh = Mesh(m["kind"], m["p"], m["cells"], m["length"], m.get("stretch", 1.0), m.get("central", 0))
+    xi, w, opp = velocity_set(cfg["velset"])
+    par = ost.Params(cfg["dt"], cfg["gamma"], cfg["Pr"], cfg["mu_ref"], cfg["T_ref"], cfg["mu_exp"], cfg["bcs"])
+    rho, u, T = initial_fields(cfg, mesh.X)
+    rng = np.random.default_rng(14)
+    nodes = np.unique(np.concatenate([rng.integers(0, mesh.n_nodes, 60), np.arange(40),
+                                      mesh.n_nodes - 1 - np.arange(40)]))
+    rec = trace(mesh, xi, opp, cfg["dt"], cfg["bcs"], nodes=nodes)
+    f1, g1 = ost.step_sample_from_fields(mesh, rec, rho, u, T, xi, w, par)
+    sim = Sim(cfg, stream_mode=10)
+    assert sim.info.stream_mode == 10
+    sim.init_state(rho, u, T)
+    sim.step(1)
+    assert sim.step_kernel() == "k_step_rows_pairs"
+    fg, gg = sim.get_state()
+    worst = max(_scale_err(fg[:, nodes], f1, w), _scale_err(gg[:, nodes], g1, w))
+    assert worst < 1e-5
+    print(f"PARITY rows_pairs fullsize channel: {len(nodes)} sampled nodes, populations {worst:.2e}")
+    sim.close()

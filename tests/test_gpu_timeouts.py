@@ -75,28 +75,32 @@ def test_bulk_copy_wait_timeout_is_reported_and_recoverable(built_lib, name, cel
     ref.close()
 
 
-@pytest.mark.parametrize("name,cells", [("channel", (32, 3, 3)), ("learned", 16)])
-def test_row_tile_wait_timeout_is_reported_and_recoverable(built_lib, name, cells):
-    """The tensor-memory row-tile kernel (SLLBM_STREAM_ROWS_TMEM): under the
-    test limit its consumers also wait on a barrier that nothing completes,
+@pytest.mark.parametrize("name,cells,mode,kernel", [("channel", (32, 3, 3), 7, "k_step_rows_tmem"),
+                                                    ("learned", 16, 7, "k_step_rows_tmem"),
+                                                    ("channel", (32, 3, 2), 10, "k_step_rows_pairs"),
+                                                    ("learned", 32, 10, "k_step_rows_pairs")])
+def test_row_tile_wait_timeout_is_reported_and_recoverable(built_lib, name, cells, mode, kernel):
+    """The tensor-memory row-tile kernels (SLLBM_STREAM_ROWS_TMEM and
+    SLLBM_STREAM_ROWS_PAIRS): under the test limit their consumers also wait on a barrier that nothing completes,
     record the timeout, stop waiting and storing; the producers wait (with
     the default limit) for the copies they issued; the CTA frees its tensor
     memory and exits."""
     from paper_2412_09051_gb300 import capi
     from paper_2412_09051_gb300.sim import Sim
     cfg = get_config(name, cells=cells)
-    s = Sim(cfg, stream_mode=capi.STREAM_ROWS_TMEM)
+    s = Sim(cfg, stream_mode=mode)
+    assert s.info.stream_mode == mode
     X = s.node_coords()
     s.init_state(*initial_fields(cfg, X))
     s.debug_wait_limit(1)
     s.step(1)
-    assert s.step_kernel() == "k_step_rows_tmem"
+    assert s.step_kernel() == kernel
     assert s.device_status() & capi.DEV_COPY_TIMEOUT
     s.debug_wait_limit(0)
     s.init_state(*initial_fields(cfg, X))
     s.step(2)
     assert s.device_status() == 0
-    ref = Sim(cfg, stream_mode=capi.STREAM_ROWS_TMEM)
+    ref = Sim(cfg, stream_mode=mode)
     ref.init_state(*initial_fields(cfg, X))
     ref.step(2)
     assert np.array_equal(s.get_state_raw(), ref.get_state_raw())
