@@ -127,7 +127,8 @@ extern "C" {
                                        memory and stages every source row a tile reads once in
                                        shared memory with the bulk-copy (TMA) engine.  With
                                        D3Q45, SLLBM_STREAM_AUTO and SLLBM_STREAM_STRUCTURED use
-                                       this kernel wherever it applies                           */
+                                       this kernel where SLLBM_STREAM_ROWS_PAIRS does not apply
+                                       (rows of 32 nodes)                                        */
 #define SLLBM_STREAM_ROW_SMEM    8  /* as SLLBM_STREAM_STRUCTURED without the tensor-memory
                                        row-tile kernel (the one-block-per-row and warp-tiled
                                        kernels): for comparisons                                 */
@@ -142,10 +143,13 @@ extern "C" {
                                        (elsewhere as SLLBM_STREAM_ROWS_TMEM), opt-in: slower than
                                        the CUDA-core contraction                                 */
 #define SLLBM_STREAM_ROWS_PAIRS 10  /* the SLLBM_STREAM_ROWS_TMEM design with two arrival nodes
-                                       (x even, x + 1) per consumer thread and one TMA tensor copy
-                                       per (source population, velocity, tile): D3Q45 rows of 64
-                                       or 128 nodes, D2Q19 rows of 64 or 128, periodic x and z
-                                       (elsewhere as SLLBM_STREAM_ROWS_TMEM)                     */
+                                       (x even, x + 1) per consumer thread while streaming, one
+                                       TMA tensor copy per (source population, velocity, tile) and
+                                       stages of up to six velocities: D3Q45 rows of 64 or 128
+                                       nodes, D2Q19 rows of 64 or 128, periodic x and z (elsewhere
+                                       as SLLBM_STREAM_ROWS_TMEM).  With D3Q45,
+                                       SLLBM_STREAM_AUTO and SLLBM_STREAM_STRUCTURED use this
+                                       kernel wherever it applies                                */
 
 /* ------------------------------------------------------------------ descriptors */
 typedef struct {

@@ -97,8 +97,9 @@ bool rows_tmem_shape(int D, int nx, int& ty, int& tz);
 bool rows_pairs_shape(int D, int nx, int& ty, int& tz);
 size_t rows_pairs_smem(int D, int nx, const TmGeom2& T);
 int launch_rows_pairs(int vs, int nx, const float2* fg, float2* fgo, const void* maps, const int32_t* head,
-                      const TmRec2* recs, const uint64_t* xmask, const float* tw, const StepGeom& G,
-                      const CollideConst<float>& C, const TmGeom2& T, int* status, cudaStream_t s, int grid);
+                      const TmRec2* recs, const uint64_t* xmask, const uint64_t* smask, const float* tw,
+                      const StepGeom& G, const CollideConst<float>& C, const TmGeom2& T, int* status, cudaStream_t s,
+                      int grid);
 size_t rows_tmem_smem_bytes(int D, int nx, const TmGeom& T);
 int launch_rows_tmem(int vs, int nx, const float2* fg, float2* fgo, const float* bop, const int32_t* head,
                      const TmRec* recs, const uint64_t* xmask, const float* tw, const StepGeom& G,
@@ -550,7 +551,7 @@ bool build_rows_tmem(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::ve
 // weights of its even and odd nodes over six row sums; per tile class the
 // velocities whose x factor is not the identity.  False where it does not apply.
 bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::vector<int32_t>& head,
-                      std::vector<TmRec2>& recs, std::vector<uint64_t>& xmask) {
+                      std::vector<TmRec2>& recs, std::vector<uint64_t>& xmask, std::vector<uint64_t>& smask) {
     const HostMesh& m = c->mesh;
     const StepGeom& G = c->geom;
     const int Q = c->vs.Q, D = m.D, NX = m.N[0], N1 = m.N[1], N2 = D == 3 ? m.N[2] : 1;
@@ -628,7 +629,7 @@ bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::v
                 for (size_t k = 0; k < shapes.size(); ++k)
                     if (shapes[k] == (ny | (nz << 8))) map = int(k);
                 if (map < 0) {
-                    if (int(shapes.size()) == TM2_MAX_MAPS) return false;
+                    if (int(shapes.size()) == TM2_MAX_MAPS - 1) return false;     // one map left for the records
                     map = int(shapes.size());
                     shapes.push_back(ny | (nz << 8));
                 }
@@ -678,14 +679,65 @@ bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::v
             }
             if (xchg) xmask[tc] |= uint64_t(1) << i;
         }
-    T.rows_bytes = max_rows * NX * 8;
-    T.stage_bytes = T.rows_bytes + NR * int(sizeof(TmRec2));
+    // Stages: two rings (one per consumer group) of two stages of `cap` rows
+    // and the records of up to TM2_MAX_VEL velocities (measured on the
+    // channel: two large stages per ring beat three smaller ones)
+    const int rec_bytes = NR * int(sizeof(TmRec2));
     const size_t fixed = sizeof(float2) * 4 * NR * (NX + 4) + 8 + 16;     // two halo rows per group
     const size_t budget = 227 * 1024;
-    int nst = int((budget - fixed) / (size_t(T.stage_bytes) + 16));
-    nst = std::min(nst, 16) & ~1;          // two rings (one per consumer group) of nst / 2 stages
-    if (nst < 4) return false;
+    int cap = 0, nst = 0;
+    for (int n : {4}) {
+        const long long room = (static_cast<long long>(budget) - static_cast<long long>(fixed)) / n - 16 -
+                               TM2_MAX_VEL * rec_bytes;
+        const int k = int(std::max(0LL, room) / (NX * 8));
+        if (k >= max_rows) {
+            cap = k;
+            nst = n;
+            break;
+        }
+    }
+    if (!nst) return false;
+    // pack each group's velocities (i = h, h + 2, ...) into stages, per tile
+    // class: consecutive velocities while their rows fit `cap`; a velocity's
+    // slots and its records' tap offsets move by the rows before it
+    smask.assign(size_t(2) * T.n_tc, 0);
+    for (int tc = 0; tc < T.n_tc; ++tc)
+        for (int hg = 0; hg < 2; ++hg) {
+            const int nv = (Q - hg + 1) / 2;
+            int j0 = 0;
+            while (j0 < nv) {
+                int rows = 0, n = 0;
+                while (j0 + n < nv && n < TM2_MAX_VEL) {
+                    const int i = hg + 2 * (j0 + n);
+                    const int r_i = head[(size_t(i) * T.n_tc + tc) * TM2_HEAD + 1];
+                    if (rows + r_i > cap) break;
+                    rows += r_i;
+                    ++n;
+                }
+                if (n == 0) return false;
+                smask[size_t(tc) * 2 + hg] |= uint64_t(1) << j0;
+                int base = 0;
+                for (int q = 0; q < n; ++q) {
+                    const int i = hg + 2 * (j0 + q);
+                    int32_t* h = &head[(size_t(i) * T.n_tc + tc) * TM2_HEAD];
+                    for (int b = 0; b < h[0]; ++b) h[2 + TM2_MAX_BOXES + b] += base;
+                    for (int r = 0; r < NR; ++r) {
+                        TmRec2& ro = recs[(size_t(i) * T.n_tc + tc) * NR + r];
+                        if ((ro.meta & 15) == REC_EQ) continue;
+                        for (int k = 0; k < ro.ntap; ++k) ro.off[k] += base * NX * 8;
+                    }
+                    base += h[1];
+                }
+                int32_t* h0 = &head[(size_t(hg + 2 * j0) * T.n_tc + tc) * TM2_HEAD];
+                h0[14] = 1 | (n << 8);
+                h0[15] = rows * NX * 8 + n * rec_bytes;
+                j0 += n;
+            }
+        }
+    T.rows_bytes = cap * NX * 8;
+    T.stage_bytes = T.rows_bytes + TM2_MAX_VEL * rec_bytes;
     T.nst = nst;
+    T.rec_map = int(shapes.size());
     c->tm2 = T;
     c->tm2_box = shapes;
     return true;
@@ -693,7 +745,8 @@ bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::v
 
 // TMA tensor maps of the two-nodes-per-thread row-tile kernel: state buffer b
 // viewed as the 4D FP32 tensor [Q][Nz][Ny][2 NX] (innermost last), one map
-// per box shape {2 NX, rows along y, rows along z, 1}; maps[b * shapes + k].
+// per box shape {2 NX, rows along y, rows along z, 1}, then one of the
+// records; maps[b * (shapes + 1) + k].
 // The encoder comes from the driver through the runtime's entry-point query.
 int encode_tm2_maps(sllbm_ctx* c) {
     const HostMesh& m = c->mesh;
@@ -706,8 +759,22 @@ int encode_tm2_maps(sllbm_ctx* c) {
         return fail(c, SLLBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     const int nm = int(c->tm2_box.size());
-    std::vector<CUtensorMap> maps(size_t(2) * nm);
-    for (int b = 0; b < 2; ++b)
+    int ty = 0, tz = 0;
+    rows_pairs_shape(m.D, NX, ty, tz);
+    std::vector<CUtensorMap> maps(size_t(2) * (nm + 1));
+    for (int b = 0; b < 2; ++b) {
+        // the records [Q][n_tc][TY TZ] of 128 bytes as FP32 [Q][n_tc][TY TZ][32]:
+        // one box per (velocity, tile class)
+        const cuuint64_t rdims[4] = {32, cuuint64_t(ty * tz), cuuint64_t(c->tm2.n_tc), cuuint64_t(Q)};
+        const cuuint64_t rstrides[3] = {128, cuuint64_t(128) * ty * tz, cuuint64_t(128) * ty * tz * c->tm2.n_tc};
+        const cuuint32_t rbox[4] = {32, cuuint32_t(ty * tz), 1, 1};
+        const cuuint32_t res[4] = {1, 1, 1, 1};
+        const CUresult rr = enc(&maps[size_t(b) * (nm + 1) + nm], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->tm2_recs,
+                                rdims, rstrides, rbox, res, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (rr != CUDA_SUCCESS)
+            return fail(c, SLLBM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the records (code " +
+                                               std::to_string(int(rr)) + ")");
         for (int k = 0; k < nm; ++k) {
             const cuuint64_t dims[4] = {cuuint64_t(2 * NX), cuuint64_t(N1), cuuint64_t(N2), cuuint64_t(Q)};
             const cuuint64_t strides[3] = {cuuint64_t(2 * NX) * 4, cuuint64_t(2 * NX) * N1 * 4,
@@ -715,12 +782,13 @@ int encode_tm2_maps(sllbm_ctx* c) {
             const cuuint32_t box[4] = {cuuint32_t(2 * NX), cuuint32_t(c->tm2_box[k] & 255),
                                        cuuint32_t(c->tm2_box[k] >> 8), 1};
             const cuuint32_t es[4] = {1, 1, 1, 1};
-            const CUresult r = enc(&maps[size_t(b) * nm + k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->fg[b], dims,
-                                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            const CUresult r = enc(&maps[size_t(b) * (nm + 1) + k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->fg[b],
+                                   dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS)
                 return fail(c, SLLBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string(int(r)) + ")");
         }
+    }
     cudaError_t e = cudaMalloc(&c->tm2_maps, sizeof(CUtensorMap) * maps.size());
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
     e = cudaMemcpyAsync(c->tm2_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
@@ -739,10 +807,10 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
             ctx->step_kernel = "k_step_rows_pairs";
             const int b = static_cast<const void*>(L.fg) == ctx->fg[0] ? 0 : 1;
             const char* maps = static_cast<const char*>(ctx->tm2_maps) +
-                               size_t(b) * ctx->tm2_box.size() * sizeof(CUtensorMap);
+                               size_t(b) * (ctx->tm2_box.size() + 1) * sizeof(CUtensorMap);
             return launch_rows_pairs(vs, ctx->mesh.N[0], L.fg, L.fgo, maps, ctx->tm2_head,
-                                     static_cast<const TmRec2*>(ctx->tm2_recs), ctx->tm_xmask, L.tw, L.G, *L.C,
-                                     ctx->tm2, ctx->d_status, L.stream, ctx->tm_grid);
+                                     static_cast<const TmRec2*>(ctx->tm2_recs), ctx->tm_xmask, ctx->tm2_smask, L.tw,
+                                     L.G, *L.C, ctx->tm2, ctx->d_status, L.stream, ctx->tm_grid);
         }
         if (st && ctx->rows_tmem && !ctx->row_copy) {
             ctx->step_kernel = ctx->tm.kp ? "k_step_rows_tmem_tc" : "k_step_rows_tmem";
@@ -1013,7 +1081,7 @@ int sllbm_destroy(sllbm_ctx* ctx) {
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->row_tab, ctx->d_red, ctx->d_flag,
                     ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status,
                     ctx->d_plane, ctx->d_cp, ctx->d_plane_acc, ctx->tm_head, ctx->tm_recs, ctx->tm_xmask,
-                    ctx->tm_bop, ctx->d_layers, ctx->tm2_head, ctx->tm2_recs, ctx->tm2_maps};
+                    ctx->tm_bop, ctx->d_layers, ctx->tm2_head, ctx->tm2_recs, ctx->tm2_maps, ctx->tm2_smask};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -1082,14 +1150,16 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
         ctx->row_copy = true;
         mode = SLLBM_STREAM_STRUCTURED;
     }
-    // the row-tile kernel with the node state in tensor memory: requested
+    // the row-tile kernels with the node state in tensor memory: requested
     // explicitly, or by default for the 45-velocity set on structured meshes
-    // (faster there; the one-block-per-row kernel stays the default in 2D)
-    if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_TENSOR || mode == SLLBM_STREAM_ROWS_PAIRS ||
-        ((mode == SLLBM_STREAM_AUTO || mode == SLLBM_STREAM_STRUCTURED) && velset == SLLBM_D3Q45))
+    // (faster there; the one-block-per-row kernel stays the default in 2D):
+    // two nodes per thread where the rows allow it (64 or 128 nodes), else
+    // one node per thread
+    const bool d3_default = (mode == SLLBM_STREAM_AUTO || mode == SLLBM_STREAM_STRUCTURED) && velset == SLLBM_D3Q45;
+    if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_TENSOR || mode == SLLBM_STREAM_ROWS_PAIRS || d3_default)
         ctx->want_tmem = true;
     ctx->want_tc = mode == SLLBM_STREAM_TENSOR;
-    ctx->want_tm2 = mode == SLLBM_STREAM_ROWS_PAIRS;
+    ctx->want_tm2 = mode == SLLBM_STREAM_ROWS_PAIRS || d3_default;
     if (mode == SLLBM_STREAM_ROWS_TMEM || mode == SLLBM_STREAM_ROW_SMEM || mode == SLLBM_STREAM_TENSOR ||
         mode == SLLBM_STREAM_ROWS_PAIRS)
         mode = SLLBM_STREAM_STRUCTURED;
@@ -1295,7 +1365,11 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
                     std::vector<uint64_t> tx;
                     std::vector<float> tb;
                     std::vector<TmRec2> tr2;
-                    if (ctx->want_tm2 && build_rows_pairs(ctx, t, th, tr2, tx)) {
+                    std::vector<uint64_t> ts;
+                    if (ctx->want_tm2 && build_rows_pairs(ctx, t, th, tr2, tx, ts)) {
+                        CK(cudaMalloc(&ctx->tm2_smask, sizeof(uint64_t) * ts.size()));
+                        CK(cudaMemcpyAsync(ctx->tm2_smask, ts.data(), sizeof(uint64_t) * ts.size(),
+                                           cudaMemcpyHostToDevice, s));
                         CK(cudaMalloc(&ctx->tm2_head, sizeof(int32_t) * th.size()));
                         CK(cudaMalloc(&ctx->tm2_recs, sizeof(TmRec2) * tr2.size()));
                         CK(cudaMalloc(&ctx->tm_xmask, sizeof(uint64_t) * tx.size()));

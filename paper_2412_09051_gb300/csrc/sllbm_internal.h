@@ -156,17 +156,20 @@ struct alignas(16) TmRec2 {
 static_assert(sizeof(TmRec2) == 128, "eight 16-byte loads per record");
 
 constexpr int TM2_MAX_BOXES = 4;     // boxes (one per source population) per (velocity, tile class)
-constexpr int TM2_HEAD = 16;         // ints per copy list: boxes, rows, per box: entry, first slot,
-                                     // rows along y | along z << 8 (2 + 3 * 4 = 14, padded)
+constexpr int TM2_MAX_VEL = 6;       // velocities per stage
+constexpr int TM2_HEAD = 16;         // ints per copy list: boxes, rows, per box: entry, first slot in
+                                     // the stage, rows along y | along z << 8 (2 + 3 * 4 = 14); then
+                                     // stage start | velocities of the stage << 8, the stage's bytes
 constexpr int TM2_MAX_ROWS = 64;     // rows of one velocity's boxes
 constexpr int TM2_MAX_MAPS = 32;     // box shapes (tensor maps)
 
 struct TmGeom2 {
     int ntile_y, ntile_z, ntiles;    // tiles along y, along z, total
     int n_tc;                        // tile classes (y tiles on a non-periodic y axis, else 1)
-    int nst;                         // pipeline stages, a multiple of the 2 producer warps
-    int rows_bytes;                  // bytes of source rows per stage (max rows x NX x 8)
-    int stage_bytes;                 // rows_bytes + the tile's records
+    int nst;                         // pipeline stages: two rings (one per consumer group) of nst / 2
+    int rows_bytes;                  // bytes of source rows per stage (its row capacity x NX x 8)
+    int stage_bytes;                 // rows_bytes + the records of TM2_MAX_VEL velocities
+    int rec_map;                     // index of the records' tensor map
 };
 
 // one box of a copy list: population, first y and z relative to the tile
@@ -215,6 +218,7 @@ struct sllbm_ctx {
     bool rows_tm2 = false;               // tables of the two-nodes-per-thread row-tile kernel built
     sllbm::TmGeom2 tm2{};
     int32_t* tm2_head = nullptr;         // box lists [Q][n_tc][TM2_HEAD]
+    uint64_t* tm2_smask = nullptr;       // stage starts per (tile class, consumer group), bit j: velocity j
     void* tm2_recs = nullptr;            // TmRec2 [Q][n_tc][TY TZ]
     void* tm2_maps = nullptr;            // TMA tensor maps [2 state buffers][box shapes]
     std::vector<int> tm2_box;            // box shapes: rows along y | rows along z << 8

@@ -24,11 +24,13 @@ size_t rows_pairs_smem(int D, int nx, const TmGeom2& T) {
 }
 
 int launch_rows_pairs(int vs, int nx, const float2* fg, float2* fgo, const void* maps, const int32_t* head,
-                      const TmRec2* recs, const uint64_t* xmask, const float* tw, const StepGeom& G,
-                      const CollideConst<float>& C, const TmGeom2& T, int* status, cudaStream_t s, int grid) {
-#define TPCASE(VS, NX, TY, TZ) \
-    if (vs == VS && nx == NX)  \
-        return launch_step_rows_pairs<VS, NX, TY, TZ>(fg, fgo, maps, head, recs, xmask, tw, G, C, T, status, s, grid);
+                      const TmRec2* recs, const uint64_t* xmask, const uint64_t* smask, const float* tw,
+                      const StepGeom& G, const CollideConst<float>& C, const TmGeom2& T, int* status, cudaStream_t s,
+                      int grid) {
+#define TPCASE(VS, NX, TY, TZ)                                                                                  \
+    if (vs == VS && nx == NX)                                                                                   \
+        return launch_step_rows_pairs<VS, NX, TY, TZ>(fg, fgo, maps, head, recs, xmask, smask, tw, G, C, T, status, \
+                                                      s, grid);
     TPCASE(3, 128, 2, 2)
     TPCASE(3, 64, 4, 2)
     TPCASE(1, 128, 4, 1)

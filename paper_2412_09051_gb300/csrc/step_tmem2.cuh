@@ -2,17 +2,23 @@
 // step_tmem.cuh (persistent CTAs owning tiles of TY x TZ whole periodic x
 // rows, the 2Q streamed values of every node in tensor memory, the source
 // rows of each velocity staged once per tile in shared memory) with
-//   * one consumer thread per pair of x nodes (x even, x + 1): one stage wait,
-//     one row record (the (y, z) taps are the same for both x parities) and
-//     16-byte tap loads serve two nodes, and the x factor of both comes from
-//     a window of six row sums read as three 16-byte loads;
+//   * one consumer thread per pair of x nodes (x even, x + 1) while
+//     streaming: one record (the (y, z) taps are the same for both x
+//     parities) and 16-byte tap loads serve two nodes, and the x factor of
+//     both comes from a window of six row sums read as three 16-byte loads;
+//     two consumer groups take alternate velocities, then every consumer
+//     thread collides one node;
 //   * one TMA tensor copy per source population and velocity: the union of a
 //     tile's (y, z) taps of one population is a box of rows (y range x z
 //     range: each row's taps are a product of y and z offsets), copied with
 //     cp.async.bulk.tensor over the state viewed as [Q][Nz][Ny][2 NX] FP32
-//     (row by row with bulk copies where a box crosses a periodic seam).
-// Collision: collide_tmem (step_tmem.cuh) once per node of the pair.  Every
-// wait is bounded, with the abort protocol of step_tmem.cuh.
+//     (row by row with bulk copies where a box crosses a periodic seam);
+//   * stages of up to six consecutive velocities of a group, whose boxes and
+//     records one producer warp issues in a single instruction (one lane per
+//     copy): the copy engine's cost is per issuing instruction far more than
+//     per byte, so few large stages move the rows fastest.
+// Collision: collide_tmem (step_tmem.cuh).  Every wait is bounded, with the
+// abort protocol of step_tmem.cuh.
 #pragma once
 #include "step_tmem.cuh"
 
@@ -58,8 +64,9 @@ template <int VS, int NX, int TY, int TZ>
 __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
     k_step_rows_pairs(const float2* __restrict__ fg, float2* __restrict__ fgo, const void* __restrict__ maps,
                       const int32_t* __restrict__ head, const TmRec2* __restrict__ recs,
-                      const uint64_t* __restrict__ xmask, const float* __restrict__ twt, const StepGeom G,
-                      const CollideConst<float> C, const TmGeom2 T, int* __restrict__ status) {
+                      const uint64_t* __restrict__ xmask, const uint64_t* __restrict__ smask,
+                      const float* __restrict__ twt, const StepGeom G, const CollideConst<float> C, const TmGeom2 T,
+                      int* __restrict__ status) {
     using VSET = VelSet<VS>;
     constexpr int Q = VSET::Q;
     constexpr int D = VSET::D;
@@ -110,48 +117,50 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
 
     if (warp >= NW) {
         // ------------------------------------------------ producer warps
-        // Producer h issues the velocities of group h, as the sequence
-        // k = (tile, j) with velocity i = h + 2 j, into stages
-        // h nst / 2 + (k mod nst / 2).  The box list of its next velocity is
-        // loaded while the current one is issued.
+        // Producer h issues the stages of group h (velocities i = h + 2 j)
+        // into stages h nst / 2 + (stage count mod nst / 2), all copies of a
+        // stage in one instruction: lane 4 q + b the box b of the stage's
+        // velocity q, lane 4 TM2_MAX_VEL + q that velocity's records.  The
+        // head of its next stage is loaded while the current one is issued.
         const int h = warp - NW;
         const int nv = (Q - h + 1) / 2;                       // velocities of this group
         const int total = my_tiles * nv;
+        constexpr int LB = 4 * TM2_MAX_VEL;                   // lanes of the boxes
+        static_assert(TM2_MAX_BOXES == 4 && 5 * TM2_MAX_VEL <= 32, "one lane per copy");
+        const int q = lane < LB ? (lane >> 2) : lane - LB;    // this lane's velocity in the stage
+        const int b = lane & 3;                               // this lane's box
         int s = 0, ph = 0;
         long long seq = 0;
-        int cur_tile = -1, y0 = 0, z0 = 0, tc = 0;
-        struct Hd {
-            int n, rows, e, sl, bd;      // boxes, rows; this lane's box, its first slot, its shape
-        };
+        struct Sd {
+            int nvs, bytes, tile, i, n, e, sl, bd;   // velocities, bytes, tile; this lane's velocity, its
+        };                                           // boxes, this lane's box, its first slot, its shape
         auto fetch = [&](int k) {
-            Hd hd{0, 0, 0, 0, 0};
+            Sd d{1, 0, 0, 0, 0, 0, 0, 0};
             if (k < total) {
-                const int tile = int(blockIdx.x) + (k / nv) * int(gridDim.x), i = h + 2 * (k % nv);
-                const int tcl = py ? 0 : tile % T.ntile_y;
-                const int32_t* hp = head + (size_t(i) * T.n_tc + tcl) * TM2_HEAD;
-                hd.n = __ldg(hp);
-                hd.rows = __ldg(hp + 1);
-                if (lane < TM2_MAX_BOXES) {
-                    hd.e = __ldg(hp + 2 + lane);
-                    hd.sl = __ldg(hp + 2 + TM2_MAX_BOXES + lane);
-                    hd.bd = __ldg(hp + 2 + 2 * TM2_MAX_BOXES + lane);
+                const int kt = k / nv, j0 = k - kt * nv;
+                d.tile = int(blockIdx.x) + kt * int(gridDim.x);
+                const int tcl = py ? 0 : d.tile % T.ntile_y;
+                const int32_t* h0 = head + (size_t(h + 2 * j0) * T.n_tc + tcl) * TM2_HEAD;
+                d.nvs = max(__ldg(h0 + 14) >> 8, 1);
+                d.bytes = __ldg(h0 + 15);
+                if (lane < LB + TM2_MAX_VEL && q < d.nvs) {
+                    d.i = h + 2 * (j0 + q);
+                    const int32_t* hp = head + (size_t(d.i) * T.n_tc + tcl) * TM2_HEAD;
+                    d.n = __ldg(hp);
+                    if (lane < LB && b < d.n) {
+                        d.e = __ldg(hp + 2 + b);
+                        d.sl = __ldg(hp + 2 + TM2_MAX_BOXES + b);
+                        d.bd = __ldg(hp + 2 + 2 * TM2_MAX_BOXES + b);
+                    }
                 }
             }
-            return hd;
+            return d;
         };
-        Hd ha = fetch(0);
+        Sd da = fetch(0);
 #pragma unroll 1
-        for (int k = 0; k < total; ++k) {
-            const Hd hb = fetch(k + 1);
-            const int kt = k / nv, i = h + 2 * (k - kt * nv);
-            if (kt != cur_tile) {
-                cur_tile = kt;
-                const int tile = int(blockIdx.x) + kt * int(gridDim.x);
-                const int ty = tile % T.ntile_y, tz = tile / T.ntile_y;
-                y0 = ty * TY;
-                z0 = tz * TZ;
-                tc = py ? 0 : ty;
-            }
+        for (int k = 0; k < total;) {
+            const int kn = k + da.nvs;
+            const Sd db = fetch(kn);
             const int sg = h * nsh + s;                        // the stage
             if (seq >= nsh) {
                 // the stage's previous contents have been read by every warp of the group
@@ -170,62 +179,77 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             }
             const uint32_t fb = full0 + 8u * uint32_t(sg);
             const uint32_t sb = st0 + uint32_t(sg) * uint32_t(T.stage_bytes);
-            if (lane == 0) mbar_arrive_expect_tx(fb, uint32_t(ha.rows * NX * 8 + REC_BYTES));
+            if (lane == 0) mbar_arrive_expect_tx(fb, uint32_t(da.bytes));
             __syncwarp();
-            if (lane < ha.n) {
-                // this lane's box: population, first y and z (relative to the
-                // tile), shape (tensor map); rows [slot, slot + by bz) of the stage
-                const int e = ha.e;
-                const int src = min(e & 63, Q - 1), map = (e >> 22) & 63;
-                const int by = ha.bd & 255, bz = ha.bd >> 8;
-                const int ys = y0 + ((e >> 6) & 255) - 128;
-                const int zs = D == 3 ? z0 + ((e >> 14) & 255) - 128 : 0;
-                const uint32_t dst = sb + uint32_t(ha.sl * NX * 8);
-                if (ys >= 0 && ys + by <= N1 && zs >= 0 && zs + bz <= N2) {
-                    tma_load_4d(dst, static_cast<const char*>(maps) + size_t(map) * 128, 0, ys, zs, src, fb);
-                } else {
-                    // a box across a periodic seam: its rows one z at a time,
-                    // each y run in one or two pieces (bulk copies)
-                    for (int dz = 0; dz < bz; ++dz) {
-                        int z = zs + dz;
-                        if (D == 3) {
-                            z += z < 0 ? N2 : 0;
-                            z -= z >= N2 ? N2 : 0;
-                        }
-                        z = min(max(z, 0), N2 - 1);      // every copy stays inside the mesh
-                        const float2* pop = fg + size_t(src) * NN + size_t(z) * N1 * NX;
-                        const uint32_t d = dst + uint32_t(dz * by * NX * 8);
-                        int y = ys;
-                        if (py) {
-                            y += y < 0 ? N1 : 0;
-                            y -= y >= N1 ? N1 : 0;
-                            y = min(max(y, 0), N1 - 1);
-                            const int l1 = min(by, N1 - y);
-                            bulk_g2s(d, pop + size_t(y) * NX, uint32_t(l1 * NX * 8), fb);
-                            if (by > l1) bulk_g2s(d + uint32_t(l1 * NX * 8), pop, uint32_t((by - l1) * NX * 8), fb);
-                        } else {
-                            y = min(max(y, 0), N1 - by);
-                            bulk_g2s(d, pop + size_t(y) * NX, uint32_t(by * NX * 8), fb);
-                        }
+            const int ty = da.tile % T.ntile_y, tz = da.tile / T.ntile_y;
+            const int y0 = ty * TY, z0 = tz * TZ, tcl = py ? 0 : ty;
+            bool act = false, seam = false;
+            uint32_t dst = 0;
+            int c1 = 0, c2 = 0, c3 = 0, map = 0, by = 0, bz = 0;
+            if (lane < LB && q < da.nvs && b < da.n) {
+                // a box: population, first y and z (relative to the tile),
+                // shape (tensor map); rows [slot, slot + by bz) of the stage
+                const int e = da.e;
+                c3 = min(e & 63, Q - 1);
+                map = (e >> 22) & 63;
+                by = da.bd & 255;
+                bz = da.bd >> 8;
+                c1 = y0 + ((e >> 6) & 255) - 128;
+                c2 = D == 3 ? z0 + ((e >> 14) & 255) - 128 : 0;
+                dst = sb + uint32_t(da.sl * NX * 8);
+                act = c1 >= 0 && c1 + by <= N1 && c2 >= 0 && c2 + bz <= N2;
+                seam = !act;
+            } else if (lane >= LB && lane < LB + TM2_MAX_VEL && q < da.nvs) {
+                // the velocity's records of this tile class: rows [0, NR) of
+                // the records tensor [Q][n_tc][NR][32 FP32]
+                map = T.rec_map;
+                c1 = 0;
+                c2 = tcl;
+                c3 = da.i;
+                dst = sb + uint32_t(T.rows_bytes + q * REC_BYTES);
+                act = true;
+            }
+            if (act) tma_load_4d(dst, static_cast<const char*>(maps) + size_t(map) * 128, 0, c1, c2, c3, fb);
+            if (seam) {
+                // a box across a periodic seam: its rows one z at a time,
+                // each y run in one or two pieces (bulk copies)
+                for (int dz = 0; dz < bz; ++dz) {
+                    int z = c2 + dz;
+                    if (D == 3) {
+                        z += z < 0 ? N2 : 0;
+                        z -= z >= N2 ? N2 : 0;
+                    }
+                    z = min(max(z, 0), N2 - 1);      // every copy stays inside the mesh
+                    const float2* pop = fg + size_t(c3) * NN + size_t(z) * N1 * NX;
+                    const uint32_t d = dst + uint32_t(dz * by * NX * 8);
+                    int y = c1;
+                    if (py) {
+                        y += y < 0 ? N1 : 0;
+                        y -= y >= N1 ? N1 : 0;
+                        y = min(max(y, 0), N1 - 1);
+                        const int l1 = min(by, N1 - y);
+                        bulk_g2s(d, pop + size_t(y) * NX, uint32_t(l1 * NX * 8), fb);
+                        if (by > l1) bulk_g2s(d + uint32_t(l1 * NX * 8), pop, uint32_t((by - l1) * NX * 8), fb);
+                    } else {
+                        y = min(max(y, 0), N1 - by);
+                        bulk_g2s(d, pop + size_t(y) * NX, uint32_t(by * NX * 8), fb);
                     }
                 }
             }
-            if (lane == 31)
-                bulk_g2s(sb + uint32_t(T.rows_bytes), recs + (size_t(i) * T.n_tc + tc) * NR, uint32_t(REC_BYTES),
-                         fb);
             ++seq;
             if (++s == nsh) {
                 s = 0;
                 ph ^= 1;
             }
-            ha = hb;
+            k = kn;
+            da = db;
         }
         // on an abort: wait (bounded, default limit) for every copy issued,
         // so that none lands in shared memory after the CTA has exited
         if (*abort_flag && lane == 0) {
             const long long first = seq > nsh ? seq - nsh : 0;
-            for (long long q = first; q < seq; ++q)
-                mbar_wait(full0 + 8u * uint32_t(h * nsh + int(q % nsh)), uint32_t((q / nsh) & 1));
+            for (long long u = first; u < seq; ++u)
+                mbar_wait(full0 + 8u * uint32_t(h * nsh + int(u % nsh)), uint32_t((u / nsh) & 1));
         }
     } else {
         // ------------------------------------------------ consumers
@@ -249,22 +273,31 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             // class: read from global memory, so that every thread of a row
             // takes the same barriers whatever the stage holds
             const uint64_t xm = __ldg(xmask + (py ? 0 : ty));
+            // velocities of this group that begin a stage
+            const uint64_t sm = __ldg(smask + 2 * (py ? 0 : ty) + h);
+            bool live = false;
+            int q = 0;
+            uint32_t sa = st0;
 #pragma unroll 1
             for (int j = 0; j < nv; ++j) {
                 const int i = h + 2 * j;
                 const int sg = h * nsh + s;
-                const uint32_t fb = full0 + 8u * uint32_t(sg);
-                bool live = !*abort_flag;
-                // under a test wait limit the first velocity also waits on the
-                // barrier that nothing completes (sllbm_debug_wait_limit)
-                if (live && (!mbar_wait(fb, uint32_t(ph), lim) ||
-                             (lim < kWaitLimit && j == 0 && !mbar_wait(full0 + 16u * uint32_t(T.nst), 0, lim)))) {
-                    atomicOr(status, SLLBM_DEV_COPY_TIMEOUT);
-                    *abort_flag = 1;
-                    live = false;
+                if ((sm >> j) & 1) {
+                    q = 0;
+                    sa = st0 + uint32_t(sg) * uint32_t(T.stage_bytes);
+                    live = !*abort_flag;
+                    // under a test wait limit the first stage also waits on the
+                    // barrier that nothing completes (sllbm_debug_wait_limit)
+                    if (live && (!mbar_wait(full0 + 8u * uint32_t(sg), uint32_t(ph), lim) ||
+                                 (lim < kWaitLimit && j == 0 && !mbar_wait(full0 + 16u * uint32_t(T.nst), 0, lim)))) {
+                        atomicOr(status, SLLBM_DEV_COPY_TIMEOUT);
+                        *abort_flag = 1;
+                        live = false;
+                    }
+                } else {
+                    ++q;
                 }
-                const uint32_t sa = st0 + uint32_t(sg) * uint32_t(T.stage_bytes);
-                const uint32_t ra = sa + uint32_t(T.rows_bytes) + uint32_t(r * int(sizeof(TmRec2)));
+                const uint32_t ra = sa + uint32_t(T.rows_bytes + q * REC_BYTES) + uint32_t(r * int(sizeof(TmRec2)));
                 const bool xc = (xm >> i) & 1;
                 // after an abort the stage may never have been written: nothing
                 // is read from it (an empty equilibrium record instead)
@@ -316,9 +349,15 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                         sb2 = __fadd2_rn(sb2, sb2b);
                     }
                 }
-                // this warp has read the stage: release it to the producer
-                __syncwarp();
-                if (lane == 0) mbar_arrive(empty0 + 8u * uint32_t(sg));
+                if (j == nv - 1 || ((sm >> (j + 1)) & 1)) {
+                    // this warp has read the stage's last velocity: release it to the producer
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty0 + 8u * uint32_t(sg));
+                    if (++s == nsh) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
                 float2 oa = sa2, ob = sb2;
                 if (xc) {
                     // x factor: each node's three x taps among the six row
@@ -360,10 +399,6 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                 }
                 tm_st2(tl + 2 * i, oa.x, oa.y);
                 tm_st2(tl + TM_COLS + 2 * i, ob.x, ob.y);
-                if (++s == nsh) {
-                    s = 0;
-                    ph ^= 1;
-                }
             }
             // both groups' values of the tile are in tensor memory
             tm_wait_st();
@@ -401,14 +436,14 @@ inline size_t rows_pairs_smem_bytes(const TmGeom2& T, int nx, int nr) {
 
 template <int VS, int NX, int TY, int TZ>
 int launch_step_rows_pairs(const float2* fg, float2* fgo, const void* maps, const int32_t* head, const TmRec2* recs,
-                           const uint64_t* xmask, const float* tw, const StepGeom& G, const CollideConst<float>& C,
-                           const TmGeom2& T, int* status, cudaStream_t stream, int grid) {
+                           const uint64_t* xmask, const uint64_t* smask, const float* tw, const StepGeom& G,
+                           const CollideConst<float>& C, const TmGeom2& T, int* status, cudaStream_t stream, int grid) {
     const size_t smem = rows_pairs_smem_bytes(T, NX, TY * TZ);
     if (cudaFuncSetAttribute(k_step_rows_pairs<VS, NX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(smem)) != cudaSuccess)
         return SLLBM_ERR_CUDA;
-    k_step_rows_pairs<VS, NX, TY, TZ><<<grid, NX * TY * TZ + 64, smem, stream>>>(fg, fgo, maps, head, recs, xmask, tw,
-                                                                                 G, C, T, status);
+    k_step_rows_pairs<VS, NX, TY, TZ><<<grid, NX * TY * TZ + 64, smem, stream>>>(fg, fgo, maps, head, recs, xmask,
+                                                                                 smask, tw, G, C, T, status);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 

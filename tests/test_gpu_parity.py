@@ -28,6 +28,8 @@ CASES = {
     "box_row32_d2q19_fp32": (lambda: get_config("learned", cells=16), "fp32"),
     # 32-node rows between equilibrium boundaries: the row kernels' equilibrium records
     "mixing_row32_fp32": (lambda: get_config("mixing", cells=(16, 8, 3)), "fp32"),
+    # 64-node rows with walls: the row-tile kernels of both kinds (modes 7 and 10)
+    "channel_row64_fp32": (lambda: get_config("channel", cells=(32, 3, 2)), "fp32"),
     # order p = 4, the order of every case in Sec. 4
     "tgv2d_p4_fp64": (lambda: dict(get_config("tgv2d", cells=4), mesh=dict(kind=0, p=4, cells=(4, 3),
                                                                            length=(6.2831853, 5.0))), "fp64"),
@@ -155,14 +157,15 @@ def test_setup_matches_oracle(built_lib, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5, 6, 7, 10])
 def test_steps_match_oracle(built_lib, name, mode):
     """Every streaming mode (0 auto: warp-tiled with shared-memory state where
     eligible, 1 gather with register state, 3 one thread per node with
     class records, 4 warp-tiled with register state, 5 gather with
     shared-memory state, 6 rows staged by the bulk-copy engine where a
     periodic row fits one block, 7 tiles of rows with the node state in
-    tensor memory where eligible) against the oracle."""
+    tensor memory where eligible, 10 the same with two nodes per thread
+    where eligible) against the oracle."""
     cfg, prec, mesh, xi, w, opp, par, rec = _oracle(name)
     if mode not in (0, 5) and mesh.kind == 3:
         pytest.skip("curved mesh runs the gather modes (0 = 1)")
@@ -194,6 +197,8 @@ def test_steps_match_oracle(built_lib, name, mode):
         assert kern == "k_step_row_copy"                 # the same rows staged by bulk copies
     if name == "box_row32_d2q19_fp32" and mode == 7:
         assert kern == "k_step_rows_tmem"                # 16 rows of 32 nodes per tile
+    if name == "channel_row64_fp32" and mode in (0, 10):
+        assert kern == "k_step_rows_pairs"               # 4 x 2 rows of 64 nodes, two nodes per thread
     print(f"PARITY step {name} mode {sim.info.stream_mode} ({kern}): populations {worst:.2e} moments {em:.2e}")
     sim.close()
 

@@ -86,17 +86,22 @@ def test_rows_tmem_agrees_with_row_kernel(built_lib):
     b.close()
 
 
-def test_rows_tmem_is_the_default_for_d3q45(built_lib):
+def test_row_tiles_are_the_default_for_d3q45(built_lib):
     """With the 45-velocity set, the automatic and the structured modes take
-    the row-tile kernel where it applies; SLLBM_STREAM_ROW_SMEM does not."""
+    the two-nodes-per-thread row-tile kernel on rows of 64 or 128 nodes, the
+    one-node-per-thread row-tile kernel on rows of 32; SLLBM_STREAM_ROW_SMEM
+    takes neither."""
     from paper_2412_09051_gb300.sim import Sim
-    cfg = get_config("channel", cells=(32, 3, 3))
-    for mode, kernel in ((0, "k_step_rows_tmem"), (2, "k_step_rows_tmem"), (8, "k_step_row_smem")):
+    info = {"k_step_rows_pairs": 10, "k_step_rows_tmem": MODE, "k_step_row_smem": 2}
+    for cells, mode, kernel in (((32, 3, 3), 0, "k_step_rows_pairs"), ((32, 3, 3), 2, "k_step_rows_pairs"),
+                                ((64, 3, 3), 0, "k_step_rows_pairs"), ((16, 4, 4), 0, "k_step_rows_tmem"),
+                                ((32, 3, 3), 7, "k_step_rows_tmem"), ((32, 3, 3), 8, "k_step_row_smem")):
+        cfg = get_config("channel", cells=cells)
         s = Sim(cfg, stream_mode=mode)
         s.init_state(*initial_fields(cfg, s.node_coords()))
         s.step(1)
-        assert s.step_kernel() == kernel, (mode, s.step_kernel())
-        assert s.info.stream_mode == (MODE if kernel == "k_step_rows_tmem" else 2)
+        assert s.step_kernel() == kernel, (cells, mode, s.step_kernel())
+        assert s.info.stream_mode == info[kernel]
         s.close()
 
 
