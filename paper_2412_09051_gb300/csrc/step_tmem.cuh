@@ -212,7 +212,17 @@ __device__ __forceinline__ void collide_tmem(const CollideConst<float>& C, uint3
     const float rhoT_d = rho_d + rho * t;
     float q0 = 0.f, q1 = 0.f, q2 = 0.f;
     const bool second = C.quasi || C.forced;
-    // ---- relaxation (BGK); heat flux of the quasi-equilibrium term
+    // Kupershtokh exact-difference forcing (Sec. 4.3), du = F dt / rho: the
+    // equilibrium at the shifted velocity v = u + du minus the one at u (the
+    // relaxation's own P1), added in the relaxation pass
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, V = 0.f;
+    if (C.forced) {
+        v0 = u0 + C.force_dt[0] * inv_rho;
+        v1 = u1 + C.force_dt[1] * inv_rho;
+        v2 = D == 3 ? u2 + C.force_dt[2] * inv_rho : 0.f;
+        V = v0 * v0 + v1 * v1 + v2 * v2;
+    }
+    // ---- relaxation (BGK); heat flux of the quasi-equilibrium term; forcing
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
         float v[16];
@@ -233,6 +243,16 @@ __device__ __forceinline__ void collide_tmem(const CollideConst<float>& C, uint3
                 if (D == 3) q2 += (C.xi[i][2] - u2) * h;
                 v[2 * j] = f - om * fn;
                 v[2 * j + 1] = g - om * gn;
+                if (C.forced) {
+                    const int sh = VSET::shell(i);
+                    float cw = C.xi[i][0] * v0 + C.xi[i][1] * v1;
+                    if (D == 3) cw += C.xi[i][2] * v2;
+                    const float k2 = 0.5f - 0.25f * V + 0.25f * t * C.sC[sh];
+                    const float k1 = 1.0f - 0.5f * V + 0.5f * t * C.sB[sh];
+                    const float k0 = -0.5f * V + 0.125f * V * V + 0.5f * t * C.sA[sh] - 0.25f * t * V * C.sB[sh] +
+                                     0.125f * t * t * C.sE[sh];
+                    v[2 * j] += C.w[i] * rho * (eq_poly1(cw, k0, k1, k2) - P1);
+                }
                 if (!second && store) out[i * NN] = make_float2(v[2 * j], v[2 * j + 1]);
             }
         }
@@ -244,28 +264,8 @@ __device__ __forceinline__ void collide_tmem(const CollideConst<float>& C, uint3
     q0 *= C.quasi ? a : 0.f;
     q1 *= C.quasi ? a : 0.f;
     q2 *= C.quasi ? a : 0.f;
-    if (!C.forced) {
+    // ---- the heat-flux correction of g
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            float v[16];
-            tc_ld16(tl + 16 * c, v);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int i = 8 * c + j;
-                if (i < Q) {
-                    float dq = C.xi[i][0] * q0 + C.xi[i][1] * q1;
-                    if (D == 3) dq += C.xi[i][2] * q2;
-                    if (store) out[i * NN] = make_float2(v[2 * j], v[2 * j + 1] + C.w[i] * dq);
-                }
-            }
-        }
-        return;
-    }
-    // Kupershtokh exact-difference forcing (Sec. 4.3), du = F dt / rho
-    const float v0 = u0 + C.force_dt[0] * inv_rho, v1 = u1 + C.force_dt[1] * inv_rho;
-    const float v2 = D == 3 ? u2 + C.force_dt[2] * inv_rho : 0.f;
-    const float V = v0 * v0 + v1 * v1 + v2 * v2;
-#pragma unroll 1
     for (int c = 0; c < NCH; ++c) {
         float v[16];
         tc_ld16(tl + 16 * c, v);
@@ -275,21 +275,7 @@ __device__ __forceinline__ void collide_tmem(const CollideConst<float>& C, uint3
             if (i < Q) {
                 float dq = C.xi[i][0] * q0 + C.xi[i][1] * q1;
                 if (D == 3) dq += C.xi[i][2] * q2;
-                float cu = C.xi[i][0] * u0 + C.xi[i][1] * u1;
-                if (D == 3) cu += C.xi[i][2] * u2;
-                const float k2a = 0.5f - 0.25f * U + 0.25f * t * C.sCv[i];
-                const float k1a = 1.0f - 0.5f * U + 0.5f * t * C.sBv[i];
-                const float k0a = -0.5f * U + 0.125f * U * U + 0.5f * t * C.sAv[i] - 0.25f * t * U * C.sBv[i] +
-                                  0.125f * t * t * C.sEv[i];
-                const float pa = eq_poly1(cu, k0a, k1a, k2a);
-                float cw = C.xi[i][0] * v0 + C.xi[i][1] * v1;
-                if (D == 3) cw += C.xi[i][2] * v2;
-                const float k2 = 0.5f - 0.25f * V + 0.25f * t * C.sCv[i];
-                const float k1 = 1.0f - 0.5f * V + 0.5f * t * C.sBv[i];
-                const float k0 = -0.5f * V + 0.125f * V * V + 0.5f * t * C.sAv[i] - 0.25f * t * V * C.sBv[i] +
-                                 0.125f * t * t * C.sEv[i];
-                const float fo = v[2 * j] + C.w[i] * rho * (eq_poly1(cw, k0, k1, k2) - pa);
-                if (store) out[i * NN] = make_float2(fo, v[2 * j + 1] + C.w[i] * dq);
+                if (store) out[i * NN] = make_float2(v[2 * j], v[2 * j + 1] + C.w[i] * dq);
             }
         }
     }

@@ -39,6 +39,36 @@ def test_forced_steps_match_oracle(built_lib, name, over, prec, F, mode):
         assert (np.abs(a - b) / s).max() < tol
 
 
+@pytest.mark.parametrize("cells", [(32, 3, 2), (64, 3, 2)])
+@pytest.mark.parametrize("mode,kernel", [(7, "k_step_rows_tmem"), (10, "k_step_rows_pairs")])
+def test_forced_row_tiles_match_oracle(built_lib, cells, mode, kernel):
+    """The row-tile kernels (rows of 64 and 128 nodes) with the body force:
+    the forcing term enters in the relaxation pass of their collision."""
+    cfg = get_config("channel", cells=cells)
+    F = (0.05, 0.0, 0.01)
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    par.force = np.array(F)
+    sim = _sim(cfg, "fp32", mode)
+    assert sim.info.stream_mode == mode
+    sim.set_force(F)
+    rho, u, T = initial_fields(cfg, mesh.X)
+    sim.init_state(rho, u, T)
+    f, g = ost.init_equilibrium(rho, u, T, xi, w, par.cv)
+    Tw = ost.isothermal_nodes(rec, par)
+    for _ in range(3):
+        f, g = ost.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
+    sim.step(3)
+    assert sim.step_kernel() == kernel
+    fg, gg = sim.get_state()
+    worst = 0.0
+    for a, b in ((fg, f), (gg, g)):
+        s = np.maximum(np.abs(b).max(axis=1, keepdims=True), w[:, None])
+        worst = max(worst, float((np.abs(a - b) / s).max()))
+    assert worst < 1e-5
+    print(f"PARITY forced {kernel} {mesh.N}: populations {worst:.2e}")
+    sim.close()
+
+
 def test_uniform_acceleration(built_lib):
     """Closed form: u(t) = u0 + F t / rho for a uniform state in a periodic box."""
     F = np.array([0.02, 0.005])
