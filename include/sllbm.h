@@ -85,6 +85,28 @@ extern "C" {
 #define SLLBM_D2Q19   1
 #define SLLBM_D2Q25   2
 #define SLLBM_D3Q45   3
+/* Sets run by the generic kernels (the velocity count known at run time, the
+ * per-velocity constants in a device table; gather streaming, no learned
+ * collision), created with sllbm_create_desc:
+ *   D3Q125  product 5-point Gauss-Hermite rule (degree 9), x fastest over the
+ *           nodes of D2Q25
+ *   CUSTOM  the caller's abscissae xi[Q][D] and weights w[Q] (Q <= SLLBM_QMAX_GENERIC,
+ *           in units of sqrt(T0)): the set must be symmetric under xi -> -xi and
+ *           reproduce the weight function's moments to second order (sum w = 1,
+ *           sum w xi = 0, sum w xi xi = identity, to 1e-10); the equilibrium
+ *           of Sec. 3.1 is exact only where the set integrates degree 9 */
+#define SLLBM_D3Q125        4
+#define SLLBM_VELSET_CUSTOM 5
+#define SLLBM_QMAX_GENERIC  128
+
+typedef struct {
+    int32_t kind;          /* SLLBM_D2Q9 .. SLLBM_VELSET_CUSTOM                          */
+    int32_t Q;             /* CUSTOM: number of velocities (else ignored)              */
+    int32_t D;             /* CUSTOM: dimension, equal to the mesh's (else ignored)    */
+    int32_t reserved;      /* 0                                                        */
+    const double* xi;      /* CUSTOM: host array xi[Q][D]; read during the call only   */
+    const double* w;       /* CUSTOM: host array w[Q]; read during the call only       */
+} sllbm_velset_desc;
 
 /* Boundary kinds (Sec. 3.3).  Boundary id 0 is the low-y side of channel /
  * mixing meshes and the profile wall of the NACA O-grid; id 1 is the high-y
@@ -215,6 +237,16 @@ typedef struct sllbm_ctx sllbm_ctx;
  * On error *out is NULL and the message is available from sllbm_last_error(NULL). */
 int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params* params,
                  sllbm_ctx** out);
+
+/* sllbm_create with a velocity-set descriptor (Sec. 3.2): the four sets above
+ * by kind (exactly as sllbm_create), D3Q125, or a caller's set.  The generic
+ * kinds (D3Q125, CUSTOM) take the gather streaming whatever params->stream_mode
+ * asks, orders p = 2, 3, 4, FP64 or FP32; the learned collision is not
+ * available on them (SLLBM_ERR_UNSUPPORTED).
+ * Errors as sllbm_create; a custom set that fails the checks above gives
+ * SLLBM_ERR_ARG before any device work. */
+int sllbm_create_desc(const sllbm_mesh_desc* mesh, const sllbm_velset_desc* velset, const sllbm_params* params,
+                      sllbm_ctx** out);
 
 /* Free everything the context owns.  NULL is accepted. */
 int sllbm_destroy(sllbm_ctx* ctx);

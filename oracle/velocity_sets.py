@@ -9,6 +9,10 @@ the paper; the rules below are closed-form fully symmetric degree-9 rules:
   D2Q19  rest point, ring A at angles k*60 deg with r^2 = (48 - 8 sqrt15)/7,
          ring B at 30 + k*60 deg with r = 2 sqrt2, ring C at k*60 deg with
          r^2 = (48 + 8 sqrt15)/7.
+  D3Q125 product of the 5-point Gauss-Hermite rule (nodes 0, +-sqrt(5 -+
+         sqrt10), the roots of He_5), x fastest, then y, then z: the 3D
+         member of the product family whose 2D member D2Q25 the paper uses;
+         exact to degree 9 in each variable.
   D3Q45  rest point, shell A: icosahedron (cyclic perms of (0, +-phi, +-1))
          at radius sqrt3, shell B: dodecahedron ((+-1)^3 and cyclic perms of
          (0, +-1/phi, +-phi)) at radius 3, shell C: icosahedron of the same
@@ -71,6 +75,11 @@ def abscissae(name):
         r2 = math.sqrt(5.0 + math.sqrt(10.0))
         nodes = [0.0, r1, r2, -r1, -r2]
         return np.array([(a, b) for b in nodes for a in nodes], dtype=np.float64)
+    if name == "D3Q125":
+        r1 = math.sqrt(5.0 - math.sqrt(10.0))
+        r2 = math.sqrt(5.0 + math.sqrt(10.0))
+        nodes = [0.0, r1, r2, -r1, -r2]
+        return np.array([(a, b, c) for c in nodes for b in nodes for a in nodes], dtype=np.float64)
     if name == "D2Q19":
         ra = math.sqrt((48.0 - 8.0 * math.sqrt(15.0)) / 7.0)
         rb = 2.0 * math.sqrt(2.0)
@@ -101,7 +110,7 @@ def _orbits(name, xi):
     if name == "D2Q9":
         r2 = np.round((xi ** 2).sum(1), 9)
         return [np.nonzero(r2 == v)[0] for v in np.unique(r2)]
-    if name == "D2Q25":
+    if name in ("D2Q25", "D3Q125"):
         key = [tuple(sorted(np.round(np.abs(x), 9))) for x in xi]
         uniq = sorted(set(key))
         return [np.array([i for i in range(Q) if key[i] == u]) for u in uniq]
@@ -118,6 +127,18 @@ def velocity_set(name):
     for D2Q9)."""
     xi = abscissae(name)
     Q, D = xi.shape
+    if name == "D3Q125":
+        # a product rule: the 1D weights of the 5 Gauss-Hermite nodes solve
+        # the 1D moment equations of degree 0 .. 4 (a Vandermonde system;
+        # with the roots of He_5 as nodes the rule is then exact to degree
+        # 9), and the 3D weight is the product over the coordinates.  (The
+        # symmetric degree-9 equations in 3D do not fix its 10 orbit weights.)
+        x = abscissae("D2Q25")[:5, 0]
+        V = np.vander(x, 5, increasing=True).T
+        w1 = np.linalg.solve(V, np.array([gaussian_moment_1d(k) for k in range(5)]))
+        w = np.array([w1[i % 5] * w1[(i // 5) % 5] * w1[i // 25] for i in range(Q)])
+        opp = np.array([int(np.argmin(np.abs(xi + xi[i]).sum(1))) for i in range(Q)])
+        return xi, w, opp
     orbits = _orbits(name, xi)
     degree = 5 if name == "D2Q9" else 9
     mons = monomials(D, degree)
@@ -138,6 +159,15 @@ def velocity_set(name):
     for c, orb in enumerate(orbits):
         w[orb] = wo[c]
     opp = np.array([int(np.argmin(np.abs(xi + xi[i]).sum(1))) for i in range(Q)])
+    return xi, w, opp
+
+
+def custom_set(xi, w):
+    """A caller's set (xi [Q,D], w [Q]) with its opposites, for oracle cases
+    of the library's SLLBM_VELSET_CUSTOM kind."""
+    xi = np.asarray(xi, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    opp = np.array([int(np.argmin(np.abs(xi + xi[i]).sum(1))) for i in range(len(xi))])
     return xi, w, opp
 
 

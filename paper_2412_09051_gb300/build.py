@@ -23,7 +23,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompil
          "-I", os.path.join(HERE, "..", "include")]
 SOURCES = ["capi.cu", "setup.cu", "util.cu", "step_f32.cu", "step_f32_3d.cu", "step_f64.cu", "step_p4.cu",
            "step_p4_f64.cu", "host_geometry.cpp", "mlp_train.cu", "stats.cu", "step_rowcopy.cu", "step_tmem.cu",
-           "step_tmem2.cu"]
+           "step_tmem2.cu", "generic.cu"]
 
 
 def _nvcc():

@@ -16,7 +16,8 @@ ERRORS = {-1: "SLLBM_ERR_ARG", -2: "SLLBM_ERR_CUDA", -3: "SLLBM_ERR_ARCH", -4: "
           -5: "SLLBM_ERR_DP_NOT_FOUND", -6: "SLLBM_ERR_UNSTABLE", -7: "SLLBM_ERR_STATE",
           -8: "SLLBM_ERR_UNSUPPORTED"}
 MESH = dict(box=0, channel=1, mixing=2, naca=3)
-VELSET = dict(D2Q9=0, D2Q19=1, D2Q25=2, D3Q45=3)
+VELSET = dict(D2Q9=0, D2Q19=1, D2Q25=2, D3Q45=3, D3Q125=4, CUSTOM=5)
+QMAX_GENERIC = 128
 MLP_TENSOR, MLP_SIMT = 0, 1
 DEV_TC_TIMEOUT, DEV_BAD_NODE, DEV_BAD_POP, DEV_BAD_REC, DEV_BAD_SMEM, DEV_COPY_TIMEOUT = 1, 2, 4, 8, 16, 32
 BUILD_CHECKED = 1
@@ -44,6 +45,11 @@ class Params(C.Structure):
                 ("max_walk", C.c_int32), ("stream", C.c_void_p)]
 
 
+class VelsetDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("Q", C.c_int32), ("D", C.c_int32), ("reserved", C.c_int32),
+                ("xi", C.c_void_p), ("w", C.c_void_p)]
+
+
 class Control(C.Structure):
     _fields_ = [("target_momentum", C.c_double), ("force0", C.c_double), ("kp", C.c_double), ("ki", C.c_double),
                 ("control_every", C.c_int32), ("rescale_every", C.c_int32), ("target_mass", C.c_double)]
@@ -60,6 +66,7 @@ class Info(C.Structure):
 _P = C.c_void_p
 _SIGS = {
     "sllbm_create": (C.c_int, [C.POINTER(MeshDesc), C.c_int32, C.POINTER(Params), C.POINTER(_P)]),
+    "sllbm_create_desc": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(VelsetDesc), C.POINTER(Params), C.POINTER(_P)]),
     "sllbm_destroy": (C.c_int, [_P]),
     "sllbm_last_error": (C.c_char_p, [_P]),
     "sllbm_info": (C.c_int, [_P, C.POINTER(Info)]),

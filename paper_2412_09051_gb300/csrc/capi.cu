@@ -38,6 +38,18 @@ template <typename real>
 int launch_conserve(int vs, int D, const typename Vec2<real>::T* fg, int64_t N, const CollideConst<double>& C,
                     double* part, int* flag, double* out, cudaStream_t s);
 int conserve_blocks();
+void k_reduce_parts_launch(const double* part, int nblk, int K, double* out, cudaStream_t s);
+template <typename real>
+int launch_step_generic(int p, int D, const StepLaunch<real>& L, const GenVel<real>* V, int Q);
+template <typename real>
+int launch_init_generic(const double* rho, const double* u, const double* T, int64_t N, const GenVel<double>* V,
+                        int Q, int D, typename Vec2<real>::T* fg, cudaStream_t s);
+template <typename real>
+int launch_moments_generic(const typename Vec2<real>::T* fg, int64_t N, const GenVel<double>* V, int Q, int D,
+                           double cv, double* rho, double* u, double* T, cudaStream_t s);
+template <typename real>
+int launch_conserve_generic(const typename Vec2<real>::T* fg, int64_t N, const GenVel<double>* V, int Q, int D,
+                            double cv, int grid_stride, unsigned blocks, double* part, int* flag, cudaStream_t s);
 template <typename V2>
 int launch_x_layers(V2* fg, V2* buf, int64_t NN, int Nx, int rows, int x0, int nx, int Q, int dir, cudaStream_t s);
 template <typename real>
@@ -164,7 +176,10 @@ void fill_collide_const(sllbm_ctx* c, CollideConst<real>& C) {
     const int D = vs.D;
     const double cv = 1.0 / (c->params.gamma - 1.0);
     const double gf = 2.0 * cv - D;
-    for (int i = 0; i < vs.Q; ++i) {
+    // the per-velocity arrays hold the compiled sets (Q <= SLLBM_QMAX); the
+    // generic sets keep theirs in the GenVel table
+    const int Qc = std::min(vs.Q, SLLBM_QMAX);
+    for (int i = 0; i < Qc; ++i) {
         for (int d = 0; d < D; ++d) C.xi[i][d] = real(vs.xi[i * D + d]);
         C.w[i] = real(vs.w[i]);
         C.wg[i] = real(vs.w[i] * gf);
@@ -198,15 +213,57 @@ void fill_collide_const(sllbm_ctx* c, CollideConst<real>& C) {
     for (int d = 0; d < 3; ++d) C.force_dt[d] = real(d < D ? c->force[d] * c->params.dt : 0.0);
     for (int b = 0; b < 2; ++b) {
         const sllbm_bc& bc = c->desc.bc[b];
-        double fe[SLLBM_QMAX], ge[SLLBM_QMAX];
-        host_eq_dev(c, bc.rho, bc.u, bc.T, fe, ge);
-        for (int i = 0; i < vs.Q; ++i) {
+        std::vector<double> fe(vs.Q), ge(vs.Q);
+        host_eq_dev(c, bc.rho, bc.u, bc.T, fe.data(), ge.data());
+        for (int i = 0; i < Qc; ++i) {
             C.eqf[b][i] = real(fe[i]);
             C.eqg[b][i] = real(ge[i]);
             double cu = 0;
             for (int d = 0; d < D; ++d) cu += vs.xi[i * D + d] * bc.u[d];
             C.mw[b][i] = real(2.0 * vs.w[i] * bc.rho * cu);
         }
+    }
+}
+
+// The generic kernels' per-velocity table (GenVel): the quantities
+// fill_collide_const puts in CollideConst's per-velocity arrays, for any Q.
+template <typename real>
+void build_gen_table(const sllbm_ctx* c, std::vector<GenVel<real>>& out) {
+    const HostVelSet& vs = c->vs;
+    const int D = vs.D, Q = vs.Q;
+    const double cv = 1.0 / (c->params.gamma - 1.0);
+    const double gf = 2.0 * cv - D;
+    out.assign(Q, GenVel<real>{});
+    std::vector<double> fe[2], ge[2];
+    for (int b = 0; b < 2; ++b) {
+        fe[b].resize(Q);
+        ge[b].resize(Q);
+        const sllbm_bc& bc = c->desc.bc[b];
+        host_eq_dev(c, bc.rho, bc.u, bc.T, fe[b].data(), ge[b].data());
+    }
+    for (int i = 0; i < Q; ++i) {
+        GenVel<real>& v = out[i];
+        double s = 0;
+        for (int d = 0; d < D; ++d) {
+            v.xi[d] = real(vs.xi[i * D + d]);
+            s += vs.xi[i * D + d] * vs.xi[i * D + d];
+        }
+        v.w = real(vs.w[i]);
+        v.wg = real(vs.w[i] * gf);
+        v.s2 = real(s);
+        v.sA = real(s - D);
+        v.sB = real(s - D - 2);
+        v.sC = real(s - D - 4);
+        v.sE = real(s * s - 2.0 * (D + 2) * s + D * (D + 2.0));
+        for (int b = 0; b < 2; ++b) {
+            const sllbm_bc& bc = c->desc.bc[b];
+            v.eqf[b] = real(fe[b][i]);
+            v.eqg[b] = real(ge[b][i]);
+            double cu = 0;
+            for (int d = 0; d < D; ++d) cu += vs.xi[i * D + d] * bc.u[d];
+            v.mw[b] = real(2.0 * vs.w[i] * bc.rho * cu);
+        }
+        v.opp = vs.opp[i];
     }
 }
 
@@ -801,6 +858,10 @@ int encode_tm2_maps(sllbm_ctx* c) {
 template <typename real>
 int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
     const int vs = ctx->velset, p = ctx->mesh.p;
+    if (ctx->generic) {
+        ctx->step_kernel = "k_step_generic";
+        return launch_step_generic<real>(p, ctx->mesh.D, L, static_cast<const GenVel<real>*>(ctx->gen_v), ctx->vs.Q);
+    }
     const bool st = ctx->mode != SLLBM_STREAM_GATHER && ctx->mode != SLLBM_STREAM_GATHER_SMEM;
     if constexpr (std::is_same<real, float>::value) {
         if (st && ctx->rows_tm2 && !ctx->row_copy) {
@@ -918,7 +979,10 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
                 "velocity set / order combination not built (p must be 2 or 4, or 3 for D2Q19)");
 }
 
-bool supported(int vs, int p) { return p == 2 || p == 4 || (vs == SLLBM_D2Q19 && p == 3); }
+bool supported(int vs, int p) {
+    if (vs == SLLBM_D3Q125 || vs == SLLBM_VELSET_CUSTOM) return p >= 2 && p <= 4;     // the generic kernels
+    return p == 2 || p == 4 || (vs == SLLBM_D2Q19 && p == 3);
+}
 
 // The warp-tiled kernel needs p = 2, periodic x, x-tap offsets within +-3
 // nodes, and y/z factors (and record kinds) independent of the x parity.
@@ -1077,11 +1141,13 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     if (!ctx) return SLLBM_OK;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->gen_v == ctx->gen_v64) ctx->gen_v = nullptr;       // one table in FP64 contexts
     void* ptrs[] = {ctx->dV[0], ctx->dV[1], ctx->dV[2], ctx->dX, ctx->rec64, ctx->cls_tab, ctx->g_code, ctx->g_xi,
                     ctx->tw_tab, ctx->fg[0], ctx->fg[1], ctx->tile_tab, ctx->row_tab, ctx->d_red, ctx->d_flag,
                     ctx->d_mom, ctx->mlp_img, ctx->d_feat, ctx->d_wref, ctx->mlp_tc, ctx->d_status,
                     ctx->d_plane, ctx->d_cp, ctx->d_plane_acc, ctx->tm_head, ctx->tm_recs, ctx->tm_xmask,
-                    ctx->tm_bop, ctx->d_layers, ctx->tm2_head, ctx->tm2_recs, ctx->tm2_maps, ctx->tm2_smask};
+                    ctx->tm_bop, ctx->d_layers, ctx->tm2_head, ctx->tm2_recs, ctx->tm2_maps, ctx->tm2_smask,
+                    ctx->gen_v, ctx->gen_v64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -1089,7 +1155,11 @@ int sllbm_destroy(sllbm_ctx* ctx) {
     return SLLBM_OK;
 }
 
-int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params* params, sllbm_ctx** out) {
+namespace {
+// sllbm_create and sllbm_create_desc: `vs_in` is a checked caller's set
+// (SLLBM_VELSET_CUSTOM), else the set of kind `velset` is built here
+int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs_in, const sllbm_params* params,
+               sllbm_ctx** out) {
     if (!out) return fail(nullptr, SLLBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!mesh || !params) return fail(nullptr, SLLBM_ERR_ARG, "NULL descriptor");
@@ -1120,7 +1190,12 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
         sllbm_destroy(ctx);
         return code;
     };
-    int rc = build_velocity_set(velset, ctx->vs, ctx->last_error);
+    ctx->generic = velset == SLLBM_D3Q125 || velset == SLLBM_VELSET_CUSTOM;
+    int rc = SLLBM_OK;
+    if (vs_in)
+        ctx->vs = *vs_in;
+    else
+        rc = build_velocity_set(velset, ctx->vs, ctx->last_error);
     if (rc) return bail(rc);
     rc = build_mesh(*mesh, ctx->mesh, ctx->last_error);
     if (rc) return bail(rc);
@@ -1129,7 +1204,8 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
         return bail(SLLBM_ERR_ARG);
     }
     if (!supported(velset, ctx->mesh.p)) {
-        ctx->last_error = "velocity set / order combination not built (p must be 2, or 3 for D2Q19)";
+        ctx->last_error = ctx->generic ? "the generic velocity-set kernels are built for p = 2, 3, 4"
+                                       : "velocity set / order combination not built (p must be 2, or 3 for D2Q19)";
         return bail(SLLBM_ERR_UNSUPPORTED);
     }
     for (int b = 0; b < 2; ++b) {
@@ -1146,6 +1222,7 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
     const bool axis = ctx->mesh.kind != SLLBM_MESH_NACA;
     int mode = params->stream_mode;
     if (mode == SLLBM_STREAM_AUTO) mode = axis ? SLLBM_STREAM_STRUCTURED : SLLBM_STREAM_GATHER;
+    if (ctx->generic) mode = SLLBM_STREAM_GATHER;       // one departure record per (node, velocity)
     if (mode == SLLBM_STREAM_ROW_COPY) {
         ctx->row_copy = true;
         mode = SLLBM_STREAM_STRUCTURED;
@@ -1443,6 +1520,24 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
         for (int b = 0; b < 2; ++b) {
             CK(cudaMalloc(&ctx->fg[b], 2 * rs * N * Q));
         }
+        if (ctx->generic) {
+            // the generic kernels' per-velocity table, in the context's
+            // precision and in FP64 (initialisation, moments, conservation)
+            std::vector<GenVel<double>> g64;
+            build_gen_table<double>(ctx, g64);
+            CK(cudaMalloc(&ctx->gen_v64, sizeof(GenVel<double>) * g64.size()));
+            CK(cudaMemcpyAsync(ctx->gen_v64, g64.data(), sizeof(GenVel<double>) * g64.size(), cudaMemcpyHostToDevice,
+                               s));
+            if (rs == 8) {
+                ctx->gen_v = ctx->gen_v64;
+            } else {
+                std::vector<GenVel<float>> g32;
+                build_gen_table<float>(ctx, g32);
+                CK(cudaMalloc(&ctx->gen_v, sizeof(GenVel<float>) * g32.size()));
+                CK(cudaMemcpyAsync(ctx->gen_v, g32.data(), sizeof(GenVel<float>) * g32.size(),
+                                   cudaMemcpyHostToDevice, s));
+            }
+        }
         if (ctx->rows_tm2) {
             const int r3 = encode_tm2_maps(ctx);          // the maps name the state buffers
             if (r3 != SLLBM_OK) return r3;
@@ -1454,6 +1549,28 @@ int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params
     if (rc) return bail(rc);
     *out = ctx;
     return SLLBM_OK;
+}
+}  // namespace
+
+int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params* params, sllbm_ctx** out) {
+    if (velset == SLLBM_VELSET_CUSTOM) {
+        if (out) *out = nullptr;
+        return fail(nullptr, SLLBM_ERR_ARG, "a custom velocity set needs sllbm_create_desc");
+    }
+    return create_ctx(mesh, velset, nullptr, params, out);
+}
+
+int sllbm_create_desc(const sllbm_mesh_desc* mesh, const sllbm_velset_desc* velset, const sllbm_params* params,
+                      sllbm_ctx** out) {
+    if (out) *out = nullptr;
+    if (!velset) return fail(nullptr, SLLBM_ERR_ARG, "NULL velocity-set descriptor");
+    if (velset->kind != SLLBM_VELSET_CUSTOM) return create_ctx(mesh, velset->kind, nullptr, params, out);
+    // a caller's set is copied and checked before any device work
+    HostVelSet vs;
+    std::string err;
+    const int rc = build_custom_velocity_set(*velset, vs, err);
+    if (rc) return fail(nullptr, rc, err);
+    return create_ctx(mesh, SLLBM_VELSET_CUSTOM, &vs, params, out);
 }
 
 int sllbm_info(const sllbm_ctx* ctx, sllbm_info_t* o) {
@@ -1523,7 +1640,13 @@ int sllbm_init_state(sllbm_ctx* ctx, const double* rho, const double* u, const d
         du = tmp + N;
         dT = tmp + N * (D + 1);
     }
-    int rc = ctx->precision == SLLBM_FP64
+    const GenVel<double>* gv = static_cast<const GenVel<double>*>(ctx->gen_v64);
+    const int Qg = ctx->vs.Q, Dg = ctx->mesh.D;
+    int rc = ctx->generic
+                 ? (ctx->precision == SLLBM_FP64
+                        ? launch_init_generic<double>(dr, du, dT, N, gv, Qg, Dg, (double2*)ctx->fg[0], s)
+                        : launch_init_generic<float>(dr, du, dT, N, gv, Qg, Dg, (float2*)ctx->fg[0], s))
+             : ctx->precision == SLLBM_FP64
                  ? launch_init<double>(ctx->velset, dr, du, dT, N, ctx->cc64, (double2*)ctx->fg[0], s)
                  : launch_init<float>(ctx->velset, dr, du, dT, N, ctx->cc64, (float2*)ctx->fg[0], s);
     if (tmp) {
@@ -1808,7 +1931,14 @@ int sllbm_read_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int32_
         dT = T ? tmp + N * (D + 1) : nullptr;
     }
     const int c = ctx->cur;
-    int rc = ctx->precision == SLLBM_FP64
+    const GenVel<double>* gv = static_cast<const GenVel<double>*>(ctx->gen_v64);
+    int rc = ctx->generic
+                 ? (ctx->precision == SLLBM_FP64
+                        ? launch_moments_generic<double>((double2*)ctx->fg[c], N, gv, ctx->vs.Q, D, ctx->cc64.cv, dr,
+                                                         du, dT, s)
+                        : launch_moments_generic<float>((float2*)ctx->fg[c], N, gv, ctx->vs.Q, D, ctx->cc64.cv, dr, du,
+                                                        dT, s))
+             : ctx->precision == SLLBM_FP64
                  ? launch_moments<double>(ctx->velset, (double2*)ctx->fg[c], N, ctx->cc64, dr, du, dT, s)
                  : launch_moments_f32(ctx->velset, (float2*)ctx->fg[c], N, ctx->cc32, ctx->cc64.cv, dr, du, dT, s);
     if (rc) return fail(ctx, rc, "moments launch failed");
@@ -1832,11 +1962,26 @@ int sllbm_conservation(sllbm_ctx* ctx, double* out) {
     double* dout = ctx->d_red + conserve_blocks() * 5;
     CK(cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s));
     const int c = ctx->cur;
-    int rc = ctx->precision == SLLBM_FP64
+    int rc;
+    if (ctx->generic) {
+        const GenVel<double>* gv = static_cast<const GenVel<double>*>(ctx->gen_v64);
+        const unsigned nb = unsigned(conserve_blocks());
+        rc = ctx->precision == SLLBM_FP64
+                 ? launch_conserve_generic<double>((double2*)ctx->fg[c], N, gv, ctx->vs.Q, D, ctx->cc64.cv, 1, nb,
+                                                   part, ctx->d_flag + 1, s)
+                 : launch_conserve_generic<float>((float2*)ctx->fg[c], N, gv, ctx->vs.Q, D, ctx->cc64.cv, 1, nb,
+                                                  part, ctx->d_flag + 1, s);
+        if (!rc) {
+            k_reduce_parts_launch(part, int(nb), D + 2, dout, s);
+            rc = cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
+        }
+    } else {
+        rc = ctx->precision == SLLBM_FP64
                  ? launch_conserve<double>(ctx->velset, D, (double2*)ctx->fg[c], N, ctx->cc64, part,
                                            ctx->d_flag + 1, dout, s)
                  : launch_conserve<float>(ctx->velset, D, (float2*)ctx->fg[c], N, ctx->cc64, part,
                                           ctx->d_flag + 1, dout, s);
+    }
     if (rc) return fail(ctx, rc, "conservation launch failed");
     int flag = 0;
     CK(cudaMemcpyAsync(out, dout, sizeof(double) * (D + 2), cudaMemcpyDeviceToHost, s));

@@ -109,6 +109,24 @@ int build_velocity_set(int kind, HostVelSet& vs, std::string& err) {
         for (int k = 0; k < 20; ++k) vs.w.push_back(1.0 / 216.0);
         for (int k = 0; k < 12; ++k) vs.w.push_back(1.0 / 2160.0);
         vs.shell_s = {0.0, 3.0, 9.0, 15.0};
+    } else if (kind == SLLBM_D3Q125) {
+        // product of the 5-point Gauss-Hermite rule (weight exp(-x^2/2) / sqrt(2 pi)):
+        // nodes 0, +-sqrt(5 -+ sqrt10), weights 8/15 and (7 +- 2 sqrt10)/60
+        vs.Q = 125;
+        vs.D = 3;
+        const double r10 = std::sqrt(10.0);
+        const double r1 = std::sqrt(5.0 - r10), r2 = std::sqrt(5.0 + r10);
+        const double x[5] = {0.0, r1, r2, -r1, -r2};
+        const double w1d[5] = {8.0 / 15.0, (7.0 + 2.0 * r10) / 60.0, (7.0 - 2.0 * r10) / 60.0,
+                               (7.0 + 2.0 * r10) / 60.0, (7.0 - 2.0 * r10) / 60.0};
+        for (int c = 0; c < 5; ++c)
+            for (int b = 0; b < 5; ++b)
+                for (int a = 0; a < 5; ++a) {
+                    vs.xi.push_back(x[a]);
+                    vs.xi.push_back(x[b]);
+                    vs.xi.push_back(x[c]);
+                    vs.w.push_back(w1d[a] * w1d[b] * w1d[c]);
+                }
     } else {
         err = "unknown velocity set";
         return SLLBM_ERR_ARG;
@@ -129,6 +147,67 @@ int build_velocity_set(int kind, HostVelSet& vs, std::string& err) {
             err = "velocity set is not symmetric";
             return SLLBM_ERR_ARG;
         }
+    }
+    return SLLBM_OK;
+}
+
+int build_custom_velocity_set(const sllbm_velset_desc& d, HostVelSet& vs, std::string& err) {
+    if (d.Q < 1 || d.Q > SLLBM_QMAX_GENERIC || (d.D != 2 && d.D != 3) || !d.xi || !d.w) {
+        err = "custom velocity set: 1 <= Q <= " + std::to_string(SLLBM_QMAX_GENERIC) +
+              ", D = 2 or 3 and both arrays required";
+        return SLLBM_ERR_ARG;
+    }
+    vs.Q = d.Q;
+    vs.D = d.D;
+    vs.xi.assign(d.xi, d.xi + size_t(d.Q) * d.D);
+    vs.w.assign(d.w, d.w + d.Q);
+    vs.opp.assign(d.Q, -1);
+    vs.shell_s.clear();
+    for (double v : vs.xi)
+        if (!std::isfinite(v)) {
+            err = "custom velocity set: non-finite abscissa";
+            return SLLBM_ERR_ARG;
+        }
+    for (double v : vs.w)
+        if (!std::isfinite(v) || !(v > 0.0)) {
+            err = "custom velocity set: weights must be positive and finite";
+            return SLLBM_ERR_ARG;
+        }
+    const int D = d.D;
+    for (int i = 0; i < d.Q; ++i) {
+        double best = 1e300;
+        for (int j = 0; j < d.Q; ++j) {
+            double dd = 0;
+            for (int a = 0; a < D; ++a) dd += std::fabs(vs.xi[i * D + a] + vs.xi[j * D + a]);
+            if (dd < best) {
+                best = dd;
+                vs.opp[i] = j;
+            }
+        }
+        if (best > 1e-12 || std::fabs(vs.w[vs.opp[i]] - vs.w[i]) > 1e-14 * std::max(1.0, vs.w[i])) {
+            err = "custom velocity set: not symmetric under xi -> -xi (with equal weights)";
+            return SLLBM_ERR_ARG;
+        }
+    }
+    // moments of the weight function to second order: sum w = 1, sum w xi = 0,
+    // sum w xi xi = identity (units of sqrt(T0))
+    double m0 = 0, m1[3] = {0, 0, 0}, m2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int i = 0; i < d.Q; ++i) {
+        m0 += vs.w[i];
+        for (int a = 0; a < D; ++a) {
+            m1[a] += vs.w[i] * vs.xi[i * D + a];
+            for (int b = 0; b < D; ++b) m2[a][b] += vs.w[i] * vs.xi[i * D + a] * vs.xi[i * D + b];
+        }
+    }
+    bool ok = std::fabs(m0 - 1.0) <= 1e-10;
+    for (int a = 0; a < D; ++a) {
+        ok = ok && std::fabs(m1[a]) <= 1e-10;
+        for (int b = 0; b < D; ++b) ok = ok && std::fabs(m2[a][b] - (a == b ? 1.0 : 0.0)) <= 1e-10;
+    }
+    if (!ok) {
+        err = "custom velocity set: moments to second order differ from the weight function's "
+              "(sum w = 1, sum w xi = 0, sum w xi xi = I within 1e-10)";
+        return SLLBM_ERR_ARG;
     }
     return SLLBM_OK;
 }

@@ -23,6 +23,20 @@ struct HostVelSet {
     std::vector<double> shell_s;   // |xi|^2 per shell (compile-time shell map)
 };
 int build_velocity_set(int kind, HostVelSet& vs, std::string& err);
+// a caller's set (SLLBM_VELSET_CUSTOM): copied and checked (symmetry, moments to second order)
+int build_custom_velocity_set(const sllbm_velset_desc& d, HostVelSet& vs, std::string& err);
+
+// Per-velocity constants of the generic kernels (generic.cu): abscissa, the
+// weights of f and g, |xi|^2 and the shell constants of the equilibrium, the
+// boundary equilibria and moving-wall terms per boundary id, the opposite
+// velocity.
+template <typename real>
+struct GenVel {
+    real xi[3];
+    real w, wg, s2, sA, sB, sC, sE;
+    real eqf[2], eqg[2], mw[2];
+    int32_t opp, pad;
+};
 
 struct HostMesh {
     int kind = 0, D = 0, p = 0;
@@ -53,8 +67,8 @@ struct MeshView {
 
 struct TraceArgs {            // setup kernel arguments
     MeshView M;
-    double xi[SLLBM_QMAX][3];
-    int opp[SLLBM_QMAX];
+    double xi[SLLBM_QMAX_GENERIC][3];
+    int opp[SLLBM_QMAX_GENERIC];
     int Q;
     double dt;
     int max_newton, max_walk;
@@ -215,6 +229,9 @@ struct sllbm_ctx {
     int32_t* tm_head = nullptr;          // copy lists [Q][n_tc][TM_HEAD]
     void* tm_recs = nullptr;             // TmRec [Q][n_tc][TY TZ][2]
     bool want_tm2 = false;               // SLLBM_STREAM_ROWS_PAIRS requested
+    bool generic = false;                // a D3Q125 or caller's set: the generic kernels (generic.cu)
+    void* gen_v = nullptr;               // GenVel<real> [Q] in the context's precision
+    void* gen_v64 = nullptr;             // GenVel<double> [Q] (initialisation, moments, conservation)
     bool rows_tm2 = false;               // tables of the two-nodes-per-thread row-tile kernel built
     sllbm::TmGeom2 tm2{};
     int32_t* tm2_head = nullptr;         // box lists [Q][n_tc][TM2_HEAD]

@@ -167,6 +167,10 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nblk, int K,
     out[k] = s;
 }
 
+void k_reduce_parts_launch(const double* part, int nblk, int K, double* out, cudaStream_t s) {
+    k_reduce_parts<<<1, 32, 0, s>>>(part, nblk, K, out);
+}
+
 // ------------------------------------------------------------ launchers
 template <typename real>
 int launch_init(int vs, const double* rho, const double* u, const double* T, int64_t N, const CollideConst<double>& C,
@@ -320,6 +324,10 @@ constexpr int kStaticScratchDoubles = 1 << 17;
 constexpr int kStaticHead = 16;
 static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
+template <typename real>
+int launch_conserve_generic(const typename Vec2<real>::T* fg, int64_t N, const GenVel<double>* V, int Q, int D,
+                            double cv, int grid_stride, unsigned blocks, double* part, int* flag, cudaStream_t s);
+
 // one block per 256 nodes (no grid-stride loop): partial sums of
 // (rho, rho u, 2 rho E) and the positivity flag
 template <int VS, typename real>
@@ -418,11 +426,22 @@ extern "C" int sllbm_conservation_static(sllbm_ctx* ctx, double* out) {
         return SLLBM_ERR_CUDA;
     }
     const int c = ctx->cur;
-    int rc = ctx->precision == SLLBM_FP64
+    int rc;
+    if (ctx->generic) {
+        // one node per thread, the same block layout (generic.cu)
+        const GenVel<double>* gv = static_cast<const GenVel<double>*>(ctx->gen_v64);
+        rc = ctx->precision == SLLBM_FP64
+                 ? launch_conserve_generic<double>((const double2*)ctx->fg[c], N, gv, ctx->vs.Q, D, ctx->cc64.cv, 0,
+                                                   unsigned(blocks), part, flag, s)
+                 : launch_conserve_generic<float>((const float2*)ctx->fg[c], N, gv, ctx->vs.Q, D, ctx->cc64.cv, 0,
+                                                  unsigned(blocks), part, flag, s);
+    } else {
+        rc = ctx->precision == SLLBM_FP64
                  ? launch_conserve_blocks<double>(ctx->velset, (const double2*)ctx->fg[c], N, ctx->cc64, part, flag,
                                                   unsigned(blocks), s)
                  : launch_conserve_blocks<float>(ctx->velset, (const float2*)ctx->fg[c], N, ctx->cc64, part, flag,
                                                  unsigned(blocks), s);
+    }
     if (rc == SLLBM_OK) {
         k_reduce_parts<<<1, 32, 0, s>>>(part, int(blocks), D + 2, sums);
         if (cudaGetLastError() != cudaSuccess) rc = SLLBM_ERR_CUDA;

@@ -59,6 +59,25 @@ def params(cfg, precision=None, stream_mode=0, device=0, stream=None):
     return p
 
 
+def velset_desc(cfg):
+    """The velocity-set descriptor of a config: cfg["velset"] names a set
+    (D2Q9 .. D3Q125), or is "CUSTOM" with the caller's abscissae
+    cfg["velset_xi"] [Q][D] and weights cfg["velset_w"] [Q].  Returns the
+    descriptor and the arrays it points to (kept alive by the caller)."""
+    import numpy as np
+    d = capi.VelsetDesc()
+    d.kind = capi.VELSET[cfg["velset"]]
+    keep = ()
+    if cfg["velset"] == "CUSTOM":
+        xi = np.ascontiguousarray(cfg["velset_xi"], dtype=np.float64)
+        w = np.ascontiguousarray(cfg["velset_w"], dtype=np.float64)
+        d.Q, d.D = xi.shape
+        d.xi = xi.ctypes.data
+        d.w = w.ctypes.data
+        keep = (xi, w)
+    return d, keep
+
+
 class Sim:
     """One library context built from a workload config dict."""
 
@@ -68,7 +87,9 @@ class Sim:
         self._desc = mesh_desc(cfg)
         self._par = params(cfg, precision, stream_mode, device, stream)
         h = C.c_void_p()
-        rc = L.sllbm_create(C.byref(self._desc), capi.VELSET[cfg["velset"]], C.byref(self._par), C.byref(h))
+        vd, keep = velset_desc(cfg)
+        rc = L.sllbm_create_desc(C.byref(self._desc), C.byref(vd), C.byref(self._par), C.byref(h))
+        del keep
         if rc != capi.OK:
             msg = L.sllbm_last_error(None)
             raise capi.SllbmError(rc, msg.decode() if msg else "")

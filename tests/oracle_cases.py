@@ -4,14 +4,17 @@ import numpy as np
 from oracle import step as st
 from oracle.departure import trace
 from oracle.mesh import Mesh
-from oracle.velocity_sets import velocity_set
+from oracle.velocity_sets import custom_set, velocity_set
 
 
 def oracle_case(cfg):
     m = cfg["mesh"]
     mesh = Mesh(m["kind"], m["p"], m["cells"], m["length"], m.get("stretch", 1.0), m.get("central", 0),
                 m.get("thickness", 0.12))
-    xi, w, opp = velocity_set(cfg["velset"])
+    if cfg["velset"] == "CUSTOM":
+        xi, w, opp = custom_set(cfg["velset_xi"], cfg["velset_w"])
+    else:
+        xi, w, opp = velocity_set(cfg["velset"])
     par = st.Params(cfg["dt"], cfg["gamma"], cfg["Pr"], cfg["mu_ref"], cfg["T_ref"], cfg["mu_exp"], cfg["bcs"])
     rec = trace(mesh, xi, opp, cfg["dt"], cfg["bcs"])
     return mesh, xi, w, opp, par, rec

@@ -54,3 +54,55 @@ def test_release_build_flags_and_null_context_arguments(built_lib):
     code = ctypes.c_int32(7)
     assert built_lib.sllbm_device_status(None, ctypes.byref(code)) == -1
     assert built_lib.sllbm_mlp_path(None, 0) == -1
+
+
+def _custom_cfg(xi, w):
+    from workloads import get_config
+    cfg = get_config("tgv2d", cells=4)
+    cfg["velset"] = "CUSTOM"
+    cfg["velset_xi"] = xi
+    cfg["velset_w"] = w
+    return cfg
+
+
+def test_custom_velocity_sets_are_checked_before_any_device_work(built_lib):
+    """sllbm_create_desc copies and checks a caller's set (Sec. 3.2) before it
+    queries a device: a set that is not symmetric, does not reproduce the
+    weight function's moments to second order, has a non-positive weight or
+    too many velocities fails with SLLBM_ERR_ARG and a message naming the
+    check; a valid set passes them (and then, without a GPU, stops at the
+    device query with SLLBM_ERR_ARCH)."""
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2412_09051_gb300.capi import SllbmError
+    from paper_2412_09051_gb300.sim import Sim
+    from oracle.velocity_sets import velocity_set
+    xi, w, _ = velocity_set("D2Q9")
+    cases = [
+        (xi[:8], w[:8] / w[:8].sum(), "symmetric"),                          # drops (s, -s): no opposite left
+        (xi * 1.1, w, "moments"),                                             # second moment 1.21
+        (xi, np.where(np.arange(9) == 0, -w, w), "positive"),
+        (np.zeros((129, 2)), np.full(129, 1 / 129), "Q <= 128"),
+    ]
+    for bad_xi, bad_w, word in cases:
+        with pytest.raises(SllbmError) as e:
+            Sim(_custom_cfg(bad_xi, bad_w))
+        assert e.value.code == -1, (word, e.value)
+        assert word in str(e.value), (word, str(e.value))
+    with pytest.raises(SllbmError) as e:
+        Sim(_custom_cfg(xi, w))
+    assert e.value.code == -3
+
+
+def test_custom_kind_needs_the_descriptor(built_lib):
+    """sllbm_create with the custom kind (no arrays to read) is an argument error."""
+    from paper_2412_09051_gb300 import capi
+    from paper_2412_09051_gb300.sim import mesh_desc, params
+    from workloads import get_config
+    cfg = get_config("tgv2d", cells=4)
+    h = ctypes.c_void_p()
+    d, p = mesh_desc(cfg), params(cfg)
+    assert built_lib.sllbm_create(ctypes.byref(d), capi.VELSET["CUSTOM"], ctypes.byref(p), ctypes.byref(h)) == -1
+    assert b"sllbm_create_desc" in built_lib.sllbm_last_error(None)

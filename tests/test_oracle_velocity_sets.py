@@ -9,7 +9,7 @@ import pytest
 from oracle.velocity_sets import gaussian_moment, moment_error, monomials, velocity_set
 
 
-@pytest.mark.parametrize("name,deg", [("D2Q19", 9), ("D3Q45", 9), ("D2Q25", 9), ("D2Q9", 5)])
+@pytest.mark.parametrize("name,deg", [("D2Q19", 9), ("D3Q45", 9), ("D2Q25", 9), ("D2Q9", 5), ("D3Q125", 9)])
 def test_exact_to_degree(name, deg):
     xi, w, opp = velocity_set(name)
     assert moment_error(xi, w, deg) < 1e-11
@@ -17,7 +17,7 @@ def test_exact_to_degree(name, deg):
     assert abs(w.sum() - 1.0) < 1e-14
 
 
-@pytest.mark.parametrize("name,deg", [("D2Q19", 10), ("D3Q45", 10), ("D2Q25", 10), ("D2Q9", 6)])
+@pytest.mark.parametrize("name,deg", [("D2Q19", 10), ("D3Q45", 10), ("D2Q25", 10), ("D2Q9", 6), ("D3Q125", 10)])
 def test_not_exact_beyond_degree(name, deg):
     """The rules are exactly of the stated degree (Sec. 3.2: N = 9), not more."""
     xi, w, _ = velocity_set(name)
@@ -56,7 +56,7 @@ def test_gauss_hermite_nodes_are_roots_of_He5():
     assert np.abs(he5).max() < 1e-10
 
 
-@pytest.mark.parametrize("name", ["D2Q9", "D2Q19", "D2Q25", "D3Q45"])
+@pytest.mark.parametrize("name", ["D2Q9", "D2Q19", "D2Q25", "D3Q45", "D3Q125"])
 def test_opposites(name):
     xi, w, opp = velocity_set(name)
     assert np.abs(xi[opp] + xi).max() < 1e-14
@@ -78,3 +78,24 @@ def test_second_moment_isotropy():
     for name in ("D2Q19", "D3Q45", "D2Q25"):
         xi, w, _ = velocity_set(name)
         assert np.abs(np.einsum("q,qa,qb->ab", w, xi, xi) - np.eye(xi.shape[1])).max() < 1e-13
+
+
+def test_d3q125_is_the_gauss_hermite_product():
+    """D3Q125: every weight is the product of the three 1D 5-point
+    Gauss-Hermite weights of its coordinates (closed form; the oracle solves
+    the weights from the moment equations), nodes x fastest, then y, then z;
+    each coordinate a root of He_5."""
+    r10 = math.sqrt(10)
+    r1, r2 = math.sqrt(5 - r10), math.sqrt(5 + r10)
+    nodes = [0.0, r1, r2, -r1, -r2]
+    w1 = [8 / 15, (7 + 2 * r10) / 60, (7 - 2 * r10) / 60, (7 + 2 * r10) / 60, (7 - 2 * r10) / 60]
+    xi, w, _ = velocity_set("D3Q125")
+    assert xi.shape == (125, 3)
+    for i in range(125):
+        a, b, c = i % 5, (i // 5) % 5, i // 25
+        assert np.abs(xi[i] - [nodes[a], nodes[b], nodes[c]]).max() < 1e-15
+        assert abs(w[i] - w1[a] * w1[b] * w1[c]) < 1e-14
+    x = np.unique(np.round(xi.ravel(), 12))
+    assert np.abs(x ** 5 - 10 * x ** 3 + 15 * x).max() < 1e-10
+    # a product rule integrates x^8 y^8 z^8 exactly although its degree is 24
+    assert abs(float((w * (xi ** 8).prod(1)).sum()) - 105.0 ** 3) < 1e-7 * 105.0 ** 3
