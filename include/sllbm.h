@@ -36,6 +36,7 @@
 #ifndef SLLBM_H
 #define SLLBM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -250,6 +251,24 @@ int sllbm_create_desc(const sllbm_mesh_desc* mesh, const sllbm_velset_desc* vels
 
 /* Free everything the context owns.  NULL is accepted. */
 int sllbm_destroy(sllbm_ctx* ctx);
+
+/* Device memory from the caller (e.g. a framework's caching allocator).
+ * Contexts created after this call take every device buffer they own (state
+ * buffers, departure tables, scratch, the staging of host reads) from
+ * alloc(bytes, user) and give it back with release(ptr, user), from the
+ * thread that calls the library; contexts created before keep their own.
+ * The memory must be device memory of the context's GPU and 256-byte
+ * aligned: anything else is released at once and the call that asked for it
+ * fails with SLLBM_ERR_ARG; alloc returning NULL fails it with
+ * SLLBM_ERR_NOMEM.  A context releases its buffers in sllbm_destroy (after
+ * synchronising its stream) and temporaries before the call that took them
+ * returns.  Both NULL: cudaMalloc / cudaFree again (the default); exactly one
+ * NULL: SLLBM_ERR_ARG.  Process-wide; not synchronised with concurrent
+ * sllbm_create calls on other threads.  The training context
+ * (sllbm_train_create) allocates with cudaMalloc. */
+typedef void* (*sllbm_alloc_fn)(size_t bytes, void* user);
+typedef void (*sllbm_free_fn)(void* ptr, void* user);
+int sllbm_set_allocator(sllbm_alloc_fn alloc, sllbm_free_fn release, void* user);
 
 /* Message of the last failing call on ctx (ctx may be NULL: last create error). */
 const char* sllbm_last_error(const sllbm_ctx* ctx);

@@ -64,10 +64,13 @@ class Info(C.Structure):
 
 
 _P = C.c_void_p
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)     # sllbm_alloc_fn
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)            # sllbm_free_fn
 _SIGS = {
     "sllbm_create": (C.c_int, [C.POINTER(MeshDesc), C.c_int32, C.POINTER(Params), C.POINTER(_P)]),
     "sllbm_create_desc": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(VelsetDesc), C.POINTER(Params), C.POINTER(_P)]),
     "sllbm_destroy": (C.c_int, [_P]),
+    "sllbm_set_allocator": (C.c_int, [ALLOC_FN, FREE_FN, _P]),
     "sllbm_last_error": (C.c_char_p, [_P]),
     "sllbm_info": (C.c_int, [_P, C.POINTER(Info)]),
     "sllbm_node_coords": (C.c_int, [_P, _P, C.c_int32]),
@@ -148,3 +151,39 @@ def check(rc, ctx=None):
         msg = lib().sllbm_last_error(ctx)
         raise SllbmError(rc, msg.decode() if msg else "")
     return rc
+
+
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator
+    (sllbm_set_allocator): every buffer a context created while installed
+    owns is a torch uint8 tensor on the given device, held here until the
+    library releases it.  Keep the object alive while such contexts exist
+    (they call back into it).  Argument marshalling only."""
+
+    def __init__(self, device=0):
+        self.device = device
+        self.blocks = {}
+        self._alloc = ALLOC_FN(self._take)
+        self._free = FREE_FN(self._give)
+
+    def _take(self, nbytes, user):
+        import torch
+        t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=f"cuda:{self.device}")
+        self.blocks[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _give(self, ptr, user):
+        self.blocks.pop(ptr, None)
+
+    def install(self):
+        check(lib().sllbm_set_allocator(self._alloc, self._free, None))
+        return self
+
+    def uninstall(self):
+        check(lib().sllbm_set_allocator(ALLOC_FN(), FREE_FN(), None))
+
+    def __enter__(self):
+        return self.install()
+
+    def __exit__(self, *exc):
+        self.uninstall()

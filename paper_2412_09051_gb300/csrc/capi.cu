@@ -132,8 +132,43 @@ int fail(sllbm_ctx* c, int code, const std::string& msg) {
 }
 
 int cuda_fail(sllbm_ctx* c, cudaError_t e, const char* what) {
+    if (c && c->bad_alloc) {
+        c->bad_alloc = false;
+        return fail(c, SLLBM_ERR_ARG,
+                    std::string(what) + ": the allocator returned memory that is not 256-byte aligned device "
+                                        "memory of the context's GPU");
+    }
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
     return fail(c, e == cudaErrorMemoryAllocation ? SLLBM_ERR_NOMEM : SLLBM_ERR_CUDA, m);
+}
+
+// Device memory of a context: from the caller's allocator when one was set
+// (sllbm_set_allocator) at the context's creation, else cudaMalloc / cudaFree.
+// The caller's memory must be device memory of the context's GPU, 256-byte
+// aligned; anything else is handed back and reported.
+cudaError_t dev_alloc(sllbm_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (!c->alloc_fn) return cudaMalloc(p, bytes);
+    void* q = c->alloc_fn(bytes, c->alloc_user);
+    if (!q) return cudaErrorMemoryAllocation;
+    cudaPointerAttributes at{};
+    const bool ok = (reinterpret_cast<uintptr_t>(q) % 256) == 0 && cudaPointerGetAttributes(&at, q) == cudaSuccess &&
+                    at.type == cudaMemoryTypeDevice && at.device == c->device;
+    if (!ok) {
+        cudaGetLastError();
+        c->free_fn(q, c->alloc_user);
+        c->bad_alloc = true;
+        return cudaErrorInvalidValue;
+    }
+    *p = q;
+    return cudaSuccess;
+}
+void dev_free(sllbm_ctx* c, void* p) {
+    if (!p) return;
+    if (c->alloc_fn)
+        c->free_fn(p, c->alloc_user);
+    else
+        cudaFree(p);
 }
 
 #define CK(call)                                                   \
@@ -318,7 +353,7 @@ int ensure_mlp_image(sllbm_ctx* ctx) {
     for (int k = 0; k < (D + 2) * (D + 2); ++k) img[o_gi + k] = float(Ginv[k]);
     img[n - 1] = 1.0f;
     ctx->mlp_host = img;
-    CK(cudaMalloc(&ctx->mlp_img, sizeof(float) * n));
+    CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->mlp_img), sizeof(float) * n));
     CK(cudaMemcpyAsync(ctx->mlp_img, img.data(), sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return SLLBM_OK;
@@ -846,7 +881,7 @@ int encode_tm2_maps(sllbm_ctx* c) {
                 return fail(c, SLLBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string(int(r)) + ")");
         }
     }
-    cudaError_t e = cudaMalloc(&c->tm2_maps, sizeof(CUtensorMap) * maps.size());
+    cudaError_t e = dev_alloc(c, reinterpret_cast<void**>(&c->tm2_maps), sizeof(CUtensorMap) * maps.size());
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
     e = cudaMemcpyAsync(c->tm2_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                         c->stream);
@@ -1149,13 +1184,18 @@ int sllbm_destroy(sllbm_ctx* ctx) {
                     ctx->tm_bop, ctx->d_layers, ctx->tm2_head, ctx->tm2_recs, ctx->tm2_maps, ctx->tm2_smask,
                     ctx->gen_v, ctx->gen_v64};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) dev_free(ctx, p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return SLLBM_OK;
 }
 
 namespace {
+// the allocator of contexts created from now on (sllbm_set_allocator)
+sllbm_alloc_fn g_alloc_fn = nullptr;
+sllbm_free_fn g_free_fn = nullptr;
+void* g_alloc_user = nullptr;
+
 // sllbm_create and sllbm_create_desc: `vs_in` is a checked caller's set
 // (SLLBM_VELSET_CUSTOM), else the set of kind `velset` is built here
 int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs_in, const sllbm_params* params,
@@ -1190,6 +1230,9 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
         sllbm_destroy(ctx);
         return code;
     };
+    ctx->alloc_fn = g_alloc_fn;
+    ctx->free_fn = g_free_fn;
+    ctx->alloc_user = g_alloc_user;
     ctx->generic = velset == SLLBM_D3Q125 || velset == SLLBM_VELSET_CUSTOM;
     int rc = SLLBM_OK;
     if (vs_in)
@@ -1272,7 +1315,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
         const int64_t N = m.n_nodes;
         cudaStream_t s = ctx->stream;
         // ---- geometry upload
-        CK(cudaMalloc(&ctx->dX, sizeof(double) * N * D));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->dX), sizeof(double) * N * D));
         CK(cudaMemcpyAsync(ctx->dX, m.X.data(), sizeof(double) * N * D, cudaMemcpyHostToDevice, s));
         MeshView MV;
         std::memset(&MV, 0, sizeof(MV));
@@ -1287,7 +1330,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
         }
         if (axis)
             for (int d = 0; d < D; ++d) {
-                CK(cudaMalloc(&ctx->dV[d], sizeof(double) * m.V[d].size()));
+                CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->dV[d]), sizeof(double) * m.V[d].size()));
                 CK(cudaMemcpyAsync(ctx->dV[d], m.V[d].data(), sizeof(double) * m.V[d].size(),
                                    cudaMemcpyHostToDevice, s));
                 MV.V[d] = ctx->dV[d];
@@ -1326,7 +1369,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
             G.ncls[d] = d < D ? (m.periodic[d] ? m.p : m.N[d]) : 1;
             G.n_classes *= G.ncls[d];
         }
-        CK(cudaMalloc(&ctx->d_status, 2 * sizeof(int)));       // status word, test wait limit
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_status), 2 * sizeof(int)));       // status word, test wait limit
         CK(cudaMemsetAsync(ctx->d_status, 0, 2 * sizeof(int), ctx->stream));
 #ifdef SLLBM_CHECKED
         G.status = ctx->d_status;
@@ -1335,8 +1378,8 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
         ctx->n_rec_units = st ? G.n_classes : N;
         const int64_t U = ctx->n_rec_units;
         // ---- FP64 trace
-        CK(cudaMalloc(&ctx->rec64, sizeof(Rec64) * U * Q));
-        CK(cudaMalloc(&ctx->d_flag, sizeof(int) * 4));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->rec64), sizeof(Rec64) * U * Q));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_flag), sizeof(int) * 4));
         CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int) * 4, s));
         int r2 = launch_trace(A, ctx->dX, U, st ? 1 : 0, G.ncls[0], G.ncls[1], ctx->rec64, ctx->d_flag, s);
         if (r2) return fail(ctx, r2, "trace launch failed");
@@ -1354,9 +1397,9 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
         double* d_bcT = nullptr;
         double* d_tw64 = nullptr;
         unsigned long long* d_cnt = nullptr;
-        CK(cudaMalloc(&d_bcT, sizeof(bcT)));
-        CK(cudaMalloc(&d_tw64, sizeof(double) * U));
-        CK(cudaMalloc(&d_cnt, sizeof(unsigned long long) * 2));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&d_bcT), sizeof(bcT)));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&d_tw64), sizeof(double) * U));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&d_cnt), sizeof(unsigned long long) * 2));
         CK(cudaMemcpyAsync(d_bcT, bcT, sizeof(bcT), cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * 2, s));
         r2 = launch_isothermal(ctx->rec64, U, Q, d_bcT, d_tw64, d_cnt, s);
@@ -1366,9 +1409,9 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
         CK(cudaMemcpyAsync(tw.data(), d_tw64, sizeof(double) * U, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        cudaFree(d_bcT);
-        cudaFree(d_tw64);
-        cudaFree(d_cnt);
+        dev_free(ctx, d_bcT);
+        dev_free(ctx, d_tw64);
+        dev_free(ctx, d_cnt);
         ctx->n_boundary_records = int64_t(cnt[0]);
         ctx->n_isothermal_nodes = int64_t(cnt[1]);
         if (st) {   // isothermal count per node = per class x class multiplicity
@@ -1379,7 +1422,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
             ctx->n_isothermal_nodes *= mult;
         }
         const size_t rs = real_size(ctx);
-        CK(cudaMalloc(&ctx->tw_tab, rs * U));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tw_tab), rs * U));
         if (rs == 8) {
             CK(cudaMemcpyAsync(ctx->tw_tab, tw.data(), 8 * U, cudaMemcpyHostToDevice, s));
         } else {
@@ -1400,12 +1443,12 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
                 if (rs == 8) {
                     std::vector<TileRecP<double, 4>> t;
                     build_tile_table_p(ctx, rec, t);
-                    CK(cudaMalloc(&ctx->tile_tab, sizeof(t[0]) * t.size()));
+                    CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tile_tab), sizeof(t[0]) * t.size()));
                     CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(t[0]) * t.size(), cudaMemcpyHostToDevice, s));
                 } else {
                     std::vector<TileRecP<float, 4>> t;
                     build_tile_table_p(ctx, rec, t);
-                    CK(cudaMalloc(&ctx->tile_tab, sizeof(t[0]) * t.size()));
+                    CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tile_tab), sizeof(t[0]) * t.size()));
                     CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(t[0]) * t.size(), cudaMemcpyHostToDevice, s));
                 }
                 CK(cudaStreamSynchronize(s));
@@ -1415,7 +1458,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
                 if (rs == 8) {
                     std::vector<TileRec<double>> t;
                     build_tile_table(ctx, rec, t);
-                    CK(cudaMalloc(&ctx->tile_tab, sizeof(TileRec<double>) * t.size()));
+                    CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tile_tab), sizeof(TileRec<double>) * t.size()));
                     CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(TileRec<double>) * t.size(),
                                        cudaMemcpyHostToDevice, s));
                 } else {
@@ -1434,7 +1477,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
                         }
                         for (int q = 0; q < 3; ++q) o.wx[q] = t[k].wx[q];
                     }
-                    CK(cudaMalloc(&ctx->row_tab, sizeof(RowRec) * rr.size()));
+                    CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->row_tab), sizeof(RowRec) * rr.size()));
                     CK(cudaMemcpyAsync(ctx->row_tab, rr.data(), sizeof(RowRec) * rr.size(), cudaMemcpyHostToDevice, s));
                     CK(cudaStreamSynchronize(s));
                     std::vector<int32_t> th;
@@ -1444,12 +1487,12 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
                     std::vector<TmRec2> tr2;
                     std::vector<uint64_t> ts;
                     if (ctx->want_tm2 && build_rows_pairs(ctx, t, th, tr2, tx, ts)) {
-                        CK(cudaMalloc(&ctx->tm2_smask, sizeof(uint64_t) * ts.size()));
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm2_smask), sizeof(uint64_t) * ts.size()));
                         CK(cudaMemcpyAsync(ctx->tm2_smask, ts.data(), sizeof(uint64_t) * ts.size(),
                                            cudaMemcpyHostToDevice, s));
-                        CK(cudaMalloc(&ctx->tm2_head, sizeof(int32_t) * th.size()));
-                        CK(cudaMalloc(&ctx->tm2_recs, sizeof(TmRec2) * tr2.size()));
-                        CK(cudaMalloc(&ctx->tm_xmask, sizeof(uint64_t) * tx.size()));
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm2_head), sizeof(int32_t) * th.size()));
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm2_recs), sizeof(TmRec2) * tr2.size()));
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm_xmask), sizeof(uint64_t) * tx.size()));
                         CK(cudaMemcpyAsync(ctx->tm2_head, th.data(), sizeof(int32_t) * th.size(),
                                            cudaMemcpyHostToDevice, s));
                         CK(cudaMemcpyAsync(ctx->tm2_recs, tr2.data(), sizeof(TmRec2) * tr2.size(),
@@ -1466,13 +1509,13 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
                     }
                     if (!ctx->rows_tm2 && ctx->want_tmem && build_rows_tmem(ctx, t, th, tr, tx, tb)) {
                         if (!tb.empty()) {
-                            CK(cudaMalloc(&ctx->tm_bop, sizeof(float) * tb.size()));
+                            CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm_bop), sizeof(float) * tb.size()));
                             CK(cudaMemcpyAsync(ctx->tm_bop, tb.data(), sizeof(float) * tb.size(),
                                                cudaMemcpyHostToDevice, s));
                         }
-                        CK(cudaMalloc(&ctx->tm_head, sizeof(int32_t) * th.size()));
-                        CK(cudaMalloc(&ctx->tm_recs, sizeof(TmRec) * tr.size()));
-                        CK(cudaMalloc(&ctx->tm_xmask, sizeof(uint64_t) * tx.size()));
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm_head), sizeof(int32_t) * th.size()));
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm_recs), sizeof(TmRec) * tr.size()));
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm_xmask), sizeof(uint64_t) * tx.size()));
                         CK(cudaMemcpyAsync(ctx->tm_head, th.data(), sizeof(int32_t) * th.size(),
                                            cudaMemcpyHostToDevice, s));
                         CK(cudaMemcpyAsync(ctx->tm_recs, tr.data(), sizeof(TmRec) * tr.size(),
@@ -1485,7 +1528,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
                         ctx->tm_grid = std::min(ctx->tm.ntiles, sms);
                         ctx->rows_tmem = true;
                     }
-                    CK(cudaMalloc(&ctx->tile_tab, sizeof(TileRec<float>) * t.size()));
+                    CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tile_tab), sizeof(TileRec<float>) * t.size()));
                     CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(TileRec<float>) * t.size(),
                                        cudaMemcpyHostToDevice, s));
                 }
@@ -1494,7 +1537,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
             if (rs == 8) {
                 std::vector<ClassRec<double>> t;
                 build_class_table(ctx, rec, t);
-                CK(cudaMalloc(&ctx->cls_tab, sizeof(ClassRec<double>) * t.size()));
+                CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->cls_tab), sizeof(ClassRec<double>) * t.size()));
                 CK(cudaMemcpyAsync(ctx->cls_tab, t.data(), sizeof(ClassRec<double>) * t.size(),
                                    cudaMemcpyHostToDevice, s));
                 ctx->table_bytes = int64_t(sizeof(ClassRec<double>) * t.size());
@@ -1502,15 +1545,15 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
             } else {
                 std::vector<ClassRec<float>> t;
                 build_class_table(ctx, rec, t);
-                CK(cudaMalloc(&ctx->cls_tab, sizeof(ClassRec<float>) * t.size()));
+                CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->cls_tab), sizeof(ClassRec<float>) * t.size()));
                 CK(cudaMemcpyAsync(ctx->cls_tab, t.data(), sizeof(ClassRec<float>) * t.size(),
                                    cudaMemcpyHostToDevice, s));
                 ctx->table_bytes = int64_t(sizeof(ClassRec<float>) * t.size());
                 CK(cudaStreamSynchronize(s));
             }
         } else {
-            CK(cudaMalloc(&ctx->g_code, sizeof(int32_t) * N * Q));
-            CK(cudaMalloc(&ctx->g_xi, rs * N * Q * D));
+            CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->g_code), sizeof(int32_t) * N * Q));
+            CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->g_xi), rs * N * Q * D));
             ctx->table_bytes = int64_t((4 + rs * D) * N * Q);
             r2 = rs == 8 ? launch_pack_gather<double>(ctx->rec64, N, Q, D, ctx->g_code, (double*)ctx->g_xi, s)
                          : launch_pack_gather<float>(ctx->rec64, N, Q, D, ctx->g_code, (float*)ctx->g_xi, s);
@@ -1518,14 +1561,14 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
         }
         // ---- state buffers
         for (int b = 0; b < 2; ++b) {
-            CK(cudaMalloc(&ctx->fg[b], 2 * rs * N * Q));
+            CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->fg[b]), 2 * rs * N * Q));
         }
         if (ctx->generic) {
             // the generic kernels' per-velocity table, in the context's
             // precision and in FP64 (initialisation, moments, conservation)
             std::vector<GenVel<double>> g64;
             build_gen_table<double>(ctx, g64);
-            CK(cudaMalloc(&ctx->gen_v64, sizeof(GenVel<double>) * g64.size()));
+            CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->gen_v64), sizeof(GenVel<double>) * g64.size()));
             CK(cudaMemcpyAsync(ctx->gen_v64, g64.data(), sizeof(GenVel<double>) * g64.size(), cudaMemcpyHostToDevice,
                                s));
             if (rs == 8) {
@@ -1533,7 +1576,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
             } else {
                 std::vector<GenVel<float>> g32;
                 build_gen_table<float>(ctx, g32);
-                CK(cudaMalloc(&ctx->gen_v, sizeof(GenVel<float>) * g32.size()));
+                CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->gen_v), sizeof(GenVel<float>) * g32.size()));
                 CK(cudaMemcpyAsync(ctx->gen_v, g32.data(), sizeof(GenVel<float>) * g32.size(),
                                    cudaMemcpyHostToDevice, s));
             }
@@ -1542,7 +1585,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
             const int r3 = encode_tm2_maps(ctx);          // the maps name the state buffers
             if (r3 != SLLBM_OK) return r3;
         }
-        CK(cudaMalloc(&ctx->d_red, sizeof(double) * (conserve_blocks() * 5 + 8)));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_red), sizeof(double) * (conserve_blocks() * 5 + 8)));
         CK(cudaStreamSynchronize(s));
         return SLLBM_OK;
     }();
@@ -1551,6 +1594,15 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
     return SLLBM_OK;
 }
 }  // namespace
+
+int sllbm_set_allocator(sllbm_alloc_fn alloc, sllbm_free_fn release, void* user) {
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(nullptr, SLLBM_ERR_ARG, "sllbm_set_allocator needs both functions, or neither");
+    g_alloc_fn = alloc;
+    g_free_fn = release;
+    g_alloc_user = alloc ? user : nullptr;
+    return SLLBM_OK;
+}
 
 int sllbm_create(const sllbm_mesh_desc* mesh, int32_t velset, const sllbm_params* params, sllbm_ctx** out) {
     if (velset == SLLBM_VELSET_CUSTOM) {
@@ -1632,7 +1684,7 @@ int sllbm_init_state(sllbm_ctx* ctx, const double* rho, const double* u, const d
     const double *dr = rho, *du = u, *dT = T;
     double* tmp = nullptr;
     if (!on_device) {
-        CK(cudaMalloc(&tmp, sizeof(double) * N * (D + 2)));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&tmp), sizeof(double) * N * (D + 2)));
         CK(cudaMemcpyAsync(tmp, rho, sizeof(double) * N, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(tmp + N, u, sizeof(double) * N * D, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(tmp + N * (D + 1), T, sizeof(double) * N, cudaMemcpyHostToDevice, s));
@@ -1651,7 +1703,7 @@ int sllbm_init_state(sllbm_ctx* ctx, const double* rho, const double* u, const d
                  : launch_init<float>(ctx->velset, dr, du, dT, N, ctx->cc64, (float2*)ctx->fg[0], s);
     if (tmp) {
         CK(cudaStreamSynchronize(s));
-        cudaFree(tmp);
+        dev_free(ctx, tmp);
     }
     if (rc) return fail(ctx, rc, "init launch failed");
     ctx->cur = 0;
@@ -1668,7 +1720,7 @@ int state_io(sllbm_ctx* ctx, double* f, double* g, const double* cf, const doubl
     cudaStream_t s = ctx->stream;
     const size_t bytes = sizeof(double) * N * Q;
     double* buf = nullptr;
-    CK(cudaMalloc(&buf, 2 * bytes + sizeof(double) * 2 * Q));
+    CK(dev_alloc(ctx, reinterpret_cast<void**>(&buf), 2 * bytes + sizeof(double) * 2 * Q));
     double* dw = buf + 2 * N * Q;
     std::vector<double> wv(2 * Q);
     const double gf = 2.0 / (ctx->params.gamma - 1.0) - ctx->mesh.D;
@@ -1692,7 +1744,7 @@ int state_io(sllbm_ctx* ctx, double* f, double* g, const double* cf, const doubl
         if (g) CK(cudaMemcpyAsync(g, buf + N * Q, bytes, k_out, s));
     }
     CK(cudaStreamSynchronize(s));
-    cudaFree(buf);
+    dev_free(ctx, buf);
     return rc ? fail(ctx, rc, "convert launch failed") : SLLBM_OK;
 }
 }  // namespace
@@ -1797,7 +1849,7 @@ int sllbm_step_features(sllbm_ctx* ctx, float* z, int32_t on_device) {
     const size_t bytes = sizeof(float) * ctx->mesh.n_nodes * ctx->vs.Q;
     float* dz = z;
     if (!on_device) {
-        if (!ctx->d_feat) CK(cudaMalloc(&ctx->d_feat, bytes));
+        if (!ctx->d_feat) CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_feat), bytes));
         dz = ctx->d_feat;
     }
     rc = step_once(ctx, dz);
@@ -1852,9 +1904,9 @@ int sllbm_mlp_set(sllbm_ctx* ctx, const uint16_t* w_bf16, const float* biases, c
         for (int q = 0; q < H; ++q) put(TC::B1, j, q, H, W2[j * H + q]);
     for (int i = 0; i < Q; ++i)
         for (int q = 0; q < H; ++q) put(TC::B1 + TC::B2, i, q, H, W3[i * H + q]);
-    if (!ctx->mlp_tc) CK(cudaMalloc(&ctx->mlp_tc, TC::B_BYTES));
+    if (!ctx->mlp_tc) CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->mlp_tc), TC::B_BYTES));
     if (!ctx->d_status) {
-        CK(cudaMalloc(&ctx->d_status, 2 * sizeof(int)));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_status), 2 * sizeof(int)));
         CK(cudaMemsetAsync(ctx->d_status, 0, 2 * sizeof(int), ctx->stream));
     }
     CK(cudaMemcpyAsync(ctx->mlp_tc, tiles.data(), TC::B_BYTES, cudaMemcpyHostToDevice, ctx->stream));
@@ -1924,7 +1976,7 @@ int sllbm_read_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int32_
     cudaStream_t s = ctx->stream;
     double *dr = rho, *du = u, *dT = T, *tmp = nullptr;
     if (!on_device) {
-        if (!ctx->d_mom) CK(cudaMalloc(&ctx->d_mom, sizeof(double) * N * (D + 2)));
+        if (!ctx->d_mom) CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_mom), sizeof(double) * N * (D + 2)));
         tmp = ctx->d_mom;
         dr = rho ? tmp : nullptr;
         du = u ? tmp + N : nullptr;
@@ -2068,10 +2120,10 @@ int x_layers(sllbm_ctx* ctx, int32_t x0, int32_t nx, void* buf, int32_t on_devic
     void* dbuf = buf;
     if (!on_device) {
         if (ctx->layer_bytes < bytes) {
-            if (ctx->d_layers) cudaFree(ctx->d_layers);
+            if (ctx->d_layers) dev_free(ctx, ctx->d_layers);
             ctx->d_layers = nullptr;
             ctx->layer_bytes = 0;
-            CK(cudaMalloc(&ctx->d_layers, bytes));
+            CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_layers), bytes));
             ctx->layer_bytes = bytes;
         }
         dbuf = ctx->d_layers;
@@ -2141,7 +2193,7 @@ int sllbm_rescale_mass(sllbm_ctx* ctx, double target_mass) {
             wv[i] = ctx->vs.w[i];
             wv[Q + i] = ctx->vs.w[i] * gf;
         }
-        CK(cudaMalloc(&ctx->d_wref, sizeof(double) * 2 * Q));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_wref), sizeof(double) * 2 * Q));
         CK(cudaMemcpy(ctx->d_wref, wv.data(), sizeof(double) * 2 * Q, cudaMemcpyHostToDevice));
     }
     const int c = ctx->cur;
@@ -2191,7 +2243,7 @@ namespace {
 int moments_on_device(sllbm_ctx* ctx, double*& r, double*& u, double*& T) {
     const int64_t N = ctx->mesh.n_nodes;
     const int D = ctx->mesh.D;
-    if (!ctx->d_mom) CK(cudaMalloc(&ctx->d_mom, sizeof(double) * N * (D + 2)));
+    if (!ctx->d_mom) CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_mom), sizeof(double) * N * (D + 2)));
     r = ctx->d_mom;
     u = ctx->d_mom + N;
     T = ctx->d_mom + N * (D + 1);
@@ -2215,7 +2267,7 @@ int plane_means(sllbm_ctx* ctx, std::vector<double>& S) {
     double *r = nullptr, *u = nullptr, *T = nullptr;
     rc = moments_on_device(ctx, r, u, T);
     if (rc) return rc;
-    if (!ctx->d_plane) CK(cudaMalloc(&ctx->d_plane, sizeof(double) * m.N[1] * K));
+    if (!ctx->d_plane) CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_plane), sizeof(double) * m.N[1] * K));
     rc = launch_plane_sums(r, u, T, m.D, m.N[0], m.N[1], m.D == 3 ? m.N[2] : 1, ctx->d_plane, 0, ctx->stream);
     if (rc) return fail(ctx, rc, "plane statistics launch failed");
     S.assign(size_t(m.N[1]) * K, 0.0);
@@ -2291,7 +2343,7 @@ int sllbm_stats_accumulate(sllbm_ctx* ctx) {
     const HostMesh& m = ctx->mesh;
     const int K = plane_stat_count(m.D);
     if (!ctx->d_plane_acc) {
-        CK(cudaMalloc(&ctx->d_plane_acc, sizeof(double) * m.N[1] * K));
+        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_plane_acc), sizeof(double) * m.N[1] * K));
         CK(cudaMemsetAsync(ctx->d_plane_acc, 0, sizeof(double) * m.N[1] * K, ctx->stream));
         ctx->stats_samples = 0;
     }
@@ -2386,7 +2438,7 @@ int sllbm_plane_cp(sllbm_ctx* ctx, int32_t side, double p0, double mach, double*
         double *r = nullptr, *u = nullptr, *T = nullptr;
         int rc = moments_on_device(ctx, r, u, T);
         if (rc) return rc;
-        if (!ctx->d_cp) CK(cudaMalloc(&ctx->d_cp, sizeof(double) * M));
+        if (!ctx->d_cp) CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_cp), sizeof(double) * M));
         const double denom = 0.5 * ctx->params.gamma * p0 * mach * mach;
         rc = launch_plane_cp(r, T, m.N[0], m.N[1], N2, j, p0, denom, ctx->d_cp, ctx->stream);
         if (rc) return fail(ctx, rc, "pressure coefficient launch failed");

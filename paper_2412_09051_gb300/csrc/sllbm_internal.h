@@ -229,6 +229,10 @@ struct sllbm_ctx {
     int32_t* tm_head = nullptr;          // copy lists [Q][n_tc][TM_HEAD]
     void* tm_recs = nullptr;             // TmRec [Q][n_tc][TY TZ][2]
     bool want_tm2 = false;               // SLLBM_STREAM_ROWS_PAIRS requested
+    sllbm_alloc_fn alloc_fn = nullptr;   // caller's device allocator (sllbm_set_allocator), or cudaMalloc
+    sllbm_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    bool bad_alloc = false;              // the allocator returned unusable memory (reported as an argument error)
     bool generic = false;                // a D3Q125 or caller's set: the generic kernels (generic.cu)
     void* gen_v = nullptr;               // GenVel<real> [Q] in the context's precision
     void* gen_v64 = nullptr;             // GenVel<double> [Q] (initialisation, moments, conservation)

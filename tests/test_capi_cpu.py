@@ -106,3 +106,13 @@ def test_custom_kind_needs_the_descriptor(built_lib):
     d, p = mesh_desc(cfg), params(cfg)
     assert built_lib.sllbm_create(ctypes.byref(d), capi.VELSET["CUSTOM"], ctypes.byref(p), ctypes.byref(h)) == -1
     assert b"sllbm_create_desc" in built_lib.sllbm_last_error(None)
+
+
+def test_set_allocator_arguments(built_lib):
+    """sllbm_set_allocator needs both functions or neither (no device work)."""
+    from paper_2412_09051_gb300 import capi
+    alloc = capi.TorchAllocator()
+    assert built_lib.sllbm_set_allocator(alloc._alloc, capi.FREE_FN(), None) == -1
+    assert b"both functions" in built_lib.sllbm_last_error(None)
+    assert built_lib.sllbm_set_allocator(capi.ALLOC_FN(), alloc._free, None) == -1
+    assert built_lib.sllbm_set_allocator(capi.ALLOC_FN(), capi.FREE_FN(), None) == 0
