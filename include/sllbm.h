@@ -71,6 +71,13 @@ extern "C" {
                                    dim 0 around (periodic),
                                    dim 1 radial, growth factor s per cell up to a circle of
                                    radius L_1 about mid-chord; isoparametric degree-p cells  */
+#define SLLBM_MESH_EXPLICIT  4  /* axis-aligned cells on the caller's vertex coordinates per
+                                   dimension (vertices[d]: cells[d] + 1 strictly increasing
+                                   values, lengths taken from them); x and z periodic, y
+                                   periodic when both boundary kinds are SLLBM_BC_PERIODIC,
+                                   else bounded by them; a periodic dimension starts at 0.
+                                   Uniform periodic dimensions keep every streaming mode;
+                                   non-uniform ones take the gather streaming               */
 
 /* Velocity sets (Sec. 3.2).  Ordering: index 0 rest, then shells; inside a
  * shell of n points the second half are the negatives of the first half.
@@ -192,6 +199,9 @@ typedef struct {
     int32_t  central;      /* mixing: number of uniform central cells in y         */
     double   thickness;    /* NACA relative thickness t (0.12 for NACA-0012)       */
     sllbm_bc bc[2];        /* boundary ids 0 and 1                                 */
+    const double* vertices[3];  /* EXPLICIT: host arrays of cells[d] + 1 vertex
+                                   coordinates per dimension, read during the call
+                                   (other kinds: ignored)                              */
 } sllbm_mesh_desc;
 
 typedef struct {

@@ -22,14 +22,18 @@ Kinds
            centred at mid-chord; cells are isoparametric of degree p over
            their own support points (curved cells).
 
-For the box / channel / mixing kinds cells are axis-aligned boxes and the cell
-map is affine per dimension.
+  explicit axis-aligned cells on given vertex coordinates per dimension; x and
+           z periodic, y periodic when `periodic_y`; a periodic dimension
+           starts at 0 and its length is its last vertex.
+
+For the box / channel / mixing / explicit kinds cells are axis-aligned boxes
+and the cell map is affine per dimension.
 """
 import math
 
 import numpy as np
 
-KIND_BOX, KIND_CHANNEL, KIND_MIXING, KIND_NACA = 0, 1, 2, 3
+KIND_BOX, KIND_CHANNEL, KIND_MIXING, KIND_NACA, KIND_EXPLICIT = 0, 1, 2, 3, 4
 TE_BLEND = 0.25
 
 
@@ -77,11 +81,15 @@ def naca_half_thickness(x, t):
 
 
 class Mesh:
-    def __init__(self, kind, p, cells, length, stretch=1.0, central=0, thickness=0.12):
+    def __init__(self, kind, p, cells, length, stretch=1.0, central=0, thickness=0.12, vertices=None,
+                 periodic_y=False):
         self.kind = kind
         self.p = p
         self.cells = tuple(int(c) for c in cells)
         self.D = len(self.cells)
+        if kind == KIND_EXPLICIT:
+            self._given = [np.asarray(v, dtype=np.float64) for v in vertices]
+            length = [float(v[-1] - v[0]) for v in self._given]
         self.length = tuple(float(v) for v in length)
         self.stretch = float(stretch)
         self.central = int(central)
@@ -94,6 +102,8 @@ class Mesh:
         elif kind == KIND_NACA:
             assert D == 2
             self.periodic = (True, False)
+        elif kind == KIND_EXPLICIT:
+            self.periodic = tuple(d != 1 or bool(periodic_y) for d in range(D))
         else:
             raise ValueError(kind)
         self.N = tuple(c * p if per else c * p + 1 for c, per in zip(self.cells, self.periodic))
@@ -109,6 +119,8 @@ class Mesh:
 
     # ---------------------------------------------------------------- geometry
     def _vertices_1d(self, d):
+        if self.kind == KIND_EXPLICIT:
+            return self._given[d].copy()
         C, L = self.cells[d], self.length[d]
         j = np.arange(C + 1, dtype=np.float64)
         if d != 1 or self.kind == KIND_BOX:

@@ -15,7 +15,7 @@ OK = 0
 ERRORS = {-1: "SLLBM_ERR_ARG", -2: "SLLBM_ERR_CUDA", -3: "SLLBM_ERR_ARCH", -4: "SLLBM_ERR_NOMEM",
           -5: "SLLBM_ERR_DP_NOT_FOUND", -6: "SLLBM_ERR_UNSTABLE", -7: "SLLBM_ERR_STATE",
           -8: "SLLBM_ERR_UNSUPPORTED"}
-MESH = dict(box=0, channel=1, mixing=2, naca=3)
+MESH = dict(box=0, channel=1, mixing=2, naca=3, explicit=4)
 VELSET = dict(D2Q9=0, D2Q19=1, D2Q25=2, D3Q45=3, D3Q125=4, CUSTOM=5)
 QMAX_GENERIC = 128
 MLP_TENSOR, MLP_SIMT = 0, 1
@@ -35,7 +35,7 @@ class Bc(C.Structure):
 class MeshDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dim", C.c_int32), ("p", C.c_int32), ("cells", C.c_int32 * 3),
                 ("length", C.c_double * 3), ("stretch", C.c_double), ("central", C.c_int32),
-                ("thickness", C.c_double), ("bc", Bc * 2)]
+                ("thickness", C.c_double), ("bc", Bc * 2), ("vertices", C.c_void_p * 3)]
 
 
 class Params(C.Structure):

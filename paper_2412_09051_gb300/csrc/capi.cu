@@ -1203,15 +1203,6 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
     if (!out) return fail(nullptr, SLLBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!mesh || !params) return fail(nullptr, SLLBM_ERR_ARG, "NULL descriptor");
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
-        return fail(nullptr, SLLBM_ERR_ARCH, "no CUDA device available");
-    if (params->device < 0 || params->device >= ndev) return fail(nullptr, SLLBM_ERR_ARG, "bad device ordinal");
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, params->device) != cudaSuccess)
-        return fail(nullptr, SLLBM_ERR_CUDA, "cudaGetDeviceProperties failed");
-    if (!(prop.major == 10 && prop.minor == 3))
-        return fail(nullptr, SLLBM_ERR_ARCH, "device is not compute capability 10.3 (sm_103)");
     if (!(params->dt > 0) || !(params->gamma > 1.0) || !(params->Pr > 0) || !(params->mu_ref > 0) ||
         !(params->T_ref > 0))
         return fail(nullptr, SLLBM_ERR_ARG, "dt > 0, gamma > 1, Pr > 0, mu_ref > 0, T_ref > 0 required");
@@ -1257,15 +1248,41 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
             ctx->last_error = "bad boundary descriptor";
             return bail(SLLBM_ERR_ARG);
         }
-        if (ctx->mesh.kind != SLLBM_MESH_BOX && k == SLLBM_BC_PERIODIC) {
+        if (ctx->mesh.kind != SLLBM_MESH_BOX && !(ctx->mesh.kind == SLLBM_MESH_EXPLICIT && ctx->mesh.periodic[1]) &&
+            k == SLLBM_BC_PERIODIC) {
             ctx->last_error = "non-periodic boundary needs a boundary kind";
             return bail(SLLBM_ERR_ARG);
+        }
+    }
+    // the host-side descriptors are checked; now the device
+    {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+            cudaGetLastError();
+            ctx->last_error = "no CUDA device available";
+            return bail(SLLBM_ERR_ARCH);
+        }
+        if (params->device < 0 || params->device >= ndev) {
+            ctx->last_error = "bad device ordinal";
+            return bail(SLLBM_ERR_ARG);
+        }
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, params->device) != cudaSuccess) {
+            ctx->last_error = "cudaGetDeviceProperties failed";
+            return bail(SLLBM_ERR_CUDA);
+        }
+        if (!(prop.major == 10 && prop.minor == 3)) {
+            ctx->last_error = "device is not compute capability 10.3 (sm_103)";
+            return bail(SLLBM_ERR_ARCH);
         }
     }
     const bool axis = ctx->mesh.kind != SLLBM_MESH_NACA;
     int mode = params->stream_mode;
     if (mode == SLLBM_STREAM_AUTO) mode = axis ? SLLBM_STREAM_STRUCTURED : SLLBM_STREAM_GATHER;
     if (ctx->generic) mode = SLLBM_STREAM_GATHER;       // one departure record per (node, velocity)
+    // the class records assume translation invariance along periodic
+    // dimensions: a non-uniform one takes the gather streaming
+    if (!ctx->mesh.uniform_periodic) mode = SLLBM_STREAM_GATHER;
     if (mode == SLLBM_STREAM_ROW_COPY) {
         ctx->row_copy = true;
         mode = SLLBM_STREAM_STRUCTURED;

@@ -232,7 +232,7 @@ int build_mesh(const sllbm_mesh_desc& d, HostMesh& m, std::string& err) {
     if (d.p < 1 || d.p > 4) { err = "p must be in 1..4"; return SLLBM_ERR_ARG; }
     for (int k = 0; k < d.dim; ++k) {
         if (d.cells[k] < 1 || d.cells[k] > (1 << 20)) { err = "bad cell count"; return SLLBM_ERR_ARG; }
-        if (!(d.length[k] > 0)) { err = "lengths must be positive"; return SLLBM_ERR_ARG; }
+        if (!(d.length[k] > 0) && d.kind != SLLBM_MESH_EXPLICIT) { err = "lengths must be positive"; return SLLBM_ERR_ARG; }
         m.cells[k] = d.cells[k];
         m.length[k] = d.length[k];
     }
@@ -247,6 +247,24 @@ int build_mesh(const sllbm_mesh_desc& d, HostMesh& m, std::string& err) {
         if (d.dim != 2) { err = "NACA mesh is 2D"; return SLLBM_ERR_ARG; }
         m.periodic[1] = 0;
         if (d.cells[0] < 8 || d.cells[1] < 1) { err = "NACA mesh too small"; return SLLBM_ERR_ARG; }
+    } else if (d.kind == SLLBM_MESH_EXPLICIT) {
+        const bool p0 = d.bc[0].kind == SLLBM_BC_PERIODIC, p1 = d.bc[1].kind == SLLBM_BC_PERIODIC;
+        if (p0 != p1) { err = "explicit mesh: y is periodic at both ends or at neither"; return SLLBM_ERR_ARG; }
+        m.periodic[1] = p0 ? 1 : 0;
+        for (int k = 0; k < d.dim; ++k) {
+            const double* v = d.vertices[k];
+            if (!v) { err = "explicit mesh: vertices[" + std::to_string(k) + "] is NULL"; return SLLBM_ERR_ARG; }
+            for (int j = 0; j <= d.cells[k]; ++j)
+                if (!std::isfinite(v[j]) || (j > 0 && !(v[j] > v[j - 1]))) {
+                    err = "explicit mesh: vertices[" + std::to_string(k) + "] must be finite and strictly increasing";
+                    return SLLBM_ERR_ARG;
+                }
+            if (m.periodic[k] && v[0] != 0.0) {
+                err = "explicit mesh: a periodic dimension starts at 0 (vertices[" + std::to_string(k) + "][0])";
+                return SLLBM_ERR_ARG;
+            }
+            m.length[k] = v[d.cells[k]] - v[0];
+        }
     } else {
         err = "unknown mesh kind";
         return SLLBM_ERR_ARG;
@@ -275,7 +293,12 @@ int build_mesh(const sllbm_mesh_desc& d, HostMesh& m, std::string& err) {
             const double L = m.length[dd];
             auto& V = m.V[dd];
             V.resize(C + 1);
-            if (dd != 1 || d.kind == SLLBM_MESH_BOX) {
+            if (d.kind == SLLBM_MESH_EXPLICIT) {
+                V.assign(d.vertices[dd], d.vertices[dd] + C + 1);
+                if (m.periodic[dd])
+                    for (int j = 0; j < C; ++j)
+                        if (std::fabs((V[j + 1] - V[j]) - L / C) > 1e-12 * L) m.uniform_periodic = false;
+            } else if (dd != 1 || d.kind == SLLBM_MESH_BOX) {
                 for (int j = 0; j <= C; ++j) V[j] = L * j / C;
             } else if (d.kind == SLLBM_MESH_CHANNEL) {
                 const double b = d.stretch;

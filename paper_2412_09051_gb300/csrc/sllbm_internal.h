@@ -48,6 +48,7 @@ struct HostMesh {
     int central = 0;
     int64_t n_nodes = 0, n_cells = 0;
     std::vector<double> V[3];     // cell vertices per dimension (axis-aligned kinds)
+    bool uniform_periodic = true; // every periodic dimension has uniform cells (class records apply)
     std::vector<double> X;        // node coordinates [N][D]
     std::vector<double> glc;      // p+1 reference nodes
 };

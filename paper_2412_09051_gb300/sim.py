@@ -22,6 +22,10 @@ def _ptr(a):
 
 
 def mesh_desc(cfg):
+    """The mesh descriptor of a config.  The explicit kind (4) takes
+    m["vertices"], one array of cells[d] + 1 coordinates per dimension; the
+    arrays the descriptor points to are kept on it (``d._keep``)."""
+    import numpy as np
     m = cfg["mesh"]
     d = capi.MeshDesc()
     d.kind = m["kind"]
@@ -30,6 +34,10 @@ def mesh_desc(cfg):
     for k, c in enumerate(m["cells"]):
         d.cells[k] = c
         d.length[k] = m["length"][k]
+    if m["kind"] == capi.MESH["explicit"]:
+        d._keep = [np.ascontiguousarray(v, dtype=np.float64) for v in m["vertices"]]
+        for k, v in enumerate(d._keep):
+            d.vertices[k] = v.ctypes.data
     d.stretch = m.get("stretch", 1.0)
     d.central = m.get("central", 0)
     d.thickness = m.get("thickness", 0.12)

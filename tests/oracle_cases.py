@@ -10,7 +10,8 @@ from oracle.velocity_sets import custom_set, velocity_set
 def oracle_case(cfg):
     m = cfg["mesh"]
     mesh = Mesh(m["kind"], m["p"], m["cells"], m["length"], m.get("stretch", 1.0), m.get("central", 0),
-                m.get("thickness", 0.12))
+                m.get("thickness", 0.12), vertices=m.get("vertices"),
+                periodic_y=all(b["kind"] == 0 for b in cfg["bcs"]))
     if cfg["velset"] == "CUSTOM":
         xi, w, opp = custom_set(cfg["velset_xi"], cfg["velset_w"])
     else:

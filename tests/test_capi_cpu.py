@@ -116,3 +116,37 @@ def test_set_allocator_arguments(built_lib):
     assert b"both functions" in built_lib.sllbm_last_error(None)
     assert built_lib.sllbm_set_allocator(capi.ALLOC_FN(), alloc._free, None) == -1
     assert built_lib.sllbm_set_allocator(capi.ALLOC_FN(), capi.FREE_FN(), None) == 0
+
+
+def test_explicit_mesh_descriptors_are_checked_before_device_work(built_lib):
+    """SLLBM_MESH_EXPLICIT: vertex arrays that are missing, not strictly
+    increasing, or (on a periodic dimension) not starting at 0, and a y axis
+    periodic at one end only, fail with SLLBM_ERR_ARG before the device query;
+    a valid descriptor reaches it (SLLBM_ERR_ARCH without a GPU)."""
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2412_09051_gb300.capi import SllbmError
+    from paper_2412_09051_gb300.sim import Sim
+    from workloads import get_config
+
+    def cfg(vx, vy, vz, bc_kinds=(3, 3)):
+        c = get_config("channel", cells=(4, 3, 2))
+        c = dict(c, mesh=dict(c["mesh"], kind=4, vertices=[vx, vy, vz]))
+        c["bcs"] = [dict(c["bcs"][b], kind=bc_kinds[b]) for b in range(2)]
+        return c
+
+    vx, vy, vz = np.linspace(0, 4, 5), np.array([0.0, 0.2, 1.0, 2.0]), np.linspace(0, 1, 3)
+    bad = [
+        (cfg(vx, vy[::-1], vz), "strictly increasing"),
+        (cfg(vx + 1.0, vy, vz), "starts at 0"),
+        (cfg(vx, vy, vz, bc_kinds=(0, 3)), "at both ends"),
+    ]
+    for c, word in bad:
+        with pytest.raises(SllbmError) as e:
+            Sim(c)
+        assert e.value.code == -1 and word in str(e.value), (word, str(e.value))
+    with pytest.raises(SllbmError) as e:
+        Sim(cfg(vx, vy, vz))
+    assert e.value.code == -3

@@ -123,3 +123,18 @@ def test_locator_finds_points():
     assert (cc == c).all() and np.abs(xr - xi).max() < 1e-10
     cc, _ = loc.locate(np.array([[0.5, 0.0], [30.0, 0.0]]))   # inside the profile / beyond the far field
     assert (cc == -1).all()
+
+
+def test_explicit_mesh_reproduces_the_analytic_kinds():
+    """The explicit kind on the vertices of a channel (walls in y) or a box
+    (periodic y) gives the same nodes, counts and periodicity: its
+    construction is pinned to the analytic kinds'."""
+    import numpy as np
+    from oracle.mesh import KIND_BOX, KIND_CHANNEL, KIND_EXPLICIT, Mesh
+    ch = Mesh(KIND_CHANNEL, 2, (4, 5, 3), (6.0, 2.0, 3.0), stretch=2.0)
+    ex = Mesh(KIND_EXPLICIT, 2, (4, 5, 3), (0.0, 0.0, 0.0), vertices=ch.vertices)
+    assert ex.periodic == ch.periodic and ex.N == ch.N and ex.length == ch.length
+    assert np.array_equal(ex.X, ch.X)
+    bx = Mesh(KIND_BOX, 3, (3, 4), (2.0, 1.5))
+    ex = Mesh(KIND_EXPLICIT, 3, (3, 4), (0.0, 0.0), vertices=bx.vertices, periodic_y=True)
+    assert ex.periodic == (True, True) and np.array_equal(ex.X, bx.X)
