@@ -582,6 +582,15 @@ int sllbm_train_epoch(sllbm_trainer* tr, int32_t batch, float lr, float* loss);
 /* Gradient (host, flattened like the parameters) and loss of the samples
  * [offset, offset + count) as one minibatch, without an update. */
 int sllbm_train_grads(sllbm_trainer* tr, int64_t offset, int32_t count, float* grads, float* loss);
+/* Where the trainer's forward and backward passes run: SLLBM_MLP_TENSOR
+ * (default; 5th-generation tensor cores, one tile of 128 samples per block:
+ * the three layers, the two backward products and the weight and bias
+ * gradients as BF16 products with FP32 accumulators in tensor memory, the
+ * activations and deltas split into BF16 hi and lo parts, the projection and
+ * the loss on the CUDA cores) or SLLBM_MLP_SIMT (CUDA cores, FP32).  Both
+ * give the same gradients to FP32 rounding; a tensor-core wait that runs out
+ * makes the call that launched it fail with SLLBM_ERR_CUDA. */
+int sllbm_train_path(sllbm_trainer* tr, int32_t path);
 int sllbm_train_params(const sllbm_trainer* tr, float* params);
 int sllbm_train_set_params(sllbm_trainer* tr, const float* params);
 /* BF16 weights (layout of sllbm_mlp_set) and FP32 biases. */

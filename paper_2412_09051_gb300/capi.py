@@ -113,6 +113,7 @@ _SIGS = {
     "sllbm_train_scales": (C.c_int, [_P, _P, _P]),
     "sllbm_train_epoch": (C.c_int, [_P, C.c_int32, C.c_float, _P]),
     "sllbm_train_grads": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P]),
+    "sllbm_train_path": (C.c_int, [_P, C.c_int32]),
     "sllbm_train_params": (C.c_int, [_P, _P]),
     "sllbm_train_set_params": (C.c_int, [_P, _P]),
     "sllbm_train_export": (C.c_int, [_P, _P, _P]),

@@ -258,6 +258,12 @@ __global__ void __launch_bounds__(TT) k_train_batch(const TrainBufs B, int64_t o
     }
 }
 
+}  // namespace sllbm
+
+#include "mlp_train_tc.cuh"
+
+namespace sllbm {
+
 template <int Q>
 size_t train_smem() {
     return sizeof(float) * (POff<Q>::N + Q * Q + Q + TS * Q * 3 + TS * MLP_H * 4);
@@ -347,6 +353,8 @@ struct sllbm_trainer {
     float *d_p = nullptr, *d_pr = nullptr, *d_grad = nullptr, *d_m = nullptr, *d_v = nullptr;
     float *d_P = nullptr, *d_w = nullptr, *d_loss = nullptr;
     float *d_X = nullptr, *d_Y = nullptr, *d_sin = nullptr;
+    int* d_status = nullptr;           // tensor-core waits: status bits, test wait limit (log2)
+    int path = SLLBM_MLP_TENSOR;       // forward / backward on the tensor cores or the CUDA cores
     int64_t M = 0;
     float sigma = 1.f;
     std::vector<float> s_in;
@@ -364,11 +372,25 @@ int tfail(sllbm_trainer* t, int code, const std::string& m) {
         if (e_ != cudaSuccess) return tfail(tr, SLLBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+template <int Q>
+int launch_train_tc(sllbm_trainer* tr, const TrainBufs& B, int64_t off, int count, float scale) {
+    using L = TrainTc<Q>;
+    if (cudaFuncSetAttribute(k_train_tc<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM) != cudaSuccess)
+        return tfail(tr, SLLBM_ERR_CUDA, "cudaFuncSetAttribute failed");
+    const unsigned grid = unsigned((count + L::S - 1) / L::S);
+    k_train_tc<Q><<<grid, 128, L::SMEM, tr->stream>>>(B, off, count, scale, tr->d_status);
+    return SLLBM_OK;
+}
+
 int launch_batch(sllbm_trainer* tr, int64_t off, int count, int batch_norm) {
     TrainBufs B{tr->Q, tr->M, tr->d_X, tr->d_Y, tr->d_pr, tr->d_grad, tr->d_P, tr->d_w, tr->d_loss};
     const unsigned grid = unsigned((count + TS - 1) / TS);
     const float scale = 2.0f / float(batch_norm);
-    if (tr->Q == 19) {
+    if (tr->path == SLLBM_MLP_TENSOR && (tr->Q == 19 || tr->Q == 45)) {
+        const int rc = tr->Q == 19 ? launch_train_tc<19>(tr, B, off, count, scale)
+                                   : launch_train_tc<45>(tr, B, off, count, scale);
+        if (rc) return rc;
+    } else if (tr->Q == 19) {
         const size_t sm = train_smem<19>();
         cudaFuncSetAttribute(k_train_batch<19>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_train_batch<19><<<grid, TT, sm, tr->stream>>>(B, off, count, scale);
@@ -419,6 +441,8 @@ int sllbm_train_create(const sllbm_ctx* ctx, const float* init_params, sllbm_tra
     if (cudaMalloc(&tr->d_w, sizeof(float) * tr->Q) != cudaSuccess) return bail(SLLBM_ERR_NOMEM);
     if (cudaMalloc(&tr->d_loss, sizeof(float)) != cudaSuccess) return bail(SLLBM_ERR_NOMEM);
     if (cudaMalloc(&tr->d_sin, sizeof(float) * tr->Q) != cudaSuccess) return bail(SLLBM_ERR_NOMEM);
+    if (cudaMalloc(&tr->d_status, 2 * sizeof(int)) != cudaSuccess) return bail(SLLBM_ERR_NOMEM);
+    cudaMemset(tr->d_status, 0, 2 * sizeof(int));
     std::vector<float> Pf(tr->P.begin(), tr->P.end()), wf(tr->w.begin(), tr->w.end());
     cudaMemcpy(tr->d_P, Pf.data(), sizeof(float) * Pf.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(tr->d_w, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice);
@@ -442,7 +466,14 @@ int sllbm_train_destroy(sllbm_trainer* tr) {
                      tr->d_X, tr->d_Y, tr->d_sin};
     for (float* b : bufs)
         if (b) cudaFree(b);
+    if (tr->d_status) cudaFree(tr->d_status);
     delete tr;
+    return SLLBM_OK;
+}
+
+int sllbm_train_path(sllbm_trainer* tr, int32_t path) {
+    if (!tr || (path != SLLBM_MLP_TENSOR && path != SLLBM_MLP_SIMT)) return SLLBM_ERR_ARG;
+    tr->path = path;
     return SLLBM_OK;
 }
 
@@ -523,9 +554,12 @@ int sllbm_train_grads(sllbm_trainer* tr, int64_t offset, int32_t count, float* g
     if (rc) return rc;
     if (grads) TCK(cudaMemcpyAsync(grads, tr->d_grad, sizeof(float) * n, cudaMemcpyDeviceToHost, tr->stream));
     float l = 0;
+    int st = 0;
     TCK(cudaMemcpyAsync(&l, tr->d_loss, sizeof(float), cudaMemcpyDeviceToHost, tr->stream));
+    TCK(cudaMemcpyAsync(&st, tr->d_status, sizeof(int), cudaMemcpyDeviceToHost, tr->stream));
     TCK(cudaMemsetAsync(tr->d_grad, 0, sizeof(float) * n, tr->stream));
     TCK(cudaStreamSynchronize(tr->stream));
+    if (st) return tfail(tr, SLLBM_ERR_CUDA, "a tensor-core wait of the trainer ran out (status " + std::to_string(st) + ")");
     if (loss) *loss = l / float(count);
     return SLLBM_OK;
 }
@@ -548,8 +582,11 @@ int sllbm_train_epoch(sllbm_trainer* tr, int32_t batch, float lr, float* loss) {
         TCK(cudaGetLastError());
     }
     float l = 0;
+    int st = 0;
     TCK(cudaMemcpyAsync(&l, tr->d_loss, sizeof(float), cudaMemcpyDeviceToHost, tr->stream));
+    TCK(cudaMemcpyAsync(&st, tr->d_status, sizeof(int), cudaMemcpyDeviceToHost, tr->stream));
     TCK(cudaStreamSynchronize(tr->stream));
+    if (st) return tfail(tr, SLLBM_ERR_CUDA, "a tensor-core wait of the trainer ran out (status " + std::to_string(st) + ")");
     const int64_t nb = tr->M / batch;
     if (loss) *loss = nb > 0 ? l / float(nb * batch) : 0.f;
     return SLLBM_OK;

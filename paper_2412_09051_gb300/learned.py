@@ -78,6 +78,11 @@ class Trainer:
         self._chk(capi.lib().sllbm_train_epoch(self.h, batch, C.c_float(lr), C.byref(loss)))
         return loss.value
 
+    def path(self, path):
+        """capi.MLP_TENSOR (default) or capi.MLP_SIMT: where the forward and
+        backward passes run."""
+        self._chk(capi.lib().sllbm_train_path(self.h, path))
+
     def grads(self, offset, count):
         g = np.zeros(n_params(self.Q), np.float32)
         loss = C.c_float()

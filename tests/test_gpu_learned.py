@@ -175,7 +175,12 @@ def test_tensor_core_path_matches_cuda_cores(built_lib):
     assert np.abs(gt - gs).max() < 1e-5 * np.abs(gs).max()
 
 
-def test_training_gradients_match_oracle(built_lib):
+@pytest.mark.parametrize("path", ["tensor", "simt"])
+def test_training_gradients_match_oracle(built_lib, path):
+    """The trainer's loss and gradients (forward and backward on the tensor
+    cores, or on the CUDA cores) against the FP64 oracle's, on a partial tile
+    (64 samples from offset 10)."""
+    from paper_2412_09051_gb300 import capi
     from paper_2412_09051_gb300.learned import Trainer
     from paper_2412_09051_gb300.sim import Sim
     s = Sim(_small())
@@ -188,6 +193,7 @@ def test_training_gradients_match_oracle(built_lib):
     R = r.normal(0, 2e-3, (M, Q)).astype(np.float32)
     p = _random_model(Q, 9).astype(np.float32)
     tr = Trainer(s, p)
+    tr.path(capi.MLP_TENSOR if path == "tensor" else capi.MLP_SIMT)
     tr.set_data(Z, R, 0)
     s_in, sigma = tr.scales()
     # oracle definitions of the data scales
@@ -206,6 +212,39 @@ def test_training_gradients_match_oracle(built_lib):
     gref = np.concatenate([a.ravel() for a in gref])
     assert abs(loss - lref) < 1e-4 * lref
     assert np.abs(g - gref).max() < 1e-4 * np.abs(gref).max()
+    print(f"PARITY training gradients ({path}): loss {abs(loss - lref) / lref:.2e}, "
+          f"gradients {np.abs(g - gref).max() / np.abs(gref).max():.2e} of the largest")
+
+
+def test_training_paths_agree_on_full_tiles(built_lib):
+    """Several full 128-sample tiles and a ragged one: the tensor-core and the
+    CUDA-core trainer give the same loss and gradients to FP32 rounding, and
+    one epoch of Adam steps from the same start stays together."""
+    from paper_2412_09051_gb300 import capi
+    from paper_2412_09051_gb300.learned import Trainer
+    from paper_2412_09051_gb300.sim import Sim
+    s = Sim(_small())
+    _, w, _ = s.velocity_set()
+    Q = len(w)
+    r = np.random.default_rng(8)
+    M = 1000
+    Z = r.normal(0, 1e-3, (M, Q)).astype(np.float32)
+    Z[:, :3] = 0.0
+    R = r.normal(0, 2e-3, (M, Q)).astype(np.float32)
+    p = _random_model(Q, 10).astype(np.float32)
+    out = {}
+    for path in ("tensor", "simt"):
+        tr = Trainer(s, p)
+        tr.path(capi.MLP_TENSOR if path == "tensor" else capi.MLP_SIMT)
+        tr.set_data(Z, R, 0)
+        g, loss = tr.grads(3, 700)                   # 5 full tiles and a ragged one
+        tr.epoch(256, 1e-3)
+        out[path] = (g, loss, tr.params())
+    (gt, lt, pt), (gs, ls, ps) = out["tensor"], out["simt"]
+    assert abs(lt - ls) < 1e-5 * ls
+    assert np.abs(gt - gs).max() < 1e-4 * np.abs(gs).max()
+    assert np.abs(pt - ps).max() < 1e-4 * np.abs(ps).max()
+    print(f"PARITY tensor-core vs CUDA-core trainer: gradients {np.abs(gt - gs).max() / np.abs(gs).max():.2e}")
 
 
 def test_learned_beats_plain(built_lib):
