@@ -106,10 +106,9 @@ int launch_plane_cp(const double* rho, const double* T, int N0, int N1, int N2, 
 void build_moment_basis(const HostVelSet& vs, std::vector<double>& Phi, std::vector<double>& Ginv,
                         std::vector<double>& P);
 bool rows_tmem_shape(int D, int nx, int& ty, int& tz);
-bool rows_pairs_shape(int D, int nx, int& ty, int& tz);
-size_t rows_pairs_smem(int D, int nx, const TmGeom2& T);
+bool rows_pairs_shape(int D, int nx, int p, int& ty, int& tz);
 int launch_rows_pairs(int vs, int nx, const float2* fg, float2* fgo, const void* maps, const int32_t* head,
-                      const TmRec2* recs, const uint64_t* xmask, const uint64_t* smask, const float* tw,
+                      const void* recs, const uint64_t* xmask, const uint64_t* smask, const float* tw,
                       const StepGeom& G, const CollideConst<float>& C, const TmGeom2& T, int* status, cudaStream_t s,
                       int grid);
 size_t rows_tmem_smem_bytes(int D, int nx, const TmGeom& T);
@@ -634,6 +633,81 @@ bool build_rows_tmem(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::ve
     return true;
 }
 
+// The stages of the two-nodes-per-thread kernel (both orders): two rings (one
+// per consumer group) of two stages (one where the largest velocity needs
+// more room) of `cap` rows and the records of up to
+// maxv <= TM2_MAX_VEL velocities (measured on the channel: two large stages
+// per ring beat three smaller ones); each group's velocities (i = h, h + 2, ...) are
+// packed into stages per tile class, consecutive velocities while their rows
+// fit `cap`; a velocity's slots and its records' tap offsets move by the rows
+// before it.  Sets the kernel geometry; false where the stages do not fit.
+template <class REC>
+bool pack_rows_pairs(sllbm_ctx* c, TmGeom2& T, int NX, int NR, int max_rows, const std::vector<int>& shapes,
+                     std::vector<int32_t>& head, std::vector<REC>& recs, std::vector<uint64_t>& smask) {
+    const int Q = c->vs.Q;
+    const int rec_bytes = NR * int(sizeof(REC));
+    const size_t fixed = sizeof(float2) * 4 * NR * (NX + 2 * T.p) + 8 + 16;     // two halo rows per group
+    const size_t budget = 227 * 1024;
+    // two stages per ring where the largest velocity's rows fit, else one;
+    // the most velocities per stage whose records leave room for those rows
+    int cap = 0, nst = 0, maxv = 0;
+    for (int n : {4, 2}) {
+        for (int v = TM2_MAX_VEL; v >= 1 && !maxv; --v) {
+            const long long room = (static_cast<long long>(budget) - static_cast<long long>(fixed)) / n - 16 -
+                                   static_cast<long long>(v) * rec_bytes;
+            const int k = int(std::max(0LL, room) / (NX * 8));
+            if (k >= max_rows) {
+                cap = k;
+                maxv = v;
+                nst = n;
+            }
+        }
+        if (maxv) break;
+    }
+    if (!maxv) return false;
+    smask.assign(size_t(2) * T.n_tc, 0);
+    for (int tc = 0; tc < T.n_tc; ++tc)
+        for (int hg = 0; hg < 2; ++hg) {
+            const int nv = (Q - hg + 1) / 2;
+            int j0 = 0;
+            while (j0 < nv) {
+                int rows = 0, n = 0;
+                while (j0 + n < nv && n < maxv) {
+                    const int i = hg + 2 * (j0 + n);
+                    const int r_i = head[(size_t(i) * T.n_tc + tc) * TM2_HEAD + 1];
+                    if (rows + r_i > cap) break;
+                    rows += r_i;
+                    ++n;
+                }
+                if (n == 0) return false;
+                smask[size_t(tc) * 2 + hg] |= uint64_t(1) << j0;
+                int base = 0;
+                for (int q = 0; q < n; ++q) {
+                    const int i = hg + 2 * (j0 + q);
+                    int32_t* h = &head[(size_t(i) * T.n_tc + tc) * TM2_HEAD];
+                    for (int b = 0; b < h[0]; ++b) h[2 + TM2_MAX_BOXES + b] += base;
+                    for (int r = 0; r < NR; ++r) {
+                        REC& ro = recs[(size_t(i) * T.n_tc + tc) * NR + r];
+                        if ((ro.meta & 15) == REC_EQ) continue;
+                        for (int k = 0; k < ro.ntap; ++k) ro.off[k] += base * NX * 8;
+                    }
+                    base += h[1];
+                }
+                int32_t* h0 = &head[(size_t(hg + 2 * j0) * T.n_tc + tc) * TM2_HEAD];
+                h0[14] = 1 | (n << 8);
+                h0[15] = rows * NX * 8 + n * rec_bytes;
+                j0 += n;
+            }
+        }
+    T.rows_bytes = cap * NX * 8;
+    T.stage_bytes = T.rows_bytes + maxv * rec_bytes;
+    T.nst = nst;
+    T.rec_map = int(shapes.size());
+    c->tm2 = T;
+    c->tm2_box = shapes;
+    return true;
+}
+
 // Tables of the row-tile kernel with two nodes per thread (step_tmem2.cuh):
 // tiles of TY x TZ whole x rows.  Per (velocity, tile class): one box of
 // source rows per population (the y range times the z range of the (y, z)
@@ -650,7 +724,7 @@ bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::v
     int TY = 0, TZ = 0;
     if (c->precision != SLLBM_FP32 || m.p != 2 || !c->tiled || !c->row_uniform) return false;
     if (!((c->velset == SLLBM_D3Q45 && D == 3) || (c->velset == SLLBM_D2Q19 && D == 2))) return false;
-    if (!rows_pairs_shape(D, NX, TY, TZ) || G.ncls[0] != 2 || !m.periodic[0]) return false;
+    if (!rows_pairs_shape(D, NX, 2, TY, TZ) || G.ncls[0] != 2 || !m.periodic[0]) return false;
     const bool py = m.periodic[1] != 0;
     if (py && N1 % TY) return false;
     if (D == 3 && (!m.periodic[2] || N2 % TZ)) return false;
@@ -771,68 +845,157 @@ bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::v
             }
             if (xchg) xmask[tc] |= uint64_t(1) << i;
         }
-    // Stages: two rings (one per consumer group) of two stages of `cap` rows
-    // and the records of up to TM2_MAX_VEL velocities (measured on the
-    // channel: two large stages per ring beat three smaller ones)
-    const int rec_bytes = NR * int(sizeof(TmRec2));
-    const size_t fixed = sizeof(float2) * 4 * NR * (NX + 4) + 8 + 16;     // two halo rows per group
-    const size_t budget = 227 * 1024;
-    int cap = 0, nst = 0;
-    for (int n : {4}) {
-        const long long room = (static_cast<long long>(budget) - static_cast<long long>(fixed)) / n - 16 -
-                               TM2_MAX_VEL * rec_bytes;
-        const int k = int(std::max(0LL, room) / (NX * 8));
-        if (k >= max_rows) {
-            cap = k;
-            nst = n;
-            break;
-        }
-    }
-    if (!nst) return false;
-    // pack each group's velocities (i = h, h + 2, ...) into stages, per tile
-    // class: consecutive velocities while their rows fit `cap`; a velocity's
-    // slots and its records' tap offsets move by the rows before it
-    smask.assign(size_t(2) * T.n_tc, 0);
-    for (int tc = 0; tc < T.n_tc; ++tc)
-        for (int hg = 0; hg < 2; ++hg) {
-            const int nv = (Q - hg + 1) / 2;
-            int j0 = 0;
-            while (j0 < nv) {
-                int rows = 0, n = 0;
-                while (j0 + n < nv && n < TM2_MAX_VEL) {
-                    const int i = hg + 2 * (j0 + n);
-                    const int r_i = head[(size_t(i) * T.n_tc + tc) * TM2_HEAD + 1];
-                    if (rows + r_i > cap) break;
-                    rows += r_i;
-                    ++n;
-                }
-                if (n == 0) return false;
-                smask[size_t(tc) * 2 + hg] |= uint64_t(1) << j0;
-                int base = 0;
-                for (int q = 0; q < n; ++q) {
-                    const int i = hg + 2 * (j0 + q);
-                    int32_t* h = &head[(size_t(i) * T.n_tc + tc) * TM2_HEAD];
-                    for (int b = 0; b < h[0]; ++b) h[2 + TM2_MAX_BOXES + b] += base;
-                    for (int r = 0; r < NR; ++r) {
-                        TmRec2& ro = recs[(size_t(i) * T.n_tc + tc) * NR + r];
-                        if ((ro.meta & 15) == REC_EQ) continue;
-                        for (int k = 0; k < ro.ntap; ++k) ro.off[k] += base * NX * 8;
+    T.ncy = py ? 1 : T.ntile_y;
+    T.ncz = 1;
+    T.p = 2;
+    return pack_rows_pairs(c, T, NX, NR, max_rows, shapes, head, recs, smask);
+}
+
+// The same tables at order p = 4 from the order-P class records (TileRecP:
+// factorised 1D weights, packed offsets).  Tiles of TY x TZ rows; on a
+// periodic axis the classes of a tile's rows repeat with period 4 / gcd(4,
+// extent), so tile classes are (y tile or y tile mod that period, z tile mod
+// it).  Per row one 352-byte record: the (y, z) taps shared by all x classes
+// (the class records guarantee it), and for each pair class (x mod 4 = 0, 2)
+// the nine x weights of its even and odd node over ten row sums.
+bool build_rows_pairs4(sllbm_ctx* c, const std::vector<TileRecP<float, 4>>& t, std::vector<int32_t>& head,
+                       std::vector<TmRec4>& recs, std::vector<uint64_t>& xmask, std::vector<uint64_t>& smask) {
+    const HostMesh& m = c->mesh;
+    const StepGeom& G = c->geom;
+    const int Q = c->vs.Q, D = m.D, NX = m.N[0], N1 = m.N[1], N2 = D == 3 ? m.N[2] : 1;
+    constexpr int P = 4;
+    int TY = 0, TZ = 0;
+    if (c->precision != SLLBM_FP32 || m.p != P || D != 3 || c->velset != SLLBM_D3Q45) return false;
+    if (!rows_pairs_shape(D, NX, P, TY, TZ) || G.ncls[0] != P || !m.periodic[0] || !m.periodic[2]) return false;
+    const bool py = m.periodic[1] != 0;
+    if ((py && N1 % TY) || N2 % TZ) return false;
+    if (int64_t(Q) * m.n_nodes >= (int64_t(1) << 31)) return false;
+    auto period = [](int extent) { return extent % 4 == 0 ? 1 : (extent % 2 == 0 ? 2 : 4); };
+    const int NR = TY * TZ;
+    TmGeom2 T{};
+    T.ntile_y = (N1 + TY - 1) / TY;
+    T.ntile_z = N2 / TZ;
+    T.ntiles = T.ntile_y * T.ntile_z;
+    T.ncy = py ? period(TY) : T.ntile_y;
+    T.ncz = period(TZ);
+    T.n_tc = T.ncy * T.ncz;
+    T.p = P;
+    const int64_t U = G.n_classes;
+    head.assign(size_t(Q) * T.n_tc * TM2_HEAD, 0);
+    recs.assign(size_t(Q) * T.n_tc * NR, TmRec4{});
+    xmask.assign(size_t(T.n_tc), 0);
+    int max_rows = 1;
+    std::vector<int> shapes;
+    struct Tap {
+        int src, dy, dz;
+        float w;
+    };
+    struct Box {
+        int src, ylo, yhi, zlo, zhi, slot;
+    };
+    auto cls_of = [&](int kx, int y, int z) { return int64_t(kx) + G.ncls[0] * ((py ? y % P : y) + G.ncls[1] * (z % P)); };
+    for (int i = 0; i < Q; ++i)
+        for (int tc = 0; tc < T.n_tc; ++tc) {
+            const int cy = tc % T.ncy, cz = tc / T.ncy;
+            const int y0 = cy * TY, z0 = cz * TZ;       // a tile of this class
+            int32_t* h = &head[(size_t(i) * T.n_tc + tc) * TM2_HEAD];
+            std::vector<std::vector<Tap>> taps(NR);
+            std::vector<int64_t> u0(NR, -1);
+            for (int r = 0; r < NR; ++r) {
+                const int ry = r % TY, rz = r / TY;
+                const int y = y0 + ry, z = z0 + rz;
+                if (y >= N1) continue;                   // beyond a ragged last tile: an idle row
+                u0[r] = cls_of(0, y, z);
+                const TileRecP<float, P>& a = t[size_t(i * U + u0[r])];
+                if ((a.meta & 15) == REC_EQ) continue;
+                for (int ka = 0; ka <= P; ++ka)
+                    for (int kb = 0; kb <= P; ++kb) {
+                        const float wk = a.wy[ka] * a.wz[kb];
+                        if (std::fabs(wk) < 1e-12f) continue;
+                        const int dy = ((a.dyp >> (4 * ka)) & 15) - 8;
+                        const int dz = ((a.dzp >> (4 * kb)) & 15) - 8;
+                        taps[r].push_back({a.meta >> 8, ry + dy, rz + dz, wk});
                     }
-                    base += h[1];
-                }
-                int32_t* h0 = &head[(size_t(hg + 2 * j0) * T.n_tc + tc) * TM2_HEAD];
-                h0[14] = 1 | (n << 8);
-                h0[15] = rows * NX * 8 + n * rec_bytes;
-                j0 += n;
+                if (taps[r].size() > 25) return false;
             }
+            std::vector<Box> boxes;
+            for (int r = 0; r < NR; ++r)
+                for (const Tap& tp : taps[r]) {
+                    bool found = false;
+                    for (Box& b : boxes)
+                        if (b.src == tp.src) {
+                            b.ylo = std::min(b.ylo, tp.dy);
+                            b.yhi = std::max(b.yhi, tp.dy);
+                            b.zlo = std::min(b.zlo, tp.dz);
+                            b.zhi = std::max(b.zhi, tp.dz);
+                            found = true;
+                        }
+                    if (!found) boxes.push_back({tp.src, tp.dy, tp.dy, tp.dz, tp.dz, 0});
+                }
+            if (int(boxes.size()) > TM2_MAX_BOXES) return false;
+            int nrows = 0;
+            for (size_t q = 0; q < boxes.size(); ++q) {
+                Box& b = boxes[q];
+                const int ny = b.yhi - b.ylo + 1, nz = b.zhi - b.zlo + 1;
+                if (b.ylo + 128 < 0 || b.yhi + 128 > 255 || b.zlo + 128 < 0 || b.zhi + 128 > 255 || ny > 64 ||
+                    nz > 64 || ny > N1 || nz > N2)
+                    return false;
+                int map = -1;
+                for (size_t k = 0; k < shapes.size(); ++k)
+                    if (shapes[k] == (ny | (nz << 8))) map = int(k);
+                if (map < 0) {
+                    if (int(shapes.size()) == TM2_MAX_MAPS - 1) return false;     // one map left for the records
+                    map = int(shapes.size());
+                    shapes.push_back(ny | (nz << 8));
+                }
+                b.slot = nrows;
+                nrows += ny * nz;
+                h[2 + q] = tm2_pack_box(b.src, b.ylo, b.zlo, map);
+                h[2 + TM2_MAX_BOXES + q] = b.slot;
+                h[2 + 2 * TM2_MAX_BOXES + q] = ny | (nz << 8);
+            }
+            if (nrows > TM2_MAX_ROWS) return false;
+            h[0] = int(boxes.size());
+            h[1] = nrows;
+            max_rows = std::max(max_rows, nrows);
+            bool xchg = false;
+            for (int r = 0; r < NR; ++r) {
+                TmRec4& ro = recs[(size_t(i) * T.n_tc + tc) * NR + r];
+                ro.meta = REC_EQ;
+                if (u0[r] < 0) continue;                 // an idle row
+                const TileRecP<float, P>& a = t[size_t(i * U + u0[r])];
+                ro.meta = a.meta;
+                ro.ntap = int(taps[r].size());
+                if ((a.meta & 15) == REC_EQ) continue;
+                for (size_t q = 0; q < taps[r].size(); ++q) {
+                    const Tap& tp = taps[r][q];
+                    int sl = -1;
+                    for (const Box& bx : boxes)
+                        if (bx.src == tp.src) sl = bx.slot + (tp.dz - bx.zlo) * (bx.yhi - bx.ylo + 1) + (tp.dy - bx.ylo);
+                    ro.off[q] = sl * NX * 8;
+                    ro.w[q] = tp.w;
+                }
+                // x weights: pair class pc (x mod 4 = 2 pc), node e (x + e):
+                // a tap at offset d from node x + e sits in slot d + 4 of
+                // that node's window (x - 4 + e .. x + 4 + e)
+                const int ry = r % TY, rz = r / TY;
+                for (int pc = 0; pc < 2; ++pc)
+                    for (int e = 0; e < 2; ++e) {
+                        const TileRecP<float, P>& b = t[size_t(i * U + cls_of(2 * pc + e, y0 + ry, z0 + rz))];
+                        if (b.meta != a.meta) return false;
+                        float* wx = ro.wx[pc][e];
+                        for (int ka = 0; ka <= P; ++ka) {
+                            const int d = ((b.dxp >> (4 * ka)) & 15) - 8;
+                            if (d < -4 || d > 4) return false;
+                            wx[d + 4] += b.wx[ka];
+                        }
+                        for (int q = 0; q < 9; ++q)
+                            if (std::fabs(double(wx[q]) - (q == 4 ? 1.0 : 0.0)) > 1e-12) xchg = true;
+                    }
+            }
+            if (xchg) xmask[tc] |= uint64_t(1) << i;
         }
-    T.rows_bytes = cap * NX * 8;
-    T.stage_bytes = T.rows_bytes + TM2_MAX_VEL * rec_bytes;
-    T.nst = nst;
-    T.rec_map = int(shapes.size());
-    c->tm2 = T;
-    c->tm2_box = shapes;
-    return true;
+    return pack_rows_pairs(c, T, NX, NR, max_rows, shapes, head, recs, smask);
 }
 
 // TMA tensor maps of the two-nodes-per-thread row-tile kernel: state buffer b
@@ -852,14 +1015,16 @@ int encode_tm2_maps(sllbm_ctx* c) {
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     const int nm = int(c->tm2_box.size());
     int ty = 0, tz = 0;
-    rows_pairs_shape(m.D, NX, ty, tz);
+    rows_pairs_shape(m.D, NX, c->tm2.p, ty, tz);
     std::vector<CUtensorMap> maps(size_t(2) * (nm + 1));
     for (int b = 0; b < 2; ++b) {
-        // the records [Q][n_tc][TY TZ] of 128 bytes as FP32 [Q][n_tc][TY TZ][32]:
-        // one box per (velocity, tile class)
-        const cuuint64_t rdims[4] = {32, cuuint64_t(ty * tz), cuuint64_t(c->tm2.n_tc), cuuint64_t(Q)};
-        const cuuint64_t rstrides[3] = {128, cuuint64_t(128) * ty * tz, cuuint64_t(128) * ty * tz * c->tm2.n_tc};
-        const cuuint32_t rbox[4] = {32, cuuint32_t(ty * tz), 1, 1};
+        // the records [Q][n_tc][TY TZ] (128 or 352 bytes) as FP32
+        // [Q][n_tc][TY TZ][32 or 88]: one box per (velocity, tile class)
+        const int rf = c->tm2.p == 4 ? int(sizeof(TmRec4) / 4) : int(sizeof(TmRec2) / 4);   // floats per record
+        const cuuint64_t rdims[4] = {cuuint64_t(rf), cuuint64_t(ty * tz), cuuint64_t(c->tm2.n_tc), cuuint64_t(Q)};
+        const cuuint64_t rstrides[3] = {cuuint64_t(4 * rf), cuuint64_t(4 * rf) * ty * tz,
+                                        cuuint64_t(4 * rf) * ty * tz * c->tm2.n_tc};
+        const cuuint32_t rbox[4] = {cuuint32_t(rf), cuuint32_t(ty * tz), 1, 1};
         const cuuint32_t res[4] = {1, 1, 1, 1};
         const CUresult rr = enc(&maps[size_t(b) * (nm + 1) + nm], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->tm2_recs,
                                 rdims, rstrides, rbox, res, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -905,7 +1070,7 @@ int dispatch_step(sllbm_ctx* ctx, const StepLaunch<real>& L) {
             const char* maps = static_cast<const char*>(ctx->tm2_maps) +
                                size_t(b) * (ctx->tm2_box.size() + 1) * sizeof(CUtensorMap);
             return launch_rows_pairs(vs, ctx->mesh.N[0], L.fg, L.fgo, maps, ctx->tm2_head,
-                                     static_cast<const TmRec2*>(ctx->tm2_recs), ctx->tm_xmask, ctx->tm2_smask, L.tw,
+                                     ctx->tm2_recs, ctx->tm_xmask, ctx->tm2_smask, L.tw,
                                      L.G, *L.C, ctx->tm2, ctx->d_status, L.stream, ctx->tm_grid);
         }
         if (st && ctx->rows_tmem && !ctx->row_copy) {
@@ -1467,6 +1632,29 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
                     build_tile_table_p(ctx, rec, t);
                     CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tile_tab), sizeof(t[0]) * t.size()));
                     CK(cudaMemcpyAsync(ctx->tile_tab, t.data(), sizeof(t[0]) * t.size(), cudaMemcpyHostToDevice, s));
+                    // the two-nodes-per-thread row tiles at order 4
+                    std::vector<int32_t> th;
+                    std::vector<TmRec4> tr4;
+                    std::vector<uint64_t> tx, ts;
+                    if (ctx->want_tm2 && build_rows_pairs4(ctx, t, th, tr4, tx, ts)) {
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm2_smask), sizeof(uint64_t) * ts.size()));
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm2_head), sizeof(int32_t) * th.size()));
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm2_recs), sizeof(TmRec4) * tr4.size()));
+                        CK(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->tm_xmask), sizeof(uint64_t) * tx.size()));
+                        CK(cudaMemcpyAsync(ctx->tm2_smask, ts.data(), sizeof(uint64_t) * ts.size(),
+                                           cudaMemcpyHostToDevice, s));
+                        CK(cudaMemcpyAsync(ctx->tm2_head, th.data(), sizeof(int32_t) * th.size(),
+                                           cudaMemcpyHostToDevice, s));
+                        CK(cudaMemcpyAsync(ctx->tm2_recs, tr4.data(), sizeof(TmRec4) * tr4.size(),
+                                           cudaMemcpyHostToDevice, s));
+                        CK(cudaMemcpyAsync(ctx->tm_xmask, tx.data(), sizeof(uint64_t) * tx.size(),
+                                           cudaMemcpyHostToDevice, s));
+                        CK(cudaStreamSynchronize(s));
+                        int sms = 0;
+                        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+                        ctx->tm_grid = std::min(ctx->tm2.ntiles, sms);
+                        ctx->rows_tm2 = true;
+                    }
                 }
                 CK(cudaStreamSynchronize(s));
                 ctx->tiled_p = 4;

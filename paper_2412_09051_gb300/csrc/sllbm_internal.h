@@ -170,12 +170,24 @@ struct alignas(16) TmRec2 {
 };
 static_assert(sizeof(TmRec2) == 128, "eight 16-byte loads per record");
 
+// The same record at order p = 4 (352 bytes): up to 25 (y, z) taps, and the x
+// weights of the two pair classes (x mod 4 = 0 and 2), each node's nine
+// weights over a window of ten row sums (x - 4 .. x + 5 of the even node x)
+struct alignas(16) TmRec4 {
+    int32_t meta;       // kind | bid << 4 | src << 8
+    int32_t ntap;       // (y, z) taps
+    int32_t off[25];    // byte offsets of the taps' source rows within the stage
+    float w[25];        // (y, z) weight products
+    float wx[2][2][9];  // [pair class][even, odd node][row sum x - 4 + m (odd: x - 3 + m)]
+};
+static_assert(sizeof(TmRec4) == 352, "22 16-byte loads per record");
+
 constexpr int TM2_MAX_BOXES = 4;     // boxes (one per source population) per (velocity, tile class)
 constexpr int TM2_MAX_VEL = 6;       // velocities per stage
 constexpr int TM2_HEAD = 16;         // ints per copy list: boxes, rows, per box: entry, first slot in
                                      // the stage, rows along y | along z << 8 (2 + 3 * 4 = 14); then
                                      // stage start | velocities of the stage << 8, the stage's bytes
-constexpr int TM2_MAX_ROWS = 64;     // rows of one velocity's boxes
+constexpr int TM2_MAX_ROWS = 96;     // rows of one velocity's boxes
 constexpr int TM2_MAX_MAPS = 32;     // box shapes (tensor maps)
 
 struct TmGeom2 {
@@ -183,8 +195,11 @@ struct TmGeom2 {
     int n_tc;                        // tile classes (y tiles on a non-periodic y axis, else 1)
     int nst;                         // pipeline stages: two rings (one per consumer group) of nst / 2
     int rows_bytes;                  // bytes of source rows per stage (its row capacity x NX x 8)
-    int stage_bytes;                 // rows_bytes + the records of TM2_MAX_VEL velocities
+    int stage_bytes;                 // rows_bytes + the records of up to TM2_MAX_VEL velocities
     int rec_map;                     // index of the records' tensor map
+    int ncy, ncz;                    // tile classes along y and z: class cy + ncy cz (cy = ty on a
+                                     // non-periodic y axis, else ty mod ncy; cz = tz mod ncz)
+    int p;                           // Lagrange order (2 or 4)
 };
 
 // one box of a copy list: population, first y and z relative to the tile

@@ -20,6 +20,8 @@
 // Collision: collide_tmem (step_tmem.cuh).  Every wait is bounded, with the
 // abort protocol of step_tmem.cuh.
 #pragma once
+#include <type_traits>
+
 #include "step_tmem.cuh"
 
 namespace sllbm {
@@ -53,6 +55,12 @@ __device__ __forceinline__ void sts4f(uint32_t a, float4 v) {
                  : "memory");
 }
 
+// tile class of tile (ty, tz): cy + ncy cz, cy = ty on a non-periodic y axis
+// (else ty mod ncy), cz = tz mod ncz
+__device__ __forceinline__ int tm2_tile_class(const TmGeom2& T, int ty, int tz, bool py) {
+    return (py ? ty % T.ncy : ty) + T.ncy * (tz % T.ncz);
+}
+
 // Two consumer groups of NX / 2 x TY x TZ threads and one producer warp per
 // group.  Group h streams the velocities i = h, h + 2, ... for every pair of
 // the tile (thread (row, pair) writes both nodes' values into its tensor-memory
@@ -60,10 +68,10 @@ __device__ __forceinline__ void sts4f(uint32_t a, float4 v) {
 // that every stage has one producer and one group of consumers.  After the
 // tile's velocities a barrier of all consumers; then thread (h, pair) collides
 // node h of its pair (one node per thread).
-template <int VS, int NX, int TY, int TZ>
+template <int VS, int NX, int TY, int TZ, int P>
 __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
     k_step_rows_pairs(const float2* __restrict__ fg, float2* __restrict__ fgo, const void* __restrict__ maps,
-                      const int32_t* __restrict__ head, const TmRec2* __restrict__ recs,
+                      const int32_t* __restrict__ head, const void* __restrict__ recs,
                       const uint64_t* __restrict__ xmask, const uint64_t* __restrict__ smask,
                       const float* __restrict__ twt, const StepGeom G, const CollideConst<float> C, const TmGeom2 T,
                       int* __restrict__ status) {
@@ -76,8 +84,11 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
     constexpr int NT = 2 * NG;                    // consumer threads
     constexpr int NW = NT / 32;                   // consumer warps
     constexpr int NWG = NW / 2;                   // consumer warps per group
-    constexpr int XBW = NX + 4;                   // halo row of the x exchange
-    constexpr int REC_BYTES = NR * int(sizeof(TmRec2));
+    static_assert(P == 2 || P == 4, "orders 2 and 4");
+    using REC = typename std::conditional<P == 2, TmRec2, TmRec4>::type;
+    constexpr int XBW = NX + 2 * P;               // halo row of the x exchange: slot k holds x = k - P
+    constexpr int NXW = 2 * P + 1;                // x weights of a node
+    constexpr int REC_BYTES = NR * int(sizeof(REC));
     static_assert(NG == 256 && NW == 16, "two groups of 256 pairs: 512 nodes per tile");
     static_assert(NP % 32 == 0 && (NP == 32 || 2 * NR <= 14), "whole warps per row; named barriers 1 .. 2 NR");
     extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             if (k < total) {
                 const int kt = k / nv, j0 = k - kt * nv;
                 d.tile = int(blockIdx.x) + kt * int(gridDim.x);
-                const int tcl = py ? 0 : d.tile % T.ntile_y;
+                const int tcl = tm2_tile_class(T, d.tile % T.ntile_y, d.tile / T.ntile_y, py);
                 const int32_t* h0 = head + (size_t(h + 2 * j0) * T.n_tc + tcl) * TM2_HEAD;
                 d.nvs = max(__ldg(h0 + 14) >> 8, 1);
                 d.bytes = __ldg(h0 + 15);
@@ -182,7 +193,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             if (lane == 0) mbar_arrive_expect_tx(fb, uint32_t(da.bytes));
             __syncwarp();
             const int ty = da.tile % T.ntile_y, tz = da.tile / T.ntile_y;
-            const int y0 = ty * TY, z0 = tz * TZ, tcl = py ? 0 : ty;
+            const int y0 = ty * TY, z0 = tz * TZ, tcl = tm2_tile_class(T, ty, tz, py);
             bool act = false, seam = false;
             uint32_t dst = 0;
             int c1 = 0, c2 = 0, c3 = 0, map = 0, by = 0, bz = 0;
@@ -272,9 +283,10 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             // velocities whose x factor needs the row exchange, for this tile
             // class: read from global memory, so that every thread of a row
             // takes the same barriers whatever the stage holds
-            const uint64_t xm = __ldg(xmask + (py ? 0 : ty));
+            const int tcl = tm2_tile_class(T, ty, tz, py);
+            const uint64_t xm = __ldg(xmask + tcl);
             // velocities of this group that begin a stage
-            const uint64_t sm = __ldg(smask + 2 * (py ? 0 : ty) + h);
+            const uint64_t sm = __ldg(smask + 2 * tcl + h);
             bool live = false;
             int q = 0;
             uint32_t sa = st0;
@@ -297,21 +309,64 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                 } else {
                     ++q;
                 }
-                const uint32_t ra = sa + uint32_t(T.rows_bytes + q * REC_BYTES) + uint32_t(r * int(sizeof(TmRec2)));
+                const uint32_t ra = sa + uint32_t(T.rows_bytes + q * REC_BYTES) + uint32_t(r * int(sizeof(REC)));
                 const bool xc = (xm >> i) & 1;
                 // after an abort the stage may never have been written: nothing
                 // is read from it (an empty equilibrium record instead)
                 int meta = REC_EQ;
                 float2 sa2 = make_float2(0.f, 0.f), sb2 = make_float2(0.f, 0.f), sa2b = sa2, sb2b = sb2;
-                float wxe[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, wxo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-                if (live) {
+                float wxe[NXW], wxo[NXW];
+#pragma unroll
+                for (int m = 0; m < NXW; ++m) wxe[m] = wxo[m] = 0.f;
+                if constexpr (P == 4) {
+                    if (live) {
+                    // order 4: up to 25 taps; the x weights of this pair's class
+                    const REC* R = reinterpret_cast<const REC*>(dyn_smem + (ra - st0));
+                    meta = R->meta;
+                    const int ntap = R->ntap;
+                    if (xc) {
+                        const int pc = xp & 1;
+#pragma unroll
+                        for (int m = 0; m < NXW; ++m) {
+                            wxe[m] = reinterpret_cast<const float*>(&R->wx)[(2 * pc) * 9 + m];
+                            wxo[m] = reinterpret_cast<const float*>(&R->wx)[(2 * pc + 1) * 9 + m];
+                        }
+                    }
+                    const uint32_t bx = sa + uint32_t(16 * xp);
+#pragma unroll
+                    for (int k = 0; k < 25; ++k) {
+                        if (k < ntap) {
+                            const int o = reinterpret_cast<const int32_t*>(&R->off)[k];
+                            const float4 v = lds4f(bx + uint32_t(SLLBM_CHK(o, T.rows_bytes, G.status,
+                                                                             SLLBM_DEV_BAD_SMEM)));
+                            const float wk1 = reinterpret_cast<const float*>(&R->off)[25 + k];
+                            const float2 wk = make_float2(wk1, wk1);
+                            if (k & 1) {
+                                sa2b = __ffma2_rn(wk, make_float2(v.x, v.y), sa2b);
+                                sb2b = __ffma2_rn(wk, make_float2(v.z, v.w), sb2b);
+                            } else {
+                                sa2 = __ffma2_rn(wk, make_float2(v.x, v.y), sa2);
+                                sb2 = __ffma2_rn(wk, make_float2(v.z, v.w), sb2);
+                            }
+                        }
+                    }
+                    sa2 = __fadd2_rn(sa2, sa2b);
+                    sb2 = __fadd2_rn(sb2, sb2b);
+                    }
+                }
+                if constexpr (P == 2) {
+                    if (live) {
                     const int4 q0 = lds4(ra), q1 = lds4(ra + 16), q2 = lds4(ra + 32);
                     meta = q0.x;
                     const int ntap = q0.y;
                     if (xc) {
                         const float4 q5 = lds4f(ra + 80), q6 = lds4f(ra + 96), q7 = lds4f(ra + 112);
-                        wxe[0] = q5.x; wxe[1] = q5.y; wxe[2] = q5.z; wxe[3] = q5.w; wxe[4] = q6.x;
-                        wxo[0] = q6.y; wxo[1] = q6.z; wxo[2] = q6.w; wxo[3] = q7.x; wxo[4] = q7.y;
+                        const float wr[10] = {q5.x, q5.y, q5.z, q5.w, q6.x, q6.y, q6.z, q6.w, q7.x, q7.y};
+#pragma unroll
+                        for (int m = 0; m < NXW; ++m) {
+                            wxe[m] = wr[m];
+                            wxo[m] = wr[NXW + m];
+                        }
                     }
                     if (ntap > 0) {
                         const int4 q3 = lds4(ra + 48), q4 = lds4(ra + 64);
@@ -348,6 +403,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                         sa2 = __fadd2_rn(sa2, sa2b);
                         sb2 = __fadd2_rn(sb2, sb2b);
                     }
+                    }
                 }
                 if (j == nv - 1 || ((sm >> (j + 1)) & 1)) {
                     // this warp has read the stage's last velocity: release it to the producer
@@ -360,28 +416,29 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                 }
                 float2 oa = sa2, ob = sb2;
                 if (xc) {
-                    // x factor: each node's three x taps among the six row
-                    // sums x - 2 .. x + 3 (halo row: slot k holds x = k - 2,
-                    // with the periodic images of the first and last two)
+                    // x factor: each node's 2P + 1 x taps among the 2P + 2 row
+                    // sums x - P .. x + P + 1 (halo row: slot k holds x = k - P,
+                    // with the periodic images of the first and last P)
                     const uint32_t xr = xb0 + (xb ? XBB : 0u);
                     const float4 pr = make_float4(sa2.x, sa2.y, sb2.x, sb2.y);
-                    sts4f(xr + uint32_t(8 * (x + 2)), pr);
-                    if (xp == 0) sts4f(xr + uint32_t(8 * (NX + 2)), pr);
-                    if (xp == NP - 1) sts4f(xr, pr);
+                    sts4f(xr + uint32_t(8 * (x + P)), pr);
+                    if (x < P) sts4f(xr + uint32_t(8 * (x + NX + P)), pr);
+                    if (x >= NX - P) sts4f(xr + uint32_t(8 * (x - NX + P)), pr);
                     if (NP == 32)
                         __syncwarp();
                     else
                         row_bar(1 + r + h * NR, NP);
-                    const float4 w0 = lds4f(xr + uint32_t(8 * x));           // x - 2, x - 1
-                    const float4 w1 = lds4f(xr + uint32_t(8 * (x + 2)));     // x, x + 1
-                    const float4 w2 = lds4f(xr + uint32_t(8 * (x + 4)));     // x + 2, x + 3
-                    const float2 win[6] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w),
-                                           make_float2(w1.x, w1.y), make_float2(w1.z, w1.w),
-                                           make_float2(w2.x, w2.y), make_float2(w2.z, w2.w)};
+                    float2 win[2 * P + 2];
+#pragma unroll
+                    for (int m = 0; m <= P; ++m) {
+                        const float4 wv = lds4f(xr + uint32_t(8 * (x + 2 * m)));   // x - P + 2m, x - P + 2m + 1
+                        win[2 * m] = make_float2(wv.x, wv.y);
+                        win[2 * m + 1] = make_float2(wv.z, wv.w);
+                    }
                     oa = __fmul2_rn(make_float2(wxe[0], wxe[0]), win[0]);
                     ob = __fmul2_rn(make_float2(wxo[0], wxo[0]), win[1]);
 #pragma unroll
-                    for (int m = 1; m < 5; ++m) {
+                    for (int m = 1; m < NXW; ++m) {
                         oa = __ffma2_rn(make_float2(wxe[m], wxe[m]), win[m], oa);
                         ob = __ffma2_rn(make_float2(wxo[m], wxo[m]), win[m + 1], ob);
                     }
@@ -407,7 +464,9 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             tc_fence_after();
             // thread (h, pair) collides node x + h
             const int n = x + h + NX * (y + N1 * z);
-            const int cls = G.ncls[0] * ((py ? (y & 1) : (real ? y : 0)) + G.ncls[1] * (D == 3 ? (z & 1) : 0)) + h;
+            // the node's class: x mod p, y (mod p on a periodic axis), z mod p
+            const int cls = (x + h) % P +
+                            G.ncls[0] * ((py ? y % P : (real ? y : 0)) + G.ncls[1] * (D == 3 ? z % P : 0));
             const float qnan = __int_as_float(0x7fc00000);
             collide_tmem<VSET>(C, tl + uint32_t(h * TM_COLS), real ? __ldg(twt + cls) : qnan, fgo + n, NN,
                                real && !*abort_flag);
@@ -429,21 +488,21 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
 // barriers, the tensor-memory slot; at least 120 KB, so that one CTA resides
 // per SM (each allocates all of the SM's tensor-memory columns)
 inline size_t rows_pairs_smem_bytes(const TmGeom2& T, int nx, int nr) {
-    const size_t b = size_t(T.nst) * T.stage_bytes + sizeof(float2) * 4 * nr * (nx + 4) +
+    const size_t b = size_t(T.nst) * T.stage_bytes + sizeof(float2) * 4 * nr * (nx + 2 * T.p) +
                      sizeof(uint64_t) * (2 * T.nst + 1) + 16;
     return b < 120 * 1024 ? 120 * 1024 : b;
 }
 
-template <int VS, int NX, int TY, int TZ>
-int launch_step_rows_pairs(const float2* fg, float2* fgo, const void* maps, const int32_t* head, const TmRec2* recs,
+template <int VS, int NX, int TY, int TZ, int P>
+int launch_step_rows_pairs(const float2* fg, float2* fgo, const void* maps, const int32_t* head, const void* recs,
                            const uint64_t* xmask, const uint64_t* smask, const float* tw, const StepGeom& G,
                            const CollideConst<float>& C, const TmGeom2& T, int* status, cudaStream_t stream, int grid) {
     const size_t smem = rows_pairs_smem_bytes(T, NX, TY * TZ);
-    if (cudaFuncSetAttribute(k_step_rows_pairs<VS, NX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_step_rows_pairs<VS, NX, TY, TZ, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(smem)) != cudaSuccess)
         return SLLBM_ERR_CUDA;
-    k_step_rows_pairs<VS, NX, TY, TZ><<<grid, NX * TY * TZ + 64, smem, stream>>>(fg, fgo, maps, head, recs, xmask,
-                                                                                 smask, tw, G, C, T, status);
+    k_step_rows_pairs<VS, NX, TY, TZ, P><<<grid, NX * TY * TZ + 64, smem, stream>>>(fg, fgo, maps, head, recs, xmask,
+                                                                                    smask, tw, G, C, T, status);
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ERR_CUDA;
 }
 

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("name,over", [("channel", {}), ("mixing", {}), ("naca", {}), ("tgv2d", {}),
-                                       # the paper's order p = 4 at the channel's node count (tiled order-4 kernel)
+                                       # the paper's order p = 4 at the channel's node count (order-4 row tiles)
                                        ("channel", {"cells": (32, 24, 24), "p": 4})])
 def test_fullsize_sampled_step(built_lib, name, over):
     from paper_2412_09051_gb300.sim import Sim
@@ -32,7 +32,7 @@ def test_fullsize_sampled_step(built_lib, name, over):
     f1, g1 = ost.step_sample_from_fields(mesh, rec, rho, u, T, xi, w, par)
     sim = Sim(cfg)
     if over.get("p") == 4:
-        assert sim.info.stream_mode == 2              # the warp-tiled order-4 kernel, as bench.py runs it
+        assert sim.info.stream_mode == 10             # the order-4 two-nodes-per-thread row tiles, as bench.py runs it
     assert np.abs(sim.node_coords() - mesh.X).max() < 1e-12 * np.abs(mesh.X).max()
     sim.init_state(rho, u, T)
     sim.step(1)

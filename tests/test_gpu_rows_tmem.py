@@ -291,3 +291,59 @@ def test_rows_pairs_fullsize_channel_sampled(built_lib):
     assert worst < 1e-5
     print(f"PARITY rows_pairs fullsize channel: {len(nodes)} sampled nodes, populations {worst:.2e}")
     sim.close()
+
+
+PAIR4_CASES = {
+    "channel_p4_nx128": lambda: get_config("channel", cells=(32, 3, 3), p=4),   # 4 x 1 rows of 128, ragged y tile
+    "channel_p4_nx64": lambda: get_config("channel", cells=(16, 3, 3), p=4),    # 8 x 1 rows of 64, ragged y tile
+}
+
+
+@pytest.mark.parametrize("name", list(PAIR4_CASES))
+def test_rows_pairs_order4_matches_oracle(built_lib, name):
+    """The two-nodes-per-thread row tiles at the paper's order p = 4 (25
+    (y, z) taps, nine x taps per node over ten row sums, two pair classes):
+    3 steps against the oracle at the FP32 tolerance."""
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = PAIR4_CASES[name]()
+    mesh, xi, w, opp, par, rec = oracle_case(cfg)
+    sim = Sim(cfg, precision="fp32", stream_mode=10)
+    assert sim.info.stream_mode == 10, "the order-4 row tiles must be eligible for this mesh"
+    rho, u, T = initial_fields(cfg, mesh.X)
+    sim.init_state(rho, u, T)
+    f, g = ost.init_equilibrium(rho, u, T, xi, w, par.cv)
+    Tw = ost.isothermal_nodes(rec, par)
+    worst = 0.0
+    for k in range(3):
+        f, g = ost.step(mesh, rec, f, g, xi, w, par, Tw=Tw)
+        sim.step(1)
+        assert sim.step_kernel() == "k_step_rows_pairs"
+        fg, gg = sim.get_state()
+        ef, eg = _scale_err(fg, f, w), _scale_err(gg, g, w)
+        assert ef < 1e-5 and eg < 1e-5, (k, ef, eg)
+        worst = max(worst, ef, eg)
+    assert sim.device_status() == 0
+    print(f"PARITY rows_pairs order 4 {name} {mesh.N}: populations {worst:.2e}")
+    sim.close()
+
+
+def test_rows_pairs_order4_agrees_with_row_kernel(built_lib):
+    """5 steps of the order-4 channel (128-node rows) against the order-4
+    one-block-per-row kernel: the same step up to FP32 summation order."""
+    from paper_2412_09051_gb300.sim import Sim
+    cfg = get_config("channel", cells=(32, 4, 3), p=4)
+    a, b = Sim(cfg, stream_mode=10), Sim(cfg, stream_mode=8)
+    X = a.node_coords()
+    rho, u, T = initial_fields(cfg, X)
+    for s in (a, b):
+        s.init_state(rho, u, T)
+        s.step(5)
+    assert a.step_kernel() == "k_step_rows_pairs" and b.step_kernel() == "k_step_row_p"
+    fa, ga = a.get_state()
+    fb, gb = b.get_state()
+    _, w, _ = a.velocity_set()
+    ef, eg = _scale_err(fa, fb, w), _scale_err(ga, gb, w)
+    assert ef < 1e-5 and eg < 1e-5, (ef, eg)
+    print(f"PARITY rows_pairs order 4 vs row kernel, 5 channel steps: {max(ef, eg):.2e}")
+    a.close()
+    b.close()
