@@ -647,7 +647,9 @@ bool pack_rows_pairs(sllbm_ctx* c, TmGeom2& T, int NX, int NR, int max_rows, con
     const int Q = c->vs.Q;
     const int rec_bytes = NR * int(sizeof(REC));
     const size_t fixed = sizeof(float2) * 4 * NR * (NX + 2 * T.p) + 8 + 16;     // two halo rows per group
-    const size_t budget = 227 * 1024;
+    // all of an SM's shared memory for a 512-node tile (one CTA per SM), half
+    // of it for a 256-node tile (two CTAs per SM)
+    const size_t budget = NX * NR == 512 ? 227 * 1024 : 112 * 1024;
     // two stages per ring where the largest velocity's rows fit, else one;
     // the most velocities per stage whose records leave room for those rows
     int cap = 0, nst = 0, maxv = 0;
@@ -708,6 +710,43 @@ bool pack_rows_pairs(sllbm_ctx* c, TmGeom2& T, int NX, int NR, int max_rows, con
     return true;
 }
 
+// CTAs per SM of the two-nodes-per-thread kernel: one for tiles of 512
+// nodes, two for tiles of 256 (each with half of the SM's tensor memory and
+// shared memory)
+int rows_pairs_ctas_per_sm(const sllbm_ctx* c) {
+    int ty = 0, tz = 0;
+    rows_pairs_shape(c->mesh.D, c->mesh.N[0], c->tm2.p, ty, tz);
+    return c->mesh.N[0] * ty * tz == 256 ? 2 : 1;
+}
+
+// The pair structure the paired collision of the two-nodes-per-thread kernel
+// assumes for D3Q45 (PairLayout<3>): base and opposite exactly negated, the
+// pair's zero component exactly zero, equal weights within a shell, a rest
+// velocity at index 0.
+bool pair_layout_holds(const HostVelSet& vs) {
+    using PL = PairLayout<3>;
+    if (vs.Q != 2 * PL::NPAIR + 1 || vs.D != 3) return false;
+    for (int d = 0; d < 3; ++d)
+        if (vs.xi[d] != 0.0) return false;
+    for (int k = 0; k < PL::NPAIR; ++k) {
+        const int b = PL::base(k), o = PL::opp(b);
+        for (int d = 0; d < 3; ++d) {
+            if (vs.xi[o * 3 + d] != -vs.xi[b * 3 + d]) return false;
+            if (PL::zero(b) == d && vs.xi[b * 3 + d] != 0.0) return false;
+        }
+        const int sh = VelSet<3>::shell(b);
+        const int rep = PL::base(sh == 1 ? 0 : (sh == 2 ? 6 : 16));
+        if (VelSet<3>::shell(o) != sh || vs.w[o] != vs.w[b] || vs.w[b] != vs.w[rep]) return false;
+    }
+    bool seen[64] = {};
+    for (int i = 0; i < vs.Q; ++i) {
+        const int sl = PL::slot(i);
+        if (sl < 0 || sl >= vs.Q || seen[sl]) return false;
+        seen[sl] = true;
+    }
+    return true;
+}
+
 // Tables of the row-tile kernel with two nodes per thread (step_tmem2.cuh):
 // tiles of TY x TZ whole x rows.  Per (velocity, tile class): one box of
 // source rows per population (the y range times the z range of the (y, z)
@@ -723,7 +762,8 @@ bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::v
     const int Q = c->vs.Q, D = m.D, NX = m.N[0], N1 = m.N[1], N2 = D == 3 ? m.N[2] : 1;
     int TY = 0, TZ = 0;
     if (c->precision != SLLBM_FP32 || m.p != 2 || !c->tiled || !c->row_uniform) return false;
-    if (!((c->velset == SLLBM_D3Q45 && D == 3) || (c->velset == SLLBM_D2Q19 && D == 2))) return false;
+    if (!((c->velset == SLLBM_D3Q45 && D == 3 && pair_layout_holds(c->vs)) || (c->velset == SLLBM_D2Q19 && D == 2)))
+        return false;
     if (!rows_pairs_shape(D, NX, 2, TY, TZ) || G.ncls[0] != 2 || !m.periodic[0]) return false;
     const bool py = m.periodic[1] != 0;
     if (py && N1 % TY) return false;
@@ -734,7 +774,12 @@ bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::v
     T.ntile_y = (N1 + TY - 1) / TY;
     T.ntile_z = D == 3 ? N2 / TZ : 1;
     T.ntiles = T.ntile_y * T.ntile_z;
-    T.n_tc = py ? 1 : T.ntile_y;
+    // tile classes: node classes repeat with period 2 along a periodic axis,
+    // so a tile's classes depend on its y tile (non-periodic y) or on the
+    // parity of its first y, and on the parity of its first z
+    T.ncy = py ? (TY % 2 ? 2 : 1) : T.ntile_y;
+    T.ncz = D == 3 && TZ % 2 ? 2 : 1;
+    T.n_tc = T.ncy * T.ncz;
     head.assign(size_t(Q) * T.n_tc * TM2_HEAD, 0);
     recs.assign(size_t(Q) * T.n_tc * NR, TmRec2{});
     xmask.assign(size_t(T.n_tc), 0);
@@ -750,13 +795,13 @@ bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::v
     };
     for (int i = 0; i < Q; ++i)
         for (int tc = 0; tc < T.n_tc; ++tc) {
-            const int y0 = py ? 0 : tc * TY;
+            const int y0 = (tc % T.ncy) * TY, z0 = (tc / T.ncy) * TZ;
             int32_t* h = &head[(size_t(i) * T.n_tc + tc) * TM2_HEAD];
             std::vector<std::vector<Tap>> taps(NR);
             std::vector<int> cls0(NR, -1);
             for (int r = 0; r < NR; ++r) {
                 const int ry = r % TY, rz = r / TY;
-                const int y = y0 + ry, z = rz;
+                const int y = y0 + ry, z = z0 + rz;
                 if (y >= N1) continue;                   // beyond a ragged last tile: an idle row
                 cls0[r] = G.ncls[0] * ((py ? (y & 1) : y) + G.ncls[1] * (D == 3 ? (z & 1) : 0));
                 const TileRec<float>& a = t[size_t(i) * G.n_classes + cls0[r]];
@@ -845,8 +890,6 @@ bool build_rows_pairs(sllbm_ctx* c, const std::vector<TileRec<float>>& t, std::v
             }
             if (xchg) xmask[tc] |= uint64_t(1) << i;
         }
-    T.ncy = py ? 1 : T.ntile_y;
-    T.ncz = 1;
     T.p = 2;
     return pack_rows_pairs(c, T, NX, NR, max_rows, shapes, head, recs, smask);
 }
@@ -865,7 +908,8 @@ bool build_rows_pairs4(sllbm_ctx* c, const std::vector<TileRecP<float, 4>>& t, s
     const int Q = c->vs.Q, D = m.D, NX = m.N[0], N1 = m.N[1], N2 = D == 3 ? m.N[2] : 1;
     constexpr int P = 4;
     int TY = 0, TZ = 0;
-    if (c->precision != SLLBM_FP32 || m.p != P || D != 3 || c->velset != SLLBM_D3Q45) return false;
+    if (c->precision != SLLBM_FP32 || m.p != P || D != 3 || c->velset != SLLBM_D3Q45 || !pair_layout_holds(c->vs))
+        return false;
     if (!rows_pairs_shape(D, NX, P, TY, TZ) || G.ncls[0] != P || !m.periodic[0] || !m.periodic[2]) return false;
     const bool py = m.periodic[1] != 0;
     if ((py && N1 % TY) || N2 % TZ) return false;
@@ -1652,7 +1696,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
                         CK(cudaStreamSynchronize(s));
                         int sms = 0;
                         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-                        ctx->tm_grid = std::min(ctx->tm2.ntiles, sms);
+                        ctx->tm_grid = std::min(ctx->tm2.ntiles, sms * rows_pairs_ctas_per_sm(ctx));
                         ctx->rows_tm2 = true;
                     }
                 }
@@ -1707,7 +1751,7 @@ int create_ctx(const sllbm_mesh_desc* mesh, int32_t velset, const HostVelSet* vs
                         CK(cudaStreamSynchronize(s));
                         int sms = 0;
                         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-                        ctx->tm_grid = std::min(ctx->tm2.ntiles, sms);
+                        ctx->tm_grid = std::min(ctx->tm2.ntiles, sms * rows_pairs_ctas_per_sm(ctx));
                         ctx->rows_tm2 = true;
                         th.clear();
                         tx.clear();

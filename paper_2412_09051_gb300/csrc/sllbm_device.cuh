@@ -64,6 +64,36 @@ template <> struct VelSet<3> {   // D3Q45
     }
 };
 
+// Opposite pairs of a velocity set (xi_o = -xi_b, w_o = w_b), for the paired
+// collision: pair k = (base(k), opp(base(k))); zero(b) is the component that
+// is zero in both (-1: none); slot(i) places pair k at slots 2k (base) and
+// 2k + 1 (opposite) and the rest velocity at slot 2 NPAIR.  The host checks
+// the numeric table against this structure before a kernel relies on it.
+template <int VS> struct PairLayout {
+    static constexpr bool on = false;
+};
+template <> struct PairLayout<3> {   // D3Q45: icosahedron, dodecahedron, icosahedron shells
+    static constexpr bool on = true;
+    static constexpr int NPAIR = 22;
+    // bases 1..6 (shell 1), 13..22 (shell 2), 33..38 (shell 3)
+    __host__ __device__ static constexpr int base(int k) { return k < 6 ? 1 + k : (k < 16 ? 7 + k : 17 + k); }
+    __host__ __device__ static constexpr int opp(int b) { return b + ((b >= 13 && b <= 22) ? 10 : 6); }
+    // the cyclic (0, a, b) patterns: x, y, z zero in consecutive index pairs;
+    // 13..16 are the (+-1, +-1, +-1) directions
+    __host__ __device__ static constexpr int zero(int b) {
+        return b <= 12 ? (b - 1) / 2 : (b <= 16 ? -1 : (b <= 32 ? (b - 17) / 2 : (b - 33) / 2));
+    }
+    __host__ __device__ static constexpr int slot(int i) {
+        return i == 0    ? 2 * NPAIR
+               : i <= 6  ? 2 * (i - 1)
+               : i <= 12 ? 2 * (i - 7) + 1
+               : i <= 22 ? 2 * (i - 7)
+               : i <= 32 ? 2 * (i - 17) + 1
+               : i <= 38 ? 2 * (i - 17)
+                         : 2 * (i - 23) + 1;
+    }
+};
+
 // ------------------------------------------------------------ constants
 template <typename real>
 struct CollideConst {

@@ -17,8 +17,10 @@ bool rows_pairs_shape(int D, int nx, int p, int& ty, int& tz) {
         return false;
     }
     if (D == 3) {
-        if (nx == 128) { ty = 2; tz = 2; return true; }
-        if (nx == 64) { ty = 4; tz = 2; return true; }
+        // tiles of 256 nodes, two CTAs per SM: one CTA's collision overlaps
+        // the other's streaming
+        if (nx == 128) { ty = 2; tz = 1; return true; }
+        if (nx == 64) { ty = 2; tz = 2; return true; }
         return false;
     }
     if (nx == 128) { ty = 4; tz = 1; return true; }
@@ -34,8 +36,8 @@ int launch_rows_pairs(int vs, int nx, const float2* fg, float2* fgo, const void*
     if (vs == VS && nx == NX && T.p == P)                                                                     \
         return launch_step_rows_pairs<VS, NX, TY, TZ, P>(fg, fgo, maps, head, recs, xmask, smask, tw, G, C, T, \
                                                          status, s, grid);
-    TPCASE(3, 128, 2, 2, 2)
-    TPCASE(3, 64, 4, 2, 2)
+    TPCASE(3, 128, 2, 1, 2)
+    TPCASE(3, 64, 2, 2, 2)
     TPCASE(1, 128, 4, 1, 2)
     TPCASE(1, 64, 8, 1, 2)
     TPCASE(3, 128, 4, 1, 4)

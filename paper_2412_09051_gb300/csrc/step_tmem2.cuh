@@ -61,6 +61,307 @@ __device__ __forceinline__ int tm2_tile_class(const TmGeom2& T, int ty, int tz, 
     return (py ? ty % T.ncy : ty) + T.ncy * (tz % T.ncz);
 }
 
+// ------------------------------------------------------------ paired collision
+// tensor-memory slot of velocity i: the pair layout where the set has one
+template <int VS>
+__host__ __device__ constexpr int tm2_slot(int i) {
+    if constexpr (PairLayout<VS>::on)
+        return PairLayout<VS>::slot(i);
+    else
+        return i;
+}
+// the D3Q45 slots as a constant table (one uniform load per streamed velocity)
+struct Tm2Slots {
+    unsigned char s[64];
+};
+constexpr Tm2Slots tm2_slots45() {
+    Tm2Slots t{};
+    for (int i = 0; i < VelSet<3>::Q; ++i) t.s[i] = static_cast<unsigned char>(tm2_slot<3>(i));
+    return t;
+}
+static __constant__ Tm2Slots c_tm2_slots45 = tm2_slots45();
+
+// G chunks of 16 FP32 columns of this thread's tensor-memory lane, issued
+// together and waited for once (warp-collective)
+template <int G>
+__device__ __forceinline__ void tm_ld_chunks(uint32_t taddr, float (&v)[16 * G]) {
+    static_assert(G == 1 || G == 2, "one or two chunks");
+    if constexpr (G == 1) {
+        tc_ld16(taddr, v);
+    } else {
+        uint32_t r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr)
+            : "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+    }
+}
+
+// xi_b . a over the components of base b that are not zero
+template <int VS>
+__device__ __forceinline__ float pair_dot(const CollideConst<float>& C, int b, float a0, float a1, float a2) {
+    using PL = PairLayout<VS>;
+    float s = 0.f;
+    bool first = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (PL::zero(b) != d) {
+            const float a = d == 0 ? a0 : (d == 1 ? a1 : a2);
+            s = first ? C.xi[b][d] * a : fmaf(C.xi[b][d], a, s);
+            first = false;
+        }
+    }
+    return s;
+}
+
+// chunks of 16 columns per tensor-memory load of the paired collision
+constexpr int kPairLoadChunks = 1;
+
+// The arithmetic of collide_tmem (moments, isothermal correction, BGK
+// relaxation with the quasi-equilibrium heat flux, forcing) for a velocity set
+// of opposite pairs, on the pair layout of the node's block: pair k's base
+// (f, g) in columns [4k, 4k + 2), its opposite in [4k + 2, 4k + 4), the rest
+// velocity in [4 NPAIR, 4 NPAIR + 2).  Each pair is taken at once: with
+// c = xi_b . u for the base and -c for the opposite, the equilibrium
+// polynomial P1(+-c) = E(c^2) +- c O(c^2) (its even and odd parts); the
+// momentum and heat-flux sums take xi_b times the pair's difference, the heat
+// flux as sum xi h - u sum h; the correction of g is +-w xi_b . q.  Same
+// quantities as collide_tmem up to FP32 rounding order.
+template <int VS, int GL = kPairLoadChunks>
+__device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C, uint32_t tl, float Tw, float2* out,
+                                                   int NN, bool store) {
+    using VSET = VelSet<VS>;
+    using PL = PairLayout<VS>;
+    constexpr int NPAIR = PL::NPAIR;
+    constexpr int NCH = (4 * NPAIR + 2 + 15) / 16;
+    static_assert(VSET::D == 3 && 2 * NPAIR + 1 == VSET::Q, "three-dimensional set of pairs and a rest velocity");
+    // ---- moments: plain sums within a chunk (four pairs), Kahan across chunks
+    Acc<float> arho, aj0, aj1, aj2, ae;
+#pragma unroll
+    for (int cg = 0; cg < NCH; cg += GL) {
+        float vg[16 * GL];
+        tm_ld_chunks<GL>(tl + 16 * cg, vg);
+#pragma unroll
+        for (int cc = 0; cc < GL; ++cc) {
+        const int c = cg + cc;
+        float* v = vg + 16 * cc;
+        float br = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, be = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int k = 4 * c + m;
+            if (k < NPAIR) {
+                const int b = PL::base(k);
+                const float fs = v[4 * m] + v[4 * m + 2], fd = v[4 * m] - v[4 * m + 2];
+                br += fs;
+                if (PL::zero(b) != 0) b0 = fmaf(C.xi[b][0], fd, b0);
+                if (PL::zero(b) != 1) b1 = fmaf(C.xi[b][1], fd, b1);
+                if (PL::zero(b) != 2) b2 = fmaf(C.xi[b][2], fd, b2);
+                be = fmaf(C.s2[VSET::shell(b)], fs, be) + (v[4 * m + 1] + v[4 * m + 3]);
+            } else if (k == NPAIR) {
+                // the rest velocity: xi = 0, |xi|^2 = 0
+                br += v[4 * m];
+                be += v[4 * m + 1];
+            }
+        }
+        arho.add(br);
+        aj0.add(b0);
+        aj1.add(b1);
+        aj2.add(b2);
+        ae.add(be);
+        }
+    }
+    const float rho_d = arho.get();
+    const float rho = 1.f + rho_d;
+    const float inv_rho = 1.f / rho;
+    const float u0 = aj0.get() * inv_rho, u1 = aj1.get() * inv_rho, u2 = aj2.get() * inv_rho;
+    const float U = u0 * u0 + u1 * u1 + u2 * u2;
+    float t = (ae.get() - rho * U - 2.f * C.cv * rho_d) * inv_rho / (2.f * C.cv);
+    // ---- isothermal wall correction (Eq. thermalBC), on the warps that hold such a node
+    const bool iso = !(Tw != Tw);
+    if (__any_sync(0xffffffffu, iso)) {
+        const float tw = iso ? Tw - 1.f : t;
+        const float rT0 = rho * (1.f + t), rT1 = rho * (1.f + tw);
+#pragma unroll 1
+        for (int c = 0; c < NCH; ++c) {
+            float v[16];
+            tc_ld16(tl + 16 * c, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int sl = 8 * c + j;   // runtime slot: the per-velocity tables
+                if (sl <= 2 * NPAIR) {
+                    const int k = sl >> 1;
+                    const int i = k == NPAIR ? 0 : ((sl & 1) ? PL::opp(PL::base(k)) : PL::base(k));
+                    const float cv = C.xi[i][0] * u0 + C.xi[i][1] * u1 + C.xi[i][2] * u2;
+                    const float k2a = 0.5f - 0.25f * U + 0.25f * t * C.sCv[i];
+                    const float k1a = 1.0f - 0.5f * U + 0.5f * t * C.sBv[i];
+                    const float k0a = -0.5f * U + 0.125f * U * U + 0.5f * t * C.sAv[i] - 0.25f * t * U * C.sBv[i] +
+                                      0.125f * t * t * C.sEv[i];
+                    const float k2b = 0.5f - 0.25f * U + 0.25f * tw * C.sCv[i];
+                    const float k1b = 1.0f - 0.5f * U + 0.5f * tw * C.sBv[i];
+                    const float k0b = -0.5f * U + 0.125f * U * U + 0.5f * tw * C.sAv[i] - 0.25f * tw * U * C.sBv[i] +
+                                      0.125f * tw * tw * C.sEv[i];
+                    const float a0 = eq_poly1(cv, k0a, k1a, k2a), a1 = eq_poly1(cv, k0b, k1b, k2b);
+                    if (iso) {
+                        v[2 * j] += C.w[i] * rho * (a1 - a0);
+                        v[2 * j + 1] += C.wg[i] * ((rT1 * a1 + (rT1 - 1.f)) - (rT0 * a0 + (rT0 - 1.f)));
+                    }
+                }
+            }
+            tm_st16(tl + 16 * c, v);
+        }
+        tm_wait_st();
+        if (iso) t = tw;
+    }
+    const float T = 1.f + t;
+    float mu = C.mu_ref;
+    if (C.var_mu) mu *= powf(T * C.inv_T_ref, C.mu_exp);
+    const float tau = mu / (rho * T * C.dt) + 0.5f;
+    const float om = 1.f / tau;
+    const float om_pr = 1.f / ((tau - 0.5f) * C.inv_Pr + 0.5f);
+    const float rhoT = rho * T;
+    const float rhoT_d = rho_d + rho * t;
+    const bool second = C.quasi || C.forced;
+    // Kupershtokh exact-difference forcing (Sec. 4.3), du = F dt / rho: the
+    // equilibrium at v = u + du minus the one at u, added in the relaxation pass
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, V = 0.f;
+    if (C.forced) {
+        v0 = u0 + C.force_dt[0] * inv_rho;
+        v1 = u1 + C.force_dt[1] * inv_rho;
+        v2 = u2 + C.force_dt[2] * inv_rho;
+        V = v0 * v0 + v1 * v1 + v2 * v2;
+    }
+    // per-shell coefficients: k0 + k1 c + k2 c^2 + c^3 / 6 + c^4 / 24 at u
+    // (and at v), |xi|^2 + U, and the weights times rho, rho_d, rho T, rho T_d
+    // (the weights are equal within a shell)
+    auto rep = [](int sh) { return sh == 0 ? 0 : PL::base(sh == 1 ? 0 : (sh == 2 ? 6 : 16)); };
+    float k0[VSET::NS], k1[VSET::NS], k2[VSET::NS], sU[VSET::NS], wr[VSET::NS], wrd[VSET::NS], wgr[VSET::NS],
+        wgrd[VSET::NS], k0f[VSET::NS], k1f[VSET::NS], k2f[VSET::NS];
+#pragma unroll
+    for (int sh = 0; sh < VSET::NS; ++sh) {
+        k2[sh] = 0.5f - 0.25f * U + 0.25f * t * C.sC[sh];
+        k1[sh] = 1.0f - 0.5f * U + 0.5f * t * C.sB[sh];
+        k0[sh] = -0.5f * U + 0.125f * U * U + 0.5f * t * C.sA[sh] - 0.25f * t * U * C.sB[sh] +
+                 0.125f * t * t * C.sE[sh];
+        k2f[sh] = 0.5f - 0.25f * V + 0.25f * t * C.sC[sh];
+        k1f[sh] = 1.0f - 0.5f * V + 0.5f * t * C.sB[sh];
+        k0f[sh] = -0.5f * V + 0.125f * V * V + 0.5f * t * C.sA[sh] - 0.25f * t * V * C.sB[sh] +
+                  0.125f * t * t * C.sE[sh];
+        sU[sh] = C.s2[sh] + U;
+        wr[sh] = C.w[rep(sh)] * rho;
+        wrd[sh] = C.w[rep(sh)] * rho_d;
+        wgr[sh] = C.wg[rep(sh)] * rhoT;
+        wgrd[sh] = C.wg[rep(sh)] * rhoT_d;
+    }
+    float q0 = 0.f, q1 = 0.f, q2 = 0.f, hs = 0.f;
+    // ---- relaxation (BGK); heat flux of the quasi-equilibrium term; forcing
+#pragma unroll
+    for (int cg = 0; cg < NCH; cg += GL) {
+        float vg[16 * GL];
+        tm_ld_chunks<GL>(tl + 16 * cg, vg);
+#pragma unroll
+        for (int cc = 0; cc < GL; ++cc) {
+        const int c = cg + cc;
+        float* v = vg + 16 * cc;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int k = 4 * c + m;
+            if (k < NPAIR) {
+                const int b = PL::base(k), o = PL::opp(b), sh = VSET::shell(b);
+                const float cu = pair_dot<VS>(C, b, u0, u1, u2);
+                const float c2 = cu * cu;
+                const float E = fmaf(c2, fmaf(c2, 1.f / 24.f, k2[sh]), k0[sh]);
+                const float cO = cu * fmaf(c2, 1.f / 6.f, k1[sh]);
+                const float Pb = E + cO, Po = E - cO;
+                const float fb = v[4 * m], gb = v[4 * m + 1], fo = v[4 * m + 2], go = v[4 * m + 3];
+                const float fnb = fb - fmaf(wr[sh], Pb, wrd[sh]), gnb = gb - fmaf(wgr[sh], Pb, wgrd[sh]);
+                const float fno = fo - fmaf(wr[sh], Po, wrd[sh]), gno = go - fmaf(wgr[sh], Po, wgrd[sh]);
+                const float hb = fmaf(fmaf(-2.f, cu, sU[sh]), fnb, gnb);
+                const float ho = fmaf(fmaf(2.f, cu, sU[sh]), fno, gno);
+                const float hd = hb - ho;
+                hs += hb + ho;
+                if (PL::zero(b) != 0) q0 = fmaf(C.xi[b][0], hd, q0);
+                if (PL::zero(b) != 1) q1 = fmaf(C.xi[b][1], hd, q1);
+                if (PL::zero(b) != 2) q2 = fmaf(C.xi[b][2], hd, q2);
+                float rfb = fmaf(-om, fnb, fb), rfo = fmaf(-om, fno, fo);
+                const float rgb = fmaf(-om, gnb, gb), rgo = fmaf(-om, gno, go);
+                if (C.forced) {
+                    const float cw = pair_dot<VS>(C, b, v0, v1, v2);
+                    const float w2 = cw * cw;
+                    const float dE = fmaf(w2, fmaf(w2, 1.f / 24.f, k2f[sh]), k0f[sh]) - E;
+                    const float dO = fmaf(cw, fmaf(w2, 1.f / 6.f, k1f[sh]), -cO);
+                    rfb = fmaf(wr[sh], dE + dO, rfb);
+                    rfo = fmaf(wr[sh], dE - dO, rfo);
+                }
+                if (second) {
+                    v[4 * m] = rfb;
+                    v[4 * m + 1] = rgb;
+                    v[4 * m + 2] = rfo;
+                    v[4 * m + 3] = rgo;
+                } else if (store) {
+                    out[b * NN] = make_float2(rfb, rgb);
+                    out[o * NN] = make_float2(rfo, rgo);
+                }
+            } else if (k == NPAIR) {
+                // the rest velocity: c = 0, P1 = k0
+                const float f = v[4 * m], g = v[4 * m + 1];
+                const float fn = f - fmaf(wr[0], k0[0], wrd[0]), gn = g - fmaf(wgr[0], k0[0], wgrd[0]);
+                hs += fmaf(sU[0], fn, gn);
+                float rf = fmaf(-om, fn, f);
+                const float rg = fmaf(-om, gn, g);
+                if (C.forced) rf = fmaf(wr[0], k0f[0] - k0[0], rf);
+                if (second) {
+                    v[4 * m] = rf;
+                    v[4 * m + 1] = rg;
+                } else if (store) {
+                    out[0] = make_float2(rf, rg);
+                }
+            }
+        }
+        if (second) tm_st16(tl + 16 * c, *reinterpret_cast<float(*)[16]>(v));
+        }
+    }
+    if (!second) return;
+    tm_wait_st();
+    const float a = C.quasi ? om - om_pr : 0.f;
+    q0 = a * fmaf(-u0, hs, q0);
+    q1 = a * fmaf(-u1, hs, q1);
+    q2 = a * fmaf(-u2, hs, q2);
+    // ---- the heat-flux correction of g: +- w xi_b . q for the pair
+#pragma unroll
+    for (int cg = 0; cg < NCH; cg += GL) {
+        float vg[16 * GL];
+        tm_ld_chunks<GL>(tl + 16 * cg, vg);
+#pragma unroll
+        for (int cc = 0; cc < GL; ++cc) {
+        const int c = cg + cc;
+        float* v = vg + 16 * cc;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int k = 4 * c + m;
+            if (k < NPAIR) {
+                const int b = PL::base(k), o = PL::opp(b);
+                const float wdq = C.w[b] * pair_dot<VS>(C, b, q0, q1, q2);
+                if (store) {
+                    out[b * NN] = make_float2(v[4 * m], v[4 * m + 1] + wdq);
+                    out[o * NN] = make_float2(v[4 * m + 2], v[4 * m + 3] - wdq);
+                }
+            } else if (k == NPAIR && store) {
+                out[0] = make_float2(v[4 * m], v[4 * m + 1]);
+            }
+        }
+        }
+    }
+}
+
 // Two consumer groups of NX / 2 x TY x TZ threads and one producer warp per
 // group.  Group h streams the velocities i = h, h + 2, ... for every pair of
 // the tile (thread (row, pair) writes both nodes' values into its tensor-memory
@@ -69,7 +370,7 @@ __device__ __forceinline__ int tm2_tile_class(const TmGeom2& T, int ty, int tz, 
 // tile's velocities a barrier of all consumers; then thread (h, pair) collides
 // node h of its pair (one node per thread).
 template <int VS, int NX, int TY, int TZ, int P>
-__global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
+__global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2)
     k_step_rows_pairs(const float2* __restrict__ fg, float2* __restrict__ fgo, const void* __restrict__ maps,
                       const int32_t* __restrict__ head, const void* __restrict__ recs,
                       const uint64_t* __restrict__ xmask, const uint64_t* __restrict__ smask,
@@ -89,7 +390,11 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
     constexpr int XBW = NX + 2 * P;               // halo row of the x exchange: slot k holds x = k - P
     constexpr int NXW = 2 * P + 1;                // x weights of a node
     constexpr int REC_BYTES = NR * int(sizeof(REC));
-    static_assert(NG == 256 && NW == 16, "two groups of 256 pairs: 512 nodes per tile");
+    static_assert((NG == 256 && NW == 16) || (NG == 128 && NW == 8),
+                  "two groups of 256 pairs (512 nodes per tile, one CTA per SM) or of 128 pairs (256 nodes per "
+                  "tile, two CTAs per SM)");
+    constexpr int CPS = NG == 256 ? 1 : 2;        // CTAs per SM
+    constexpr int TMA_COLS = TM_ALLOC / CPS;      // tensor-memory columns of this CTA
     static_assert(NP % 32 == 0 && (NP == 32 || 2 * NR <= 14), "whole warps per row; named barriers 1 .. 2 NR");
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     unsigned char* stages = dyn_smem;                                         // [nst][rows | records]
@@ -117,7 +422,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
         *abort_flag = 0;
     }
     if (warp == 0) {
-        tc_alloc(smem_u32(slot), TM_ALLOC);
+        tc_alloc(smem_u32(slot), TMA_COLS);
         tc_relinquish();
     }
     tc_fence_before();
@@ -272,7 +577,8 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
         const int r = pt / NP, xp = pt % NP, x = 2 * xp;
         const int ry = r % TY, rz = r / TY;
         const int nv = (Q - h + 1) / 2;
-        const uint32_t tl = tbase + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(2 * TM_COLS * ((warp & 7) >> 2));
+        const uint32_t tl =
+            tbase + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(2 * TM_COLS * ((warp % NWG) >> 2));
         const uint32_t xb0 = smem_u32(XB) + uint32_t((2 * h * NR + r) * XBW * 8);   // this row's halo row, buffer 0
         constexpr uint32_t XBB = uint32_t(NR * XBW * 8);                           // bytes of one buffer
         int s = 0, ph = 0, xb = 0;
@@ -454,8 +760,9 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
                         ob.x += C.mw[bid][i];
                     }
                 }
-                tm_st2(tl + 2 * i, oa.x, oa.y);
-                tm_st2(tl + TM_COLS + 2 * i, ob.x, ob.y);
+                const int sl = PairLayout<VS>::on ? int(c_tm2_slots45.s[i]) : i;
+                tm_st2(tl + 2 * sl, oa.x, oa.y);
+                tm_st2(tl + TM_COLS + 2 * sl, ob.x, ob.y);
             }
             // both groups' values of the tile are in tensor memory
             tm_wait_st();
@@ -468,8 +775,12 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
             const int cls = (x + h) % P +
                             G.ncls[0] * ((py ? y % P : (real ? y : 0)) + G.ncls[1] * (D == 3 ? z % P : 0));
             const float qnan = __int_as_float(0x7fc00000);
-            collide_tmem<VSET>(C, tl + uint32_t(h * TM_COLS), real ? __ldg(twt + cls) : qnan, fgo + n, NN,
-                               real && !*abort_flag);
+            if constexpr (PairLayout<VS>::on)
+                collide_tmem_pairs<VS>(C, tl + uint32_t(h * TM_COLS), real ? __ldg(twt + cls) : qnan, fgo + n, NN,
+                                       real && !*abort_flag);
+            else
+                collide_tmem<VSET>(C, tl + uint32_t(h * TM_COLS), real ? __ldg(twt + cls) : qnan, fgo + n, NN,
+                                   real && !*abort_flag);
             // every collision has read its node before the next tile's stores
             tc_fence_before();
             row_bar(15, NT);
@@ -480,17 +791,20 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, 1)
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tc_dealloc(tbase, TM_ALLOC);
+        tc_dealloc(tbase, TMA_COLS);
     }
 }
 
 // shared memory of one CTA: the stages, the x-exchange halo rows, the
-// barriers, the tensor-memory slot; at least 120 KB, so that one CTA resides
-// per SM (each allocates all of the SM's tensor-memory columns)
+// barriers, the tensor-memory slot; at least 120 KB for tiles of 512 nodes,
+// so that one CTA resides per SM (each allocates all of the SM's
+// tensor-memory columns), at least 80 KB for tiles of 256 nodes (two CTAs
+// per SM, half of the columns each, never three)
 inline size_t rows_pairs_smem_bytes(const TmGeom2& T, int nx, int nr) {
     const size_t b = size_t(T.nst) * T.stage_bytes + sizeof(float2) * 4 * nr * (nx + 2 * T.p) +
                      sizeof(uint64_t) * (2 * T.nst + 1) + 16;
-    return b < 120 * 1024 ? 120 * 1024 : b;
+    const size_t lo = nx * nr == 512 ? 120 * 1024 : 80 * 1024;
+    return b < lo ? lo : b;
 }
 
 template <int VS, int NX, int TY, int TZ, int P>
