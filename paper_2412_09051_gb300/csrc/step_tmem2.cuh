@@ -17,8 +17,13 @@
 //     records one producer warp issues in a single instruction (one lane per
 //     copy): the copy engine's cost is per issuing instruction far more than
 //     per byte, so few large stages move the rows fastest.
-// Collision: collide_tmem (step_tmem.cuh).  Every wait is bounded, with the
-// abort protocol of step_tmem.cuh.
+// Tiles of 512 nodes run one CTA per SM; tiles of 256 nodes two, each with
+// half of the SM's tensor-memory columns and shared memory, so that one CTA's
+// collision overlaps the other's streaming.
+// Collision: collide_tmem_pairs for D3Q45 (opposite velocities taken as
+// pairs, tensor-memory columns in the pair layout), collide_tmem
+// (step_tmem.cuh) for the 2D set.  Every wait is bounded, with the abort
+// protocol of step_tmem.cuh.
 #pragma once
 #include <type_traits>
 
@@ -152,31 +157,31 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
         tm_ld_chunks<GL>(tl + 16 * cg, vg);
 #pragma unroll
         for (int cc = 0; cc < GL; ++cc) {
-        const int c = cg + cc;
-        float* v = vg + 16 * cc;
-        float br = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, be = 0.f;
+            const int c = cg + cc;
+            float* v = vg + 16 * cc;
+            float br = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, be = 0.f;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int k = 4 * c + m;
-            if (k < NPAIR) {
-                const int b = PL::base(k);
-                const float fs = v[4 * m] + v[4 * m + 2], fd = v[4 * m] - v[4 * m + 2];
-                br += fs;
-                if (PL::zero(b) != 0) b0 = fmaf(C.xi[b][0], fd, b0);
-                if (PL::zero(b) != 1) b1 = fmaf(C.xi[b][1], fd, b1);
-                if (PL::zero(b) != 2) b2 = fmaf(C.xi[b][2], fd, b2);
-                be = fmaf(C.s2[VSET::shell(b)], fs, be) + (v[4 * m + 1] + v[4 * m + 3]);
-            } else if (k == NPAIR) {
-                // the rest velocity: xi = 0, |xi|^2 = 0
-                br += v[4 * m];
-                be += v[4 * m + 1];
+            for (int m = 0; m < 4; ++m) {
+                const int k = 4 * c + m;
+                if (k < NPAIR) {
+                    const int b = PL::base(k);
+                    const float fs = v[4 * m] + v[4 * m + 2], fd = v[4 * m] - v[4 * m + 2];
+                    br += fs;
+                    if (PL::zero(b) != 0) b0 = fmaf(C.xi[b][0], fd, b0);
+                    if (PL::zero(b) != 1) b1 = fmaf(C.xi[b][1], fd, b1);
+                    if (PL::zero(b) != 2) b2 = fmaf(C.xi[b][2], fd, b2);
+                    be = fmaf(C.s2[VSET::shell(b)], fs, be) + (v[4 * m + 1] + v[4 * m + 3]);
+                } else if (k == NPAIR) {
+                    // the rest velocity: xi = 0, |xi|^2 = 0
+                    br += v[4 * m];
+                    be += v[4 * m + 1];
+                }
             }
-        }
-        arho.add(br);
-        aj0.add(b0);
-        aj1.add(b1);
-        aj2.add(b2);
-        ae.add(be);
+            arho.add(br);
+            aj0.add(b0);
+            aj1.add(b1);
+            aj2.add(b2);
+            ae.add(be);
         }
     }
     const float rho_d = arho.get();
@@ -269,64 +274,64 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
         tm_ld_chunks<GL>(tl + 16 * cg, vg);
 #pragma unroll
         for (int cc = 0; cc < GL; ++cc) {
-        const int c = cg + cc;
-        float* v = vg + 16 * cc;
+            const int c = cg + cc;
+            float* v = vg + 16 * cc;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int k = 4 * c + m;
-            if (k < NPAIR) {
-                const int b = PL::base(k), o = PL::opp(b), sh = VSET::shell(b);
-                const float cu = pair_dot<VS>(C, b, u0, u1, u2);
-                const float c2 = cu * cu;
-                const float E = fmaf(c2, fmaf(c2, 1.f / 24.f, k2[sh]), k0[sh]);
-                const float cO = cu * fmaf(c2, 1.f / 6.f, k1[sh]);
-                const float Pb = E + cO, Po = E - cO;
-                const float fb = v[4 * m], gb = v[4 * m + 1], fo = v[4 * m + 2], go = v[4 * m + 3];
-                const float fnb = fb - fmaf(wr[sh], Pb, wrd[sh]), gnb = gb - fmaf(wgr[sh], Pb, wgrd[sh]);
-                const float fno = fo - fmaf(wr[sh], Po, wrd[sh]), gno = go - fmaf(wgr[sh], Po, wgrd[sh]);
-                const float hb = fmaf(fmaf(-2.f, cu, sU[sh]), fnb, gnb);
-                const float ho = fmaf(fmaf(2.f, cu, sU[sh]), fno, gno);
-                const float hd = hb - ho;
-                hs += hb + ho;
-                if (PL::zero(b) != 0) q0 = fmaf(C.xi[b][0], hd, q0);
-                if (PL::zero(b) != 1) q1 = fmaf(C.xi[b][1], hd, q1);
-                if (PL::zero(b) != 2) q2 = fmaf(C.xi[b][2], hd, q2);
-                float rfb = fmaf(-om, fnb, fb), rfo = fmaf(-om, fno, fo);
-                const float rgb = fmaf(-om, gnb, gb), rgo = fmaf(-om, gno, go);
-                if (C.forced) {
-                    const float cw = pair_dot<VS>(C, b, v0, v1, v2);
-                    const float w2 = cw * cw;
-                    const float dE = fmaf(w2, fmaf(w2, 1.f / 24.f, k2f[sh]), k0f[sh]) - E;
-                    const float dO = fmaf(cw, fmaf(w2, 1.f / 6.f, k1f[sh]), -cO);
-                    rfb = fmaf(wr[sh], dE + dO, rfb);
-                    rfo = fmaf(wr[sh], dE - dO, rfo);
-                }
-                if (second) {
-                    v[4 * m] = rfb;
-                    v[4 * m + 1] = rgb;
-                    v[4 * m + 2] = rfo;
-                    v[4 * m + 3] = rgo;
-                } else if (store) {
-                    out[b * NN] = make_float2(rfb, rgb);
-                    out[o * NN] = make_float2(rfo, rgo);
-                }
-            } else if (k == NPAIR) {
-                // the rest velocity: c = 0, P1 = k0
-                const float f = v[4 * m], g = v[4 * m + 1];
-                const float fn = f - fmaf(wr[0], k0[0], wrd[0]), gn = g - fmaf(wgr[0], k0[0], wgrd[0]);
-                hs += fmaf(sU[0], fn, gn);
-                float rf = fmaf(-om, fn, f);
-                const float rg = fmaf(-om, gn, g);
-                if (C.forced) rf = fmaf(wr[0], k0f[0] - k0[0], rf);
-                if (second) {
-                    v[4 * m] = rf;
-                    v[4 * m + 1] = rg;
-                } else if (store) {
-                    out[0] = make_float2(rf, rg);
+            for (int m = 0; m < 4; ++m) {
+                const int k = 4 * c + m;
+                if (k < NPAIR) {
+                    const int b = PL::base(k), o = PL::opp(b), sh = VSET::shell(b);
+                    const float cu = pair_dot<VS>(C, b, u0, u1, u2);
+                    const float c2 = cu * cu;
+                    const float E = fmaf(c2, fmaf(c2, 1.f / 24.f, k2[sh]), k0[sh]);
+                    const float cO = cu * fmaf(c2, 1.f / 6.f, k1[sh]);
+                    const float Pb = E + cO, Po = E - cO;
+                    const float fb = v[4 * m], gb = v[4 * m + 1], fo = v[4 * m + 2], go = v[4 * m + 3];
+                    const float fnb = fb - fmaf(wr[sh], Pb, wrd[sh]), gnb = gb - fmaf(wgr[sh], Pb, wgrd[sh]);
+                    const float fno = fo - fmaf(wr[sh], Po, wrd[sh]), gno = go - fmaf(wgr[sh], Po, wgrd[sh]);
+                    const float hb = fmaf(fmaf(-2.f, cu, sU[sh]), fnb, gnb);
+                    const float ho = fmaf(fmaf(2.f, cu, sU[sh]), fno, gno);
+                    const float hd = hb - ho;
+                    hs += hb + ho;
+                    if (PL::zero(b) != 0) q0 = fmaf(C.xi[b][0], hd, q0);
+                    if (PL::zero(b) != 1) q1 = fmaf(C.xi[b][1], hd, q1);
+                    if (PL::zero(b) != 2) q2 = fmaf(C.xi[b][2], hd, q2);
+                    float rfb = fmaf(-om, fnb, fb), rfo = fmaf(-om, fno, fo);
+                    const float rgb = fmaf(-om, gnb, gb), rgo = fmaf(-om, gno, go);
+                    if (C.forced) {
+                        const float cw = pair_dot<VS>(C, b, v0, v1, v2);
+                        const float w2 = cw * cw;
+                        const float dE = fmaf(w2, fmaf(w2, 1.f / 24.f, k2f[sh]), k0f[sh]) - E;
+                        const float dO = fmaf(cw, fmaf(w2, 1.f / 6.f, k1f[sh]), -cO);
+                        rfb = fmaf(wr[sh], dE + dO, rfb);
+                        rfo = fmaf(wr[sh], dE - dO, rfo);
+                    }
+                    if (second) {
+                        v[4 * m] = rfb;
+                        v[4 * m + 1] = rgb;
+                        v[4 * m + 2] = rfo;
+                        v[4 * m + 3] = rgo;
+                    } else if (store) {
+                        out[b * NN] = make_float2(rfb, rgb);
+                        out[o * NN] = make_float2(rfo, rgo);
+                    }
+                } else if (k == NPAIR) {
+                    // the rest velocity: c = 0, P1 = k0
+                    const float f = v[4 * m], g = v[4 * m + 1];
+                    const float fn = f - fmaf(wr[0], k0[0], wrd[0]), gn = g - fmaf(wgr[0], k0[0], wgrd[0]);
+                    hs += fmaf(sU[0], fn, gn);
+                    float rf = fmaf(-om, fn, f);
+                    const float rg = fmaf(-om, gn, g);
+                    if (C.forced) rf = fmaf(wr[0], k0f[0] - k0[0], rf);
+                    if (second) {
+                        v[4 * m] = rf;
+                        v[4 * m + 1] = rg;
+                    } else if (store) {
+                        out[0] = make_float2(rf, rg);
+                    }
                 }
             }
-        }
-        if (second) tm_st16(tl + 16 * c, *reinterpret_cast<float(*)[16]>(v));
+            if (second) tm_st16(tl + 16 * c, *reinterpret_cast<float(*)[16]>(v));
         }
     }
     if (!second) return;
@@ -342,22 +347,22 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
         tm_ld_chunks<GL>(tl + 16 * cg, vg);
 #pragma unroll
         for (int cc = 0; cc < GL; ++cc) {
-        const int c = cg + cc;
-        float* v = vg + 16 * cc;
+            const int c = cg + cc;
+            float* v = vg + 16 * cc;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int k = 4 * c + m;
-            if (k < NPAIR) {
-                const int b = PL::base(k), o = PL::opp(b);
-                const float wdq = C.w[b] * pair_dot<VS>(C, b, q0, q1, q2);
-                if (store) {
-                    out[b * NN] = make_float2(v[4 * m], v[4 * m + 1] + wdq);
-                    out[o * NN] = make_float2(v[4 * m + 2], v[4 * m + 3] - wdq);
+            for (int m = 0; m < 4; ++m) {
+                const int k = 4 * c + m;
+                if (k < NPAIR) {
+                    const int b = PL::base(k), o = PL::opp(b);
+                    const float wdq = C.w[b] * pair_dot<VS>(C, b, q0, q1, q2);
+                    if (store) {
+                        out[b * NN] = make_float2(v[4 * m], v[4 * m + 1] + wdq);
+                        out[o * NN] = make_float2(v[4 * m + 2], v[4 * m + 3] - wdq);
+                    }
+                } else if (k == NPAIR && store) {
+                    out[0] = make_float2(v[4 * m], v[4 * m + 1]);
                 }
-            } else if (k == NPAIR && store) {
-                out[0] = make_float2(v[4 * m], v[4 * m + 1]);
             }
-        }
         }
     }
 }
@@ -572,7 +577,8 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
         // thread (group h, row r, pair xp): nodes x = 2 xp (even) and x + 1
         // (odd); their 2Q values in columns [0, 96) and [96, 192) of a
         // 192-column block of the thread's tensor-memory lane, the same lane
-        // and block for both groups (warps w and w + 8)
+        // and block for both groups (warps w and w + NWG); velocity i in the
+        // columns of its slot (the pair layout for D3Q45)
         const int h = tid / NG, pt = tid % NG;
         const int r = pt / NP, xp = pt % NP, x = 2 * xp;
         const int ry = r % TY, rz = r / TY;
