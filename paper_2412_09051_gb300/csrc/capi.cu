@@ -646,7 +646,7 @@ bool pack_rows_pairs(sllbm_ctx* c, TmGeom2& T, int NX, int NR, int max_rows, con
                      std::vector<int32_t>& head, std::vector<REC>& recs, std::vector<uint64_t>& smask) {
     const int Q = c->vs.Q;
     const int rec_bytes = NR * int(sizeof(REC));
-    const size_t fixed = sizeof(float2) * 4 * NR * (NX + 2 * T.p) + 8 + 16;     // two halo rows per group
+    const size_t fixed = sizeof(float2) * 4 * NR * NX + 8 + 16;     // two exchange rows per group and row
     // all of an SM's shared memory for a 512-node tile (one CTA per SM), half
     // of it for a 256-node tile (two CTAs per SM)
     const size_t budget = NX * NR == 512 ? 227 * 1024 : 112 * 1024;

@@ -118,6 +118,8 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 // limit, which would hide a short one.
 constexpr long long kWaitLimit = 1ll << 31;
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitLimit) {
+    // a phase already complete under the default bound needs no clock read
+    if (limit >= kWaitLimit && mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     if (limit < kWaitLimit) {
         while (!mbar_test(bar, parity))

@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
     constexpr int NWG = NW / 2;                   // consumer warps per group
     static_assert(P == 2 || P == 4, "orders 2 and 4");
     using REC = typename std::conditional<P == 2, TmRec2, TmRec4>::type;
-    constexpr int XBW = NX + 2 * P;               // halo row of the x exchange: slot k holds x = k - P
+    constexpr int XBW = NX;                       // row of the x exchange: slot k holds x = k (periodic)
     constexpr int NXW = 2 * P + 1;                // x weights of a node
     constexpr int REC_BYTES = NR * int(sizeof(REC));
     static_assert((NG == 256 && NW == 16) || (NG == 128 && NW == 8),
@@ -401,6 +401,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
     constexpr int CPS = NG == 256 ? 1 : 2;        // CTAs per SM
     constexpr int TMA_COLS = TM_ALLOC / CPS;      // tensor-memory columns of this CTA
     static_assert(NP % 32 == 0 && (NP == 32 || 2 * NR <= 14), "whole warps per row; named barriers 1 .. 2 NR");
+    static_assert((NP & (NP - 1)) == 0, "pairs of a row a power of two (the exchange indexes modulo NP)");
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     unsigned char* stages = dyn_smem;                                         // [nst][rows | records]
     float2* XB = reinterpret_cast<float2*>(stages + size_t(T.nst) * T.stage_bytes);   // [group][2][NR][XBW]
@@ -729,13 +730,10 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
                 float2 oa = sa2, ob = sb2;
                 if (xc) {
                     // x factor: each node's 2P + 1 x taps among the 2P + 2 row
-                    // sums x - P .. x + P + 1 (halo row: slot k holds x = k - P,
-                    // with the periodic images of the first and last P)
+                    // sums x - P .. x + P + 1, the pairs xp - P / 2 .. xp + P / 2
+                    // of the exchange row taken modulo the periodic row
                     const uint32_t xr = xb0 + (xb ? XBB : 0u);
-                    const float4 pr = make_float4(sa2.x, sa2.y, sb2.x, sb2.y);
-                    sts4f(xr + uint32_t(8 * (x + P)), pr);
-                    if (x < P) sts4f(xr + uint32_t(8 * (x + NX + P)), pr);
-                    if (x >= NX - P) sts4f(xr + uint32_t(8 * (x - NX + P)), pr);
+                    sts4f(xr + uint32_t(16 * xp), make_float4(sa2.x, sa2.y, sb2.x, sb2.y));
                     if (NP == 32)
                         __syncwarp();
                     else
@@ -743,7 +741,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
                     float2 win[2 * P + 2];
 #pragma unroll
                     for (int m = 0; m <= P; ++m) {
-                        const float4 wv = lds4f(xr + uint32_t(8 * (x + 2 * m)));   // x - P + 2m, x - P + 2m + 1
+                        const float4 wv = lds4f(xr + uint32_t(16 * ((xp + m - P / 2) & (NP - 1))));   // x - P + 2m, + 1
                         win[2 * m] = make_float2(wv.x, wv.y);
                         win[2 * m + 1] = make_float2(wv.z, wv.w);
                     }
@@ -807,7 +805,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
 // tensor-memory columns), at least 80 KB for tiles of 256 nodes (two CTAs
 // per SM, half of the columns each, never three)
 inline size_t rows_pairs_smem_bytes(const TmGeom2& T, int nx, int nr) {
-    const size_t b = size_t(T.nst) * T.stage_bytes + sizeof(float2) * 4 * nr * (nx + 2 * T.p) +
+    const size_t b = size_t(T.nst) * T.stage_bytes + sizeof(float2) * 4 * nr * nx +
                      sizeof(uint64_t) * (2 * T.nst + 1) + 16;
     const size_t lo = nx * nr == 512 ? 120 * 1024 : 80 * 1024;
     return b < lo ? lo : b;
