@@ -456,6 +456,10 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
         struct Sd {
             int nvs, bytes, tile, i, n, e, sl, bd;   // velocities, bytes, tile; this lane's velocity, its
         };                                           // boxes, this lane's box, its first slot, its shape
+        // all loads of a stage's table entries in one round (none depends on
+        // another): this lane's velocity clamped to the group's last, so that
+        // every load stays inside the table; the entries beyond the stage or
+        // the velocity's boxes are dropped afterwards
         auto fetch = [&](int k) {
             Sd d{1, 0, 0, 0, 0, 0, 0, 0};
             if (k < total) {
@@ -463,16 +467,20 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
                 d.tile = int(blockIdx.x) + kt * int(gridDim.x);
                 const int tcl = tm2_tile_class(T, d.tile % T.ntile_y, d.tile / T.ntile_y, py);
                 const int32_t* h0 = head + (size_t(h + 2 * j0) * T.n_tc + tcl) * TM2_HEAD;
-                d.nvs = max(__ldg(h0 + 14) >> 8, 1);
-                d.bytes = __ldg(h0 + 15);
+                const int iq = h + 2 * min(j0 + (lane < LB + TM2_MAX_VEL ? q : 0), nv - 1);
+                const int32_t* hp = head + (size_t(iq) * T.n_tc + tcl) * TM2_HEAD;
+                const int w14 = __ldg(h0 + 14), w15 = __ldg(h0 + 15), n = __ldg(hp);
+                const int e = __ldg(hp + 2 + b), sl = __ldg(hp + 2 + TM2_MAX_BOXES + b),
+                          bd = __ldg(hp + 2 + 2 * TM2_MAX_BOXES + b);
+                d.nvs = max(w14 >> 8, 1);
+                d.bytes = w15;
                 if (lane < LB + TM2_MAX_VEL && q < d.nvs) {
-                    d.i = h + 2 * (j0 + q);
-                    const int32_t* hp = head + (size_t(d.i) * T.n_tc + tcl) * TM2_HEAD;
-                    d.n = __ldg(hp);
-                    if (lane < LB && b < d.n) {
-                        d.e = __ldg(hp + 2 + b);
-                        d.sl = __ldg(hp + 2 + TM2_MAX_BOXES + b);
-                        d.bd = __ldg(hp + 2 + 2 * TM2_MAX_BOXES + b);
+                    d.i = iq;
+                    d.n = n;
+                    if (lane < LB && b < n) {
+                        d.e = e;
+                        d.sl = sl;
+                        d.bd = bd;
                     }
                 }
             }
