@@ -522,7 +522,10 @@ int sllbm_mlp_path(sllbm_ctx* ctx, int32_t path);
  *   SLLBM_DEV_BAD_REC   a record slot outside its table (class, tile record),
  *                       a boundary-state id outside [0, 2), or a gather-code
  *                       cell outside [0, cells);
- *   SLLBM_DEV_BAD_SMEM  a row-buffer slot outside the block's row.
+ *   SLLBM_DEV_BAD_SMEM  a row-buffer slot outside the block's row, or a
+ *                       tensor-copy destination in shared memory that is
+ *                       not 128-byte aligned (the copy is skipped, and the
+ *                       stage's bounded wait ends the step).
  * The paper has no counterpart: it is the substitute for a memory checker. */
 #define SLLBM_DEV_TC_TIMEOUT 1
 #define SLLBM_DEV_BAD_NODE   2

@@ -645,7 +645,8 @@ template <class REC>
 bool pack_rows_pairs(sllbm_ctx* c, TmGeom2& T, int NX, int NR, int max_rows, const std::vector<int>& shapes,
                      std::vector<int32_t>& head, std::vector<REC>& recs, std::vector<uint64_t>& smask) {
     const int Q = c->vs.Q;
-    const int rec_bytes = NR * int(sizeof(REC));
+    const int rec_bytes = NR * int(sizeof(REC));               // one velocity's records, as copied
+    const int rec_slot = (rec_bytes + 127) / 128 * 128;        // their 128-byte aligned slot in a stage
     const size_t fixed = sizeof(float2) * 4 * NR * NX + 8 + 16;     // two exchange rows per group and row
     // all of an SM's shared memory for a 512-node tile (one CTA per SM), half
     // of it for a 256-node tile (two CTAs per SM)
@@ -656,7 +657,7 @@ bool pack_rows_pairs(sllbm_ctx* c, TmGeom2& T, int NX, int NR, int max_rows, con
     for (int n : {4, 2}) {
         for (int v = TM2_MAX_VEL; v >= 1 && !maxv; --v) {
             const long long room = (static_cast<long long>(budget) - static_cast<long long>(fixed)) / n - 16 -
-                                   static_cast<long long>(v) * rec_bytes;
+                                   static_cast<long long>(v) * rec_slot;
             const int k = int(std::max(0LL, room) / (NX * 8));
             if (k >= max_rows) {
                 cap = k;
@@ -702,7 +703,9 @@ bool pack_rows_pairs(sllbm_ctx* c, TmGeom2& T, int NX, int NR, int max_rows, con
             }
         }
     T.rows_bytes = cap * NX * 8;
-    T.stage_bytes = T.rows_bytes + maxv * rec_bytes;
+    T.stage_bytes = T.rows_bytes + maxv * rec_slot;
+    // every tensor copy's destination (stage, row block, records slot) 128-byte aligned
+    if (T.rows_bytes % 128 || T.stage_bytes % 128) return false;
     T.nst = nst;
     T.rec_map = int(shapes.size());
     c->tm2 = T;

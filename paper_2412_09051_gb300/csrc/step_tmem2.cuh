@@ -394,7 +394,10 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
     using REC = typename std::conditional<P == 2, TmRec2, TmRec4>::type;
     constexpr int XBW = NX;                       // row of the x exchange: slot k holds x = k (periodic)
     constexpr int NXW = 2 * P + 1;                // x weights of a node
-    constexpr int REC_BYTES = NR * int(sizeof(REC));
+    constexpr int REC_BYTES = NR * int(sizeof(REC));        // bytes of one velocity's records (copied)
+    // their slot in a stage: a tensor copy's shared-memory destination is
+    // 128-byte aligned (stages and row blocks are multiples of 128 bytes)
+    constexpr int REC_SLOT = (REC_BYTES + 127) / 128 * 128;
     static_assert((NG == 256 && NW == 16) || (NG == 128 && NW == 8),
                   "two groups of 256 pairs (512 nodes per tile, one CTA per SM) or of 128 pairs (256 nodes per "
                   "tile, two CTAs per SM)");
@@ -536,8 +539,15 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
                 c1 = 0;
                 c2 = tcl;
                 c3 = da.i;
-                dst = sb + uint32_t(T.rows_bytes + q * REC_BYTES);
+                dst = sb + uint32_t(T.rows_bytes + q * REC_SLOT);
                 act = true;
+            }
+            if (act && (dst & 127u)) {
+                // a tensor copy's shared destination must be 128-byte aligned:
+                // record it and skip the copy (the stage's bounded wait then
+                // runs out and the step ends with an error)
+                atomicOr(status, SLLBM_DEV_BAD_SMEM);
+                act = false;
             }
             if (act) tma_load_4d(dst, static_cast<const char*>(maps) + size_t(map) * 128, 0, c1, c2, c3, fb);
             if (seam) {
@@ -630,7 +640,7 @@ __global__ void __launch_bounds__(NX * TY * TZ + 64, NX * TY * TZ == 512 ? 1 : 2
                 } else {
                     ++q;
                 }
-                const uint32_t ra = sa + uint32_t(T.rows_bytes + q * REC_BYTES) + uint32_t(r * int(sizeof(REC)));
+                const uint32_t ra = sa + uint32_t(T.rows_bytes + q * REC_SLOT) + uint32_t(r * int(sizeof(REC)));
                 const bool xc = (xm >> i) & 1;
                 // after an abort the stage may never have been written: nothing
                 // is read from it (an empty equilibrium record instead)
