@@ -176,8 +176,10 @@ typedef struct {
                                        (x even, x + 1) per consumer thread while streaming, one
                                        TMA tensor copy per (source population, velocity, tile) and
                                        stages of up to six velocities: D3Q45 rows of 64 or 128
-                                       nodes, D2Q19 rows of 64 or 128, periodic x and z (elsewhere
-                                       as SLLBM_STREAM_ROWS_TMEM).  With D3Q45,
+                                       nodes (orders 2 and 4; tiles of 256 nodes, two CTAs per
+                                       SM, opposite velocities collided in pairs), D2Q19 rows of
+                                       64 or 128 (tiles of 512 nodes, one CTA per SM), periodic x
+                                       and z (elsewhere as SLLBM_STREAM_ROWS_TMEM).  With D3Q45,
                                        SLLBM_STREAM_AUTO and SLLBM_STREAM_STRUCTURED use this
                                        kernel wherever it applies                                */
 
