@@ -225,6 +225,9 @@ void fill_collide_const(sllbm_ctx* c, CollideConst<real>& C) {
         C.sBv[i] = real(s - D - 2);
         C.sCv[i] = real(s - D - 4);
         C.sEv[i] = real(s * s - 2.0 * (D + 2) * s + D * (D + 2.0));
+        static const int xa[6] = {0, 1, 2, 0, 0, 1}, xb[6] = {0, 1, 2, 1, 2, 2};
+        for (int k = 0; k < 6; ++k)
+            C.xx[i][k] = xa[k] < D && xb[k] < D ? real(vs.xi[i * D + xa[k]] * vs.xi[i * D + xb[k]]) : real(0);
     }
     for (size_t h = 0; h < vs.shell_s.size(); ++h) {
         const double s = vs.shell_s[h];

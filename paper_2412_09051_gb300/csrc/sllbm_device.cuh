@@ -115,6 +115,8 @@ struct CollideConst {
     int opp[SLLBM_QMAX];
     // per-velocity copies of the shell constants (runtime-indexed loops)
     real s2v[SLLBM_QMAX], sAv[SLLBM_QMAX], sBv[SLLBM_QMAX], sCv[SLLBM_QMAX], sEv[SLLBM_QMAX];
+    // second-moment products xi_a xi_b per velocity: (00, 11, 22, 01, 02, 12)
+    real xx[SLLBM_QMAX][6];
 };
 
 // ------------------------------------------------------------ compensated sum

@@ -138,9 +138,13 @@ constexpr int kPairLoadChunks = 1;
 // velocity in [4 NPAIR, 4 NPAIR + 2).  Each pair is taken at once: with
 // c = xi_b . u for the base and -c for the opposite, the equilibrium
 // polynomial P1(+-c) = E(c^2) +- c O(c^2) (its even and odd parts); the
-// momentum and heat-flux sums take xi_b times the pair's difference, the heat
-// flux as sum xi h - u sum h; the correction of g is +-w xi_b . q.  Same
-// quantities as collide_tmem up to FP32 rounding order.
+// momentum sums take xi_b times the pair's difference.  The heat flux of the
+// quasi-equilibrium term comes from moments summed in the same first pass
+// (the central third moment of the populations themselves, since the
+// equilibrium's vanishes on the set), so the relaxation pass applies the
+// correction +-w xi_b . q of g and stores the post-collision pairs: two
+// passes over the node state, nothing written back.  Same quantities as
+// collide_tmem up to FP32 rounding order.
 template <int VS, int GL = kPairLoadChunks>
 __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C, uint32_t tl, float Tw, float2* out,
                                                    int NN, bool store) {
@@ -151,6 +155,9 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
     static_assert(VSET::D == 3 && 2 * NPAIR + 1 == VSET::Q, "three-dimensional set of pairs and a rest velocity");
     // ---- moments: plain sums within a chunk (four pairs), Kahan across chunks
     Acc<float> arho, aj0, aj1, aj2, ae;
+    // for the heat flux: sum xi_b ((|xi|^2 - (D + 2) - g_f) (f_b - f_o) + g_b - g_o)
+    // and the second moments sum xi_a xi_b (f_b + f_o) of the deviations
+    float qx0 = 0.f, qx1 = 0.f, qx2 = 0.f, m00 = 0.f, m11 = 0.f, m22 = 0.f, m01 = 0.f, m02 = 0.f, m12 = 0.f;
 #pragma unroll
     for (int cg = 0; cg < NCH; cg += GL) {
         float vg[16 * GL];
@@ -171,6 +178,19 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
                     if (PL::zero(b) != 1) b1 = fmaf(C.xi[b][1], fd, b1);
                     if (PL::zero(b) != 2) b2 = fmaf(C.xi[b][2], fd, b2);
                     be = fmaf(C.s2[VSET::shell(b)], fs, be) + (v[4 * m + 1] + v[4 * m + 3]);
+                    {
+                        const int z = PL::zero(b);
+                        const float tq = fmaf(C.s2[VSET::shell(b)] - 5.f - C.gfac, fd, v[4 * m + 1] - v[4 * m + 3]);
+                        if (z != 0) qx0 = fmaf(C.xi[b][0], tq, qx0);
+                        if (z != 1) qx1 = fmaf(C.xi[b][1], tq, qx1);
+                        if (z != 2) qx2 = fmaf(C.xi[b][2], tq, qx2);
+                        if (z != 0) m00 = fmaf(C.xx[b][0], fs, m00);
+                        if (z != 1) m11 = fmaf(C.xx[b][1], fs, m11);
+                        if (z != 2) m22 = fmaf(C.xx[b][2], fs, m22);
+                        if (z != 0 && z != 1) m01 = fmaf(C.xx[b][3], fs, m01);
+                        if (z != 0 && z != 2) m02 = fmaf(C.xx[b][4], fs, m02);
+                        if (z != 1 && z != 2) m12 = fmaf(C.xx[b][5], fs, m12);
+                    }
                 } else if (k == NPAIR) {
                     // the rest velocity: xi = 0, |xi|^2 = 0
                     br += v[4 * m];
@@ -190,6 +210,17 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
     const float u0 = aj0.get() * inv_rho, u1 = aj1.get() * inv_rho, u2 = aj2.get() * inv_rho;
     const float U = u0 * u0 + u1 * u1 + u2 * u2;
     float t = (ae.get() - rho * U - 2.f * C.cv * rho_d) * inv_rho / (2.f * C.cv);
+    // The non-equilibrium heat flux sum_i (xi_i - u)(|xi_i - u|^2 f^neq_i +
+    // g^neq_i): the equilibrium's central third moment vanishes on the set,
+    // so it is the central moment of the node's own populations, written on
+    // the deviations with the O(u) parts folded into the sums above (small
+    // terms, little FP32 cancellation).  The isothermal correction below
+    // changes f and g by equilibria at the same rho and u, which leaves it
+    // unchanged.
+    const float sc = (5.f + C.gfac) * rho_d - ae.get() + 2.f * rho * U;
+    const float qh0 = fmaf(u0, sc, qx0) - 2.f * (m00 * u0 + m01 * u1 + m02 * u2);
+    const float qh1 = fmaf(u1, sc, qx1) - 2.f * (m01 * u0 + m11 * u1 + m12 * u2);
+    const float qh2 = fmaf(u2, sc, qx2) - 2.f * (m02 * u0 + m12 * u1 + m22 * u2);
     // ---- isothermal wall correction (Eq. thermalBC), on the warps that hold such a node
     const bool iso = !(Tw != Tw);
     if (__any_sync(0xffffffffu, iso)) {
@@ -234,7 +265,6 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
     const float om_pr = 1.f / ((tau - 0.5f) * C.inv_Pr + 0.5f);
     const float rhoT = rho * T;
     const float rhoT_d = rho_d + rho * t;
-    const bool second = C.quasi || C.forced;
     // Kupershtokh exact-difference forcing (Sec. 4.3), du = F dt / rho: the
     // equilibrium at v = u + du minus the one at u, added in the relaxation pass
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, V = 0.f;
@@ -245,10 +275,10 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
         V = v0 * v0 + v1 * v1 + v2 * v2;
     }
     // per-shell coefficients: k0 + k1 c + k2 c^2 + c^3 / 6 + c^4 / 24 at u
-    // (and at v), |xi|^2 + U, and the weights times rho, rho_d, rho T, rho T_d
+    // (and at v), and the weights times rho, rho_d, rho T, rho T_d
     // (the weights are equal within a shell)
     auto rep = [](int sh) { return sh == 0 ? 0 : PL::base(sh == 1 ? 0 : (sh == 2 ? 6 : 16)); };
-    float k0[VSET::NS], k1[VSET::NS], k2[VSET::NS], sU[VSET::NS], wr[VSET::NS], wrd[VSET::NS], wgr[VSET::NS],
+    float k0[VSET::NS], k1[VSET::NS], k2[VSET::NS], wr[VSET::NS], wrd[VSET::NS], wgr[VSET::NS],
         wgrd[VSET::NS], k0f[VSET::NS], k1f[VSET::NS], k2f[VSET::NS];
 #pragma unroll
     for (int sh = 0; sh < VSET::NS; ++sh) {
@@ -260,14 +290,16 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
         k1f[sh] = 1.0f - 0.5f * V + 0.5f * t * C.sB[sh];
         k0f[sh] = -0.5f * V + 0.125f * V * V + 0.5f * t * C.sA[sh] - 0.25f * t * V * C.sB[sh] +
                   0.125f * t * t * C.sE[sh];
-        sU[sh] = C.s2[sh] + U;
         wr[sh] = C.w[rep(sh)] * rho;
         wrd[sh] = C.w[rep(sh)] * rho_d;
         wgr[sh] = C.wg[rep(sh)] * rhoT;
         wgrd[sh] = C.wg[rep(sh)] * rhoT_d;
     }
-    float q0 = 0.f, q1 = 0.f, q2 = 0.f, hs = 0.f;
-    // ---- relaxation (BGK); heat flux of the quasi-equilibrium term; forcing
+    // the heat flux relaxes with 1 / tau_Pr: its correction of g, scaled
+    const float a = C.quasi ? om - om_pr : 0.f;
+    const float q0 = a * qh0, q1 = a * qh1, q2 = a * qh2;
+    // ---- relaxation (BGK), the heat-flux correction of g, forcing; the
+    // post-collision pairs go to HBM (one pass, nothing written back)
 #pragma unroll
     for (int cg = 0; cg < NCH; cg += GL) {
         float vg[16 * GL];
@@ -289,15 +321,8 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
                     const float fb = v[4 * m], gb = v[4 * m + 1], fo = v[4 * m + 2], go = v[4 * m + 3];
                     const float fnb = fb - fmaf(wr[sh], Pb, wrd[sh]), gnb = gb - fmaf(wgr[sh], Pb, wgrd[sh]);
                     const float fno = fo - fmaf(wr[sh], Po, wrd[sh]), gno = go - fmaf(wgr[sh], Po, wgrd[sh]);
-                    const float hb = fmaf(fmaf(-2.f, cu, sU[sh]), fnb, gnb);
-                    const float ho = fmaf(fmaf(2.f, cu, sU[sh]), fno, gno);
-                    const float hd = hb - ho;
-                    hs += hb + ho;
-                    if (PL::zero(b) != 0) q0 = fmaf(C.xi[b][0], hd, q0);
-                    if (PL::zero(b) != 1) q1 = fmaf(C.xi[b][1], hd, q1);
-                    if (PL::zero(b) != 2) q2 = fmaf(C.xi[b][2], hd, q2);
                     float rfb = fmaf(-om, fnb, fb), rfo = fmaf(-om, fno, fo);
-                    const float rgb = fmaf(-om, gnb, gb), rgo = fmaf(-om, gno, go);
+                    float rgb = fmaf(-om, gnb, gb), rgo = fmaf(-om, gno, go);
                     if (C.forced) {
                         const float cw = pair_dot<VS>(C, b, v0, v1, v2);
                         const float w2 = cw * cw;
@@ -306,12 +331,11 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
                         rfb = fmaf(wr[sh], dE + dO, rfb);
                         rfo = fmaf(wr[sh], dE - dO, rfo);
                     }
-                    if (second) {
-                        v[4 * m] = rfb;
-                        v[4 * m + 1] = rgb;
-                        v[4 * m + 2] = rfo;
-                        v[4 * m + 3] = rgo;
-                    } else if (store) {
+                    // the heat-flux correction of g: +- w xi_b . q
+                    const float wdq = C.w[b] * pair_dot<VS>(C, b, q0, q1, q2);
+                    rgb += wdq;
+                    rgo -= wdq;
+                    if (store) {
                         out[b * NN] = make_float2(rfb, rgb);
                         out[o * NN] = make_float2(rfo, rgo);
                     }
@@ -319,48 +343,10 @@ __device__ __forceinline__ void collide_tmem_pairs(const CollideConst<float>& C,
                     // the rest velocity: c = 0, P1 = k0
                     const float f = v[4 * m], g = v[4 * m + 1];
                     const float fn = f - fmaf(wr[0], k0[0], wrd[0]), gn = g - fmaf(wgr[0], k0[0], wgrd[0]);
-                    hs += fmaf(sU[0], fn, gn);
                     float rf = fmaf(-om, fn, f);
                     const float rg = fmaf(-om, gn, g);
                     if (C.forced) rf = fmaf(wr[0], k0f[0] - k0[0], rf);
-                    if (second) {
-                        v[4 * m] = rf;
-                        v[4 * m + 1] = rg;
-                    } else if (store) {
-                        out[0] = make_float2(rf, rg);
-                    }
-                }
-            }
-            if (second) tm_st16(tl + 16 * c, *reinterpret_cast<float(*)[16]>(v));
-        }
-    }
-    if (!second) return;
-    tm_wait_st();
-    const float a = C.quasi ? om - om_pr : 0.f;
-    q0 = a * fmaf(-u0, hs, q0);
-    q1 = a * fmaf(-u1, hs, q1);
-    q2 = a * fmaf(-u2, hs, q2);
-    // ---- the heat-flux correction of g: +- w xi_b . q for the pair
-#pragma unroll
-    for (int cg = 0; cg < NCH; cg += GL) {
-        float vg[16 * GL];
-        tm_ld_chunks<GL>(tl + 16 * cg, vg);
-#pragma unroll
-        for (int cc = 0; cc < GL; ++cc) {
-            const int c = cg + cc;
-            float* v = vg + 16 * cc;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int k = 4 * c + m;
-                if (k < NPAIR) {
-                    const int b = PL::base(k), o = PL::opp(b);
-                    const float wdq = C.w[b] * pair_dot<VS>(C, b, q0, q1, q2);
-                    if (store) {
-                        out[b * NN] = make_float2(v[4 * m], v[4 * m + 1] + wdq);
-                        out[o * NN] = make_float2(v[4 * m + 2], v[4 * m + 3] - wdq);
-                    }
-                } else if (k == NPAIR && store) {
-                    out[0] = make_float2(v[4 * m], v[4 * m + 1]);
+                    if (store) out[0] = make_float2(rf, rg);
                 }
             }
         }

@@ -224,3 +224,63 @@ def test_pair_form_check_catches_planted_mistakes(mistake):
     p2, q2 = pair_collide(f, g, xi, w, par, mistake=mistake)
     err = max(np.abs((p2 - f1) / w[:, None]).max(), np.abs((q2 - g1) / w[:, None]).max())
     assert err > 1e-7, (mistake, err)
+
+
+def heat_flux_from_moments(fs, gs, xi, w, par, shift=5.0):
+    """The kernel's heat flux (unscaled: sum_i (xi_i - u)(|xi_i - u|^2 f^neq_i
+    + g^neq_i)) from sums over the pairs of the deviations, taken before the
+    isothermal correction: sum xi_b ((|xi|^2 - (D + 2) - g_f)(f_b - f_o) +
+    g_b - g_o) + u ((D + 2 + g_f) rho_d - e + 2 rho U) - 2 M2 u, with M2 the
+    second moments of the deviations and e their energy sum (`shift`: the
+    D + 2 of the formula, changed only to test the check)."""
+    D = 3
+    gf = 2.0 * par.cv - D
+    df, dg = fs - w[:, None], gs - (w * gf)[:, None]
+    s2 = (xi ** 2).sum(1)
+    N = fs.shape[1]
+    rho_d, e = df[0].copy(), dg[0].copy()
+    j, qx, M2 = np.zeros((D, N)), np.zeros((D, N)), np.zeros((D, D, N))
+    for k in range(NPAIR):
+        b = base(k)
+        o = opp(b)
+        fsum, fdif = df[b] + df[o], df[b] - df[o]
+        rho_d += fsum
+        j += xi[b][:, None] * fdif[None, :]
+        e += s2[b] * fsum + dg[b] + dg[o]
+        qx += xi[b][:, None] * ((s2[b] - shift - gf) * fdif + dg[b] - dg[o])[None, :]
+        M2 += np.outer(xi[b], xi[b])[:, :, None] * fsum[None, None, :]
+    rho = 1.0 + rho_d
+    u = j / rho
+    U = (u ** 2).sum(0)
+    sc = (shift + gf) * rho_d - e + 2.0 * rho * U
+    return (qx + u * sc[None, :] - 2.0 * np.einsum("abn,bn->an", M2, u)).T
+
+
+def test_heat_flux_from_moments_matches_oracle():
+    """The equilibrium's central third moment vanishes on D3Q45, so the heat
+    flux of the quasi-equilibrium term is the central moment of the node's own
+    populations; taken before the isothermal-wall correction (equilibria at
+    the same rho and u, Eq. thermalBC) it equals the oracle's heat flux after
+    it."""
+    xi, w, _ = velocity_set("D3Q45")
+    rng = np.random.default_rng(45)
+    N = 200
+    par = ost.Params(0.05, gamma=1.4, Pr=0.71, mu_ref=2e-3, T_ref=0.9, mu_exp=0.7)
+    rho = 1.0 + 0.05 * rng.standard_normal(N)
+    u = 0.2 * rng.standard_normal((N, 3))
+    T = 1.0 + 0.08 * rng.standard_normal(N)
+    f, g = ost.init_equilibrium(rho, u, T, xi, w, par.cv)
+    f = f + 2e-3 * w[:, None] * rng.standard_normal(f.shape)
+    g = g + 2e-3 * w[:, None] * rng.standard_normal(g.shape)
+    Tw = np.where(rng.random(N) < 0.5, 1.0 + 0.1 * rng.standard_normal(N), np.nan)
+    fc, gc = ost.thermal_correction(f, g, xi, w, par, Tw)
+    r, uu, TT = ost.moments(fc, gc, xi, par.cv)
+    fe, ge = ost.feq(r, uu, TT, xi, w), ost.geq(r, uu, TT, xi, w, par.cv)
+    q_oracle = 2.0 * ost.heat_flux_neq(fc, gc, fe, ge, xi, uu)
+    q = heat_flux_from_moments(f, g, xi, w, par)
+    assert np.abs(q_oracle).max() > 1e-3
+    assert np.abs(q - q_oracle).max() < 1e-12
+    # the third moments shifted by D instead of D + 2 fail it (the result
+    # moves by 2 u; the reference g_f cancels and cannot be tested this way)
+    bad = heat_flux_from_moments(f, g, xi, w, par, shift=3.0)
+    assert np.abs(bad - q_oracle).max() > 1e-2
